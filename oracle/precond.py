@@ -1,0 +1,126 @@
+"""Block-diagonal preconditioner: diag(M) for the (1,1) block and a geometric
+V-cycle on the approximate Schur complement (Sec. 2.3-2.4).
+
+* M~ = diag(M_beta) (Sec. 2.3), applied as z_u = r_u / (tau M~); tau = 1 by
+  default (final proposition of Sec. 2.3; tau = 2 is Prop. 2's optimal scaling
+  for exact blocks). Essential dofs: z = r.
+* C~ approximates the (2,2) block: 1/diag(W_alpha) for grad-div; for Darcy the
+  product of the diagonals diag(W)^-1 diag(W_gamma) diag(W)^-1 (Sec. 2.4), zero
+  when gamma = 0.
+* S~ = C~ + D M~^-1 D^T (Eq. approx-schur; the paper's Sec. 2.3 prints W_alpha
+  where its own definitions give W_alpha^-1, see Eq. approx-schur-entries).
+* S^-1 is approximated by one V-cycle (the paper uses one BoomerAMG V-cycle,
+  Sec. 3.2). The geometric V-cycle used here:
+    - levels: piecewise-constant aggregation of 2 cells per direction (a trailing
+      odd cell is its own aggregate; a direction of length 1 is not coarsened),
+      until at most `coarse_max` cells remain;
+    - Galerkin coarse operators A_{l+1} = P^T A_l P;
+    - nu pre- and nu post-sweeps of l1-Jacobi (D_l1 = sum_j |A_ij|, omega = 1),
+      zero initial guess on every level, coarse correction added unscaled;
+    - coarsest level: dense Cholesky; when S~ is singular (pure Neumann Darcy
+      with gamma = 0) it factors A + s 1 1^T with s = mean(diag A)/n;
+    - singular case: the result is projected to zero mean (Sec. 4.2).
+"""
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+from .assembly import GRAD_DIV
+
+
+def approx_schur(prob):
+    """Returns (S~ as CSR, M~ diagonal (1 on essential dofs), C~ diagonal)."""
+    Mt = prob.M.diagonal().copy()
+    E = prob.lat.n_elem
+    wdiag = np.einsum("eaa->ea", prob.We)                 # (E, k^3)
+    if prob.kind == GRAD_DIV:
+        ct_loc = 1.0 / wdiag
+    else:
+        gdiag = prob.gamma[:, None] * wdiag               # diag(W_gamma) for per-element gamma
+        ct_loc = gdiag / (wdiag * wdiag)
+    Ct = np.zeros(prob.lat.n_l2)
+    Ct[prob.e2l.ravel()] = ct_loc.ravel()
+    S = (sp.diags(Ct) + prob.D @ sp.diags(1.0 / Mt) @ prob.D.T).tocsr()
+    return S, Mt, Ct
+
+
+def aggregation(dims):
+    """P (fine cells x coarse cells) for 2-per-direction aggregation; coarse dims."""
+    X, Y, Z = dims
+    cd = tuple((n + 1) // 2 if n > 1 else 1 for n in dims)
+    fx = [2 if n > 1 else 1 for n in dims]
+    I, J, K = np.meshgrid(np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
+    fine = (I + X * (J + Y * K)).ravel()
+    coarse = ((I // fx[0]) + cd[0] * ((J // fx[1]) + cd[1] * (K // fx[2]))).ravel()
+    P = sp.coo_matrix((np.ones(fine.size), (fine, coarse)),
+                      shape=(X * Y * Z, cd[0] * cd[1] * cd[2])).tocsr()
+    return P, cd
+
+
+class VCycle:
+    def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20):
+        self.nu, self.singular = nu, singular
+        self.A, self.P, self.dims, self.dl1 = [A0.tocsr()], [], [tuple(dims)], []
+        while np.prod(self.dims[-1]) > coarse_max and len(self.A) < max_levels:
+            P, cd = aggregation(self.dims[-1])
+            if cd == self.dims[-1]:
+                break
+            self.P.append(P)
+            self.A.append((P.T @ self.A[-1] @ P).tocsr())
+            self.dims.append(cd)
+        for A in self.A:
+            self.dl1.append(np.asarray(abs(A).sum(axis=1)).ravel())
+        Ac = self.A[-1].toarray()
+        if singular:
+            n = Ac.shape[0]
+            Ac = Ac + (np.mean(np.diag(Ac)) / n) * np.ones((n, n))
+        self.chol = sla.cho_factor(Ac, lower=True)
+
+    @property
+    def n_levels(self):
+        return len(self.A)
+
+    def _cycle(self, l, b):
+        if l == len(self.A) - 1:
+            return sla.cho_solve(self.chol, b)
+        A, d = self.A[l], self.dl1[l]
+        x = np.zeros_like(b)
+        for _ in range(self.nu):
+            x = x + (b - A @ x) / d
+        r = b - A @ x
+        x = x + self.P[l] @ self._cycle(l + 1, self.P[l].T @ r)
+        for _ in range(self.nu):
+            x = x + (b - A @ x) / d
+        return x
+
+    def apply(self, b):
+        z = self._cycle(0, np.asarray(b, dtype=np.float64))
+        if self.singular:
+            z = z - z.mean()
+        return z
+
+
+def is_singular(prob, Ct):
+    """S~ is singular (constants in its kernel) exactly when C~ vanishes and no
+    boundary face is free: every row of D M~^-1 D^T then sums to zero."""
+    boundary = prob.lat.ess_dofs(63)
+    return bool(np.all(Ct == 0.0)) and bool(np.all(~prob.free[boundary]))
+
+
+class BlockPrec:
+    """z = B^-1 r with B = diag(tau M~, S^)."""
+
+    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512):
+        self.prob, self.tau = prob, tau
+        self.S, self.Mt, self.Ct = approx_schur(prob)
+        self.singular = is_singular(prob, self.Ct)
+        lat = prob.lat
+        self.vc = VCycle(self.S, (lat.X, lat.Y, lat.Z), nu=nu, coarse_max=coarse_max,
+                         singular=self.singular)
+
+    def apply(self, r):
+        nrt = self.prob.lat.n_rt
+        ru, rq = r[:nrt], r[nrt:]
+        zu = np.where(self.prob.free, ru / (self.tau * self.Mt), ru)
+        zq = self.vc.apply(rq)
+        return np.concatenate([zu, zq])
