@@ -1,0 +1,200 @@
+/*
+ * hdivsp.h - C ABI of the GB300 matrix-free H(div) saddle-point library.
+ *
+ * Method: Pazner, Kolev, Vassilevski, "Matrix-free GPU-accelerated saddle-point
+ * solvers for high-order problems in H(div)" (arXiv 2304.12387). The library
+ * applies, for Raviart-Thomas (RT_k) x discontinuous L2 (Q_{k-1}) discretisations
+ * in the interpolation-histopolation basis (Sec. 2.1) on structured hexahedral
+ * meshes, the transformed block operator (Eq. transformed-saddle-point)
+ *
+ *        AA = [[ M , D^T ],
+ *              [ D , -C  ]]
+ *
+ * with M = M_beta (grad-div) or M_{1/eps} (Darcy), D the lattice divergence
+ * (two +-1 per column, Sec. 2.1), C = W_alpha^-1 (grad-div, Eq. transformed-system)
+ * or W^-1 W_gamma W^-1 (Darcy, Eq. transformed-system-darcy; 0 when gamma = 0),
+ * and the block-diagonal preconditioner diag(tau M~, S^) with M~ = diag(M) and
+ * S^-1 one multigrid V-cycle on the approximate Schur complement
+ * S~ = C~ + D M~^-1 D^T (Eq. approx-schur, Eq. approx-schur-entries), inside
+ * preconditioned MINRES (Sec. 3).
+ *
+ * Conventions (all functions):
+ *  - Every function returns hd_status (HD_OK = 0). No exception crosses the ABI.
+ *    hd_last_error(h) gives a message for the last failing call on h.
+ *  - Vector arguments of the hd_apply_* / hd_vcycle / hd_minres_solve calls are
+ *    raw DEVICE pointers to contiguous FP64 arrays (FP32 for *_f32), owned by
+ *    the caller, and must not alias each other unless stated. Vectors on the
+ *    full block space are [u (n_rt); q (n_l2)].
+ *  - All device work is enqueued on the handle's stream (hd_set_stream; default
+ *    the legacy stream) and is asynchronous with respect to the host, except
+ *    hd_create, hd_destroy, the hd_get_* calls, the *_host calls and
+ *    hd_minres_solve, which return after the device work is complete.
+ *  - The handle owns all internal device memory; hd_destroy frees it.
+ *  - Size/pointer arguments are checked on entry (HD_ERR_INVALID_ARG). CUDA
+ *    launch or runtime failures give HD_ERR_CUDA, allocation failures HD_ERR_OOM.
+ *
+ * Numbering (structured lattice, all elements unrotated): element
+ * e = ex + nx (ey + ny ez); with X = nx k, Y = ny k, Z = nz k subcells,
+ * L2 dof (cell) I + X (J + Y K); RT dofs: x-faces I + (X+1)(J + Y K), then
+ * y-faces I + X (J + (Y+1) K), then z-faces I + X (J + Y K), global orientation
+ * +x, +y, +z. Essential (u.n prescribed) RT dofs are eliminated as a
+ * constrained identity: (AA x)_ess = x_ess.
+ */
+#ifndef HDIVSP_H
+#define HDIVSP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hd_status;
+enum {
+  HD_OK = 0,
+  HD_ERR_INVALID_ARG = 1,
+  HD_ERR_CUDA = 2,
+  HD_ERR_OOM = 3,
+  HD_ERR_NOT_CONVERGED = 4,
+  HD_ERR_PREC_INDEFINITE = 5,
+  HD_ERR_NAN = 6,
+  HD_ERR_STAGNATION = 7,
+  HD_ERR_BOUNDS = 8,
+  HD_ERR_NOT_IMPLEMENTED = 9
+};
+
+/* problem kinds (Eq. grad-div and Eq. darcy) */
+enum { HD_GRAD_DIV = 0, HD_DARCY = 1 };
+
+/* how the L2 mass inverse W^-1 is applied (Sec. 3.1) */
+enum {
+  HD_WINV_DENSE = 0, /* explicit per-element inverse (getrf/getri + gemv of Sec. 3.1) */
+  HD_WINV_CG = 1     /* fused local CG in the Gauss-Legendre basis (Sec. 2.5, 3.1) */
+};
+
+/* essential-boundary side bits */
+enum {
+  HD_SIDE_X0 = 1, HD_SIDE_X1 = 2, HD_SIDE_Y0 = 4,
+  HD_SIDE_Y1 = 8, HD_SIDE_Z0 = 16, HD_SIDE_Z1 = 32
+};
+
+typedef struct hd_op* hd_handle;
+
+/* Problem description for hd_create. All pointers are HOST pointers that are
+ * only read during hd_create. */
+typedef struct {
+  int32_t kind;          /* HD_GRAD_DIV or HD_DARCY */
+  int32_t nx, ny, nz;    /* elements per direction, >= 1 */
+  int32_t k;             /* RT degree = subcells per element direction (the paper's p); 2..5 */
+  int32_t q;             /* Gauss-Legendre points per direction; 0 -> k+1 if affine else k+2;
+                            must be k+1 or k+2 */
+  const double* vx;      /* vertex coordinates, (nx+1)(ny+1)(nz+1) each; vertex (i,j,l) */
+  const double* vy;      /*   at i + (nx+1)(j + (ny+1) l); elements must have det J > 0 */
+  const double* vz;
+  const double* coef0;   /* per element: alpha > 0 (grad-div) or eps > 0 (Darcy) */
+  const double* coef1;   /* per element: beta > 0 (grad-div) or gamma >= 0 (Darcy) */
+  uint32_t ess_mask;     /* HD_SIDE_* bits: sides where u.n is essential */
+  int32_t affine;        /* caller states the mesh is affine (only selects the default q) */
+  double tau;            /* (1,1) preconditioner scaling tau M~; 0 -> 1 */
+  int32_t winv_mode;     /* HD_WINV_DENSE or HD_WINV_CG */
+  int32_t nu;            /* l1-Jacobi sweeps before and after the coarse correction; 0 -> 2 */
+  int32_t coarse_max;    /* at most this many cells on the coarsest level; 0 -> 512 */
+} hd_problem_desc;
+
+/* MINRES options and report (Sec. 3). */
+typedef struct {
+  double rtol;           /* stop when eta_j <= rtol * eta_0 (eta: B^-1-norm of the residual) */
+  int32_t maxit;         /* iteration cap */
+  int32_t use_x0;        /* 1: x holds the initial guess; 0: start from zero */
+  int32_t check_every;   /* host polls the device-side convergence word every n iterations (>= 1) */
+  int32_t precision;     /* 0: FP64 throughout; 1: FP32 operator/preconditioner inside an
+                            FP64 outer residual correction (see hd_minres_solve) */
+  double outer_rtol;     /* precision = 1: target true relative residual ||b-AAx||/||b|| */
+  int32_t max_outer;     /* precision = 1: at most this many outer corrections */
+} hd_solve_opts;
+
+typedef struct {
+  int32_t iterations;    /* total inner MINRES iterations */
+  int32_t outer;         /* outer corrections (precision = 1), else 1 */
+  double eta_ratio;      /* final eta_j / eta_0 of the last inner solve */
+  double true_relres;    /* ||b - AA x||_2 / ||b||_2 in FP64 at exit */
+  double ms_total;       /* device time of the solve (CUDA events) */
+  hd_status status;
+} hd_solve_info;
+
+/* -- lifetime ----------------------------------------------------------- */
+/* Builds the operator: 1D tables, geometric factors at quadrature points,
+ * the per-element W^-1 (dense mode), diag(M), diag(W), S~ and the V-cycle
+ * hierarchy (setup of Sec. 3.1-3.2). Uses the current CUDA device. */
+hd_status hd_create(const hd_problem_desc* desc, hd_handle* out);
+hd_status hd_destroy(hd_handle h);
+const char* hd_last_error(hd_handle h);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+hd_status hd_set_stream(hd_handle h, void* stream);
+
+/* -- sizes and index maps ----------------------------------------------- */
+hd_status hd_get_sizes(hd_handle h, int64_t* n_rt, int64_t* n_l2, int64_t* n_elem);
+/* Signed element-to-RT-dof map of Algorithm 1 (element_map, rt_local_to_global
+ * and the orientations folded in): host_out has n_elem * 3(k+1)k^2 int32 entries,
+ * row e lists the global id g of each local dof, stored as g when local and global
+ * orientation agree and as -1-g otherwise. Local order: x-component
+ * i + (k+1)(j + k l), then y-component i + k (j + (k+1) l), then z-component
+ * i + k (j + k l). */
+hd_status hd_get_e2d_map(hd_handle h, int32_t* host_out);
+/* Essential RT dofs in ascending order; *n in: capacity of host_out, out: count
+ * (host_out may be NULL to query the count). */
+hd_status hd_get_ess_dofs(hd_handle h, int64_t* host_out, int64_t* n);
+
+/* Host-only builders of the same maps from the mesh sizes (no handle, no GPU):
+ * out has nx*ny*nz * 3(k+1)k^2 entries (hd_lattice_e2d_map), or holds up to *n
+ * essential dofs (hd_lattice_ess_dofs; *n out: count; out may be NULL).
+ * Return HD_ERR_INVALID_ARG on bad sizes or when the id range exceeds int32. */
+hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out);
+hd_status hd_lattice_ess_dofs(int32_t nx, int32_t ny, int32_t nz, int32_t k, uint32_t ess_mask,
+                              int64_t* out, int64_t* n);
+
+/* -- operator blocks (Sec. 3: the per-iteration operations) ---------------- */
+/* y = M u (RT mass by sum factorisation, Eq. matrices); identity on essential dofs. */
+hd_status hd_apply_A(hd_handle h, const double* u, double* y);
+/* yq = D u (lattice divergence; essential columns dropped). */
+hd_status hd_apply_B(hd_handle h, const double* u, double* yq);
+/* yu = D^T q (zero on essential dofs). */
+hd_status hd_apply_Bt(hd_handle h, const double* q, double* yu);
+/* yq = C q: W_alpha^-1 q (grad-div) or gamma_e W^-1 q (Darcy, piecewise-constant
+ * gamma, Sec. 2.4); zero for Darcy with gamma = 0. */
+hd_status hd_apply_C(hd_handle h, const double* q, double* yq);
+/* y = AA x, x = [u; q~], in one fused element pass (Eq. transformed-saddle-point). */
+hd_status hd_apply_op(hd_handle h, const double* x, double* y);
+/* Same as hd_apply_op with HOST input and output: copies x in, applies, copies y
+ * out on the handle's stream and waits for it. */
+hd_status hd_apply_op_host(hd_handle h, const double* x_host, double* y_host);
+
+/* -- preconditioner (Sec. 2.3, 3.2) --------------------------------------- */
+/* z = B^-1 r with B = diag(tau M~, S^): z_u = r_u / (tau M~) (z = r on essential
+ * dofs), z_q = one V-cycle on S~ (projected to zero mean if S~ is singular). */
+hd_status hd_apply_prec(hd_handle h, const double* r, double* z);
+/* y = S~ x on the L2 lattice (7-point stencil, Eq. approx-schur-entries). */
+hd_status hd_apply_schur(hd_handle h, const double* x, double* y);
+/* x = one V-cycle on S~ applied to b (no projection). */
+hd_status hd_vcycle(hd_handle h, const double* b, double* x);
+/* Device copies of M~ = diag(M) (n_rt; 1 on essential dofs) and C~ (n_l2). */
+hd_status hd_get_diagonals(hd_handle h, double* mt, double* ct);
+/* Number of V-cycle levels and the lattice dimensions of level l. */
+hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3]);
+
+/* -- solver (Sec. 3) ------------------------------------------------------ */
+/* Solves AA x = b with block-preconditioned MINRES. b, x: device FP64 vectors of
+ * length n_rt + n_l2. Returns HD_OK on convergence, HD_ERR_NOT_CONVERGED when
+ * maxit is reached (x holds the last iterate), HD_ERR_PREC_INDEFINITE or
+ * HD_ERR_NAN when the recurrence breaks down. */
+hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
+                          const hd_solve_opts* opts, hd_solve_info* info);
+
+/* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
+hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);
+hd_status hd_apply_prec_f32(hd_handle h, const float* r, float* z);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDIVSP_H */

@@ -1,0 +1,227 @@
+"""Python binding of libhdivsp (matrix-free H(div) saddle-point operators on GB300).
+
+A thin ctypes layer over the C ABI declared in include/hdivsp.h: every hd_*
+function of the header is exported here under the same name and only marshals
+arguments (device vectors are torch CUDA tensors passed by data pointer; the
+handle runs on torch's current stream). All arithmetic happens in the CUDA
+library; there is no fallback path. Building: ``python -m
+paper_2304_12387_gb300.build`` (or ``__graft_entry__.build()``).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhdivsp.so")
+
+HD_OK, HD_ERR_INVALID_ARG, HD_ERR_CUDA, HD_ERR_OOM, HD_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
+HD_ERR_PREC_INDEFINITE, HD_ERR_NAN, HD_ERR_STAGNATION, HD_ERR_BOUNDS, HD_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
+HD_GRAD_DIV, HD_DARCY = 0, 1
+HD_WINV_DENSE, HD_WINV_CG = 0, 1
+STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_OOM",
+                4: "HD_ERR_NOT_CONVERGED", 5: "HD_ERR_PREC_INDEFINITE", 6: "HD_ERR_NAN",
+                7: "HD_ERR_STAGNATION", 8: "HD_ERR_BOUNDS", 9: "HD_ERR_NOT_IMPLEMENTED"}
+
+
+class HdError(RuntimeError):
+    def __init__(self, status, msg=""):
+        super().__init__("%s%s" % (STATUS_NAMES.get(status, status), (": " + msg) if msg else ""))
+        self.status = status
+
+
+class ProblemDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("nz", ctypes.c_int32), ("k", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("vx", ctypes.POINTER(ctypes.c_double)), ("vy", ctypes.POINTER(ctypes.c_double)),
+                ("vz", ctypes.POINTER(ctypes.c_double)), ("coef0", ctypes.POINTER(ctypes.c_double)),
+                ("coef1", ctypes.POINTER(ctypes.c_double)), ("ess_mask", ctypes.c_uint32),
+                ("affine", ctypes.c_int32), ("tau", ctypes.c_double), ("winv_mode", ctypes.c_int32),
+                ("nu", ctypes.c_int32), ("coarse_max", ctypes.c_int32)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("use_x0", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("outer_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("eta_ratio", ctypes.c_double),
+                ("true_relres", ctypes.c_double), ("ms_total", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
+_lib = None
+
+_VP, _H = ctypes.c_void_p, ctypes.c_void_p
+_SIGS = {
+    "hd_create": [ctypes.POINTER(ProblemDesc), ctypes.POINTER(ctypes.c_void_p)],
+    "hd_destroy": [_H],
+    "hd_set_stream": [_H, _VP],
+    "hd_get_sizes": [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                     ctypes.POINTER(ctypes.c_int64)],
+    "hd_get_e2d_map": [_H, _VP],
+    "hd_get_ess_dofs": [_H, _VP, ctypes.POINTER(ctypes.c_int64)],
+    "hd_lattice_e2d_map": [ctypes.c_int32] * 4 + [_VP],
+    "hd_lattice_ess_dofs": [ctypes.c_int32] * 4 + [ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int64)],
+    "hd_apply_A": [_H, _VP, _VP],
+    "hd_apply_B": [_H, _VP, _VP],
+    "hd_apply_Bt": [_H, _VP, _VP],
+    "hd_apply_C": [_H, _VP, _VP],
+    "hd_apply_op": [_H, _VP, _VP],
+    "hd_apply_op_host": [_H, _VP, _VP],
+    "hd_apply_prec": [_H, _VP, _VP],
+    "hd_apply_schur": [_H, _VP, _VP],
+    "hd_vcycle": [_H, _VP, _VP],
+    "hd_get_diagonals": [_H, _VP, _VP],
+    "hd_get_level": [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
+    "hd_minres_solve": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_apply_op_f32": [_H, _VP, _VP],
+    "hd_apply_prec_f32": [_H, _VP, _VP],
+}
+
+
+def lib():
+    """The loaded libhdivsp (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libhdivsp.so is not built: run python -m paper_2304_12387_gb300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int32
+        L.hd_last_error.argtypes = [_H]
+        L.hd_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(st, h=None):
+    if st != HD_OK:
+        msg = lib().hd_last_error(h).decode() if h else ""
+        raise HdError(st, msg)
+
+
+def _ptr(t):
+    """Device (or host numpy) pointer of a contiguous array."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags.c_contiguous
+        return t.ctypes.data
+    assert t.is_contiguous()
+    return t.data_ptr()
+
+
+def _dptr(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# -- same-name wrappers of the C ABI -------------------------------------------
+
+def hd_lattice_e2d_map(nx, ny, nz, k):
+    out = np.zeros((nx * ny * nz, 3 * (k + 1) * k * k), dtype=np.int32)
+    _check(lib().hd_lattice_e2d_map(nx, ny, nz, k, out.ctypes.data))
+    return out
+
+
+def hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask):
+    n = ctypes.c_int64(0)
+    _check(lib().hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask, None, ctypes.byref(n)))
+    out = np.zeros(n.value, dtype=np.int64)
+    _check(lib().hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask, out.ctypes.data, ctypes.byref(n)))
+    return out
+
+
+class Operator:
+    """Owns an hd_handle. Vectors are torch CUDA tensors (float64, or float32 for *_f32)."""
+
+    def __init__(self, nx, ny, nz, k, vx, vy, vz, coef0, coef1, kind=HD_GRAD_DIV, ess_mask=0, q=0,
+                 affine=False, tau=0.0, winv_mode=HD_WINV_DENSE, nu=0, coarse_max=0, stream=None):
+        E = nx * ny * nz
+        self._keep = []
+        arrs = []
+        for a, n in ((vx, None), (vy, None), (vz, None), (coef0, E), (coef1, E)):
+            a = np.asarray(a, dtype=np.float64)
+            if n is not None:
+                a = np.broadcast_to(a, (n,))
+            a, p = _dptr(a)
+            self._keep.append(a)
+            arrs.append(p)
+        d = ProblemDesc(kind, nx, ny, nz, k, q, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], ess_mask,
+                        int(affine), tau, winv_mode, nu, coarse_max)
+        h = ctypes.c_void_p()
+        st = lib().hd_create(ctypes.byref(d), ctypes.byref(h))
+        _check(st)
+        self.h = h
+        self.k, self.kind = k, kind
+        self.dims = (nx, ny, nz)
+        nrt, nl2, ne = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().hd_get_sizes(h, ctypes.byref(nrt), ctypes.byref(nl2), ctypes.byref(ne)), h)
+        self.n_rt, self.n_l2, self.n_elem = nrt.value, nl2.value, ne.value
+        self.n = self.n_rt + self.n_l2
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream or a raw cudaStream_t integer."""
+        s = getattr(stream, "cuda_stream", stream)
+        _check(lib().hd_set_stream(self.h, ctypes.c_void_p(s)), self.h)
+
+    def _call(self, name, *args):
+        _check(getattr(lib(), name)(self.h, *[_ptr(a) for a in args]), self.h)
+
+    def hd_apply_A(self, u, y): self._call("hd_apply_A", u, y)
+    def hd_apply_B(self, u, yq): self._call("hd_apply_B", u, yq)
+    def hd_apply_Bt(self, q, yu): self._call("hd_apply_Bt", q, yu)
+    def hd_apply_C(self, q, yq): self._call("hd_apply_C", q, yq)
+    def hd_apply_op(self, x, y): self._call("hd_apply_op", x, y)
+    def hd_apply_op_host(self, x, y): self._call("hd_apply_op_host", x, y)
+    def hd_apply_prec(self, r, z): self._call("hd_apply_prec", r, z)
+    def hd_apply_schur(self, x, y): self._call("hd_apply_schur", x, y)
+    def hd_vcycle(self, b, x): self._call("hd_vcycle", b, x)
+    def hd_apply_op_f32(self, x, y): self._call("hd_apply_op_f32", x, y)
+    def hd_apply_prec_f32(self, r, z): self._call("hd_apply_prec_f32", r, z)
+    def hd_get_diagonals(self, mt, ct): self._call("hd_get_diagonals", mt, ct)
+
+    def hd_get_e2d_map(self):
+        out = np.zeros((self.n_elem, 3 * (self.k + 1) * self.k ** 2), dtype=np.int32)
+        _check(lib().hd_get_e2d_map(self.h, out.ctypes.data), self.h)
+        return out
+
+    def hd_get_ess_dofs(self):
+        n = ctypes.c_int64(0)
+        _check(lib().hd_get_ess_dofs(self.h, None, ctypes.byref(n)), self.h)
+        out = np.zeros(n.value, dtype=np.int64)
+        _check(lib().hd_get_ess_dofs(self.h, out.ctypes.data, ctypes.byref(n)), self.h)
+        return out
+
+    def hd_get_level(self, l=0):
+        nl = ctypes.c_int32()
+        dims = (ctypes.c_int32 * 3)()
+        _check(lib().hd_get_level(self.h, l, ctypes.byref(nl), dims), self.h)
+        return nl.value, tuple(dims)
+
+    def hd_minres_solve(self, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8, precision=0,
+                        outer_rtol=1e-8, max_outer=20, raise_on_error=False):
+        o = SolveOpts(rtol, maxit, int(use_x0), check_every, precision, outer_rtol, max_outer)
+        info = SolveInfo()
+        st = lib().hd_minres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        if raise_on_error:
+            _check(st, self.h)
+        return st, {"iterations": info.iterations, "outer": info.outer, "eta_ratio": info.eta_ratio,
+                    "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status}

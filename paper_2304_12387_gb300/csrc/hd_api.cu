@@ -1,0 +1,480 @@
+// C ABI of the hdivsp library: handle lifetime, host-side setup (1D tables of
+// the interpolation-histopolation basis, index maps) and the apply entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hd_internal.h"
+#include "k_element.cuh"
+
+hd_status hd_fail(hd_op* h, hd_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+hd_status hd_cuda_check(hd_op* h, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return hd_fail(h, HD_ERR_OOM, m);
+  return hd_fail(h, HD_ERR_CUDA, m);
+}
+
+namespace {
+
+// ---- 1D tables (Sec. 2.1) -----------------------------------------------------
+// Legendre P_n and its first two derivatives on [-1,1] by the three-term recurrence.
+void legendre(int n, double x, double& p, double& dp, double& ddp) {
+  double p0 = 1.0, p1 = x, d0 = 0.0, d1 = 1.0, dd0 = 0.0, dd1 = 0.0;
+  if (n == 0) { p = 1.0; dp = 0.0; ddp = 0.0; return; }
+  for (int m = 1; m < n; ++m) {
+    double p2 = ((2 * m + 1) * x * p1 - m * p0) / (m + 1);
+    double d2 = ((2 * m + 1) * (p1 + x * d1) - m * d0) / (m + 1);
+    double dd2 = ((2 * m + 1) * (2 * d1 + x * dd1) - m * dd0) / (m + 1);
+    p0 = p1; p1 = p2; d0 = d1; d1 = d2; dd0 = dd1; dd1 = dd2;
+  }
+  p = p1; dp = d1; ddp = dd1;
+}
+
+// Gauss-Lobatto nodes on [0,1]: 0, 1 and the roots of P_k' (Newton from
+// Chebyshev-Gauss-Lobatto points).
+std::vector<double> gll(int k) {
+  std::vector<double> t(k + 1);
+  for (int i = 0; i <= k; ++i) t[i] = -std::cos(M_PI * i / k);
+  for (int i = 1; i < k; ++i) {
+    double x = t[i];
+    for (int it = 0; it < 100; ++it) {
+      double p, dp, ddp;
+      legendre(k, x, p, dp, ddp);
+      double dx = dp / ddp;
+      x -= dx;
+      if (std::fabs(dx) < 1e-16) break;
+    }
+    t[i] = x;
+  }
+  t[0] = -1.0; t[k] = 1.0;
+  for (auto& v : t) v = 0.5 * (v + 1.0);
+  return t;
+}
+
+// Gauss-Legendre points/weights on [0,1] (Newton on P_q).
+void gauss(int q, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(q); w.resize(q);
+  for (int i = 0; i < q; ++i) {
+    double z = -std::cos(M_PI * (i + 0.75) / (q + 0.5));
+    double p, dp, ddp;
+    for (int it = 0; it < 100; ++it) {
+      legendre(q, z, p, dp, ddp);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    legendre(q, z, p, dp, ddp);
+    x[i] = 0.5 * (z + 1.0);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);  // 2/((1-z^2)P'^2) scaled by 1/2
+  }
+}
+
+// Lagrange basis on `nodes`: value and derivative of l_i at x.
+double lag(const std::vector<double>& nd, int i, double x) {
+  double v = 1.0;
+  for (size_t m = 0; m < nd.size(); ++m)
+    if ((int)m != i) v *= (x - nd[m]) / (nd[i] - nd[m]);
+  return v;
+}
+double dlag(const std::vector<double>& nd, int i, double x) {
+  double s = 0.0;
+  for (size_t m = 0; m < nd.size(); ++m) {
+    if ((int)m == i) continue;
+    double t = 1.0 / (nd[i] - nd[m]);
+    for (size_t r = 0; r < nd.size(); ++r)
+      if ((int)r != i && r != m) t *= (x - nd[r]) / (nd[i] - nd[r]);
+    s += t;
+  }
+  return s;
+}
+
+void build_tables(int k, int q, ElemTables& t) {
+  std::memset(&t, 0, sizeof(t));
+  std::vector<double> xi = gll(k), gx, gw;
+  gauss(q, gx, gw);
+  for (int p = 0; p < q; ++p) {
+    t.gx[p] = gx[p];
+    t.gw[p] = gw[p];
+    for (int i = 0; i <= k; ++i) t.BI[p * (k + 1) + i] = lag(xi, i, gx[p]);
+    // h_j = sum_{i > j} l_i'  (integral of h_j over subcell m is delta_mj)
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int i = j + 1; i <= k; ++i) s += dlag(xi, i, gx[p]);
+      t.BH[p * k + j] = s;
+    }
+  }
+}
+
+hd_status dalloc(hd_op* h, double** p, int64_t n, const char* what) {
+  if (cudaMalloc(p, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, what);
+  return HD_OK;
+}
+
+hd_status elem_op(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) {
+  switch (h->k) {
+    case 2: return elem_op_k2(h, mode, u, q, yu, yq);
+    case 3: return elem_op_k3(h, mode, u, q, yu, yq);
+    case 4: return elem_op_k4(h, mode, u, q, yu, yq);
+    case 5: return elem_op_k5(h, mode, u, q, yu, yq);
+  }
+  return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
+}
+
+hd_status elem_op_f32(hd_op* h, int mode, const float* u, const float* q, float* yu, float* yq) {
+  switch (h->k) {
+    case 2: return elem_op_f32_k2(h, mode, u, q, yu, yq);
+    case 3: return elem_op_f32_k3(h, mode, u, q, yu, yq);
+    case 4: return elem_op_f32_k4(h, mode, u, q, yu, yq);
+    case 5: return elem_op_f32_k5(h, mode, u, q, yu, yq);
+  }
+  return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
+}
+
+hd_status elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
+  switch (h->k) {
+    case 2: return elem_setup_k2(h, bcoef, d_bad);
+    case 3: return elem_setup_k3(h, bcoef, d_bad);
+    case 4: return elem_setup_k4(h, bcoef, d_bad);
+    case 5: return elem_setup_k5(h, bcoef, d_bad);
+  }
+  return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
+}
+
+void destroy_all(hd_op* h) {
+  cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
+  cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag);
+  cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
+  cudaFree(h->d_coarse_inv); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
+  cudaFree(h->f_G); cudaFree(h->f_winv); cudaFree(h->f_cscale); cudaFree(h->f_mtinv); cudaFree(h->f_coarse_inv);
+  for (double* p : h->mv) cudaFree(p);
+  for (float* p : h->fv) cudaFree(p);
+  cudaFree(h->d_ms);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  precond_free(h);
+}
+
+}  // namespace
+
+// used by the Krylov layer
+hd_status apply_op_internal(hd_op* h, const double* x, double* y) {
+  HD_CK(h, cudaMemsetAsync(y, 0, sizeof(double) * h->n_rt, h->stream));
+  return elem_op(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
+}
+
+hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y) {
+  HD_CK(h, cudaMemsetAsync(y, 0, sizeof(float) * h->n_rt, h->stream));
+  return elem_op_f32(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
+}
+
+extern "C" {
+
+hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
+  if (!d || !out) return HD_ERR_INVALID_ARG;
+  *out = nullptr;
+  hd_op* h = new (std::nothrow) hd_op();
+  if (!h) return HD_ERR_OOM;
+  h->desc = *d;
+  if (d->kind != HD_GRAD_DIV && d->kind != HD_DARCY) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->nx < 1 || d->ny < 1 || d->nz < 1) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->k < 2 || d->k > HD_MAXK) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  if (!d->vx || !d->vy || !d->vz || !d->coef0 || !d->coef1) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->ess_mask > 63) { delete h; return HD_ERR_INVALID_ARG; }
+  h->kind = d->kind;
+  h->k = d->k;
+  h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
+  if (h->q != h->k + 1 && h->q != h->k + 2) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  h->winv_mode = d->winv_mode;
+  h->tau = d->tau > 0 ? d->tau : 1.0;
+  h->nu = d->nu > 0 ? d->nu : 2;
+  h->coarse_max = d->coarse_max > 0 ? d->coarse_max : 512;
+  if (h->coarse_max > 4096) { delete h; return HD_ERR_INVALID_ARG; }
+  const int k = h->k;
+  LatticeDims& L = h->L;
+  L.nx = d->nx; L.ny = d->ny; L.nz = d->nz;
+  L.X = d->nx * k; L.Y = d->ny * k; L.Z = d->nz * k;
+  int64_t nxf = (int64_t)(L.X + 1) * L.Y * L.Z, nyf = (int64_t)L.X * (L.Y + 1) * L.Z,
+          nzf = (int64_t)L.X * L.Y * (L.Z + 1);
+  h->n_rt = nxf + nyf + nzf;
+  h->n_l2 = (int64_t)L.X * L.Y * L.Z;
+  h->n_elem = (int64_t)d->nx * d->ny * d->nz;
+  if (h->n_rt + h->n_l2 >= (int64_t)1 << 31) { delete h; return HD_ERR_INVALID_ARG; }
+  L.n_xf = (int)nxf; L.n_yf = (int)nyf;
+  L.ess = d->ess_mask;
+  const int64_t E = h->n_elem, nv = (int64_t)(d->nx + 1) * (d->ny + 1) * (d->nz + 1);
+  std::vector<double> bco(E), csc(E);
+  bool gamma_zero = true;
+  for (int64_t e = 0; e < E; ++e) {
+    double c0 = d->coef0[e], c1 = d->coef1[e];
+    if (!(c0 > 0.0) || !std::isfinite(c0) || !std::isfinite(c1)) { delete h; return HD_ERR_INVALID_ARG; }
+    if (h->kind == HD_GRAD_DIV) {
+      if (!(c1 > 0.0)) { delete h; return HD_ERR_INVALID_ARG; }
+      bco[e] = c1;          // M_beta
+      csc[e] = 1.0 / c0;    // W_alpha^-1 = W^-1 / alpha (alpha constant per element)
+      gamma_zero = false;
+    } else {
+      if (!(c1 >= 0.0)) { delete h; return HD_ERR_INVALID_ARG; }
+      bco[e] = 1.0 / c0;    // M_{1/eps}
+      csc[e] = c1;          // W^-1 W_gamma W^-1 = gamma W^-1 (gamma constant per element, Sec. 2.4)
+      if (c1 != 0.0) gamma_zero = false;
+    }
+  }
+  h->singular = gamma_zero && (d->ess_mask == 63);
+  build_tables(k, h->q, h->tab);
+  const int nq = h->q * h->q * h->q, nl2 = k * k * k;
+  hd_status st = HD_OK;
+  double* d_b = nullptr;
+  int* d_bad = nullptr;
+  do {
+    if ((st = dalloc(h, &h->d_vx, nv, "vx")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_vy, nv, "vy")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_vz, nv, "vz")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_G, E * 6 * nq, "geometric factors")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_wdet, E * nq, "wdet")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_winv, E * nl2 * nl2, "W inverse")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_wdiag, E * nl2, "W diagonal")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_cscale, E, "cscale")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_mt, h->n_rt, "M diagonal")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_mtinv, h->n_rt, "M diagonal inverse")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_ct, h->n_l2, "C~")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_red, 4096, "reduction")) != HD_OK) break;
+    if ((st = dalloc(h, &d_b, E, "b coefficient")) != HD_OK) break;
+    if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "flag"); break; }
+    if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "pinned"); break; }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(h->d_vx, d->vx, nv * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_vy, d->vy, nv * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_vz, d->vz, nv * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(d_b, bco.data(), E * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemcpyAsync(h->d_cscale, csc.data(), E * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(h->d_mt, 0, h->n_rt * 8, s) != cudaSuccess || cudaMemsetAsync(d_bad, 0, 4, s) != cudaSuccess) {
+      st = hd_fail(h, HD_ERR_CUDA, "upload");
+      break;
+    }
+    if ((st = elem_setup(h, d_b, d_bad)) != HD_OK) break;
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, d_bad, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+      st = hd_fail(h, HD_ERR_CUDA, "setup");
+      break;
+    }
+    if (bad) { st = hd_fail(h, HD_ERR_INVALID_ARG, "inverted element (det J <= 0)"); break; }
+    if ((st = precond_setup(h)) != HD_OK) break;
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { st = hd_cuda_check(h, e, "setup"); break; }
+  } while (0);
+  cudaFree(d_b);
+  cudaFree(d_bad);
+  if (st != HD_OK) {
+    std::fprintf(stderr, "hd_create: %s\n", h->err.c_str());
+    destroy_all(h);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return HD_OK;
+}
+
+hd_status hd_destroy(hd_handle h) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  cudaStreamSynchronize(h->stream);
+  destroy_all(h);
+  delete h;
+  return HD_OK;
+}
+
+const char* hd_last_error(hd_handle h) { return h ? h->err.c_str() : "null handle"; }
+
+hd_status hd_set_stream(hd_handle h, void* stream) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  h->stream = (cudaStream_t)stream;
+  return HD_OK;
+}
+
+hd_status hd_get_sizes(hd_handle h, int64_t* n_rt, int64_t* n_l2, int64_t* n_elem) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  if (n_rt) *n_rt = h->n_rt;
+  if (n_l2) *n_l2 = h->n_l2;
+  if (n_elem) *n_elem = h->n_elem;
+  return HD_OK;
+}
+
+hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out) {
+  if (!out || nx < 1 || ny < 1 || nz < 1 || k < 1) return HD_ERR_INVALID_ARG;
+  const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k, Z = (int64_t)nz * k;
+  const int64_t nxf = (X + 1) * Y * Z, nyf = X * (Y + 1) * Z, nzf = X * Y * (Z + 1);
+  if (nxf + nyf + nzf >= ((int64_t)1 << 31)) return HD_ERR_INVALID_ARG;
+  const int nloc = 3 * (k + 1) * k * k;
+  const int64_t E = (int64_t)nx * ny * nz;
+  for (int64_t e = 0; e < E; ++e) {
+    int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    int32_t* row = out + e * nloc;
+    int n = 0;
+    for (int l = 0; l < k; ++l)
+      for (int j = 0; j < k; ++j)
+        for (int i = 0; i <= k; ++i) row[n++] = (int32_t)((ex * k + i) + (X + 1) * ((ey * k + j) + Y * (ez * k + l)));
+    for (int l = 0; l < k; ++l)
+      for (int j = 0; j <= k; ++j)
+        for (int i = 0; i < k; ++i)
+          row[n++] = (int32_t)(nxf + (ex * k + i) + X * ((ey * k + j) + (Y + 1) * (ez * k + l)));
+    for (int l = 0; l <= k; ++l)
+      for (int j = 0; j < k; ++j)
+        for (int i = 0; i < k; ++i)
+          row[n++] = (int32_t)(nxf + nyf + (ex * k + i) + X * ((ey * k + j) + Y * (ez * k + l)));
+    // every element is unrotated: local and global orientation agree (sign +1)
+  }
+  return HD_OK;
+}
+
+hd_status hd_lattice_ess_dofs(int32_t nx, int32_t ny, int32_t nz, int32_t k, uint32_t m, int64_t* out, int64_t* n) {
+  if (!n || nx < 1 || ny < 1 || nz < 1 || k < 1 || m > 63) return HD_ERR_INVALID_ARG;
+  const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k, Z = (int64_t)nz * k;
+  const int64_t nxf = (X + 1) * Y * Z, nyf = X * (Y + 1) * Z;
+  int64_t cnt = 0, cap = *n;
+  auto emit = [&](int64_t g) {
+    if (out && cnt < cap) out[cnt] = g;
+    ++cnt;
+  };
+  // ascending global id: x-faces, then y-faces, then z-faces, each in id order
+  for (int64_t K = 0; K < Z; ++K)
+    for (int64_t J = 0; J < Y; ++J)
+      for (int64_t I = 0; I <= X; ++I)
+        if ((I == 0 && (m & 1)) || (I == X && (m & 2))) emit(I + (X + 1) * (J + Y * K));
+  for (int64_t K = 0; K < Z; ++K)
+    for (int64_t J = 0; J <= Y; ++J)
+      for (int64_t I = 0; I < X; ++I)
+        if ((J == 0 && (m & 4)) || (J == Y && (m & 8))) emit(nxf + I + X * (J + (Y + 1) * K));
+  for (int64_t K = 0; K <= Z; ++K)
+    for (int64_t J = 0; J < Y; ++J)
+      for (int64_t I = 0; I < X; ++I)
+        if ((K == 0 && (m & 16)) || (K == Z && (m & 32))) emit(nxf + nyf + I + X * (J + Y * K));
+  bool overflow = out && cnt > cap;
+  *n = cnt;
+  return overflow ? HD_ERR_INVALID_ARG : HD_OK;
+}
+
+hd_status hd_get_e2d_map(hd_handle h, int32_t* out) {
+  if (!h || !out) return HD_ERR_INVALID_ARG;
+  return hd_lattice_e2d_map(h->L.nx, h->L.ny, h->L.nz, h->k, out);
+}
+
+hd_status hd_get_ess_dofs(hd_handle h, int64_t* out, int64_t* n) {
+  if (!h || !n) return HD_ERR_INVALID_ARG;
+  hd_status s = hd_lattice_ess_dofs(h->L.nx, h->L.ny, h->L.nz, h->k, h->L.ess, out, n);
+  if (s != HD_OK) return hd_fail(h, s, "ess dof buffer too small");
+  return HD_OK;
+}
+
+hd_status hd_apply_A(hd_handle h, const double* u, double* y) {
+  if (!h || !u || !y) return HD_ERR_INVALID_ARG;
+  HD_CK(h, cudaMemsetAsync(y, 0, sizeof(double) * h->n_rt, h->stream));
+  return elem_op(h, OP_M, u, nullptr, y, nullptr);
+}
+
+hd_status hd_apply_B(hd_handle h, const double* u, double* yq) {
+  if (!h || !u || !yq) return HD_ERR_INVALID_ARG;
+  return lattice_apply_B(h, u, yq);
+}
+
+hd_status hd_apply_Bt(hd_handle h, const double* q, double* yu) {
+  if (!h || !q || !yu) return HD_ERR_INVALID_ARG;
+  return lattice_apply_Bt(h, q, yu);
+}
+
+hd_status hd_apply_C(hd_handle h, const double* q, double* yq) {
+  if (!h || !q || !yq) return HD_ERR_INVALID_ARG;
+  return elem_op(h, OP_C | OP_CPOS, nullptr, q, nullptr, yq);
+}
+
+hd_status hd_apply_op(hd_handle h, const double* x, double* y) {
+  if (!h || !x || !y || x == y) return HD_ERR_INVALID_ARG;
+  return apply_op_internal(h, x, y);
+}
+
+hd_status hd_apply_op_host(hd_handle h, const double* xh, double* yh) {
+  if (!h || !xh || !yh) return HD_ERR_INVALID_ARG;
+  const int64_t n = h->n_rt + h->n_l2;
+  if (!h->d_stage) {
+    if (cudaMalloc(&h->d_stage, sizeof(double) * 2 * (n > 0 ? n : 1)) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "staging buffers");
+  }
+  double* dx = h->d_stage;
+  double* dy = h->d_stage + n;
+  HD_CK(h, cudaMemcpyAsync(dx, xh, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  hd_status st = apply_op_internal(h, dx, dy);
+  if (st != HD_OK) return st;
+  HD_CK(h, cudaMemcpyAsync(yh, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  return HD_OK;
+}
+
+hd_status hd_apply_prec(hd_handle h, const double* r, double* z) {
+  if (!h || !r || !z || r == z) return HD_ERR_INVALID_ARG;
+  return precond_apply(h, r, z);
+}
+
+hd_status hd_apply_schur(hd_handle h, const double* x, double* y) {
+  if (!h || !x || !y || x == y) return HD_ERR_INVALID_ARG;
+  return schur_apply(h, x, y);
+}
+
+hd_status hd_vcycle(hd_handle h, const double* b, double* x) {
+  if (!h || !b || !x || b == x) return HD_ERR_INVALID_ARG;
+  return vcycle_apply(h, b, x);
+}
+
+hd_status hd_get_diagonals(hd_handle h, double* mt, double* ct) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  if (mt) HD_CK(h, cudaMemcpyAsync(mt, h->d_mt, sizeof(double) * h->n_rt, cudaMemcpyDeviceToDevice, h->stream));
+  if (ct) HD_CK(h, cudaMemcpyAsync(ct, h->d_ct, sizeof(double) * h->n_l2, cudaMemcpyDeviceToDevice, h->stream));
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  return HD_OK;
+}
+
+hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3]) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  if (n_levels) *n_levels = (int32_t)h->lv.size();
+  if (dims) {
+    if (l < 0 || l >= (int32_t)h->lv.size()) return hd_fail(h, HD_ERR_INVALID_ARG, "level out of range");
+    dims[0] = h->lv[l].X; dims[1] = h->lv[l].Y; dims[2] = h->lv[l].Z;
+  }
+  return HD_OK;
+}
+
+hd_status hd_minres_solve(hd_handle h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
+  if (!h || !b || !x || !o || b == x || o->maxit < 1 || !(o->rtol > 0)) return HD_ERR_INVALID_ARG;
+  if (o->precision != 0) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "mixed precision solve");
+  hd_status st = minres_run(h, b, x, o, info);
+  if (info) {
+    // true residual ||b - AA x|| / ||b|| in FP64
+    const int64_t n = h->n_rt + h->n_l2;
+    if (!h->d_tmp && cudaMalloc(&h->d_tmp, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "tmp");
+    hd_status s2 = apply_op_internal(h, x, h->d_tmp);
+    if (s2 != HD_OK) return s2;
+    double rn = 0, bn = 0;
+    if ((s2 = residual_norms(h, b, h->d_tmp, &rn, &bn)) != HD_OK) return s2;
+    info->true_relres = bn > 0 ? rn / bn : rn;
+  }
+  return st;
+}
+
+hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y) {
+  if (!h || !x || !y || x == y) return HD_ERR_INVALID_ARG;
+  hd_status st = setup_f32(h);
+  if (st != HD_OK) return st;
+  return apply_op_f32_internal(h, x, y);
+}
+
+hd_status hd_apply_prec_f32(hd_handle h, const float* r, float* z) {
+  if (!h || !r || !z || r == z) return HD_ERR_INVALID_ARG;
+  return precond_apply_f32(h, r, z);
+}
+
+}  // extern "C"

@@ -1,0 +1,147 @@
+// Internal declarations of the hdivsp CUDA library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "hdivsp.h"
+
+#define HD_MAXK 5
+#define HD_MAXQ 7
+
+// 1D tables of the interpolation-histopolation basis evaluated at the
+// Gauss-Legendre points (Sec. 2.1). Passed to the element kernels by value so
+// that they live in the kernel-parameter constant bank and unrolled loops use
+// them as direct operands.
+struct ElemTables {
+  double BI[HD_MAXQ * (HD_MAXK + 1)];  // BI[p*(k+1)+i] = l_i(g_p), Lagrange at GLL nodes
+  double BH[HD_MAXQ * HD_MAXK];        // BH[p*k+j]     = h_j(g_p), histopolation
+  double gw[HD_MAXQ];                  // GL weights on [0,1]
+  double gx[HD_MAXQ];                  // GL points on [0,1]
+};
+
+// Mesh/lattice constants passed to kernels.
+struct LatticeDims {
+  int nx, ny, nz;      // elements
+  int X, Y, Z;         // subcells
+  int n_xf, n_yf;      // number of x- and y-faces (z-faces follow)
+  uint32_t ess;        // essential side mask
+};
+
+// One level of the V-cycle hierarchy: a 7-point M-matrix stencil on an
+// X x Y x Z cell lattice, stored as face weights (boundary faces included,
+// essential faces 0), per-cell mass, diagonal and inverse l1 diagonal.
+template <typename T>
+struct LevelT {
+  int X, Y, Z;
+  int fx, fy, fz;      // aggregation factor from the previous (finer) level
+  T* wx;               // (X+1) Y Z
+  T* wy;               // X (Y+1) Z
+  T* wz;               // X Y (Z+1)
+  T* mass;             // X Y Z
+  T* diag;             // mass + sum of the 6 face weights
+  T* dinv;             // 1 / (diag + sum of interior face weights)  (l1-Jacobi)
+  T* x0;               // work: iterate (ping)
+  T* x1;               // work: iterate (pong)
+  T* b;                // work: right-hand side (levels >= 1)
+  __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
+};
+
+struct MinresState;  // device-side scalars of the MINRES recurrence
+
+struct hd_op {
+  // problem
+  hd_problem_desc desc;
+  int kind, k, q;
+  LatticeDims L;
+  int64_t n_rt, n_l2, n_elem;
+  double tau;
+  int winv_mode, nu, coarse_max;
+  bool singular;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  ElemTables tab;
+  ElemTables tabW;     // tables for the W quadrature (same rule)
+
+  // device data (FP64)
+  double* d_vx = nullptr;       // vertices (SoA)
+  double* d_vy = nullptr;
+  double* d_vz = nullptr;
+  double* d_G = nullptr;        // [E][6][Q^3] w_p b_e J^T J / det J
+  double* d_wdet = nullptr;     // [E][Q^3] w_p / det J
+  double* d_winv = nullptr;     // [E][k^3][k^3] unweighted W_e^-1 (dense mode)
+  double* d_wdiag = nullptr;    // [E][k^3] diag(W_e) (unweighted)
+  double* d_cscale = nullptr;   // [E] c_e: C_e = c_e W_e^-1
+  double* d_mt = nullptr;       // [n_rt] diag(M), 1 on essential dofs
+  double* d_mtinv = nullptr;    // [n_rt] 1/(tau diag M) on free dofs, 1 on essential
+  double* d_ct = nullptr;       // [n_l2] C~
+  double* d_coarse_inv = nullptr;  // dense inverse of the coarsest level (or of A + s 11^T)
+  int coarse_n = 0;
+  std::vector<LevelT<double>> lv;
+
+  // FP32 copies for the mixed-precision inner solve
+  float* f_G = nullptr;
+  float* f_winv = nullptr;
+  float* f_cscale = nullptr;
+  float* f_mtinv = nullptr;
+  float* f_coarse_inv = nullptr;
+  std::vector<LevelT<float>> lvf;
+  bool have_f32 = false;
+
+  // scratch
+  double* d_red = nullptr;      // reduction partials
+  double* d_tmp = nullptr;      // n_rt + n_l2
+  double* h_pinned = nullptr;   // small pinned host buffer
+  double* d_stage = nullptr;    // 2 (n_rt + n_l2) staging for *_host calls
+  // MINRES work vectors (allocated on first solve)
+  std::vector<double*> mv;
+  MinresState* d_ms = nullptr;
+  std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
+};
+
+// error helpers
+hd_status hd_fail(hd_op* h, hd_status s, const std::string& msg);
+hd_status hd_cuda_check(hd_op* h, cudaError_t e, const char* what);
+#define HD_CK(h, call)                                              \
+  do {                                                              \
+    cudaError_t e_ = (call);                                        \
+    if (e_ != cudaSuccess) return hd_cuda_check((h), e_, #call);    \
+  } while (0)
+#define HD_LAUNCH_CK(h, what)                                       \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) return hd_cuda_check((h), e_, what);     \
+  } while (0)
+
+// element-kernel launchers (one translation unit per k); mode bits below
+enum {
+  OP_M = 1,      // y_u += M u
+  OP_DT = 2,     // y_u += D^T q
+  OP_D = 4,      // y_q  = D u
+  OP_C = 8,      // y_q -= C q  (or = -C q without OP_D); with OP_CPOS: y_q = +C q
+  OP_CPOS = 16,
+};
+// y_u must be zeroed by the caller when OP_M or OP_DT is set.
+hd_status launch_elem_op(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq);
+hd_status launch_elem_op_f32(hd_op* h, int mode, const float* u, const float* q, float* yu, float* yq);
+hd_status launch_elem_setup(hd_op* h);   // geometric factors, W_e^-1, diag(W), diag(M)
+
+// lattice kernels (k_lattice.cu)
+hd_status lattice_apply_B(hd_op* h, const double* u, double* yq);
+hd_status lattice_apply_Bt(hd_op* h, const double* q, double* yu);
+hd_status lattice_ess_identity(hd_op* h, const double* x, double* y);
+hd_status precond_setup(hd_op* h);
+hd_status precond_apply(hd_op* h, const double* r, double* z);
+hd_status precond_apply_f32(hd_op* h, const float* r, float* z);
+hd_status schur_apply(hd_op* h, const double* x, double* y);
+hd_status vcycle_apply(hd_op* h, const double* b, double* x);
+hd_status setup_f32(hd_op* h);
+void precond_free(hd_op* h);
+hd_status project_mean(hd_op* h, double* z);
+hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn);
+
+// Krylov (k_krylov.cu)
+hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info);
+hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, double* d_out);

@@ -1,0 +1,598 @@
+// Element kernels of the block operator, templated on the scalar type, the
+// degree K (subcells per direction) and the number Q of Gauss-Legendre points
+// per direction. One translation unit per K instantiates them (k_elem_k*.cu).
+//
+// Data layouts (element e = ex + nx (ey + ny ez)):
+//   G     [E][6][Q^3]      w_p b_e (J^T J)_{ab} / det J at point p, ab in 00,01,02,11,12,22
+//   winv  [E][K^3][K^3]    unweighted W_e^-1 (symmetric; element (b,a) read as (a,b))
+//   wdet  [E][Q^3]         w_p / det J
+// Local RT dof order: x-component i + (K+1)(j + K l); y-component
+// NX1 + i + K (j + (K+1) l); z-component 2 NX1 + i + K (j + K l), NX1 = (K+1) K^2.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "hd_internal.h"
+
+namespace hdk {
+
+template <typename T>
+struct TabT {
+  T BI[HD_MAXQ * (HD_MAXK + 1)];
+  T BH[HD_MAXQ * HD_MAXK];
+};
+
+template <typename T>
+inline TabT<T> make_tab(const ElemTables& t) {
+  TabT<T> o;
+  for (int i = 0; i < HD_MAXQ * (HD_MAXK + 1); ++i) o.BI[i] = (T)t.BI[i];
+  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BH[i] = (T)t.BH[i];
+  return o;
+}
+
+// out[o*SO] = sum_i B[o*NI + i] in[i*SI], o < NO   (B row-major NO x NI)
+template <typename T, int NI, int NO, int SI, int SO>
+__device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out, const T* B) {
+  T x[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) x[i] = in[i * SI];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    T s = B[o * NI] * x[0];
+#pragma unroll
+    for (int i = 1; i < NI; ++i) s = fma(B[o * NI + i], x[i], s);
+    out[o * SO] = s;
+  }
+}
+
+// out[o*SO] = sum_i B[i*NO + o] in[i*SI], o < NO   (transposed use of a NI x NO table)
+template <typename T, int NI, int NO, int SI, int SO>
+__device__ __forceinline__ void contractT(const T* __restrict__ in, T* __restrict__ out, const T* B) {
+  T x[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) x[i] = in[i * SI];
+#pragma unroll
+  for (int o = 0; o < NO; ++o) {
+    T s = B[o] * x[0];
+#pragma unroll
+    for (int i = 1; i < NI; ++i) s = fma(B[i * NO + o], x[i], s);
+    out[o * SO] = s;
+  }
+}
+
+template <int K, int Q>
+struct Sizes {
+  static constexpr int NX1 = (K + 1) * K * K;
+  static constexpr int NRT = 3 * NX1;
+  static constexpr int NL2 = K * K * K;
+  static constexpr int NQ = Q * Q * Q;
+  static constexpr int T1 = 3 * Q * K * (K + 1);
+  static constexpr int UQ = 3 * NQ;
+  static constexpr int R1 = (T1 > UQ ? T1 : UQ);   // T1 and the point values share a region
+  static constexpr int R2 = 3 * Q * Q * (K + 1);  // T2
+  static constexpr int PER_ELEM = NRT + NL2 + R1 + R2;
+};
+
+// global RT id and essential flag of local dof n of element (ex,ey,ez)
+template <int K>
+__device__ __forceinline__ int rt_global(const LatticeDims& L, int ex, int ey, int ez, int n, bool& ess) {
+  constexpr int NX1 = (K + 1) * K * K;
+  int I, J, Z;
+  if (n < NX1) {
+    int i = n % (K + 1), r = n / (K + 1);
+    I = ex * K + i; J = ey * K + r % K; Z = ez * K + r / K;
+    ess = (I == 0 && (L.ess & 1)) || (I == L.X && (L.ess & 2));
+    return I + (L.X + 1) * (J + L.Y * Z);
+  } else if (n < 2 * NX1) {
+    int m = n - NX1;
+    int i = m % K, r = m / K;
+    I = ex * K + i; J = ey * K + r % (K + 1); Z = ez * K + r / (K + 1);
+    ess = (J == 0 && (L.ess & 4)) || (J == L.Y && (L.ess & 8));
+    return L.n_xf + I + L.X * (J + (L.Y + 1) * Z);
+  } else {
+    int m = n - 2 * NX1;
+    int i = m % K, r = m / K;
+    I = ex * K + i; J = ey * K + r % K; Z = ez * K + r / K;
+    ess = (Z == 0 && (L.ess & 16)) || (Z == L.Z && (L.ess & 32));
+    return L.n_xf + L.n_yf + I + L.X * (J + L.Y * Z);
+  }
+}
+
+// own-cell part of (D^T q) at local face n (q: element-local L2 values)
+template <typename T, int K>
+__device__ __forceinline__ T dt_local(const T* sq, int n) {
+  constexpr int NX1 = (K + 1) * K * K;
+  T v = (T)0;
+  if (n < NX1) {
+    int i = n % (K + 1), r = n / (K + 1);  // r = j + K l
+    if (i > 0) v += sq[(i - 1) + K * r];
+    if (i < K) v -= sq[i + K * r];
+  } else if (n < 2 * NX1) {
+    int m = n - NX1;
+    int i = m % K, r = m / K;
+    int j = r % (K + 1), l = r / (K + 1);
+    if (j > 0) v += sq[i + K * ((j - 1) + K * l)];
+    if (j < K) v -= sq[i + K * (j + K * l)];
+  } else {
+    int m = n - 2 * NX1;
+    int i = m % K, r = m / K;
+    int j = r % K, l = r / K;
+    if (l > 0) v += sq[i + K * (j + K * (l - 1))];
+    if (l < K) v -= sq[i + K * (j + K * l)];
+  }
+  return v;
+}
+
+// (D u)_cell for local cell a = i + K (j + K l) from the element-local RT values
+template <typename T, int K>
+__device__ __forceinline__ T div_local(const T* su, int a) {
+  constexpr int NX1 = (K + 1) * K * K;
+  int i = a % K, j = (a / K) % K, l = a / (K * K);
+  T v = su[(i + 1) + (K + 1) * (j + K * l)] - su[i + (K + 1) * (j + K * l)];
+  v += su[NX1 + i + K * ((j + 1) + (K + 1) * l)] - su[NX1 + i + K * (j + (K + 1) * l)];
+  v += su[2 * NX1 + i + K * (j + K * (l + 1))] - su[2 * NX1 + i + K * (j + K * l)];
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Fused block-operator kernel: EB elements per CTA.
+//   OP_M : y_u += M_e u_e (sum factorisation: interpolation to the Q^3 points,
+//          the 3x3 geometric factor, transposed interpolation)
+//   OP_DT: y_u += own-cell D^T q
+//   OP_D : y_q  = D u on the element's cells
+//   OP_C : y_q -= c_e W_e^-1 q  (OP_CPOS: +)
+// Essential faces: with OP_M the owning element adds u_g (constrained
+// identity); otherwise nothing. y_u receives one atomic add per element and
+// face: a shared face gets exactly two addends on a zeroed vector, so the
+// result does not depend on their order.
+template <typename T, int K, int Q, int EB>
+__global__ void __launch_bounds__(256)
+k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem,
+          const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
+          const T* __restrict__ u, const T* __restrict__ q, T* __restrict__ yu, T* __restrict__ yq) {
+  using S = Sizes<K, Q>;
+  constexpr int NX1 = S::NX1, NRT = S::NRT, NL2 = S::NL2, NQ = S::NQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  T* su = sm;                         // [EB][NRT]  u_e, later y_e
+  T* sq = su + EB * NRT;              // [EB][NL2]
+  T* s1 = sq + EB * NL2;              // [EB][R1]   T1 / point values
+  T* s2 = s1 + EB * S::R1;            // [EB][R2]   T2
+  const int e0 = blockIdx.x * EB;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const bool needu = (mode & (OP_M | OP_D)) != 0;
+  const bool needq = (mode & (OP_DT | OP_C)) != 0;
+
+  // -- gather -----------------------------------------------------------------
+  if (needu) {
+    for (int t = tid; t < EB * NRT; t += nth) {
+      int el = t / NRT, n = t - el * NRT, e = e0 + el;
+      T v = (T)0;
+      if (e < n_elem) {
+        int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+        bool ess;
+        int g = rt_global<K>(L, ex, ey, ez, n, ess);
+        v = ess ? (T)0 : u[g];
+      }
+      su[t] = v;
+    }
+  }
+  if (needq) {
+    for (int t = tid; t < EB * NL2; t += nth) {
+      int el = t / NL2, a = t - el * NL2, e = e0 + el;
+      T v = (T)0;
+      if (e < n_elem) {
+        int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+        int i = a % K, j = (a / K) % K, l = a / (K * K);
+        v = q[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))];
+      }
+      sq[t] = v;
+    }
+  }
+  __syncthreads();
+
+  // -- L2 rows: y_q = D u - C q ------------------------------------------------
+  if (mode & (OP_D | OP_C)) {
+    for (int t = tid; t < EB * NL2; t += nth) {
+      int el = t / NL2, a = t - el * NL2, e = e0 + el;
+      if (e >= n_elem) continue;
+      T v = (T)0;
+      if (mode & OP_D) v = div_local<T, K>(su + el * NRT, a);
+      if (mode & OP_C) {
+        const T* W = winv + (size_t)e * NL2 * NL2;
+        const T* qe = sq + el * NL2;
+        T s = (T)0;
+#pragma unroll 8
+        for (int b = 0; b < NL2; ++b) s = fma(W[b * NL2 + a], qe[b], s);
+        s *= cscale[e];
+        v = (mode & OP_CPOS) ? v + s : v - s;
+      }
+      int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+      int i = a % K, j = (a / K) % K, l = a / (K * K);
+      yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = v;
+    }
+  }
+
+  if (mode & OP_M) {
+    // -- interpolation to the points: stage A (contract along x) ----------------
+    {
+      constexpr int LX = K * K, LY = (K + 1) * K, LZ = K * (K + 1);
+      for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
+        if (t < EB * LX) {
+          int el = t / LX, r = t - el * LX;  // r = j + K l
+          contract<T, K + 1, Q, 1, 1>(su + el * NRT + (K + 1) * r, s1 + el * S::R1 + Q * r, tab.BI);
+        } else if (t < EB * (LX + LY)) {
+          int tt = t - EB * LX, el = tt / LY, r = tt - el * LY;  // r = j + (K+1) l
+          contract<T, K, Q, 1, 1>(su + el * NRT + NX1 + K * r, s1 + el * S::R1 + Q * K * K + Q * r, tab.BH);
+        } else {
+          int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ;  // r = j + K l
+          contract<T, K, Q, 1, 1>(su + el * NRT + 2 * NX1 + K * r,
+                                  s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r, tab.BH);
+        }
+      }
+    }
+    __syncthreads();
+    // stage B (contract along y): T2[px + Q (py + Q l)]
+    {
+      constexpr int LX = Q * K, LY = Q * K, LZ = Q * (K + 1);
+      for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
+        if (t < EB * LX) {
+          int el = t / LX, r = t - el * LX, px = r % Q, l = r / Q;
+          contract<T, K, Q, Q, Q>(s1 + el * S::R1 + px + Q * K * l, s2 + el * S::R2 + px + Q * Q * l, tab.BH);
+        } else if (t < EB * (LX + LY)) {
+          int tt = t - EB * LX, el = tt / LY, r = tt - el * LY, px = r % Q, l = r / Q;
+          contract<T, K + 1, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l,
+                                      s2 + el * S::R2 + Q * Q * K + px + Q * Q * l, tab.BI);
+        } else {
+          int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ, px = r % Q, l = r / Q;
+          contract<T, K, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l,
+                                  s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l, tab.BH);
+        }
+      }
+    }
+    __syncthreads();
+    // stage C (contract along z): point values U_c[px + Q (py + Q pz)] in s1
+    {
+      constexpr int LL = Q * Q;
+      for (int t = tid; t < EB * 3 * LL; t += nth) {
+        int c = t / (EB * LL), tt = t - c * EB * LL, el = tt / LL, r = tt - el * LL;
+        T* out = s1 + el * S::R1 + c * NQ + r;
+        const T* in = s2 + el * S::R2 + c * Q * Q * K + r;
+        if (c == 2)
+          contract<T, K + 1, Q, Q * Q, Q * Q>(in, out, tab.BI);
+        else
+          contract<T, K, Q, Q * Q, Q * Q>(in, out, tab.BH);
+      }
+    }
+    __syncthreads();
+    // -- pointwise: v = G u --------------------------------------------------------
+    for (int t = tid; t < EB * NQ; t += nth) {
+      int el = t / NQ, p = t - el * NQ, e = e0 + el;
+      if (e >= n_elem) continue;
+      const T* g = G + (size_t)e * 6 * NQ + p;
+      T g00 = g[0], g01 = g[NQ], g02 = g[2 * NQ], g11 = g[3 * NQ], g12 = g[4 * NQ], g22 = g[5 * NQ];
+      T* U = s1 + el * S::R1 + p;
+      T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
+      U[0] = fma(g00, ux, fma(g01, uy, g02 * uz));
+      U[NQ] = fma(g01, ux, fma(g11, uy, g12 * uz));
+      U[2 * NQ] = fma(g02, ux, fma(g12, uy, g22 * uz));
+    }
+    __syncthreads();
+    // -- transposed interpolation: stage C^T (z) -------------------------------
+    {
+      constexpr int LL = Q * Q;
+      for (int t = tid; t < EB * 3 * LL; t += nth) {
+        int c = t / (EB * LL), tt = t - c * EB * LL, el = tt / LL, r = tt - el * LL;
+        const T* in = s1 + el * S::R1 + c * NQ + r;
+        T* out = s2 + el * S::R2 + c * Q * Q * K + r;
+        if (c == 2)
+          contractT<T, Q, K + 1, Q * Q, Q * Q>(in, out, tab.BI);
+        else
+          contractT<T, Q, K, Q * Q, Q * Q>(in, out, tab.BH);
+      }
+    }
+    __syncthreads();
+    // stage B^T (y): T1 from T2
+    {
+      constexpr int LX = Q * K, LY = Q * K, LZ = Q * (K + 1);
+      for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
+        if (t < EB * LX) {
+          int el = t / LX, r = t - el * LX, px = r % Q, l = r / Q;
+          contractT<T, Q, K, Q, Q>(s2 + el * S::R2 + px + Q * Q * l, s1 + el * S::R1 + px + Q * K * l, tab.BH);
+        } else if (t < EB * (LX + LY)) {
+          int tt = t - EB * LX, el = tt / LY, r = tt - el * LY, px = r % Q, l = r / Q;
+          contractT<T, Q, K + 1, Q, Q>(s2 + el * S::R2 + Q * Q * K + px + Q * Q * l,
+                                       s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l, tab.BI);
+        } else {
+          int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ, px = r % Q, l = r / Q;
+          contractT<T, Q, K, Q, Q>(s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l,
+                                   s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l, tab.BH);
+        }
+      }
+    }
+    __syncthreads();
+    // stage A^T (x): y_e into su
+    {
+      constexpr int LX = K * K, LY = (K + 1) * K, LZ = K * (K + 1);
+      for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
+        if (t < EB * LX) {
+          int el = t / LX, r = t - el * LX;
+          contractT<T, Q, K + 1, 1, 1>(s1 + el * S::R1 + Q * r, su + el * NRT + (K + 1) * r, tab.BI);
+        } else if (t < EB * (LX + LY)) {
+          int tt = t - EB * LX, el = tt / LY, r = tt - el * LY;
+          contractT<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * r, su + el * NRT + NX1 + K * r, tab.BH);
+        } else {
+          int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ;
+          contractT<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r,
+                                   su + el * NRT + 2 * NX1 + K * r, tab.BH);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // -- scatter to y_u ------------------------------------------------------------
+  if (mode & (OP_M | OP_DT)) {
+    for (int t = tid; t < EB * NRT; t += nth) {
+      int el = t / NRT, n = t - el * NRT, e = e0 + el;
+      if (e >= n_elem) continue;
+      int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+      bool ess;
+      int g = rt_global<K>(L, ex, ey, ez, n, ess);
+      T v;
+      if (ess) {
+        if (!(mode & OP_M)) continue;
+        v = u[g];
+      } else {
+        v = (mode & OP_M) ? su[t] : (T)0;
+        if (mode & OP_DT) v += dt_local<T, K>(sq + el * NL2, n);
+      }
+      atomicAdd(yu + g, v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Setup: geometric factors at the Q^3 points of each element (one thread per
+// element and point). Trilinear map from the 8 corner vertices.
+template <int Q>
+__global__ void k_geom(const ElemTables tab, const LatticeDims L, const int n_elem,
+                       const double* __restrict__ vx, const double* __restrict__ vy,
+                       const double* __restrict__ vz, const double* __restrict__ bcoef,
+                       double* __restrict__ G, double* __restrict__ wdet, int* __restrict__ bad) {
+  constexpr int NQ = Q * Q * Q;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_elem * NQ) return;
+  int e = (int)(t / NQ), p = (int)(t - (int64_t)e * NQ);
+  int px = p % Q, py = (p / Q) % Q, pz = p / (Q * Q);
+  double x1 = tab.gx[px], x2 = tab.gx[py], x3 = tab.gx[pz];
+  double w = tab.gw[px] * tab.gw[py] * tab.gw[pz];
+  int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+  double J[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+  for (int c = 0; c < 2; ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        int64_t vid = (ex + a) + (int64_t)(L.nx + 1) * ((ey + b) + (int64_t)(L.ny + 1) * (ez + c));
+        double Na = a ? x1 : 1.0 - x1, Nb = b ? x2 : 1.0 - x2, Nc = c ? x3 : 1.0 - x3;
+        double da = a ? 1.0 : -1.0, db = b ? 1.0 : -1.0, dc = c ? 1.0 : -1.0;
+        double g0 = da * Nb * Nc, g1 = Na * db * Nc, g2 = Na * Nb * dc;
+        double X[3] = {vx[vid], vy[vid], vz[vid]};
+        for (int i = 0; i < 3; ++i) {
+          J[i][0] += X[i] * g0;
+          J[i][1] += X[i] * g1;
+          J[i][2] += X[i] * g2;
+        }
+      }
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  if (!(det > 0.0)) {
+    atomicExch(bad, 1);
+    det = 1.0;
+  }
+  double s = w * bcoef[e] / det;
+  double JtJ[6];
+  int idx = 0;
+  for (int a = 0; a < 3; ++a)
+    for (int b = a; b < 3; ++b) JtJ[idx++] = J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b];
+  double* g = G + (size_t)e * 6 * NQ + p;
+  for (int c = 0; c < 6; ++c) g[c * NQ] = s * JtJ[c];
+  wdet[(size_t)e * NQ + p] = w / det;
+}
+
+// Setup: W_e = sum_p wdet_p psi_a psi_b by sum factorisation over the tensor
+// structure, then W_e^-1 by Gauss-Jordan elimination in shared memory (W_e is
+// SPD: no pivoting), symmetrised. One CTA per element.
+template <int K, int Q>
+struct WinvSmem {
+  static constexpr int NL2 = K * K * K, KK = K * K, NQ = Q * Q * Q;
+  static constexpr int OFF_HH = NQ;
+  static constexpr int OFF_T1 = OFF_HH + Q * KK;
+  static constexpr int OFF_T2 = OFF_T1 + Q * Q * KK;
+  static constexpr int OFF_A = OFF_T2 + Q * KK * KK;
+  static constexpr int OFF_COL = OFF_A + NL2 * NL2;
+  static constexpr int TOTAL = OFF_COL + NL2;
+};
+
+template <int K, int Q>
+__global__ void __launch_bounds__(128)
+k_winv(const ElemTables tab, const int n_elem, const double* __restrict__ wdet,
+       double* __restrict__ winv, double* __restrict__ wdiag) {
+  using S = WinvSmem<K, Q>;
+  constexpr int NL2 = S::NL2, KK = S::KK, NQ = S::NQ;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* sw = reinterpret_cast<double*>(smem_raw);
+  double* HH = sw + S::OFF_HH;     // HH[p][(a,b)] = h_a(g_p) h_b(g_p)
+  double* T1 = sw + S::OFF_T1;     // [p1][p2][(a3,b3)]
+  double* T2 = sw + S::OFF_T2;     // [p1][(a2,b2)][(a3,b3)]
+  double* A = sw + S::OFF_A;       // [NL2][NL2]
+  double* colp = sw + S::OFF_COL;  // pivot column
+  const int e = blockIdx.x;
+  if (e >= n_elem) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int t = tid; t < NQ; t += nth) sw[t] = wdet[(size_t)e * NQ + t];
+  for (int t = tid; t < Q * KK; t += nth) {
+    int p = t / KK, ab = t % KK, a = ab % K, b = ab / K;
+    HH[t] = tab.BH[p * K + a] * tab.BH[p * K + b];
+  }
+  __syncthreads();
+  for (int t = tid; t < Q * Q * KK; t += nth) {
+    int p12 = t / KK, ab = t % KK;
+    double s = 0.0;
+    for (int p3 = 0; p3 < Q; ++p3) s += sw[p12 + Q * Q * p3] * HH[p3 * KK + ab];
+    T1[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < Q * KK * KK; t += nth) {
+    int p1 = t / (KK * KK), r = t % (KK * KK), ab2 = r / KK, ab3 = r % KK;
+    double s = 0.0;
+    for (int p2 = 0; p2 < Q; ++p2) s += HH[p2 * KK + ab2] * T1[(p1 + Q * p2) * KK + ab3];
+    T2[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < NL2 * NL2; t += nth) {
+    int A_ = t / NL2, B_ = t % NL2;  // row (a1,a2,a3), col (b1,b2,b3)
+    int a1 = A_ % K, a2 = (A_ / K) % K, a3 = A_ / KK;
+    int b1 = B_ % K, b2 = (B_ / K) % K, b3 = B_ / KK;
+    int ab1 = a1 + K * b1, ab2 = a2 + K * b2, ab3 = a3 + K * b3;
+    double s = 0.0;
+    for (int p1 = 0; p1 < Q; ++p1) s += HH[p1 * KK + ab1] * T2[(p1 * KK + ab2) * KK + ab3];
+    A[t] = s;
+  }
+  __syncthreads();
+  for (int t = tid; t < NL2; t += nth) wdiag[(size_t)e * NL2 + t] = A[t * NL2 + t];
+  // Gauss-Jordan elimination in place (W_e is SPD: no pivoting). After step p,
+  // column p holds column p of the inverse.
+  for (int p = 0; p < NL2; ++p) {
+    __syncthreads();
+    for (int i = tid; i < NL2; i += nth) colp[i] = A[i * NL2 + p];
+    __syncthreads();
+    const double piv = 1.0 / colp[p];
+    for (int j = tid; j < NL2; j += nth) A[p * NL2 + j] = (j == p) ? piv : A[p * NL2 + j] * piv;
+    __syncthreads();
+    for (int t = tid; t < NL2 * NL2; t += nth) {
+      int i = t / NL2, j = t - i * NL2;
+      if (i == p) continue;
+      double f = colp[i];
+      A[t] = (j == p) ? -f * piv : fma(-f, A[p * NL2 + j], A[t]);
+    }
+  }
+  __syncthreads();
+  double* out = winv + (size_t)e * NL2 * NL2;
+  for (int t = tid; t < NL2 * NL2; t += nth) {
+    int i = t / NL2, j = t % NL2;
+    out[t] = 0.5 * (A[i * NL2 + j] + A[j * NL2 + i]);
+  }
+}
+
+// Setup: diag(M_e) by sum factorisation with squared 1D tables, added to the
+// global diagonal (two addends on shared faces). One thread per element and
+// local dof (direct sum over the Q^3 points: setup only).
+template <int K, int Q>
+__global__ void k_diagM(const ElemTables tab, const LatticeDims L, const int n_elem,
+                        const double* __restrict__ G, double* __restrict__ mt) {
+  constexpr int NX1 = (K + 1) * K * K, NRT = 3 * NX1, NQ = Q * Q * Q;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_elem * NRT) return;
+  int e = (int)(t / NRT), n = (int)(t - (int64_t)e * NRT);
+  int c, i, j, l;
+  if (n < NX1) { c = 0; i = n % (K + 1); j = (n / (K + 1)) % K; l = n / ((K + 1) * K); }
+  else if (n < 2 * NX1) { int m = n - NX1; c = 1; i = m % K; j = (m / K) % (K + 1); l = m / (K * (K + 1)); }
+  else { int m = n - 2 * NX1; c = 2; i = m % K; j = (m / K) % K; l = m / (K * K); }
+  const double* g = G + (size_t)e * 6 * NQ + (c == 0 ? 0 : (c == 1 ? 3 : 5)) * NQ;
+  double s = 0.0;
+  for (int pz = 0; pz < Q; ++pz) {
+    double bz = (c == 2) ? tab.BI[pz * (K + 1) + l] : tab.BH[pz * K + l];
+    for (int py = 0; py < Q; ++py) {
+      double by = (c == 1) ? tab.BI[py * (K + 1) + j] : tab.BH[py * K + j];
+      for (int px = 0; px < Q; ++px) {
+        double bx = (c == 0) ? tab.BI[px * (K + 1) + i] : tab.BH[px * K + i];
+        double v = bx * by * bz;
+        s += g[px + Q * (py + Q * pz)] * v * v;
+      }
+    }
+  }
+  int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+  bool ess;
+  int gid = rt_global<K>(L, ex, ey, ez, n, ess);
+  atomicAdd(mt + gid, s);
+}
+
+template <int K, int Q>
+constexpr int elem_eb() {
+  return 8;
+}
+
+template <typename T, int K, int Q>
+hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const T* u,
+                      const T* q, T* yu, T* yq) {
+  constexpr int EB = elem_eb<K, Q>();
+  using S = Sizes<K, Q>;
+  size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
+  auto kern = k_elem_op<T, K, Q, EB>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_elem_op)");
+    attr_set = true;
+  }
+  TabT<T> tab = make_tab<T>(h->tab);
+  int blocks = (int)((h->n_elem + EB - 1) / EB);
+  if (blocks > 0)
+    kern<<<blocks, 256, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, u, q, yu, yq);
+  HD_LAUNCH_CK(h, "k_elem_op");
+  return HD_OK;
+}
+
+template <int K, int Q>
+hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
+  constexpr int NQ = Q * Q * Q, NRT = 3 * (K + 1) * K * K;
+  int64_t n = h->n_elem * NQ;
+  if (n > 0) k_geom<Q><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      h->tab, h->L, (int)h->n_elem, h->d_vx, h->d_vy, h->d_vz, bcoef, h->d_G, h->d_wdet, d_bad);
+  HD_LAUNCH_CK(h, "k_geom");
+  if (h->winv_mode == HD_WINV_DENSE && h->n_elem > 0) {
+    size_t smem = (size_t)WinvSmem<K, Q>::TOTAL * sizeof(double);
+    cudaError_t err = cudaFuncSetAttribute(k_winv<K, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return hd_cuda_check(h, err, "cudaFuncSetAttribute(k_winv)");
+    k_winv<K, Q><<<(unsigned)h->n_elem, 128, smem, h->stream>>>(h->tab, (int)h->n_elem, h->d_wdet, h->d_winv,
+                                                                 h->d_wdiag);
+    HD_LAUNCH_CK(h, "k_winv");
+  }
+  int64_t m = h->n_elem * NRT;
+  if (m > 0) k_diagM<K, Q><<<(unsigned)((m + 255) / 256), 256, 0, h->stream>>>(h->tab, h->L, (int)h->n_elem,
+                                                                          h->d_G, h->d_mt);
+  HD_LAUNCH_CK(h, "k_diagM");
+  return HD_OK;
+}
+
+}  // namespace hdk
+
+// Per-K entry points defined in k_elem_k*.cu
+#define HD_DECLARE_K(KK)                                                                          \
+  hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,       \
+                          double* yq);                                                            \
+  hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,      \
+                              float* yq);                                                         \
+  hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad);
+
+HD_DECLARE_K(2)
+HD_DECLARE_K(3)
+HD_DECLARE_K(4)
+HD_DECLARE_K(5)
+
+#define HD_DEFINE_K(KK)                                                                                   \
+  hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) { \
+    if (h->q == KK + 1)                                                                                   \
+      return hdk::run_elem_op<double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, u, q, yu, yq); \
+    return hdk::run_elem_op<double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, u, q, yu, yq);   \
+  }                                                                                                       \
+  hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,              \
+                              float* yq) {                                                                \
+    if (h->q == KK + 1)                                                                                   \
+      return hdk::run_elem_op<float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, u, q, yu, yq);  \
+    return hdk::run_elem_op<float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, u, q, yu, yq);    \
+  }                                                                                                       \
+  hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad) {                                 \
+    if (h->q == KK + 1) return hdk::run_elem_setup<KK, KK + 1>(h, bcoef, d_bad);                          \
+    return hdk::run_elem_setup<KK, KK + 2>(h, bcoef, d_bad);                                              \
+  }

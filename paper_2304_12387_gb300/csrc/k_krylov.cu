@@ -1,0 +1,334 @@
+// Krylov layer: deterministic FP64 inner products (warp shuffles -> fixed
+// per-block partials -> one fixed-order final pass) and preconditioned MINRES
+// (Paige & Saunders 1975) with its Lanczos/Givens scalars kept on the device,
+// so an iteration needs no host round trip (Sec. 3: MINRES with the
+// block-diagonal preconditioner).
+#include <cmath>
+#include <vector>
+
+#include "hd_internal.h"
+
+namespace {
+constexpr int TPB = 256;
+constexpr int DOT_BLOCKS = 1024;  // fixed: the reduction order does not depend on the data
+inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
+  if (ln == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (w == 0) {
+    s = (ln < (int)(blockDim.x >> 5)) ? sh[ln] : 0.0;
+    s = warp_sum(s);
+  }
+  __syncthreads();
+  return s;
+}
+
+// partial[b] = sum over block b's contiguous chunk of a[i]*b[i]
+__global__ void k_dot_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                              double* __restrict__ partial) {
+  __shared__ double sh[32];
+  int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double s = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s = fma(a[i], b[i], s);
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_dot_final(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = block_sum(partial[threadIdx.x], sh);  // blockDim.x == DOT_BLOCKS
+  if (threadIdx.x == 0) out[0] = s;
+}
+
+}  // namespace
+
+struct MinresState {
+  double beta, beta_prev, alpha, c, s, d_bar, eps, eps_next, delta, gamma, phi, phi_bar, eta0, rtol;
+  double dot;       // scratch result of the last inner product
+  int done_at;      // iteration at which the recurrence stopped (-1: running)
+  int status;       // HD_OK / HD_ERR_*
+};
+
+namespace {
+
+// y -= (beta/beta_prev) r_pp (when it > 1); partial sums of v.y
+__global__ void k_mr_lanczos1(int64_t n, int it, const MinresState* __restrict__ st, const double* __restrict__ v,
+                              double* __restrict__ y, const double* __restrict__ rpp, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const double f = (it > 1) ? st->beta / st->beta_prev : 0.0;
+  int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double s = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double yi = y[i];
+    if (it > 1) yi = fma(-f, rpp[i], yi);
+    y[i] = yi;
+    s = fma(v[i], yi, s);
+  }
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void k_mr_alpha(MinresState* st, const double* __restrict__ partial) {
+  __shared__ double sh[32];
+  double s = block_sum(partial[threadIdx.x], sh);
+  if (threadIdx.x == 0) st->alpha = s;
+}
+
+// y -= (alpha/beta) r_p  (y becomes the new Lanczos vector r);  z_u = r_u * mtinv
+__global__ void k_mr_lanczos2(int64_t n, int64_t n_rt, const MinresState* __restrict__ st,
+                              double* __restrict__ y, const double* __restrict__ rp,
+                              const double* __restrict__ mtinv, double* __restrict__ z) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double f = st->alpha / st->beta;
+  double yi = fma(-f, rp[i], y[i]);
+  y[i] = yi;
+  if (i < n_rt) z[i] = yi * mtinv[i];
+}
+
+// beta_{j+1} from the partials of r.z; then the Givens update and the stopping test
+__global__ void k_mr_beta_givens(MinresState* st, const double* __restrict__ partial, int it) {
+  __shared__ double sh[32];
+  double b2 = block_sum(partial[threadIdx.x], sh);
+  if (threadIdx.x != 0 || st->done_at >= 0) return;
+  if (!(b2 >= 0.0) || !isfinite(st->alpha)) {
+    st->status = isfinite(b2) && isfinite(st->alpha) ? HD_ERR_PREC_INDEFINITE : HD_ERR_NAN;
+    st->done_at = it - 1;
+    return;
+  }
+  st->beta_prev = st->beta;
+  st->beta = sqrt(b2);
+  // previous rotation applied to the new column, then a new rotation
+  st->eps = st->eps_next;
+  double delta = st->c * st->d_bar + st->s * st->alpha;
+  double g_bar = st->s * st->d_bar - st->c * st->alpha;
+  st->eps_next = st->s * st->beta;
+  st->d_bar = -st->c * st->beta;
+  double gamma = hypot(g_bar, st->beta);
+  if (!(gamma > 0.0)) {
+    st->status = HD_ERR_NAN;
+    st->done_at = it - 1;
+    return;
+  }
+  st->c = g_bar / gamma;
+  st->s = st->beta / gamma;
+  st->delta = delta;
+  st->gamma = gamma;
+  st->phi = st->c * st->phi_bar;
+  st->phi_bar = st->s * st->phi_bar;
+  if (fabs(st->phi_bar) <= st->rtol * st->eta0) {
+    st->status = HD_OK;
+    st->done_at = it;
+  }
+}
+
+// w_new = (v - eps w_pp - delta w_p)/gamma; x += phi w_new; v_next = z / beta
+__global__ void k_mr_update(int64_t n, int it, const MinresState* __restrict__ st, const double* __restrict__ v,
+                            const double* __restrict__ wpp, const double* __restrict__ wp, double* __restrict__ wn,
+                            double* __restrict__ x, const double* __restrict__ z, double* __restrict__ vnext) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (st->done_at >= 0 && st->done_at < it) return;
+  double ig = 1.0 / st->gamma;
+  double w = (v[i] - st->eps * wpp[i] - st->delta * wp[i]) * ig;
+  wn[i] = w;
+  x[i] = fma(st->phi, w, x[i]);
+  vnext[i] = z[i] / st->beta;
+}
+
+__global__ void k_mr_init(MinresState* st, const double* __restrict__ partial, double rtol) {
+  __shared__ double sh[32];
+  double b2 = block_sum(partial[threadIdx.x], sh);
+  if (threadIdx.x != 0) return;
+  st->rtol = rtol;
+  st->beta_prev = 0.0;
+  st->c = -1.0;
+  st->s = 0.0;
+  st->d_bar = 0.0;
+  st->eps = 0.0;
+  st->eps_next = 0.0;
+  st->done_at = -1;
+  st->status = HD_OK;
+  if (!(b2 >= 0.0)) {
+    st->status = isfinite(b2) ? HD_ERR_PREC_INDEFINITE : HD_ERR_NAN;
+    st->done_at = 0;
+    st->beta = 1.0;
+    return;
+  }
+  st->beta = sqrt(b2);
+  st->eta0 = st->beta;
+  st->phi_bar = st->beta;
+  if (st->beta == 0.0) {
+    st->done_at = 0;
+    st->beta = 1.0;
+  }
+}
+
+__global__ void k_scale_div(int64_t n, const double* __restrict__ z, const MinresState* __restrict__ st,
+                            double* __restrict__ v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  v[i] = z[i] / st->beta;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  y[i] = a * x[i] + b * y[i];
+}
+
+// partial sums of (a - b)^2 and a^2
+__global__ void k_resid_partial(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                double* __restrict__ partial) {
+  __shared__ double sh[32];
+  int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+  double s = 0.0, t = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    double d = a[i] - b[i];
+    s = fma(d, d, s);
+    t = fma(a[i], a[i], t);
+  }
+  s = block_sum(s, sh);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = s;
+    partial[DOT_BLOCKS + blockIdx.x] = t;
+  }
+}
+
+__global__ void k_resid_final(const double* __restrict__ partial, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = block_sum(partial[threadIdx.x], sh);
+  double t = block_sum(partial[DOT_BLOCKS + threadIdx.x], sh);
+  if (threadIdx.x == 0) {
+    out[0] = s;
+    out[1] = t;
+  }
+}
+
+}  // namespace
+
+// ||b - y||_2 and ||b||_2 (y = AA x computed by the caller)
+hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn) {
+  const int64_t n = h->n_rt + h->n_l2;
+  k_resid_partial<<<DOT_BLOCKS, TPB, 0, h->stream>>>(n, b, y, h->d_red);
+  k_resid_final<<<1, DOT_BLOCKS, 0, h->stream>>>(h->d_red, h->d_red + 2 * DOT_BLOCKS);
+  HD_LAUNCH_CK(h, "residual norms");
+  HD_CK(h, cudaMemcpyAsync(h->h_pinned, h->d_red + 2 * DOT_BLOCKS, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  *rn = std::sqrt(h->h_pinned[0]);
+  *bn = std::sqrt(h->h_pinned[1]);
+  return HD_OK;
+}
+
+hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, double* d_out) {
+  k_dot_partial<<<DOT_BLOCKS, TPB, 0, h->stream>>>(n, a, b, h->d_red);
+  k_dot_final<<<1, DOT_BLOCKS, 0, h->stream>>>(h->d_red, d_out);
+  HD_LAUNCH_CK(h, "dot");
+  return HD_OK;
+}
+
+hd_status apply_op_internal(hd_op* h, const double* x, double* y);
+
+static hd_status ensure_minres(hd_op* h) {
+  if (!h->mv.empty()) return HD_OK;
+  int64_t n = h->n_rt + h->n_l2;
+  for (int i = 0; i < 9; ++i) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "minres work");
+    h->mv.push_back(p);
+  }
+  if (cudaMalloc(&h->d_ms, sizeof(MinresState)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "minres state");
+  return HD_OK;
+}
+
+// FP64 MINRES on AA x = b with the block preconditioner. x0 = x if use_x0.
+hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
+  hd_status st = ensure_minres(h);
+  if (st != HD_OK) return st;
+  const int64_t n = h->n_rt + h->n_l2;
+  double *rpp = h->mv[0], *rp = h->mv[1], *y = h->mv[2], *z = h->mv[3], *v = h->mv[4], *vn = h->mv[5];
+  double *wpp = h->mv[6], *wp = h->mv[7], *wn = h->mv[8];
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  HD_CK(h, cudaEventCreate(&e0));
+  HD_CK(h, cudaEventCreate(&e1));
+  HD_CK(h, cudaEventRecord(e0, s));
+  // r_p = b - AA x0 (or b)
+  if (o->use_x0) {
+    if ((st = apply_op_internal(h, x, rp)) != HD_OK) return st;
+    k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, rp);
+  } else {
+    HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    HD_CK(h, cudaMemcpyAsync(rp, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  HD_CK(h, cudaMemsetAsync(wp, 0, sizeof(double) * n, s));
+  HD_CK(h, cudaMemsetAsync(wpp, 0, sizeof(double) * n, s));
+  HD_CK(h, cudaMemsetAsync(rpp, 0, sizeof(double) * n, s));
+  if ((st = precond_apply(h, rp, z)) != HD_OK) return st;
+  k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
+  k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, o->rtol);
+  k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, h->d_ms, v);
+  HD_LAUNCH_CK(h, "minres init");
+  int check = o->check_every > 0 ? o->check_every : 1;
+  int it = 0, done_at = -1, status = HD_OK;
+  MinresState hs;
+  for (it = 1; it <= o->maxit; ++it) {
+    if ((st = apply_op_internal(h, v, y)) != HD_OK) return st;
+    k_mr_lanczos1<<<DOT_BLOCKS, TPB, 0, s>>>(n, it, h->d_ms, v, y, rpp, h->d_red);
+    k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red);
+    k_mr_lanczos2<<<nblk(n), TPB, 0, s>>>(n, h->n_rt, h->d_ms, y, rp, h->d_mtinv, z);
+    HD_LAUNCH_CK(h, "minres lanczos");
+    // z_q = V-cycle(r_q) (+ projection), on the new Lanczos vector held in y
+    if (h->n_l2 > 0) {
+      if ((st = vcycle_apply(h, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
+      if (h->singular) {
+        if ((st = project_mean(h, z + h->n_rt)) != HD_OK) return st;
+      }
+    }
+    k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, y, z, h->d_red);
+    k_mr_beta_givens<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, it);
+    k_mr_update<<<nblk(n), TPB, 0, s>>>(n, it, h->d_ms, v, wpp, wp, wn, x, z, vn);
+    HD_LAUNCH_CK(h, "minres update");
+    // rotate: r_pp <- r_p <- y(new r); w_pp <- w_p <- w_new; v <- v_next
+    double* t = rpp; rpp = rp; rp = y; y = t;
+    t = wpp; wpp = wp; wp = wn; wn = t;
+    t = v; v = vn; vn = t;
+    if (it % check == 0 || it == o->maxit) {
+      HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+      HD_CK(h, cudaStreamSynchronize(s));
+      if (hs.done_at >= 0) break;
+    }
+  }
+  HD_CK(h, cudaEventRecord(e1, s));
+  HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+  HD_CK(h, cudaStreamSynchronize(s));
+  done_at = hs.done_at;
+  status = hs.status;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (info) {
+    info->iterations = done_at >= 0 ? done_at : o->maxit;
+    info->outer = 1;
+    info->eta_ratio = hs.eta0 > 0 ? fabs(hs.phi_bar) / hs.eta0 : 0.0;
+    info->ms_total = ms;
+  }
+  if (done_at < 0) status = HD_ERR_NOT_CONVERGED;
+  if (info) info->status = status;
+  return status;
+}

@@ -1,0 +1,36 @@
+"""GPU MINRES against the oracle's MINRES (same preconditioner spec): solutions
+within 1e-8 relative, iteration counts within one."""
+import numpy as np
+import pytest
+
+from cases import close, gpu_operator, inputs, oracle_problem
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,rtol", [("c1", 1e-10), ("darcy_k3", 1e-8), ("gd_k4_ragged", 1e-8),
+                                       ("darcy_neumann", 1e-8), ("darcy_gamma", 1e-8)])
+def test_minres_matches_oracle(name, rtol):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle.minres import minres
+    from oracle.precond import BlockPrec
+    d = inputs(name)
+    prob = oracle_problem(d)
+    bp = BlockPrec(prob, nu=2, coarse_max=8)
+    b = np.random.Generator(np.random.PCG64(11)).uniform(-1, 1, prob.n)
+    b[prob.ess] = 0.0
+    if bp.singular:                       # consistent right-hand side: q part orthogonal to constants
+        b[prob.lat.n_rt:] -= b[prob.lat.n_rt:].mean()
+    xr, info_r = minres(prob.apply_op, bp.apply, b, rtol=rtol, maxit=2000)
+    op = gpu_operator(d, coarse_max=8)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_minres_solve(torch.from_numpy(b).cuda(), x, rtol=rtol, maxit=2000, check_every=4)
+    torch.cuda.synchronize()
+    assert st == 0, info
+    assert abs(info["iterations"] - info_r["iterations"]) <= 1, (info, info_r["iterations"])
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xr) <= 1e-8 * np.linalg.norm(xr)
+    assert info["true_relres"] < 1e3 * rtol
+    op.close()
