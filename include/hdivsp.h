@@ -190,6 +190,14 @@ hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3
 hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
                           const hd_solve_opts* opts, hd_solve_info* info);
 
+/* -- profiling ------------------------------------------------------------- */
+/* enable != 0: record a CUDA event pair on the handle's stream around every
+ * launch of the fused element kernel (up to 4096 launches, then recording
+ * stops). hd_profile_read waits for the stream, returns the number of recorded
+ * launches and their summed device time in ms, and clears the record. */
+hd_status hd_profile(hd_handle h, int32_t enable);
+hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms);
+
 /* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);
 hd_status hd_apply_prec_f32(hd_handle h, const float* r, float* z);

@@ -76,6 +76,8 @@ _SIGS = {
     "hd_get_diagonals": [_H, _VP, _VP],
     "hd_get_level": [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "hd_minres_solve": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_profile": [_H, ctypes.c_int32],
+    "hd_profile_read": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     "hd_apply_op_f32": [_H, _VP, _VP],
     "hd_apply_prec_f32": [_H, _VP, _VP],
 }
@@ -197,6 +199,14 @@ class Operator:
     def hd_apply_op_f32(self, x, y): self._call("hd_apply_op_f32", x, y)
     def hd_apply_prec_f32(self, r, z): self._call("hd_apply_prec_f32", r, z)
     def hd_get_diagonals(self, mt, ct): self._call("hd_get_diagonals", mt, ct)
+
+    def hd_profile(self, enable):
+        _check(lib().hd_profile(self.h, int(enable)), self.h)
+
+    def hd_profile_read(self):
+        n, ms = ctypes.c_int32(), ctypes.c_double()
+        _check(lib().hd_profile_read(self.h, ctypes.byref(n), ctypes.byref(ms)), self.h)
+        return n.value, ms.value
 
     def hd_get_e2d_map(self):
         out = np.zeros((self.n_elem, 3 * (self.k + 1) * self.k ** 2), dtype=np.int32)

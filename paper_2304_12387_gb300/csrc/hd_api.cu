@@ -156,10 +156,23 @@ void destroy_all(hd_op* h) {
   for (float* p : h->fv) cudaFree(p);
   cudaFree(h->d_ms);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   precond_free(h);
 }
 
 }  // namespace
+
+constexpr int PROF_MAX = 4096;
+
+void prof_mark(hd_op* h, bool before) {
+  if (!h->prof || h->prof_n >= PROF_MAX) return;
+  if (h->prof_ev.empty()) {
+    h->prof_ev.resize(2 * PROF_MAX);
+    for (auto& e : h->prof_ev) cudaEventCreate(&e);
+  }
+  cudaEventRecord(h->prof_ev[2 * h->prof_n + (before ? 0 : 1)], h->stream);
+  if (!before) h->prof_n++;
+}
 
 // used by the Krylov layer
 hd_status apply_op_internal(hd_op* h, const double* x, double* y) {
@@ -463,6 +476,27 @@ hd_status hd_minres_solve(hd_handle h, const double* b, double* x, const hd_solv
     info->true_relres = bn > 0 ? rn / bn : rn;
   }
   return st;
+}
+
+hd_status hd_profile(hd_handle h, int32_t enable) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  h->prof = enable != 0;
+  return HD_OK;
+}
+
+hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms) {
+  if (!h || !launches || !ms) return HD_ERR_INVALID_ARG;
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  double tot = 0.0;
+  for (int i = 0; i < h->prof_n; ++i) {
+    float t = 0.f;
+    HD_CK(h, cudaEventElapsedTime(&t, h->prof_ev[2 * i], h->prof_ev[2 * i + 1]));
+    tot += t;
+  }
+  *launches = h->prof_n;
+  *ms = tot;
+  h->prof_n = 0;
+  return HD_OK;
 }
 
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y) {

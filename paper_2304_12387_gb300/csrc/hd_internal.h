@@ -99,7 +99,14 @@ struct hd_op {
   std::vector<double*> mv;
   MinresState* d_ms = nullptr;
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
+  // profiling of the fused element kernel
+  bool prof = false;
+  std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
+  int prof_n = 0;                     // recorded pairs
 };
+
+// records the start (before=true) or stop event of an element-kernel launch
+void prof_mark(hd_op* h, bool before);
 
 // error helpers
 hd_status hd_fail(hd_op* h, hd_status s, const std::string& msg);

@@ -537,8 +537,10 @@ hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs
   }
   TabT<T> tab = make_tab<T>(h->tab);
   int blocks = (int)((h->n_elem + EB - 1) / EB);
+  prof_mark(h, true);
   if (blocks > 0)
     kern<<<blocks, 256, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, u, q, yu, yq);
+  prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;
 }
