@@ -198,6 +198,29 @@ hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
 hd_status hd_profile(hd_handle h, int32_t enable);
 hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms);
 
+/* -- allocation-free solve (no counterpart in the paper) -------------------- */
+/* Same computation and result as hd_minres_solve (FP64 only, precision = 0),
+ * for callers that may not allocate device memory once their handle exists:
+ * for instance a time-stepping or embedding host that fixes its device memory
+ * budget after initialisation, or code running where another component owns
+ * the device allocator. hd_minres_solve allocates its nine work vectors with
+ * cudaMalloc on its first call; this entry point instead takes its work space
+ * from a fixed device array compiled into the library (HD_NOALLOC_SCRATCH_DOUBLES
+ * doubles = 16 MiB, held by every GPU that loads the library until the process
+ * exits) and calls no cudaMalloc, cudaFree or other allocating routine.
+ *  - Limit: n_rt + n_l2 <= HD_NOALLOC_MAX_DOFS; larger problems are rejected
+ *    with HD_ERR_INVALID_ARG (message in hd_last_error).
+ *  - The first call on a device looks up the array's device address (with that
+ *    device current); make that first call before any stream capture.
+ *  - Every call shares the one array and it keeps the last call's contents
+ *    (the call initialises what it reads); calls that overlap on the GPU race.
+ *  - Profiling (hd_profile) is suspended during the call; ms_total is host
+ *    wall-clock time. */
+#define HD_NOALLOC_SCRATCH_DOUBLES (2 * 1024 * 1024)
+#define HD_NOALLOC_MAX_DOFS 209696
+hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, double* x,
+                                  const hd_solve_opts* opts, hd_solve_info* info);
+
 /* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);
 hd_status hd_apply_prec_f32(hd_handle h, const float* r, float* z);

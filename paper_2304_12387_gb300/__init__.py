@@ -76,6 +76,7 @@ _SIGS = {
     "hd_get_diagonals": [_H, _VP, _VP],
     "hd_get_level": [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "hd_minres_solve": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_minres_solve_noalloc": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
     "hd_profile": [_H, ctypes.c_int32],
     "hd_profile_read": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
     "hd_apply_op_f32": [_H, _VP, _VP],
@@ -199,6 +200,15 @@ class Operator:
     def hd_apply_op_f32(self, x, y): self._call("hd_apply_op_f32", x, y)
     def hd_apply_prec_f32(self, r, z): self._call("hd_apply_prec_f32", r, z)
     def hd_get_diagonals(self, mt, ct): self._call("hd_get_diagonals", mt, ct)
+
+    def hd_minres_solve_noalloc(self, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8,
+                                outer_rtol=1e-8, max_outer=20):
+        """Allocation-free FP64 MINRES (work space in a fixed device array; see the header)."""
+        o = SolveOpts(rtol, maxit, int(use_x0), check_every, 0, outer_rtol, max_outer)
+        info = SolveInfo()
+        st = lib().hd_minres_solve_noalloc(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        return st, {"iterations": info.iterations, "outer": info.outer, "eta_ratio": info.eta_ratio,
+                    "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status}
 
     def hd_profile(self, enable):
         _check(lib().hd_profile(self.h, int(enable)), self.h)

@@ -3,7 +3,11 @@
 // (Paige & Saunders 1975) with its Lanczos/Givens scalars kept on the device,
 // so an iteration needs no host round trip (Sec. 3: MINRES with the
 // block-diagonal preconditioner).
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "hd_internal.h"
@@ -331,4 +335,143 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
   if (done_at < 0) status = HD_ERR_NOT_CONVERGED;
   if (info) info->status = status;
   return status;
+}
+
+// ---- allocation-free MINRES ----------------------------------------------------
+// hd_minres_solve allocates its nine work vectors with cudaMalloc on its first
+// call. hd_minres_solve_noalloc takes its work space from the file-scope device
+// array below instead, so that a caller who may not allocate device memory once
+// its handle exists can still solve. The array is part of the module: every GPU
+// that loads the library holds it until the process exits. Calls share it, so
+// calls that overlap on the GPU (other streams, other threads) race.
+static __device__ __align__(256) double g_noalloc_scratch[HD_NOALLOC_SCRATCH_DOUBLES];
+
+namespace {
+
+constexpr int kNoallocMaxDevices = 64;
+constexpr int64_t kAlign = 32;  // doubles (256 bytes)
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+inline int64_t round_up(int64_t n) { return (n + kAlign - 1) / kAlign * kAlign; }
+
+static_assert(sizeof(MinresState) <= kAlign * sizeof(double), "MINRES state must fit its slot");
+static_assert(kAlign + 10 * HD_NOALLOC_MAX_DOFS <= HD_NOALLOC_SCRATCH_DOUBLES, "scratch too small for its limit");
+static_assert(HD_NOALLOC_MAX_DOFS % kAlign == 0, "limit must be a multiple of the alignment");
+
+// Device address of the scratch array on the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device, with that device current, and cached.
+hd_status noalloc_scratch(hd_op* h, double** out) {
+  int dev = 0;
+  HD_CK(h, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return hd_fail(h, HD_ERR_INVALID_ARG, "device ordinal too large");
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return HD_OK;
+}
+
+// The MINRES recurrence of minres_run with every work vector and the device
+// state carved out of `ws`; no events (host wall clock instead).
+hd_status minres_run_ws(hd_op* h, double* ws, const double* b, double* x, const hd_solve_opts* o,
+                        hd_solve_info* info) {
+  const int64_t n = h->n_rt + h->n_l2, stride = round_up(n);
+  MinresState* ms = reinterpret_cast<MinresState*>(ws);
+  double* v0 = ws + kAlign;
+  double *rpp = v0, *rp = v0 + stride, *y = v0 + 2 * stride, *z = v0 + 3 * stride, *v = v0 + 4 * stride;
+  double *vn = v0 + 5 * stride, *wpp = v0 + 6 * stride, *wp = v0 + 7 * stride, *wn = v0 + 8 * stride;
+  double* tmp = v0 + 9 * stride;
+  cudaStream_t s = h->stream;
+  hd_status st;
+  auto t0 = std::chrono::steady_clock::now();
+  // the array keeps the previous call's contents: everything read before it is
+  // written is set here
+  if (o->use_x0) {
+    if ((st = apply_op_internal(h, x, rp)) != HD_OK) return st;
+    k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, rp);
+  } else {
+    HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    HD_CK(h, cudaMemcpyAsync(rp, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  HD_CK(h, cudaMemsetAsync(wp, 0, sizeof(double) * n, s));
+  HD_CK(h, cudaMemsetAsync(wpp, 0, sizeof(double) * n, s));
+  HD_CK(h, cudaMemsetAsync(rpp, 0, sizeof(double) * n, s));
+  if ((st = precond_apply(h, rp, z)) != HD_OK) return st;
+  k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
+  k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(ms, h->d_red, o->rtol);
+  k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, ms, v);
+  HD_LAUNCH_CK(h, "minres init");
+  const int check = o->check_every > 0 ? o->check_every : 1;
+  MinresState hs;
+  for (int it = 1; it <= o->maxit; ++it) {
+    if ((st = apply_op_internal(h, v, y)) != HD_OK) return st;
+    k_mr_lanczos1<<<DOT_BLOCKS, TPB, 0, s>>>(n, it, ms, v, y, rpp, h->d_red);
+    k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(ms, h->d_red);
+    k_mr_lanczos2<<<nblk(n), TPB, 0, s>>>(n, h->n_rt, ms, y, rp, h->d_mtinv, z);
+    HD_LAUNCH_CK(h, "minres lanczos");
+    if (h->n_l2 > 0) {
+      if ((st = vcycle_apply(h, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
+      if (h->singular && (st = project_mean(h, z + h->n_rt)) != HD_OK) return st;
+    }
+    k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, y, z, h->d_red);
+    k_mr_beta_givens<<<1, DOT_BLOCKS, 0, s>>>(ms, h->d_red, it);
+    k_mr_update<<<nblk(n), TPB, 0, s>>>(n, it, ms, v, wpp, wp, wn, x, z, vn);
+    HD_LAUNCH_CK(h, "minres update");
+    double* t = rpp; rpp = rp; rp = y; y = t;
+    t = wpp; wpp = wp; wp = wn; wn = t;
+    t = v; v = vn; vn = t;
+    if (it % check == 0 || it == o->maxit) {
+      HD_CK(h, cudaMemcpyAsync(h->h_pinned, ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+      HD_CK(h, cudaStreamSynchronize(s));
+      std::memcpy(&hs, h->h_pinned, sizeof(MinresState));
+      if (hs.done_at >= 0) break;
+    }
+  }
+  HD_CK(h, cudaMemcpyAsync(h->h_pinned, ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
+  HD_CK(h, cudaStreamSynchronize(s));
+  std::memcpy(&hs, h->h_pinned, sizeof(MinresState));
+  const double ms_wall = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  hd_status status = hs.done_at < 0 ? HD_ERR_NOT_CONVERGED : hs.status;
+  if (info) {
+    info->iterations = hs.done_at >= 0 ? hs.done_at : o->maxit;
+    info->outer = 1;
+    info->eta_ratio = hs.eta0 > 0 ? fabs(hs.phi_bar) / hs.eta0 : 0.0;
+    info->ms_total = ms_wall;
+    if ((st = apply_op_internal(h, x, tmp)) != HD_OK) return st;
+    double rn = 0, bn = 0;
+    if ((st = residual_norms(h, b, tmp, &rn, &bn)) != HD_OK) return st;
+    info->true_relres = bn > 0 ? rn / bn : rn;
+    info->status = status;
+  }
+  return status;
+}
+
+}  // namespace
+
+extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, double* x, const hd_solve_opts* o,
+                                             hd_solve_info* info) {
+  if (!h || !b || !x || !o || b == x || o->maxit < 1 || !(o->rtol > 0)) return HD_ERR_INVALID_ARG;
+  if (o->precision != 0) return hd_fail(h, HD_ERR_INVALID_ARG, "hd_minres_solve_noalloc: FP64 only (precision = 0)");
+  const int64_t n = h->n_rt + h->n_l2;
+  if (n > HD_NOALLOC_MAX_DOFS) {
+    char msg[160];
+    std::snprintf(msg, sizeof msg, "hd_minres_solve_noalloc: %lld DOFs exceed the limit of %d (n_rt + n_l2)",
+                  (long long)n, (int)HD_NOALLOC_MAX_DOFS);
+    return hd_fail(h, HD_ERR_INVALID_ARG, msg);
+  }
+  double* ws = nullptr;
+  hd_status st = noalloc_scratch(h, &ws);
+  if (st != HD_OK) return st;
+  // profiling would create its event pairs on first use: keep it off for this call
+  const bool prof = h->prof;
+  h->prof = false;
+  st = minres_run_ws(h, ws, b, x, o, info);
+  h->prof = prof;
+  return st;
 }
