@@ -35,6 +35,9 @@ METRIC = "GDOF/s of block operator apply at p=4; MINRES time-to-1e-8 resid, mixe
 NX, K, Q, PERTURB, SIGMA, ESS, SEED = 64, 4, 6, 0.15, 2.0, 63, 2304
 # measured FP64 FMA rate of this GPU model: 152 SMs x 2 FP64 FMA lanes/clk x 2 flops
 FP64_PEAK_GFLOPS_AT_MAX_CLOCK = 152 * 2 * 2 * 2.070
+# DRAM bytes (read + write) per element of k_elem_op<double,4,6,8>, from one ncu capture of the
+# 24^3 case (674.3 MB / 13,824 elements); null once the kernel changes (profiles/k_elem_op_M64_k4q6.md)
+ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6): 674.306560e6 / 13824}
 
 
 def workload(n=NX):
@@ -158,9 +161,10 @@ def run_ours(args, rank, world, dist):
     dev = int(os.environ.get("LOCAL_RANK", 0))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    vx, vy, vz, alpha, beta = workload()
+    nx = args.n
+    vx, vy, vz, alpha, beta = workload(nx)
     t0 = time.perf_counter()
-    op = hd.Operator(NX, NX, NX, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=Q,
+    op = hd.Operator(nx, nx, nx, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=Q,
                      stream=stream)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -198,10 +202,12 @@ def run_ours(args, rank, world, dist):
     achieved = flops_launch / (kern_avg_ms * 1e-3) / 1e9
     clocks = clk.summary()
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "traffic": None,
+            "frac": achieved / FP64_PEAK_GFLOPS_AT_MAX_CLOCK,
+            "traffic": (ELEM_TRAFFIC_BYTES_PER_ELEMENT[(K, Q)] * op.n_elem
+                        if (K, Q) in ELEM_TRAFFIC_BYTES_PER_ELEMENT else None),
             "kernel": "k_elem_op<double,4,6,8>", "kernel_ms": kern_avg_ms,
             "flops_per_launch": flops_launch,
-            "algorithmic_bytes_per_launch": elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2, (NX + 1) ** 3),
+            "algorithmic_bytes_per_launch": elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3),
             "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 FMA probe: 1189 GFLOP/s at 2002 MHz)"}
     roof["hbm_frac_of_measured"] = roof["algorithmic_bytes_per_launch"] / (kern_avg_ms * 1e-3) / 1e9 / 6792.4
     # e2e: the same apply through the C ABI with pinned host buffers, copies inside the region
@@ -219,7 +225,8 @@ def run_ours(args, rank, world, dist):
     out = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "M64-perturbed: grad-div, 64^3 hex elements of the unit cube with interior "
+           "config": {"workload": ("M64-perturbed" if nx == NX else "M%d-perturbed (profiling size)" % nx)
+                                  + ": grad-div, %d^3 hex elements of the unit cube with interior " % nx +
                                   "vertices moved by U(-0.15h,0.15h) (seed 2304), RT_4 x Q_3 (k=4), q=6, "
                                   "alpha=1, beta=exp(2Z) per element, u.n=0 on all sides",
                       "dofs": n, "n_rt": op.n_rt, "n_l2": op.n_l2, "elements": op.n_elem,
@@ -254,6 +261,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", 1))
