@@ -124,13 +124,26 @@ def l2_basis(k, pts):
     return out
 
 
+_TABLES = {}
+
+
+def reference_tables(k, q):
+    """Quadrature rule and reference basis values for (k, q), evaluated once."""
+    key = (k, q)
+    if key not in _TABLES:
+        pts, w = quad_rule(q)
+        Phi, Div = rt_basis(k, pts)
+        _TABLES[key] = (pts, w, Phi, Div, l2_basis(k, pts))
+    return _TABLES[key]
+
+
 def element_matrices(V, k, q, beta, alpha, want=("M", "W", "B")):
     """Element matrices for elements with corner coordinates V (see module doc).
 
     beta, alpha: per-element coefficients (arrays of length E).
     Returns a dict with the requested 'M' (E, n, n), 'W' (E, k^3, k^3),
     'B' (E, k^3, n)."""
-    pts, w = quad_rule(q)
+    pts, w, Phi, Div, Psi = reference_tables(k, q)
     J = jacobian(V, pts)
     detJ = np.linalg.det(J)
     if np.any(detJ <= 0):
@@ -139,18 +152,15 @@ def element_matrices(V, k, q, beta, alpha, want=("M", "W", "B")):
     alpha = np.asarray(alpha, dtype=np.float64)
     out = {}
     if "M" in want:
-        Phi, _ = rt_basis(k, pts)
         A = np.einsum("epid,pnd->epin", J, Phi)                  # J phi at points
         s = np.sqrt(w[None, :] * beta[:, None] / detJ)           # (E, P)
         A = A * s[:, :, None, None]
         A = A.reshape(A.shape[0], -1, A.shape[-1])                # (E, 3P, n)
         out["M"] = np.matmul(A.transpose(0, 2, 1), A)
     if "W" in want or "B" in want:
-        Psi = l2_basis(k, pts)
         wt = w[None, :] * alpha[:, None] / detJ                  # (E, P)
         if "W" in want:
             out["W"] = np.einsum("pa,ep,pb->eab", Psi, wt, Psi)
         if "B" in want:
-            _, Div = rt_basis(k, pts)
             out["B"] = np.einsum("pa,ep,pn->ean", Psi, wt, Div)
     return out

@@ -202,7 +202,7 @@ class Operator:
     def hd_get_diagonals(self, mt, ct): self._call("hd_get_diagonals", mt, ct)
 
     def hd_minres_solve_noalloc(self, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8,
-                                outer_rtol=1e-8, max_outer=20):
+                                outer_rtol=0.0, max_outer=1):
         """Allocation-free FP64 MINRES (work space in a fixed device array; see the header)."""
         o = SolveOpts(rtol, maxit, int(use_x0), check_every, 0, outer_rtol, max_outer)
         info = SolveInfo()
@@ -237,7 +237,9 @@ class Operator:
         return nl.value, tuple(dims)
 
     def hd_minres_solve(self, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8, precision=0,
-                        outer_rtol=1e-8, max_outer=20, raise_on_error=False):
+                        outer_rtol=0.0, max_outer=1, raise_on_error=False):
+        """MINRES on AA x = b. max_outer > 1 or precision = 1 wraps it in an FP64
+        residual correction that stops at ||b - AA x|| <= outer_rtol ||b||."""
         o = SolveOpts(rtol, maxit, int(use_x0), check_every, precision, outer_rtol, max_outer)
         info = SolveInfo()
         st = lib().hd_minres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))

@@ -462,7 +462,7 @@ hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3
 
 hd_status hd_minres_solve(hd_handle h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
   if (!h || !b || !x || !o || b == x || o->maxit < 1 || !(o->rtol > 0)) return HD_ERR_INVALID_ARG;
-  if (o->precision != 0) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "mixed precision solve");
+  if (o->precision != 0 && o->precision != 1) return hd_fail(h, HD_ERR_INVALID_ARG, "precision must be 0 or 1");
   hd_status st = minres_run(h, b, x, o, info);
   if (info) {
     // true residual ||b - AA x|| / ||b|| in FP64

@@ -147,6 +147,8 @@ hd_status vcycle_apply(hd_op* h, const double* b, double* x);
 hd_status setup_f32(hd_op* h);
 void precond_free(hd_op* h);
 hd_status project_mean(hd_op* h, double* z);
+hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x);
+hd_status diag_scale(hd_op* h, const double* r, double* z);
 hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn);
 
 // Krylov (k_krylov.cu)

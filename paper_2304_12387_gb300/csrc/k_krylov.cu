@@ -246,11 +246,35 @@ hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, doub
 }
 
 hd_status apply_op_internal(hd_op* h, const double* x, double* y);
+hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y);
+
+namespace {
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+__global__ void k_f2d(int64_t n, const float* __restrict__ a, double* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+// y = b - y
+__global__ void k_rsub(int64_t n, const double* __restrict__ b, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = b[i] - y[i];
+}
+// x += e
+__global__ void k_add(int64_t n, const double* __restrict__ e, double* __restrict__ x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += e[i];
+}
+
+}  // namespace
 
 static hd_status ensure_minres(hd_op* h) {
   if (!h->mv.empty()) return HD_OK;
   int64_t n = h->n_rt + h->n_l2;
-  for (int i = 0; i < 9; ++i) {
+  for (int i = 0; i < 11; ++i) {  // 9 recurrence vectors + outer residual + correction
     double* p = nullptr;
     if (cudaMalloc(&p, sizeof(double) * (n > 0 ? n : 1)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "minres work");
     h->mv.push_back(p);
@@ -259,20 +283,59 @@ static hd_status ensure_minres(hd_op* h) {
   return HD_OK;
 }
 
-// FP64 MINRES on AA x = b with the block preconditioner. x0 = x if use_x0.
-hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
-  hd_status st = ensure_minres(h);
+static hd_status ensure_f32_work(hd_op* h) {
+  if (!h->fv.empty()) return HD_OK;
+  hd_status st = setup_f32(h);
   if (st != HD_OK) return st;
+  int64_t n = h->n_rt + h->n_l2;
+  const int64_t sizes[4] = {n, n, h->n_l2, h->n_l2};
+  for (int i = 0; i < 4; ++i) {
+    float* p = nullptr;
+    if (cudaMalloc(&p, sizeof(float) * (sizes[i] > 0 ? sizes[i] : 1)) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "f32 work");
+    h->fv.push_back(p);
+  }
+  return HD_OK;
+}
+
+// y = AA v with the operator in the inner precision (vectors stay FP64)
+static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
+  if (!f32) return apply_op_internal(h, v, y);
+  const int64_t n = h->n_rt + h->n_l2;
+  k_d2f<<<nblk(n), TPB, 0, h->stream>>>(n, v, h->fv[0]);
+  hd_status st = apply_op_f32_internal(h, h->fv[0], h->fv[1]);
+  if (st != HD_OK) return st;
+  k_f2d<<<nblk(n), TPB, 0, h->stream>>>(n, h->fv[1], y);
+  HD_LAUNCH_CK(h, "inner apply");
+  return HD_OK;
+}
+
+// z_q = V-cycle(r_q) in the inner precision, then the zero-mean projection if singular
+static hd_status inner_vcycle(hd_op* h, bool f32, const double* rq, double* zq) {
+  hd_status st;
+  if (!f32) {
+    if ((st = vcycle_apply(h, rq, zq)) != HD_OK) return st;
+  } else {
+    const int64_t m = h->n_l2;
+    k_d2f<<<nblk(m), TPB, 0, h->stream>>>(m, rq, h->fv[2]);
+    if ((st = vcycle_apply_f32(h, h->fv[2], h->fv[3])) != HD_OK) return st;
+    k_f2d<<<nblk(m), TPB, 0, h->stream>>>(m, h->fv[3], zq);
+    HD_LAUNCH_CK(h, "inner vcycle");
+  }
+  if (h->singular) return project_mean(h, zq);
+  return HD_OK;
+}
+
+// MINRES on AA x = b (x0 = x when use_x0). The Lanczos vectors, inner products and
+// Givens scalars are FP64; with f32 the operator and the V-cycle run in FP32.
+static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bool use_x0, double rtol, int maxit,
+                              int check, int* iters, MinresState* hs_out) {
   const int64_t n = h->n_rt + h->n_l2;
   double *rpp = h->mv[0], *rp = h->mv[1], *y = h->mv[2], *z = h->mv[3], *v = h->mv[4], *vn = h->mv[5];
   double *wpp = h->mv[6], *wp = h->mv[7], *wn = h->mv[8];
   cudaStream_t s = h->stream;
-  cudaEvent_t e0, e1;
-  HD_CK(h, cudaEventCreate(&e0));
-  HD_CK(h, cudaEventCreate(&e1));
-  HD_CK(h, cudaEventRecord(e0, s));
-  // r_p = b - AA x0 (or b)
-  if (o->use_x0) {
+  hd_status st;
+  if (use_x0) {
     if ((st = apply_op_internal(h, x, rp)) != HD_OK) return st;
     k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, rp);
   } else {
@@ -282,58 +345,108 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
   HD_CK(h, cudaMemsetAsync(wp, 0, sizeof(double) * n, s));
   HD_CK(h, cudaMemsetAsync(wpp, 0, sizeof(double) * n, s));
   HD_CK(h, cudaMemsetAsync(rpp, 0, sizeof(double) * n, s));
-  if ((st = precond_apply(h, rp, z)) != HD_OK) return st;
+  // z = B^-1 r: the u part by M~ scaling, the q part by the V-cycle
+  if ((st = diag_scale(h, rp, z)) != HD_OK) return st;
+  if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, rp + h->n_rt, z + h->n_rt)) != HD_OK) return st;
   k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
-  k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, o->rtol);
+  k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, rtol);
   k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, h->d_ms, v);
   HD_LAUNCH_CK(h, "minres init");
-  int check = o->check_every > 0 ? o->check_every : 1;
-  int it = 0, done_at = -1, status = HD_OK;
+  if (check < 1) check = 1;
   MinresState hs;
-  for (it = 1; it <= o->maxit; ++it) {
-    if ((st = apply_op_internal(h, v, y)) != HD_OK) return st;
+  int it;
+  for (it = 1; it <= maxit; ++it) {
+    if ((st = inner_apply(h, f32, v, y)) != HD_OK) return st;
     k_mr_lanczos1<<<DOT_BLOCKS, TPB, 0, s>>>(n, it, h->d_ms, v, y, rpp, h->d_red);
     k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red);
     k_mr_lanczos2<<<nblk(n), TPB, 0, s>>>(n, h->n_rt, h->d_ms, y, rp, h->d_mtinv, z);
     HD_LAUNCH_CK(h, "minres lanczos");
-    // z_q = V-cycle(r_q) (+ projection), on the new Lanczos vector held in y
-    if (h->n_l2 > 0) {
-      if ((st = vcycle_apply(h, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
-      if (h->singular) {
-        if ((st = project_mean(h, z + h->n_rt)) != HD_OK) return st;
-      }
-    }
+    if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
     k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, y, z, h->d_red);
     k_mr_beta_givens<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, it);
     k_mr_update<<<nblk(n), TPB, 0, s>>>(n, it, h->d_ms, v, wpp, wp, wn, x, z, vn);
     HD_LAUNCH_CK(h, "minres update");
-    // rotate: r_pp <- r_p <- y(new r); w_pp <- w_p <- w_new; v <- v_next
     double* t = rpp; rpp = rp; rp = y; y = t;
     t = wpp; wpp = wp; wp = wn; wn = t;
     t = v; v = vn; vn = t;
-    if (it % check == 0 || it == o->maxit) {
+    if (it % check == 0 || it == maxit) {
       HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
       HD_CK(h, cudaStreamSynchronize(s));
       if (hs.done_at >= 0) break;
     }
   }
-  HD_CK(h, cudaEventRecord(e1, s));
   HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
   HD_CK(h, cudaStreamSynchronize(s));
-  done_at = hs.done_at;
-  status = hs.status;
+  *iters = hs.done_at >= 0 ? hs.done_at : maxit;
+  if (hs_out) *hs_out = hs;
+  if (hs.done_at < 0) return HD_ERR_NOT_CONVERGED;
+  return hs.status;
+}
+
+// Preconditioned MINRES; with max_outer > 1 (or precision = 1) wrapped in an FP64
+// residual correction: r = b - AA x in FP64, inner MINRES on AA e = r, x += e,
+// until ||r||/||b|| <= outer_rtol.
+hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
+  hd_status st = ensure_minres(h);
+  if (st != HD_OK) return st;
+  const bool f32 = o->precision == 1;
+  if (f32 && (st = ensure_f32_work(h)) != HD_OK) return st;
+  const int64_t n = h->n_rt + h->n_l2;
+  cudaStream_t s = h->stream;
+  cudaEvent_t e0, e1;
+  HD_CK(h, cudaEventCreate(&e0));
+  HD_CK(h, cudaEventCreate(&e1));
+  HD_CK(h, cudaEventRecord(e0, s));
+  const int max_outer = o->max_outer > 0 ? o->max_outer : 1;
+  const bool refine = f32 || max_outer > 1;
+  int total = 0, outer = 0;
+  hd_status status = HD_OK;
+  MinresState hs{};
+  if (!refine) {
+    outer = 1;
+    status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs);
+  } else {
+    double* r = h->mv[9];
+    double* e = h->mv[10];
+    if (!o->use_x0) HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
+    double bn = 0, rn = 0;
+    const double target = o->outer_rtol > 0 ? o->outer_rtol : o->rtol;
+    for (outer = 0;; ++outer) {
+      if ((st = apply_op_internal(h, x, r)) != HD_OK) return st;
+      if ((st = residual_norms(h, b, r, &rn, &bn)) != HD_OK) return st;
+      if (bn == 0.0 || rn <= target * bn) {
+        status = HD_OK;
+        break;
+      }
+      if (outer == max_outer || total >= o->maxit) {
+        status = HD_ERR_NOT_CONVERGED;
+        break;
+      }
+      k_rsub<<<nblk(n), TPB, 0, s>>>(n, b, r);
+      int its = 0;
+      hd_status si = minres_inner(h, f32, r, e, false, o->rtol, o->maxit - total, o->check_every, &its, &hs);
+      total += its;
+      if (si != HD_OK && si != HD_ERR_NOT_CONVERGED) {
+        status = si;
+        break;
+      }
+      k_add<<<nblk(n), TPB, 0, s>>>(n, e, x);
+      HD_LAUNCH_CK(h, "outer update");
+    }
+  }
+  HD_CK(h, cudaEventRecord(e1, s));
+  HD_CK(h, cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (info) {
-    info->iterations = done_at >= 0 ? done_at : o->maxit;
-    info->outer = 1;
+    info->iterations = total;
+    info->outer = outer;
     info->eta_ratio = hs.eta0 > 0 ? fabs(hs.phi_bar) / hs.eta0 : 0.0;
     info->ms_total = ms;
+    info->status = status;
   }
-  if (done_at < 0) status = HD_ERR_NOT_CONVERGED;
-  if (info) info->status = status;
   return status;
 }
 

@@ -268,14 +268,15 @@ __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ 
   bc[t] = s;
 }
 
-// coarsest level: x = A^-1 b with a stored dense inverse (n <= a few hundred)
+// coarsest level: x = A^-1 b with the stored FP64 dense inverse (n <= a few hundred);
+// FP64 accumulation for either vector type (the coarsest solve stays FP64)
 template <typename T>
-__global__ void k_vc_coarse(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
+__global__ void k_vc_coarse(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  T s = (T)0;
-  for (int j = 0; j < n; ++j) s = fma(Ainv[(int64_t)j * n + i], b[j], s);
-  x[i] = s;
+  double s = 0.0;
+  for (int j = 0; j < n; ++j) s = fma(Ainv[(int64_t)j * n + i], (double)b[j], s);
+  x[i] = (T)s;
 }
 
 // z -= mean(z): single block, deterministic fixed-order reduction
@@ -317,7 +318,7 @@ __global__ void k_to_f32(int64_t n, const double* __restrict__ a, T* __restrict_
 // -- host side -----------------------------------------------------------------
 
 template <typename T>
-const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const T* coarse_inv, int l, const T* b, T* out) {
+const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse_inv, int l, const T* b, T* out) {
   LevelT<T>& L = lv[l];
   const int last = (int)lv.size() - 1;
   if (l == last) {
@@ -528,8 +529,6 @@ hd_status setup_f32(hd_op* h) {
   if ((st = conv(h->d_winv, &h->f_winv, h->n_elem * nl2 * nl2, "f32 winv")) != HD_OK) return st;
   if ((st = conv(h->d_cscale, &h->f_cscale, h->n_elem, "f32 cscale")) != HD_OK) return st;
   if ((st = conv(h->d_mtinv, &h->f_mtinv, h->n_rt, "f32 mtinv")) != HD_OK) return st;
-  if ((st = conv(h->d_coarse_inv, &h->f_coarse_inv, (int64_t)h->coarse_n * h->coarse_n, "f32 coarse")) != HD_OK)
-    return st;
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const LevelT<double>& d = h->lv[l];
     LevelT<float> f{};
@@ -574,7 +573,7 @@ hd_status vcycle_apply(hd_op* h, const double* b, double* x) {
 
 template <typename T>
 static hd_status precond_apply_t(hd_op* h, const T* r, T* z, const T* mtinv, std::vector<LevelT<T>>& lv,
-                                 const T* cinv) {
+                                 const double* cinv) {
   if (h->n_rt > 0) k_diag_scale<T><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->n_rt, mtinv, r, z);
   if (h->n_l2 > 0) {
     vcycle_level<T>(h, lv, cinv, 0, r + h->n_rt, z + h->n_rt);
@@ -594,7 +593,24 @@ hd_status precond_apply(hd_op* h, const double* r, double* z) {
 hd_status precond_apply_f32(hd_op* h, const float* r, float* z) {
   hd_status st = setup_f32(h);
   if (st != HD_OK) return st;
-  return precond_apply_t<float>(h, r, z, h->f_mtinv, h->lvf, h->f_coarse_inv);
+  return precond_apply_t<float>(h, r, z, h->f_mtinv, h->lvf, h->d_coarse_inv);
+}
+
+// FP32 V-cycle on an L2 vector (coarsest level in FP64)
+hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x) {
+  if (h->n_l2 == 0) return HD_OK;
+  hd_status st = setup_f32(h);
+  if (st != HD_OK) return st;
+  vcycle_level<float>(h, h->lvf, h->d_coarse_inv, 0, b, x);
+  HD_LAUNCH_CK(h, "vcycle f32");
+  return HD_OK;
+}
+
+// z_u = r_u / (tau M~) on the RT part (identity on essential dofs)
+hd_status diag_scale(hd_op* h, const double* r, double* z) {
+  if (h->n_rt > 0) k_diag_scale<double><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->n_rt, h->d_mtinv, r, z);
+  HD_LAUNCH_CK(h, "diag_scale");
+  return HD_OK;
 }
 
 // z -= mean(z) on an L2 vector (pure-Neumann Darcy: the Schur complement's

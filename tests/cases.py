@@ -61,3 +61,39 @@ def close(a, b, rtol):
     a, b = np.asarray(a), np.asarray(b)
     scale = max(np.abs(b).max(initial=0.0), 1e-300)
     return np.abs(a - b).max(initial=0.0) / scale
+
+
+# Full-size workloads (parity on sampled rows). name: builder returning the input dict.
+def fullsize(name, seed=2304):
+    if name == "m64":      # the bench workload: grad-div 64^3, k=4, q=6, beta = exp(2Z), u.n = 0
+        n = 64
+        vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=0.15, seed=seed)
+        return dict(kind=GRAD_DIV, nx=n, ny=n, nz=n, k=4, q=6, vx=vx, vy=vy, vz=vz, coef0=np.ones(n ** 3),
+                    coef1=synth.lognormal(n ** 3, 2.0, seed=seed + 1), ess_mask=63, affine=False)
+    if name == "c2":       # Darcy 32^3, perturbed, k=3, gamma=0, eps = exp(2Z), natural BC
+        n = 32
+        vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=0.15, seed=seed)
+        return dict(kind=DARCY, nx=n, ny=n, nz=n, k=3, q=5, vx=vx, vy=vy, vz=vz,
+                    coef0=synth.lognormal(n ** 3, 2.0, seed=seed + 1), coef1=np.zeros(n ** 3), ess_mask=0,
+                    affine=False)
+    if name == "c3":       # layered reservoir, 60 x 220 x 85 cells on [0,1200]x[0,2200]x[0,170], k=2
+        nx, ny, nz = 60, 220, 85
+        vx, vy, vz = synth.lattice_vertices(nx, ny, nz, extent=(1200.0, 2200.0, 170.0))
+        eps = synth.layered_permeability(nx, ny, nz, sigma=3.0, corr_len=10.0, seed=seed)
+        return dict(kind=DARCY, nx=nx, ny=ny, nz=nz, k=2, q=3, vx=vx, vy=vy, vz=vz, coef0=eps,
+                    coef1=np.zeros(nx * ny * nz), ess_mask=63, affine=True)
+    if name == "c4":       # bent two-material tube, grad-div 48^3, k=4
+        n = 48
+        vx, vy, vz = synth.lattice_vertices(n, n, n)
+        inside = synth.bent_tube_mask(n, n, n, seed=seed)
+        alpha = np.where(inside, 1e3, 1.0)
+        beta = np.where(inside, 1.0, 1e-3)
+        return dict(kind=GRAD_DIV, nx=n, ny=n, nz=n, k=4, q=5, vx=vx, vy=vy, vz=vz, coef0=alpha, coef1=beta,
+                    ess_mask=63, affine=True)
+    if name == "c5":       # evaluation size of the learned-preconditioner study: Darcy 96^3, k=3
+        n = 96
+        vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=0.15, seed=seed)
+        return dict(kind=DARCY, nx=n, ny=n, nz=n, k=3, q=5, vx=vx, vy=vy, vz=vz,
+                    coef0=synth.lognormal(n ** 3, 2.0, seed=seed + 1), coef1=np.zeros(n ** 3), ess_mask=0,
+                    affine=False)
+    raise KeyError(name)

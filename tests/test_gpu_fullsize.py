@@ -1,0 +1,45 @@
+"""Parity at full size: the fused block apply of every workload at its full size
+(the metric workload in the launch configuration bench.py times) against the
+oracle's element-local rows, on a seeded sample of RT rows (including essential
+rows) and L2 rows. Tolerance: |gpu - oracle| <= 1e-12 * max over the sampled
+oracle rows (norm-scaled, FP64)."""
+import numpy as np
+import pytest
+
+from cases import fullsize
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name", ["m64", "c2", "c3", "c4", "c5"])
+def test_fullsize_sampled_rows(name):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.sampled import SampledOperator
+    d = fullsize(name)
+    op = hd.Operator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                     kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"], affine=d["affine"],
+                     stream=torch.cuda.current_stream())
+    rng = np.random.Generator(np.random.PCG64(77))
+    x = rng.uniform(-1, 1, op.n)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xd)
+    op.hd_apply_op(xd, y)
+    torch.cuda.synchronize()
+    so = SampledOperator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                         kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"])
+    rt = rng.choice(op.n_rt, 24, replace=False)
+    if len(so.ess):
+        rt = np.concatenate([rt, so.ess[rng.choice(len(so.ess), 3, replace=False)]])
+    # rows on the last element layer and the first: ragged ends of the element loop
+    rt = np.concatenate([rt, [0, op.n_rt - 1]])
+    l2 = np.concatenate([rng.choice(op.n_l2, 12, replace=False), [0, op.n_l2 - 1]])
+    ref_rt = so.rt_rows(x, rt)
+    ref_l2 = so.l2_rows(x, l2)
+    got = y[torch.from_numpy(np.concatenate([rt, op.n_rt + l2])).cuda()].cpu().numpy()
+    ref = np.concatenate([ref_rt, ref_l2])
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale, (name, np.abs(got - ref).max() / scale)
+    op.close()

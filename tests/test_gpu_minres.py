@@ -34,3 +34,34 @@ def test_minres_matches_oracle(name, rtol):
     assert np.linalg.norm(xg - xr) <= 1e-8 * np.linalg.norm(xr)
     assert info["true_relres"] < 1e3 * rtol
     op.close()
+
+
+@pytest.mark.parametrize("name,precision", [("darcy_k3", 0), ("darcy_k3", 1), ("gd_k4_ragged", 1),
+                                            ("c1", 1), ("darcy_gamma", 1)])
+def test_refined_solve_reaches_true_residual(name, precision):
+    """FP64 residual correction around the inner MINRES (precision 0: FP64 inner;
+    1: FP32 operator and V-cycle inside, FP64 Lanczos vectors, dots and coarsest
+    solve): the true relative residual reaches the target and the solution matches
+    an exact sparse solve of the oracle's assembled system."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import scipy.sparse.linalg as spla
+    d = inputs(name)
+    prob = oracle_problem(d)
+    b = np.random.Generator(np.random.PCG64(12)).uniform(-1, 1, prob.n)
+    b[prob.ess] = 0.0
+    x_exact = spla.spsolve(prob.matrix().tocsc(), b)
+    op = gpu_operator(d, coarse_max=8)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_minres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-5 if precision else 1e-8,
+                                  maxit=5000, check_every=4, precision=precision, outer_rtol=1e-10,
+                                  max_outer=30)
+    torch.cuda.synchronize()
+    assert st == 0, info
+    assert info["true_relres"] <= 1e-10, info
+    xg = x.cpu().numpy()
+    r = b - prob.apply_op(xg)
+    assert np.linalg.norm(r) <= 1.01e-10 * np.linalg.norm(b)       # oracle's own residual of the result
+    err = np.linalg.norm(xg - x_exact) / np.linalg.norm(x_exact)
+    assert err <= 1e-7, err
+    op.close()
