@@ -243,8 +243,8 @@ def run_ours(args, rank, world, dist):
         sols = {}
         for key, prec, rtol in (("minres_fp64", 0, 1e-8), ("minres_mixed", 1, args.inner_rtol)):
             xs = torch.zeros_like(b)
-            st, info = op.hd_minres_solve(b, xs, rtol=rtol, maxit=20000, check_every=16, precision=prec,
-                                          outer_rtol=1e-8, max_outer=40)
+            st, info = op.hd_minres_solve(b, xs, rtol=rtol, maxit=args.solve_maxit, check_every=16,
+                                          precision=prec, outer_rtol=1e-8, max_outer=40)
             sols[key] = xs
             out[key] = {"status": int(st), "iterations": info["iterations"], "outer": info["outer"],
                         "ms": info["ms_total"], "true_relres": info["true_relres"], "inner_rtol": rtol,
@@ -271,6 +271,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--inner-rtol", type=float, default=1e-4, help="inner MINRES tolerance of the mixed solve")
+    ap.add_argument("--solve-maxit", type=int, default=20000, help="iteration cap of the MINRES solves")
     ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

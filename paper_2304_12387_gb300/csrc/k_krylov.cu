@@ -59,6 +59,9 @@ __global__ void k_dot_final(const double* __restrict__ partial, double* __restri
 
 struct MinresState {
   double beta, beta_prev, alpha, c, s, d_bar, eps, eps_next, delta, gamma, phi, phi_bar, eta0, rtol;
+  double inv_beta, inv_gamma, alpha_over_beta;  // published by the one-thread kernels: the vector
+                                                // kernels multiply (an FP64 divide per element is
+                                                // several FP64 ops on this GPU)
   double dot;       // scratch result of the last inner product
   int done_at;      // iteration at which the recurrence stopped (-1: running)
   int status;       // HD_OK / HD_ERR_*
@@ -87,7 +90,10 @@ __global__ void k_mr_lanczos1(int64_t n, int it, const MinresState* __restrict__
 __global__ void k_mr_alpha(MinresState* st, const double* __restrict__ partial) {
   __shared__ double sh[32];
   double s = block_sum(partial[threadIdx.x], sh);
-  if (threadIdx.x == 0) st->alpha = s;
+  if (threadIdx.x == 0) {
+    st->alpha = s;
+    st->alpha_over_beta = s / st->beta;
+  }
 }
 
 // y -= (alpha/beta) r_p  (y becomes the new Lanczos vector r);  z_u = r_u * mtinv
@@ -96,7 +102,7 @@ __global__ void k_mr_lanczos2(int64_t n, int64_t n_rt, const MinresState* __rest
                               const double* __restrict__ mtinv, double* __restrict__ z) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double f = st->alpha / st->beta;
+  double f = st->alpha_over_beta;
   double yi = fma(-f, rp[i], y[i]);
   y[i] = yi;
   if (i < n_rt) z[i] = yi * mtinv[i];
@@ -130,6 +136,8 @@ __global__ void k_mr_beta_givens(MinresState* st, const double* __restrict__ par
   st->s = st->beta / gamma;
   st->delta = delta;
   st->gamma = gamma;
+  st->inv_gamma = 1.0 / gamma;
+  st->inv_beta = 1.0 / st->beta;
   st->phi = st->c * st->phi_bar;
   st->phi_bar = st->s * st->phi_bar;
   if (fabs(st->phi_bar) <= st->rtol * st->eta0) {
@@ -145,11 +153,10 @@ __global__ void k_mr_update(int64_t n, int it, const MinresState* __restrict__ s
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   if (st->done_at >= 0 && st->done_at < it) return;
-  double ig = 1.0 / st->gamma;
-  double w = (v[i] - st->eps * wpp[i] - st->delta * wp[i]) * ig;
+  double w = fma(-st->eps, wpp[i], fma(-st->delta, wp[i], v[i])) * st->inv_gamma;
   wn[i] = w;
   x[i] = fma(st->phi, w, x[i]);
-  vnext[i] = z[i] / st->beta;
+  vnext[i] = z[i] * st->inv_beta;
 }
 
 __global__ void k_mr_init(MinresState* st, const double* __restrict__ partial, double rtol) {
@@ -169,6 +176,7 @@ __global__ void k_mr_init(MinresState* st, const double* __restrict__ partial, d
     st->status = isfinite(b2) ? HD_ERR_PREC_INDEFINITE : HD_ERR_NAN;
     st->done_at = 0;
     st->beta = 1.0;
+    st->inv_beta = 1.0;
     return;
   }
   st->beta = sqrt(b2);
@@ -178,13 +186,14 @@ __global__ void k_mr_init(MinresState* st, const double* __restrict__ partial, d
     st->done_at = 0;
     st->beta = 1.0;
   }
+  st->inv_beta = 1.0 / st->beta;
 }
 
 __global__ void k_scale_div(int64_t n, const double* __restrict__ z, const MinresState* __restrict__ st,
                             double* __restrict__ v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  v[i] = z[i] / st->beta;
+  v[i] = z[i] * st->inv_beta;
 }
 
 __global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, double* __restrict__ y) {

@@ -272,11 +272,15 @@ __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ 
 // FP64 accumulation for either vector type (the coarsest solve stays FP64)
 template <typename T>
 __global__ void k_vc_coarse(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per output row; the inverse is symmetric, so row i is contiguous
+  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= n) return;
+  const double* row = Ainv + (int64_t)i * n;
   double s = 0.0;
-  for (int j = 0; j < n; ++j) s = fma(Ainv[(int64_t)j * n + i], (double)b[j], s);
-  x[i] = (T)s;
+  for (int j = lane; j < n; j += 32) s = fma(row[j], (double)b[j], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[i] = (T)s;
 }
 
 // z -= mean(z): single block, deterministic fixed-order reduction
@@ -323,7 +327,7 @@ const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse
   const int last = (int)lv.size() - 1;
   if (l == last) {
     T* dst = out ? out : L.x0;
-    k_vc_coarse<T><<<nblk(L.n()), TPB, 0, h->stream>>>((int)L.n(), coarse_inv, b, dst);
+    k_vc_coarse<T><<<nblk(L.n() * 32), TPB, 0, h->stream>>>((int)L.n(), coarse_inv, b, dst);
     return dst;
   }
   LevelT<T>& C = lv[l + 1];
@@ -504,7 +508,7 @@ hd_status precond_setup(hd_op* h) {
       for (int p = i + 1; p < n; ++p) s -= R[(size_t)p * n + i] * col[p];
       col[i] = s / R[(size_t)i * n + i];
     }
-    for (int i = 0; i < n; ++i) inv[(size_t)c * n + i] = col[i];  // symmetric: column c
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = col[i];  // row-major: row i holds (A^-1)_{i,:}
   }
   h->coarse_n = n;
   if (cudaMalloc(&h->d_coarse_inv, sizeof(double) * inv.size()) != cudaSuccess)
