@@ -120,7 +120,26 @@ typedef struct {
   double true_relres;    /* ||b - AA x||_2 / ||b||_2 in FP64 at exit */
   double ms_total;       /* device time of the solve (CUDA events) */
   hd_status status;
+  int32_t fallback;      /* 1: the learned Schur preconditioner broke down and the solve was
+                            repeated with the V-cycle */
 } hd_solve_info;
+
+/* Training options and report of the learned Schur preconditioner. */
+typedef struct {
+  int32_t npairs;        /* residual/correction pairs taken from the plain solver */
+  int32_t capture_every; /* take the L2 part of every n-th Lanczos vector of a plain MINRES solve */
+  int32_t steps;         /* Adam steps on the mean loss over all pairs */
+  double lr;             /* Adam learning rate */
+  uint64_t seed;         /* seed of the random right-hand side of the data-generating solve */
+} hd_train_opts;
+
+typedef struct {
+  int32_t pairs;             /* pairs actually captured */
+  double loss_initial;       /* mean energy-norm loss before training */
+  double loss_final;         /* after the last step */
+  int32_t pcg_max_iterations;/* CG iterations of the hardest target solve */
+  double ms_total;           /* device time of data generation and training */
+} hd_train_info;
 
 /* -- lifetime ----------------------------------------------------------- */
 /* Builds the operator: 1D tables, geometric factors at quadrature points,
@@ -220,6 +239,36 @@ hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms);
 #define HD_NOALLOC_MAX_DOFS 209696
 hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, double* x,
                                   const hd_solve_opts* opts, hd_solve_info* info);
+
+/* -- learned Schur-complement preconditioner -------------------------------- */
+/* The paper preconditions S~ with one AMG V-cycle (Sec. 3.2). The learned variant
+ * replaces the V-cycle's fine level by a linear, symmetric-by-construction conv
+ * net on the L2 cell lattice plus the hierarchy's coarse correction:
+ *   P r = s C1^T C2^T C2 C1 (s r) + delta r/d + P_1 V_1 P_1^T r,  s = d^-1/2, d = diag(S~),
+ * C1 a 3x3x3 convolution 1 -> nc, C2 3x3x3 nc -> nc (nc = 32), no bias or
+ * activation; P is SPD for any weights. Weights W1[co][t] (nc x 27) and
+ * W2[co][ci][t] (nc x nc x 27), tap t = dx + 3 (dy + 3 dz) for the neighbour at
+ * offset (dx-1, dy-1, dz-1); activations FP16, accumulation FP32. */
+hd_status hd_learned_init(hd_handle h, int32_t nc, uint64_t seed, double delta);
+/* host FP32 weight arrays in the layout above */
+hd_status hd_learned_set_weights(hd_handle h, const float* W1, const float* W2);
+hd_status hd_learned_get_weights(hd_handle h, float* W1, float* W2);
+/* z = network part of P applied to an L2 vector r (device FP64) */
+hd_status hd_learned_apply(hd_handle h, const double* r, double* z);
+/* z = P_1 V_1 P_1^T r (device FP64 L2 vectors; zero with a single level) */
+hd_status hd_coarse_correction(hd_handle h, const double* r, double* z);
+/* Loss sum_p ||e_p - P r_p||_S~^2 / ||e_p||_S~^2 with P = net + Q, Q r_p = qr_p given
+ * (qr may be NULL for Q = 0), and its gradient w.r.t. W1, W2: r, e, qr are device
+ * arrays of npairs stacked L2 vectors; gW1, gW2, loss are host outputs. */
+hd_status hd_learned_grad(hd_handle h, int32_t npairs, const double* r, const double* e, const double* qr,
+                          float* gW1, float* gW2, double* loss);
+/* Generates training pairs from a plain solve (Lanczos-vector L2 parts r and
+ * e = S~^-1 r by V-cycle-preconditioned CG to 1e-10) and runs Adam. */
+hd_status hd_learned_train(hd_handle h, const hd_train_opts* opts, hd_train_info* info);
+/* 0: V-cycle (default); 1: learned network + coarse correction for the Schur
+ * block in hd_apply_prec and hd_minres_solve (FP64 solves fall back to the
+ * V-cycle if MINRES breaks down: info.fallback). */
+hd_status hd_set_schur_prec(hd_handle h, int32_t mode);
 
 /* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);

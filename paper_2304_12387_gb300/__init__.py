@@ -48,7 +48,18 @@ class SolveOpts(ctypes.Structure):
 
 class SolveInfo(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("outer", ctypes.c_int32), ("eta_ratio", ctypes.c_double),
-                ("true_relres", ctypes.c_double), ("ms_total", ctypes.c_double), ("status", ctypes.c_int32)]
+                ("true_relres", ctypes.c_double), ("ms_total", ctypes.c_double), ("status", ctypes.c_int32),
+                ("fallback", ctypes.c_int32)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("npairs", ctypes.c_int32), ("capture_every", ctypes.c_int32), ("steps", ctypes.c_int32),
+                ("lr", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+class TrainInfo(ctypes.Structure):
+    _fields_ = [("pairs", ctypes.c_int32), ("loss_initial", ctypes.c_double), ("loss_final", ctypes.c_double),
+                ("pcg_max_iterations", ctypes.c_int32), ("ms_total", ctypes.c_double)]
 
 
 _lib = None
@@ -79,6 +90,14 @@ _SIGS = {
     "hd_minres_solve_noalloc": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
     "hd_profile": [_H, ctypes.c_int32],
     "hd_profile_read": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
+    "hd_learned_init": [_H, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double],
+    "hd_learned_set_weights": [_H, _VP, _VP],
+    "hd_learned_get_weights": [_H, _VP, _VP],
+    "hd_learned_apply": [_H, _VP, _VP],
+    "hd_coarse_correction": [_H, _VP, _VP],
+    "hd_learned_grad": [_H, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)],
+    "hd_learned_train": [_H, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo)],
+    "hd_set_schur_prec": [_H, ctypes.c_int32],
     "hd_apply_op_f32": [_H, _VP, _VP],
     "hd_apply_prec_f32": [_H, _VP, _VP],
 }
@@ -246,4 +265,42 @@ class Operator:
         if raise_on_error:
             _check(st, self.h)
         return st, {"iterations": info.iterations, "outer": info.outer, "eta_ratio": info.eta_ratio,
-                    "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status}
+                    "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status,
+                    "fallback": info.fallback}
+
+    # -- learned Schur preconditioner ----------------------------------------
+    def hd_learned_init(self, nc=32, seed=2304, delta=1e-3):
+        _check(lib().hd_learned_init(self.h, nc, seed, delta), self.h)
+
+    def hd_learned_set_weights(self, W1, W2):
+        W1 = np.ascontiguousarray(W1, dtype=np.float32)
+        W2 = np.ascontiguousarray(W2, dtype=np.float32)
+        _check(lib().hd_learned_set_weights(self.h, W1.ctypes.data, W2.ctypes.data), self.h)
+
+    def hd_learned_get_weights(self, nc=32):
+        W1 = np.zeros((nc, 27), dtype=np.float32)
+        W2 = np.zeros((nc, nc, 27), dtype=np.float32)
+        _check(lib().hd_learned_get_weights(self.h, W1.ctypes.data, W2.ctypes.data), self.h)
+        return W1, W2
+
+    def hd_learned_apply(self, r, z): self._call("hd_learned_apply", r, z)
+    def hd_coarse_correction(self, r, z): self._call("hd_coarse_correction", r, z)
+
+    def hd_learned_grad(self, r, e, qr, nc=32):
+        """r, e, qr: (npairs, n_l2) device tensors (qr may be None). Returns (loss, gW1, gW2)."""
+        g1 = np.zeros((nc, 27), dtype=np.float32)
+        g2 = np.zeros((nc, nc, 27), dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(lib().hd_learned_grad(self.h, r.shape[0], _ptr(r), _ptr(e), _ptr(qr), g1.ctypes.data,
+                                     g2.ctypes.data, ctypes.byref(loss)), self.h)
+        return loss.value, g1, g2
+
+    def hd_learned_train(self, npairs=8, capture_every=4, steps=100, lr=1e-3, seed=2304):
+        o = TrainOpts(npairs, capture_every, steps, lr, seed)
+        info = TrainInfo()
+        _check(lib().hd_learned_train(self.h, ctypes.byref(o), ctypes.byref(info)), self.h)
+        return {"pairs": info.pairs, "loss_initial": info.loss_initial, "loss_final": info.loss_final,
+                "pcg_max_iterations": info.pcg_max_iterations, "ms_total": info.ms_total}
+
+    def hd_set_schur_prec(self, mode):
+        _check(lib().hd_set_schur_prec(self.h, int(mode)), self.h)

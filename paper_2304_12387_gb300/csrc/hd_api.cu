@@ -157,6 +157,7 @@ void destroy_all(hd_op* h) {
   cudaFree(h->d_ms);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  learned_free(h);
   precond_free(h);
 }
 

@@ -99,6 +99,12 @@ struct hd_op {
   std::vector<double*> mv;
   MinresState* d_ms = nullptr;
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
+  // Schur-block preconditioner: 0 = V-cycle, 1 = learned network + coarse correction
+  int schur_mode = 0;
+  struct LearnedNet* net = nullptr;
+  // capture of the Lanczos vectors' L2 parts during a solve (training data)
+  double* cap_buf = nullptr;
+  int cap_every = 1, cap_max = 0, cap_count = 0;
   // profiling of the fused element kernel
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
@@ -150,6 +156,14 @@ hd_status project_mean(hd_op* h, double* z);
 hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x);
 hd_status diag_scale(hd_op* h, const double* r, double* z);
 hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn);
+// z += P_1 V_1 P_1^T r: the coarse correction of the V-cycle hierarchy (nothing with one level)
+hd_status coarse_correction(hd_op* h, const double* r, double* z);
+// learned Schur preconditioner (k_learned.cu)
+hd_status learned_schur_apply(hd_op* h, const double* r, double* z);
+void learned_free(hd_op* h);
+// y += a x ; p = z + b p
+hd_status axpy_dev(hd_op* h, int64_t n, double a, const double* x, double* y);
+hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p);
 
 // Krylov (k_krylov.cu)
 hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info);

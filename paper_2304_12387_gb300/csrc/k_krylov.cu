@@ -307,6 +307,28 @@ static hd_status ensure_f32_work(hd_op* h) {
   return HD_OK;
 }
 
+namespace {
+__global__ void k_axpy_d(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) y[i] = fma(a, x[i], y[i]);
+}
+__global__ void k_xpay_d(int64_t n, const double* __restrict__ z, double b, double* __restrict__ p) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = fma(b, p[i], z[i]);
+}
+}  // namespace
+
+hd_status axpy_dev(hd_op* h, int64_t n, double a, const double* x, double* y) {
+  k_axpy_d<<<nblk(n), TPB, 0, h->stream>>>(n, a, x, y);
+  HD_LAUNCH_CK(h, "axpy");
+  return HD_OK;
+}
+hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p) {
+  k_xpay_d<<<nblk(n), TPB, 0, h->stream>>>(n, z, b, p);
+  HD_LAUNCH_CK(h, "xpay");
+  return HD_OK;
+}
+
 // y = AA v with the operator in the inner precision (vectors stay FP64)
 static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
   if (!f32) return apply_op_internal(h, v, y);
@@ -322,7 +344,9 @@ static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
 // z_q = V-cycle(r_q) in the inner precision, then the zero-mean projection if singular
 static hd_status inner_vcycle(hd_op* h, bool f32, const double* rq, double* zq) {
   hd_status st;
-  if (!f32) {
+  if (h->schur_mode == 1) {
+    if ((st = learned_schur_apply(h, rq, zq)) != HD_OK) return st;
+  } else if (!f32) {
     if ((st = vcycle_apply(h, rq, zq)) != HD_OK) return st;
   } else {
     const int64_t m = h->n_l2;
@@ -370,6 +394,11 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
     k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red);
     k_mr_lanczos2<<<nblk(n), TPB, 0, s>>>(n, h->n_rt, h->d_ms, y, rp, h->d_mtinv, z);
     HD_LAUNCH_CK(h, "minres lanczos");
+    if (h->cap_buf && it % h->cap_every == 0 && h->cap_count < h->cap_max && h->n_l2 > 0) {
+      HD_CK(h, cudaMemcpyAsync(h->cap_buf + (int64_t)h->cap_count * h->n_l2, y + h->n_rt, sizeof(double) * h->n_l2,
+                               cudaMemcpyDeviceToDevice, s));
+      h->cap_count++;
+    }
     if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
     k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, y, z, h->d_red);
     k_mr_beta_givens<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, it);
@@ -411,9 +440,17 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
   int total = 0, outer = 0;
   hd_status status = HD_OK;
   MinresState hs{};
+  int fallback = 0;
   if (!refine) {
     outer = 1;
     status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs);
+    if (h->schur_mode == 1 && (status == HD_ERR_PREC_INDEFINITE || status == HD_ERR_NAN)) {
+      // the learned Schur preconditioner broke down: solve again with the V-cycle
+      fallback = 1;
+      h->schur_mode = 0;
+      status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs);
+      h->schur_mode = 1;
+    }
   } else {
     double* r = h->mv[9];
     double* e = h->mv[10];
@@ -455,6 +492,7 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
     info->eta_ratio = hs.eta0 > 0 ? fabs(hs.phi_bar) / hs.eta0 : 0.0;
     info->ms_total = ms;
     info->status = status;
+    info->fallback = fallback;
   }
   return status;
 }

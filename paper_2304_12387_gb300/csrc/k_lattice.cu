@@ -591,6 +591,15 @@ static hd_status precond_apply_t(hd_op* h, const T* r, T* z, const T* mtinv, std
 }
 
 hd_status precond_apply(hd_op* h, const double* r, double* z) {
+  if (h->schur_mode == 1) {
+    hd_status st = diag_scale(h, r, z);
+    if (st != HD_OK) return st;
+    if (h->n_l2 > 0) {
+      if ((st = learned_schur_apply(h, r + h->n_rt, z + h->n_rt)) != HD_OK) return st;
+      if (h->singular && (st = project_mean(h, z + h->n_rt)) != HD_OK) return st;
+    }
+    return HD_OK;
+  }
   return precond_apply_t<double>(h, r, z, h->d_mtinv, h->lv, h->d_coarse_inv);
 }
 
@@ -598,6 +607,37 @@ hd_status precond_apply_f32(hd_op* h, const float* r, float* z) {
   hd_status st = setup_f32(h);
   if (st != HD_OK) return st;
   return precond_apply_t<float>(h, r, z, h->f_mtinv, h->lvf, h->d_coarse_inv);
+}
+
+// plain aggregation sum b_c = P^T r and injection z += P x_c between levels 0 and 1
+__global__ void k_restrict_plain(LevelT<double> lv, LevelT<double> cl, const double* __restrict__ r,
+                                 double* __restrict__ bc) {
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= cl.n()) return;
+  int Ic = (int)(t % cl.X), Jc = (int)((t / cl.X) % cl.Y), Zc = (int)(t / ((int64_t)cl.X * cl.Y));
+  double s = 0.0;
+  for (int Z = cl.fz * Zc; Z < min(cl.fz * Zc + cl.fz, lv.Z); ++Z)
+    for (int J = cl.fy * Jc; J < min(cl.fy * Jc + cl.fy, lv.Y); ++J)
+      for (int I = cl.fx * Ic; I < min(cl.fx * Ic + cl.fx, lv.X); ++I) s += r[I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z)];
+  bc[t] = s;
+}
+__global__ void k_prolong_add(LevelT<double> lv, LevelT<double> cl, const double* __restrict__ xc,
+                              double* __restrict__ z) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n()) return;
+  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  z[c] += xc[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
+}
+
+hd_status coarse_correction(hd_op* h, const double* r, double* z) {
+  if (h->lv.size() < 2) return HD_OK;
+  LevelT<double>& f = h->lv[0];
+  LevelT<double>& c = h->lv[1];
+  k_restrict_plain<<<nblk(c.n()), TPB, 0, h->stream>>>(f, c, r, c.b);
+  const double* xc = vcycle_level<double>(h, h->lv, h->d_coarse_inv, 1, c.b, nullptr);
+  k_prolong_add<<<nblk(f.n()), TPB, 0, h->stream>>>(f, c, xc, z);
+  HD_LAUNCH_CK(h, "coarse correction");
+  return HD_OK;
 }
 
 // FP32 V-cycle on an L2 vector (coarsest level in FP64)
