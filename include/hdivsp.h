@@ -99,6 +99,8 @@ typedef struct {
   int32_t winv_mode;     /* HD_WINV_DENSE or HD_WINV_CG */
   int32_t nu;            /* l1-Jacobi sweeps before and after the coarse correction; 0 -> 2 */
   int32_t coarse_max;    /* at most this many cells on the coarsest level; 0 -> 512 */
+  int32_t cycle;         /* 0 or 1: V-cycle; 2: W-cycle (two coarse corrections per level
+                            whose coarse level is not the coarsest) */
 } hd_problem_desc;
 
 /* MINRES options and report (Sec. 3). */

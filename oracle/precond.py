@@ -17,6 +17,9 @@ V-cycle on the approximate Schur complement (Sec. 2.3-2.4).
     - Galerkin coarse operators A_{l+1} = P^T A_l P;
     - nu pre- and nu post-sweeps of l1-Jacobi (D_l1 = sum_j |A_ij|, omega = 1),
       zero initial guess on every level, coarse correction added unscaled;
+    - cycle = 1 (V-cycle) or 2 (W-cycle: the coarse correction is computed
+      twice, each time from the current residual, on every level whose coarse
+      level is not the coarsest; above the coarsest one exact correction);
     - coarsest level: dense Cholesky; when S~ is singular (pure Neumann Darcy
       with gamma = 0) it factors A + s 1 1^T with s = mean(diag A)/n;
     - singular case: the result is projected to zero mean (Sec. 4.2).
@@ -58,8 +61,8 @@ def aggregation(dims):
 
 
 class VCycle:
-    def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20):
-        self.nu, self.singular = nu, singular
+    def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20, cycle=1):
+        self.nu, self.singular, self.cycle = nu, singular, cycle
         self.A, self.P, self.dims, self.dl1 = [A0.tocsr()], [], [tuple(dims)], []
         while np.prod(self.dims[-1]) > coarse_max and len(self.A) < max_levels:
             P, cd = aggregation(self.dims[-1])
@@ -87,8 +90,10 @@ class VCycle:
         x = np.zeros_like(b)
         for _ in range(self.nu):
             x = x + (b - A @ x) / d
-        r = b - A @ x
-        x = x + self.P[l] @ self._cycle(l + 1, self.P[l].T @ r)
+        repeats = self.cycle if l + 1 < len(self.A) - 1 else 1
+        for _ in range(repeats):
+            r = b - A @ x
+            x = x + self.P[l] @ self._cycle(l + 1, self.P[l].T @ r)
         for _ in range(self.nu):
             x = x + (b - A @ x) / d
         return x
@@ -110,13 +115,13 @@ def is_singular(prob, Ct):
 class BlockPrec:
     """z = B^-1 r with B = diag(tau M~, S^)."""
 
-    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512):
+    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1):
         self.prob, self.tau = prob, tau
         self.S, self.Mt, self.Ct = approx_schur(prob)
         self.singular = is_singular(prob, self.Ct)
         lat = prob.lat
         self.vc = VCycle(self.S, (lat.X, lat.Y, lat.Z), nu=nu, coarse_max=coarse_max,
-                         singular=self.singular)
+                         singular=self.singular, cycle=cycle)
 
     def apply(self, r):
         nrt = self.prob.lat.n_rt

@@ -208,6 +208,8 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->tau = d->tau > 0 ? d->tau : 1.0;
   h->nu = d->nu > 0 ? d->nu : 2;
   h->coarse_max = d->coarse_max > 0 ? d->coarse_max : 512;
+  if (d->cycle < 0 || d->cycle > 2) { delete h; return HD_ERR_INVALID_ARG; }
+  h->cycle = d->cycle == 2 ? 2 : 1;
   if (h->coarse_max > 4096) { delete h; return HD_ERR_INVALID_ARG; }
   const int k = h->k;
   LatticeDims& L = h->L;

@@ -59,6 +59,7 @@ struct hd_op {
   int64_t n_rt, n_l2, n_elem;
   double tau;
   int winv_mode, nu, coarse_max;
+  int cycle = 1;
   bool singular;
   cudaStream_t stream = nullptr;
   std::string err;

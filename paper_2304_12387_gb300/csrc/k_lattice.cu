@@ -251,6 +251,15 @@ __global__ void k_vc_jacobi_prolong(LevelT<T> lv, LevelT<T> cl, const T* __restr
   xo[c] = fma(lv.dinv[c], stencil_res_prolong<T>(lv, cl, x, xcrs, b[c], xs, I, J, Z, c), xs);
 }
 
+// x += P x_c (piecewise-constant prolongation, in place)
+template <typename T>
+__global__ void k_vc_prolong_add(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ xcrs, T* __restrict__ x) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n()) return;
+  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  x[c] += xcrs[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
+}
+
 // coarse right-hand side: sum over each aggregate of the fine residual b - S x
 template <typename T>
 __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ b, const T* __restrict__ x,
@@ -339,8 +348,15 @@ const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse
     k_vc_jacobi<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, o);
     cur = o;
   }
-  k_vc_restrict<T><<<nblk(C.n()), TPB, 0, h->stream>>>(L, C, b, cur, C.b);
-  const T* xc = vcycle_level<T>(h, lv, coarse_inv, l + 1, C.b, nullptr);
+  // W-cycle: a second coarse correction from the updated residual, except just
+  // above the coarsest level, where the first one is already exact
+  const int repeats = (h->cycle == 2 && l + 1 < last) ? 2 : 1;
+  const T* xc = nullptr;
+  for (int rep = 0; rep < repeats; ++rep) {
+    if (rep > 0) k_vc_prolong_add<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, C, xc, cur);
+    k_vc_restrict<T><<<nblk(C.n()), TPB, 0, h->stream>>>(L, C, b, cur, C.b);
+    xc = vcycle_level<T>(h, lv, coarse_inv, l + 1, C.b, nullptr);
+  }
   T* o = (nu == 1 && out) ? out : ((cur == L.x0) ? L.x1 : L.x0);
   k_vc_jacobi_prolong<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, C, b, cur, xc, o);
   cur = o;

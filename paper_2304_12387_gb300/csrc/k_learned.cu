@@ -86,6 +86,18 @@ __global__ void k_final_sum(const double* __restrict__ partial, double* __restri
   double s = block_sum_d(partial[threadIdx.x], sh);  // blockDim.x == RED_BLOCKS
   if (threadIdx.x == 0) out[0] = s;
 }
+// scal[0] = sum of squares; scal[1] = sigma = sqrt(scal[0]/n) (1 if zero); scal[8] = 1/sigma
+__global__ void k_sigma(const double* __restrict__ partial, double* __restrict__ scal, int64_t n) {
+  __shared__ double sh[32];
+  double s = block_sum_d(partial[threadIdx.x], sh);
+  if (threadIdx.x == 0) {
+    double sigma = sqrt(s / (double)n);
+    if (!(sigma > 0.0)) sigma = 1.0;
+    scal[0] = s;
+    scal[1] = sigma;
+    scal[8] = 1.0 / sigma;
+  }
+}
 
 // ---- element-wise kernels ----------------------------------------------------
 __global__ void k_sq(int64_t n, const double* __restrict__ diag, float* __restrict__ sq, double* __restrict__ dinv) {
@@ -94,15 +106,12 @@ __global__ void k_sq(int64_t n, const double* __restrict__ diag, float* __restri
   sq[i] = (float)(1.0 / sqrt(diag[i]));
   dinv[i] = 1.0 / diag[i];
 }
-// u = s r / sigma,  sigma = sqrt(sumsq / n) (sumsq at scal[0]); scal[1] <- sigma
+// u = s r / sigma (1/sigma at scal[8])
 __global__ void k_make_u(int64_t n, const double* __restrict__ r, const float* __restrict__ sq,
-                         double* __restrict__ scal, float* __restrict__ u) {
+                         const double* __restrict__ scal, float* __restrict__ u) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  double sigma = sqrt(scal[0] / (double)n);
-  if (!(sigma > 0.0)) sigma = 1.0;
-  if (i == 0) scal[1] = sigma;
   if (i >= n) return;
-  u[i] = (float)(r[i] * (double)sq[i] / sigma);
+  u[i] = (float)r[i] * sq[i] * (float)scal[8];
 }
 
 // ---- 1 -> 32 and 32 -> 1 convolutions (one warp per cell, lane = channel) ----
@@ -112,47 +121,74 @@ __device__ __forceinline__ void cell_ijk(int64_t c, int X, int Y, int& I, int& J
   K = (int)(c / ((int64_t)X * Y));
 }
 
-// out[c][co] = sum_t W1[co,t] in(c + off_t)   (zero outside)
-__global__ void k_conv1(int X, int Y, int Z, const __half* __restrict__ W1h, const float* __restrict__ in,
-                        __half* __restrict__ out) {
-  int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+// out[c][co] = sum_t W1[co,t] in(c + off_t) (zero outside): one thread per cell,
+// all 32 channels, W1 (as W1h[t][co]) in shared memory
+__global__ void __launch_bounds__(256) k_conv1(int X, int Y, int Z, const __half* __restrict__ W1h,
+                                               const float* __restrict__ in, __half* __restrict__ out) {
+  __shared__ float w[NT * NC];
+  for (int i = threadIdx.x; i < NT * NC; i += blockDim.x) w[i] = __half2float(W1h[i]);
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= (int64_t)X * Y * Z) return;
   int I, J, K;
   cell_ijk(c, X, Y, I, J, K);
-  float acc = 0.f;
+  float acc[NC];
 #pragma unroll
+  for (int co = 0; co < NC; ++co) acc[co] = 0.f;
+#pragma unroll 1
   for (int t = 0; t < NT; ++t) {
-    int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-    int i = I + dx, j = J + dy, k = K + dz;
+    const int i = I + t % 3 - 1, j = J + (t / 3) % 3 - 1, k = K + t / 9 - 1;
     if (i < 0 || i >= X || j < 0 || j >= Y || k < 0 || k >= Z) continue;
-    acc = fmaf(__half2float(W1h[t * NC + lane]), in[i + (int64_t)X * (j + (int64_t)Y * k)], acc);
+    const float v = in[i + (int64_t)X * (j + (int64_t)Y * k)];
+#pragma unroll
+    for (int co = 0; co < NC; ++co) acc[co] = fmaf(w[t * NC + co], v, acc[co]);
   }
-  out[c * NC + lane] = __float2half(acc);
+  uint4* o = reinterpret_cast<uint4*>(out + c * NC);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    __half2 h0 = __floats2half2_rn(acc[8 * q + 0], acc[8 * q + 1]), h1 = __floats2half2_rn(acc[8 * q + 2], acc[8 * q + 3]);
+    __half2 h2 = __floats2half2_rn(acc[8 * q + 4], acc[8 * q + 5]), h3 = __floats2half2_rn(acc[8 * q + 6], acc[8 * q + 7]);
+    uint4 v;
+    v.x = *reinterpret_cast<uint32_t*>(&h0);
+    v.y = *reinterpret_cast<uint32_t*>(&h1);
+    v.z = *reinterpret_cast<uint32_t*>(&h2);
+    v.w = *reinterpret_cast<uint32_t*>(&h3);
+    o[q] = v;
+  }
 }
 
 // s = sum_{t,co} W1[co,t] g[c - off_t][co]; mode 0: z = sq sigma s + delta r / d (FP64);
-// mode 1: outf = s (FP32)
-__global__ void k_conv1T(int X, int Y, int Z, const __half* __restrict__ W1h, const __half* __restrict__ g,
-                         int mode, const float* __restrict__ sq, const double* __restrict__ scal, double delta,
-                         const double* __restrict__ r, const double* __restrict__ dinv, double* __restrict__ z,
-                         float* __restrict__ outf) {
-  int64_t c = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+// mode 1: outf = s (FP32). One thread per cell.
+__global__ void __launch_bounds__(256) k_conv1T(int X, int Y, int Z, const __half* __restrict__ W1h,
+                                                const __half* __restrict__ g, int mode, const float* __restrict__ sq,
+                                                const double* __restrict__ scal, double delta,
+                                                const double* __restrict__ r, const double* __restrict__ dinv,
+                                                double* __restrict__ z, float* __restrict__ outf) {
+  __shared__ float w[NT * NC];
+  for (int i = threadIdx.x; i < NT * NC; i += blockDim.x) w[i] = __half2float(W1h[i]);
+  __syncthreads();
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= (int64_t)X * Y * Z) return;
   int I, J, K;
   cell_ijk(c, X, Y, I, J, K);
   float acc = 0.f;
-#pragma unroll
+#pragma unroll 1
   for (int t = 0; t < NT; ++t) {
-    int dx = t % 3 - 1, dy = (t / 3) % 3 - 1, dz = t / 9 - 1;
-    int i = I - dx, j = J - dy, k = K - dz;
+    const int i = I - (t % 3 - 1), j = J - ((t / 3) % 3 - 1), k = K - (t / 9 - 1);
     if (i < 0 || i >= X || j < 0 || j >= Y || k < 0 || k >= Z) continue;
-    acc = fmaf(__half2float(W1h[t * NC + lane]),
-               __half2float(g[(i + (int64_t)X * (j + (int64_t)Y * k)) * NC + lane]), acc);
+    const uint4* src = reinterpret_cast<const uint4*>(g + (i + (int64_t)X * (j + (int64_t)Y * k)) * NC);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint4 v = src[q];
+      const __half2* hv = reinterpret_cast<const __half2*>(&v);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        float2 f = __half22float2(hv[p]);
+        acc = fmaf(w[t * NC + 8 * q + 2 * p], f.x, acc);
+        acc = fmaf(w[t * NC + 8 * q + 2 * p + 1], f.y, acc);
+      }
+    }
   }
-  acc = warp_sum_f(acc);
-  if (lane != 0) return;
   if (mode == 0)
     z[c] = (double)sq[c] * scal[1] * (double)acc + delta * r[c] * dinv[c];
   else
@@ -481,14 +517,15 @@ hd_status net_forward(hd_op* h, const double* r, double* y) {
   LearnedNet* N = h->net;
   const int64_t n = N->n;
   hd_status st;
-  if ((st = net_sumsq(h, r, N->sq, n, N->scal)) != HD_OK) return st;
+  k_sumsq_partial<double><<<RED_BLOCKS, TPB, 0, h->stream>>>(n, r, N->sq, N->red);
+  k_sigma<<<1, RED_BLOCKS, 0, h->stream>>>(N->red, N->scal, n);
   k_make_u<<<nblk(n), TPB, 0, h->stream>>>(n, r, N->sq, N->scal, N->u);
-  k_conv1<<<nblk(n * 32), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->u, N->a1);
+  k_conv1<<<nblk(n), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->u, N->a1);
   HD_LAUNCH_CK(h, "conv1");
   if ((st = conv2(h, N->W2h, N->a1, N->a2)) != HD_OK) return st;
   if ((st = conv2(h, N->W2Th, N->a2, N->a3)) != HD_OK) return st;
-  k_conv1T<<<nblk(n * 32), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->a3, 0, N->sq, N->scal, N->delta, r,
-                                                 N->dinv, y, nullptr);
+  k_conv1T<<<nblk(n), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->a3, 0, N->sq, N->scal, N->delta, r,
+                                            N->dinv, y, nullptr);
   HD_LAUNCH_CK(h, "conv1T");
   return HD_OK;
 }
@@ -510,7 +547,7 @@ hd_status net_pair_grad(hd_op* h, const double* r, const double* e, const double
   k_b4<<<nblk(n), TPB, 0, h->stream>>>(n, N->serr, N->sq, N->scal, N->b4);
   if ((st = net_sumsq_f(h, N->b4, n, N->scal + 3)) != HD_OK) return st;
   k_norm_b4<<<nblk(n), TPB, 0, h->stream>>>(n, N->b4, N->scal);
-  k_conv1<<<nblk(n * 32), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->b4, N->b3);
+  k_conv1<<<nblk(n), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->b4, N->b3);
   HD_LAUNCH_CK(h, "backward conv1");
   if ((st = conv2(h, N->W2h, N->b3, N->b2)) != HD_OK) return st;
   if ((st = conv2(h, N->W2Th, N->b2, N->b1)) != HD_OK) return st;

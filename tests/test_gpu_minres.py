@@ -65,3 +65,33 @@ def test_refined_solve_reaches_true_residual(name, precision):
     err = np.linalg.norm(xg - x_exact) / np.linalg.norm(x_exact)
     assert err <= 1e-7, err
     op.close()
+
+
+@pytest.mark.parametrize("name", ["gd_k4_ragged", "darcy_k3", "darcy_neumann"])
+def test_wcycle_matches_oracle(name):
+    """W-cycle option: the V-cycle apply and the MINRES iteration count against the
+    oracle running the same W-cycle spec."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle.minres import minres
+    from oracle.precond import BlockPrec
+    d = inputs(name)
+    prob = oracle_problem(d)
+    bp = BlockPrec(prob, nu=2, coarse_max=8, cycle=2)
+    op = gpu_operator(d, coarse_max=8, cycle=2)
+    assert bp.vc.n_levels >= 3
+    r = np.random.Generator(np.random.PCG64(13)).uniform(-1, 1, prob.lat.n_l2)
+    z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
+    op.hd_vcycle(torch.from_numpy(r).cuda(), z)
+    torch.cuda.synchronize()
+    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-11) <= 1e-11
+    b = np.random.Generator(np.random.PCG64(14)).uniform(-1, 1, prob.n)
+    b[prob.ess] = 0.0
+    if bp.singular:
+        b[prob.lat.n_rt:] -= b[prob.lat.n_rt:].mean()
+    xr, ir = minres(prob.apply_op, bp.apply, b, rtol=1e-8, maxit=2000)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_minres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=2000, check_every=4)
+    assert st == 0 and abs(info["iterations"] - ir["iterations"]) <= 1, (info, ir["iterations"])
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-8 * np.linalg.norm(xr)
+    op.close()
