@@ -109,6 +109,20 @@ void build_tables(int k, int q, ElemTables& t) {
       t.BH[p * k + j] = s;
     }
   }
+  // GL nodal basis of the local CG (k Gauss-Legendre nodes): its values at the q
+  // quadrature points, and TT[j][m] = integral of L_m over subcell j (Gauss rule
+  // with k+2 points per subcell, exact for these degree-(k-1) polynomials)
+  std::vector<double> gk, wk, gs, ws;
+  gauss(k, gk, wk);
+  gauss(k + 2, gs, ws);
+  for (int p = 0; p < q; ++p)
+    for (int m = 0; m < k; ++m) t.BG[p * k + m] = lag(gk, m, gx[p]);
+  for (int j = 0; j < k; ++j)
+    for (int m = 0; m < k; ++m) {
+      double a = xi[j], b = xi[j + 1], s = 0.0;
+      for (size_t i = 0; i < gs.size(); ++i) s += ws[i] * lag(gk, m, a + (b - a) * gs[i]);
+      t.TT[j * k + m] = (b - a) * s;
+    }
 }
 
 hd_status dalloc(hd_op* h, double** p, int64_t n, const char* what) {
@@ -148,7 +162,8 @@ hd_status elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
 
 void destroy_all(hd_op* h) {
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
-  cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag);
+  cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
+  cudaFree(h->f_wdet); cudaFree(h->f_wgldiag);
   cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
   cudaFree(h->d_coarse_inv); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
   cudaFree(h->f_G); cudaFree(h->f_winv); cudaFree(h->f_cscale); cudaFree(h->f_mtinv); cudaFree(h->f_coarse_inv);
@@ -203,7 +218,7 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->k = d->k;
   h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
   if (h->q != h->k + 1 && h->q != h->k + 2) { delete h; return HD_ERR_INVALID_ARG; }
-  if (d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG) { delete h; return HD_ERR_INVALID_ARG; }
   h->winv_mode = d->winv_mode;
   h->tau = d->tau > 0 ? d->tau : 1.0;
   h->nu = d->nu > 0 ? d->nu : 2;
@@ -253,7 +268,8 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     if ((st = dalloc(h, &h->d_vz, nv, "vz")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_G, E * 6 * nq, "geometric factors")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_wdet, E * nq, "wdet")) != HD_OK) break;
-    if ((st = dalloc(h, &h->d_winv, E * nl2 * nl2, "W inverse")) != HD_OK) break;
+    if (h->winv_mode == HD_WINV_DENSE && (st = dalloc(h, &h->d_winv, E * nl2 * nl2, "W inverse")) != HD_OK) break;
+    if ((st = dalloc(h, &h->d_wgldiag, E * nl2, "GL-basis W diagonal")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_wdiag, E * nl2, "W diagonal")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_cscale, E, "cscale")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_mt, h->n_rt, "M diagonal")) != HD_OK) break;

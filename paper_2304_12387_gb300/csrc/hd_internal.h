@@ -20,6 +20,10 @@ struct ElemTables {
   double BH[HD_MAXQ * HD_MAXK];        // BH[p*k+j]     = h_j(g_p), histopolation
   double gw[HD_MAXQ];                  // GL weights on [0,1]
   double gx[HD_MAXQ];                  // GL points on [0,1]
+  double BG[HD_MAXQ * HD_MAXK];        // BG[p*k+m] = L_m(g_p): Lagrange basis on the k-point GL
+                                       //   nodes (the nodal basis of the local CG) at the q points
+  double TT[HD_MAXK * HD_MAXK];        // TT[j*k+m] = integral of L_m over subcell j: GL-nodal
+                                       //   coefficients -> histopolation coefficients
 };
 
 // Mesh/lattice constants passed to kernels.
@@ -74,6 +78,9 @@ struct hd_op {
   double* d_wdet = nullptr;     // [E][Q^3] w_p / det J
   double* d_winv = nullptr;     // [E][k^3][k^3] unweighted W_e^-1 (dense mode)
   double* d_wdiag = nullptr;    // [E][k^3] diag(W_e) (unweighted)
+  double* d_wgldiag = nullptr;  // [E][k^3] diag of W_e in the GL nodal basis (local CG)
+  float* f_wdet = nullptr;      // FP32 copies for the inner solve
+  float* f_wgldiag = nullptr;
   double* d_cscale = nullptr;   // [E] c_e: C_e = c_e W_e^-1
   double* d_mt = nullptr;       // [n_rt] diag(M), 1 on essential dofs
   double* d_mtinv = nullptr;    // [n_rt] 1/(tau diag M) on free dofs, 1 on essential

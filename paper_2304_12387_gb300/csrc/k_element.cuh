@@ -19,6 +19,8 @@ template <typename T>
 struct TabT {
   T BI[HD_MAXQ * (HD_MAXK + 1)];
   T BH[HD_MAXQ * HD_MAXK];
+  T BG[HD_MAXQ * HD_MAXK];
+  T TT[HD_MAXK * HD_MAXK];
 };
 
 template <typename T>
@@ -26,8 +28,20 @@ inline TabT<T> make_tab(const ElemTables& t) {
   TabT<T> o;
   for (int i = 0; i < HD_MAXQ * (HD_MAXK + 1); ++i) o.BI[i] = (T)t.BI[i];
   for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BH[i] = (T)t.BH[i];
+  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BG[i] = (T)t.BG[i];
+  for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.TT[i] = (T)t.TT[i];
   return o;
 }
+
+// Local CG parameters (Sec. 2.5 / 3.1: W^-1 by a fused per-element CG in the
+// Gauss-Legendre nodal basis, no global reductions).
+template <typename T>
+struct CgArgs {
+  const T* wdet;     // [E][Q^3] w_p / det J, or null: use the dense W_e^-1
+  const T* diag;     // [E][K^3] Jacobi diagonal of W_e in the GL nodal basis
+  int maxit;
+  T tol2;            // stop when ||r||^2 <= tol2 ||b||^2 (per element)
+};
 
 // out[o*SO] = sum_i B[o*NI + i] in[i*SI], o < NO   (B row-major NO x NI)
 template <typename T, int NI, int NO, int SI, int SO>
@@ -134,6 +148,176 @@ __device__ __forceinline__ T div_local(const T* su, int a) {
 }
 
 // ---------------------------------------------------------------------------
+// Per-element 3D application of the K x K map TT (or its transpose) to EB
+// element-local L2 vectors: in -> t1 -> t2 -> out, one direction per stage.
+template <typename T, int K, int EB, bool TRANS>
+__device__ __forceinline__ void apply_tt(const TabT<T>& tab, const T* in, int in_stride, T* t1, T* t2, T* out,
+                                         int buf_stride, int out_stride) {
+  constexpr int KK = K * K;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  for (int t = tid; t < EB * KK; t += nth) {  // x: lines (m2, m3)
+    int el = t / KK, r = t - el * KK;
+    if (TRANS) contractT<T, K, K, 1, 1>(in + el * in_stride + K * r, t1 + el * buf_stride + K * r, tab.TT);
+    else contract<T, K, K, 1, 1>(in + el * in_stride + K * r, t1 + el * buf_stride + K * r, tab.TT);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * KK; t += nth) {  // y: lines (i1, m3)
+    int el = t / KK, r = t - el * KK, i1 = r % K, m3 = r / K;
+    if (TRANS) contractT<T, K, K, K, K>(t1 + el * buf_stride + i1 + KK * m3, t2 + el * buf_stride + i1 + KK * m3, tab.TT);
+    else contract<T, K, K, K, K>(t1 + el * buf_stride + i1 + KK * m3, t2 + el * buf_stride + i1 + KK * m3, tab.TT);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * KK; t += nth) {  // z: lines (i1, i2)
+    int el = t / KK, r = t - el * KK;
+    if (TRANS) contractT<T, K, K, KK, KK>(t2 + el * buf_stride + r, out + el * out_stride + r, tab.TT);
+    else contract<T, K, K, KK, KK>(t2 + el * buf_stride + r, out + el * out_stride + r, tab.TT);
+  }
+  __syncthreads();
+}
+
+// w = W_GL p for EB elements: GL nodal -> quadrature points (three stages with
+// BG), times w_p / det J, and back (three transposed stages). Scratch s1.
+template <typename T, int K, int Q, int EB>
+__device__ __forceinline__ void apply_wgl(const TabT<T>& tab, const T* p, int vstride, T* w, T* s1, int s1stride,
+                                          const T* __restrict__ wdet, int e0, int n_elem) {
+  constexpr int KK = K * K, NQ = Q * Q * Q;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  T* t1b = s1;                       // [Q K K]
+  T* t2b = s1 + Q * KK;              // [Q Q K]
+  T* vb = s1 + Q * KK + Q * Q * K;   // [Q^3]
+  for (int t = tid; t < EB * KK; t += nth) {
+    int el = t / KK, r = t - el * KK;
+    contract<T, K, Q, 1, 1>(p + el * vstride + K * r, t1b + el * s1stride + Q * r, tab.BG);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * Q * K; t += nth) {
+    int el = t / (Q * K), r = t - el * Q * K, px = r % Q, m3 = r / Q;
+    contract<T, K, Q, Q, Q>(t1b + el * s1stride + px + Q * K * m3, t2b + el * s1stride + px + Q * Q * m3, tab.BG);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * Q * Q; t += nth) {
+    int el = t / (Q * Q), r = t - el * Q * Q;
+    contract<T, K, Q, Q * Q, Q * Q>(t2b + el * s1stride + r, vb + el * s1stride + r, tab.BG);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * NQ; t += nth) {
+    int el = t / NQ, pt = t - el * NQ, e = e0 + el;
+    vb[el * s1stride + pt] *= (e < n_elem) ? wdet[(size_t)e * NQ + pt] : (T)0;
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * Q * Q; t += nth) {
+    int el = t / (Q * Q), r = t - el * Q * Q;
+    contractT<T, Q, K, Q * Q, Q * Q>(vb + el * s1stride + r, t2b + el * s1stride + r, tab.BG);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * Q * K; t += nth) {
+    int el = t / (Q * K), r = t - el * Q * K, px = r % Q, m3 = r / Q;
+    contractT<T, Q, K, Q, Q>(t2b + el * s1stride + px + Q * Q * m3, t1b + el * s1stride + px + Q * K * m3, tab.BG);
+  }
+  __syncthreads();
+  for (int t = tid; t < EB * KK; t += nth) {
+    int el = t / KK, r = t - el * KK;
+    contractT<T, Q, K, 1, 1>(t1b + el * s1stride + Q * r, w + el * vstride + K * r, tab.BG);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_allsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// W_e^-1 q_e for EB elements by the local CG of Sec. 2.5: b = TT^T q (GL nodal
+// right-hand side), Jacobi-preconditioned CG on W_GL from a = 0, result TT a in
+// s1 (returned). One warp per element for the vector operations; the loop runs
+// until every element of the CTA meets its tolerance or maxit is reached.
+template <typename T, int K, int Q, int EB>
+__device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* s2, int s2stride,
+                       const CgArgs<T>& cg, int e0, int n_elem) {
+  constexpr int NL2 = K * K * K;
+  __shared__ T sc_rz[EB], sc_bb[EB];
+  __shared__ int sc_active[EB];
+  __shared__ int sc_any;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // per element in s2: a, r, p, w (NL2 each)
+  T* A = s2;
+  T* R = s2 + NL2;
+  T* P = s2 + 2 * NL2;
+  T* W = s2 + 3 * NL2;
+  apply_tt<T, K, EB, true>(tab, sq, NL2, s1, s1 + NL2, R, s1stride, s2stride);  // r = b = TT^T q
+  for (int el = warp; el < EB; el += nw) {
+    const int e = e0 + el;
+    const T* D = cg.diag + (size_t)(e < n_elem ? e : 0) * NL2;
+    T rz = 0, bb = 0;
+    for (int i = lane; i < NL2; i += 32) {
+      T r = R[el * s2stride + i];
+      T z = (e < n_elem) ? r / D[i] : (T)0;
+      A[el * s2stride + i] = 0;
+      P[el * s2stride + i] = z;
+      rz += r * z;
+      bb += r * r;
+    }
+    rz = warp_allsum(rz);
+    bb = warp_allsum(bb);
+    if (lane == 0) {
+      sc_rz[el] = rz;
+      sc_bb[el] = bb;
+      sc_active[el] = (e < n_elem) && (bb > (T)0);
+    }
+  }
+  __syncthreads();
+  for (int it = 0; it < cg.maxit; ++it) {
+    apply_wgl<T, K, Q, EB>(tab, P, s2stride, W, s1, s1stride, cg.wdet, e0, n_elem);
+    for (int el = warp; el < EB; el += nw) {
+      if (!sc_active[el]) continue;
+      T pw = 0;
+      for (int i = lane; i < NL2; i += 32) pw += P[el * s2stride + i] * W[el * s2stride + i];
+      pw = warp_allsum(pw);
+      const T alpha = sc_rz[el] / pw;
+      T rr = 0;
+      for (int i = lane; i < NL2; i += 32) {
+        A[el * s2stride + i] += alpha * P[el * s2stride + i];
+        T r = R[el * s2stride + i] - alpha * W[el * s2stride + i];
+        R[el * s2stride + i] = r;
+        rr += r * r;
+      }
+      rr = warp_allsum(rr);
+      __syncwarp();
+      if (lane == 0) sc_active[el] = (rr > cg.tol2 * sc_bb[el]) && (pw > (T)0);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int el = 0; el < EB; ++el) any |= sc_active[el];
+      sc_any = any;
+    }
+    __syncthreads();
+    if (!sc_any) break;
+    for (int el = warp; el < EB; el += nw) {
+      if (!sc_active[el]) continue;
+      const T* D = cg.diag + (size_t)(e0 + el) * NL2;
+      T rz = 0;
+      for (int i = lane; i < NL2; i += 32) {
+        T z = R[el * s2stride + i] / D[i];
+        W[el * s2stride + i] = z;
+        rz += R[el * s2stride + i] * z;
+      }
+      rz = warp_allsum(rz);
+      const T beta = rz / sc_rz[el];
+      for (int i = lane; i < NL2; i += 32) P[el * s2stride + i] = W[el * s2stride + i] + beta * P[el * s2stride + i];
+      __syncwarp();
+      if (lane == 0) sc_rz[el] = rz;
+    }
+    __syncthreads();
+  }
+  T* out = s1 + 2 * NL2;
+  apply_tt<T, K, EB, false>(tab, A, s2stride, s1, s1 + NL2, out, s1stride, s1stride);  // TT a
+  return out;
+}
+
+// ---------------------------------------------------------------------------
 // Fused block-operator kernel: EB elements per CTA.
 //   OP_M : y_u += M_e u_e (sum factorisation: interpolation to the Q^3 points,
 //          the 3x3 geometric factor, transposed interpolation)
@@ -144,11 +328,19 @@ __device__ __forceinline__ T div_local(const T* su, int a) {
 // identity); otherwise nothing. y_u receives one atomic add per element and
 // face: a shared face gets exactly two addends on a zeroed vector, so the
 // result does not depend on their order.
+#ifndef HD_ELEM_THREADS
+#define HD_ELEM_THREADS 256
+#endif
+#ifndef HD_ELEM_EB
+#define HD_ELEM_EB 8
+#endif
+
 template <typename T, int K, int Q, int EB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(HD_ELEM_THREADS)
 k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem,
           const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
-          const T* __restrict__ u, const T* __restrict__ q, T* __restrict__ yu, T* __restrict__ yq) {
+          const CgArgs<T> cg, const T* __restrict__ u, const T* __restrict__ q, T* __restrict__ yu,
+          T* __restrict__ yq) {
   using S = Sizes<K, Q>;
   constexpr int NX1 = S::NX1, NRT = S::NRT, NL2 = S::NL2, NQ = S::NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,6 +383,9 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   __syncthreads();
 
   // -- L2 rows: y_q = D u - C q ------------------------------------------------
+  const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
+  const T* cgres = nullptr;
+  if (use_cg) cgres = local_cg<T, K, Q, EB>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
   if (mode & (OP_D | OP_C)) {
     for (int t = tid; t < EB * NL2; t += nth) {
       int el = t / NL2, a = t - el * NL2, e = e0 + el;
@@ -198,11 +393,15 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       T v = (T)0;
       if (mode & OP_D) v = div_local<T, K>(su + el * NRT, a);
       if (mode & OP_C) {
-        const T* W = winv + (size_t)e * NL2 * NL2;
-        const T* qe = sq + el * NL2;
         T s = (T)0;
+        if (use_cg) {
+          s = cgres[el * S::R1 + a];
+        } else {
+          const T* W = winv + (size_t)e * NL2 * NL2;
+          const T* qe = sq + el * NL2;
 #pragma unroll 8
-        for (int b = 0; b < NL2; ++b) s = fma(W[b * NL2 + a], qe[b], s);
+          for (int b = 0; b < NL2; ++b) s = fma(W[b * NL2 + a], qe[b], s);
+        }
         s *= cscale[e];
         v = (mode & OP_CPOS) ? v + s : v - s;
       }
@@ -211,6 +410,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = v;
     }
   }
+  if (use_cg) __syncthreads();
 
   if (mode & OP_M) {
     // -- interpolation to the points: stage A (contract along x) ----------------
@@ -517,14 +717,39 @@ __global__ void k_diagM(const ElemTables tab, const LatticeDims L, const int n_e
   atomicAdd(mt + gid, s);
 }
 
+// Setup: diag of W_e = sum_p wdet_p B(p,a)^2 for the tensor basis B = B1 x B1 x B1
+// (BH: the histopolation basis; BG: the GL nodal basis of the local CG).
+template <int K, int Q>
+__global__ void k_diag_tensor(const ElemTables tab, const int n_elem, const bool gl, const double* __restrict__ wdet,
+                              double* __restrict__ out) {
+  constexpr int NL2 = K * K * K, NQ = Q * Q * Q;
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= (int64_t)n_elem * NL2) return;
+  const int e = (int)(t / NL2), a = (int)(t % NL2);
+  const int a1 = a % K, a2 = (a / K) % K, a3 = a / (K * K);
+  const double* B = gl ? tab.BG : tab.BH;
+  double s = 0.0;
+  for (int p3 = 0; p3 < Q; ++p3) {
+    double b3 = B[p3 * K + a3];
+    for (int p2 = 0; p2 < Q; ++p2) {
+      double b2 = B[p2 * K + a2];
+      for (int p1 = 0; p1 < Q; ++p1) {
+        double b = B[p1 * K + a1] * b2 * b3;
+        s += wdet[(size_t)e * NQ + p1 + Q * (p2 + Q * p3)] * b * b;
+      }
+    }
+  }
+  out[t] = s;
+}
+
 template <int K, int Q>
 constexpr int elem_eb() {
-  return 8;
+  return HD_ELEM_EB;
 }
 
 template <typename T, int K, int Q>
-hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const T* u,
-                      const T* q, T* yu, T* yq) {
+hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
+                      const T* u, const T* q, T* yu, T* yq) {
   constexpr int EB = elem_eb<K, Q>();
   using S = Sizes<K, Q>;
   size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
@@ -539,7 +764,8 @@ hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs
   int blocks = (int)((h->n_elem + EB - 1) / EB);
   prof_mark(h, true);
   if (blocks > 0)
-    kern<<<blocks, 256, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, u, q, yu, yq);
+    kern<<<blocks, HD_ELEM_THREADS, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, cg, u, q, yu,
+                                                       yq);
   prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;
@@ -552,6 +778,14 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
   if (n > 0) k_geom<Q><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
       h->tab, h->L, (int)h->n_elem, h->d_vx, h->d_vy, h->d_vz, bcoef, h->d_G, h->d_wdet, d_bad);
   HD_LAUNCH_CK(h, "k_geom");
+  if (h->n_elem > 0) {
+    constexpr int NL2 = K * K * K;
+    unsigned nb = (unsigned)((h->n_elem * NL2 + 255) / 256);
+    k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, true, h->d_wdet, h->d_wgldiag);
+    if (h->winv_mode == HD_WINV_CG)
+      k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, false, h->d_wdet, h->d_wdiag);
+    HD_LAUNCH_CK(h, "k_diag_tensor");
+  }
   if (h->winv_mode == HD_WINV_DENSE && h->n_elem > 0) {
     size_t smem = (size_t)WinvSmem<K, Q>::TOTAL * sizeof(double);
     cudaError_t err = cudaFuncSetAttribute(k_winv<K, Q>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -582,17 +816,24 @@ HD_DECLARE_K(3)
 HD_DECLARE_K(4)
 HD_DECLARE_K(5)
 
+// FP64: the dense W_e^-1, or the local CG to a relative residual of 1e-14 (HD_WINV_CG).
+// FP32 (inner solves): the dense W_e^-1 in FP32 when the handle has one (faster on
+// this GPU than the CG's barrier-bound iterations), else the local CG to 1e-6.
 #define HD_DEFINE_K(KK)                                                                                   \
   hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) { \
+    hdk::CgArgs<double> cg{h->winv_mode == HD_WINV_CG ? h->d_wdet : nullptr, h->d_wgldiag, 40, 1e-28};     \
     if (h->q == KK + 1)                                                                                   \
-      return hdk::run_elem_op<double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, u, q, yu, yq); \
-    return hdk::run_elem_op<double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, u, q, yu, yq);   \
+      return hdk::run_elem_op<double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, yu,  \
+                                                  yq);                                                    \
+    return hdk::run_elem_op<double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, yu, yq); \
   }                                                                                                       \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,              \
                               float* yq) {                                                                \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f};                     \
     if (h->q == KK + 1)                                                                                   \
-      return hdk::run_elem_op<float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, u, q, yu, yq);  \
-    return hdk::run_elem_op<float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, u, q, yu, yq);    \
+      return hdk::run_elem_op<float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, yu,   \
+                                                 yq);                                                     \
+    return hdk::run_elem_op<float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, yu, yq); \
   }                                                                                                       \
   hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad) {                                 \
     if (h->q == KK + 1) return hdk::run_elem_setup<KK, KK + 1>(h, bcoef, d_bad);                          \

@@ -546,7 +546,11 @@ hd_status setup_f32(hd_op* h) {
   int nq = h->q * h->q * h->q, nl2 = h->k * h->k * h->k;
   hd_status st;
   if ((st = conv(h->d_G, &h->f_G, h->n_elem * 6 * nq, "f32 G")) != HD_OK) return st;
-  if ((st = conv(h->d_winv, &h->f_winv, h->n_elem * nl2 * nl2, "f32 winv")) != HD_OK) return st;
+  // W^-1 for the FP32 operator: the dense inverse in FP32 when there is one, else
+  // the local CG (geometric weights and Jacobi diagonal)
+  if (h->d_winv && (st = conv(h->d_winv, &h->f_winv, h->n_elem * nl2 * nl2, "f32 winv")) != HD_OK) return st;
+  if ((st = conv(h->d_wdet, &h->f_wdet, h->n_elem * nq, "f32 wdet")) != HD_OK) return st;
+  if ((st = conv(h->d_wgldiag, &h->f_wgldiag, h->n_elem * nl2, "f32 wgl diag")) != HD_OK) return st;
   if ((st = conv(h->d_cscale, &h->f_cscale, h->n_elem, "f32 cscale")) != HD_OK) return st;
   if ((st = conv(h->d_mtinv, &h->f_mtinv, h->n_rt, "f32 mtinv")) != HD_OK) return st;
   for (size_t l = 0; l < h->lv.size(); ++l) {

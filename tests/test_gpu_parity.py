@@ -154,3 +154,35 @@ def test_f32_operator_close(pair):
     y = torch.empty(prob.n, dtype=torch.float32, device="cuda")
     op.hd_apply_op_f32(torch.from_numpy(x.astype(np.float32)).cuda(), y)
     assert close(_host(y).astype(np.float64), prob.apply_op(x), 1e-4) <= 1e-4
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_local_cg_winv_mode(name):
+    """W^-1 by the fused local CG in the Gauss-Legendre nodal basis (the paper's
+    matrix-free method, Sec. 2.5 and 3.1) instead of stored dense inverses: same
+    operator to 1e-12."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.precond import approx_schur
+    d = inputs(name)
+    prob = oracle_problem(d)
+    op = gpu_operator(d, coarse_max=8, winv_mode=hd.HD_WINV_CG)
+    rng = np.random.Generator(np.random.PCG64(15))
+    x = rng.uniform(-1, 1, prob.n)
+    y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    op.hd_apply_op(_dev(x), y)
+    assert close(_host(y), prob.apply_op(x), RTOL) <= RTOL
+    q = rng.uniform(-1, 1, prob.lat.n_l2)
+    yc = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
+    op.hd_apply_C(_dev(q), yc)
+    ref = prob.apply_C(q)
+    if np.abs(ref).max() > 0:
+        assert close(_host(yc), ref, RTOL) <= RTOL
+    _, _, Ct = approx_schur(prob)
+    mt = torch.empty(prob.lat.n_rt, dtype=torch.float64, device="cuda")
+    ct = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
+    op.hd_get_diagonals(mt, ct)
+    if np.abs(Ct).max() > 0:
+        assert close(_host(ct), Ct, RTOL) <= RTOL
+    op.close()
