@@ -35,9 +35,11 @@ METRIC = "GDOF/s of block operator apply at p=4; MINRES time-to-1e-8 resid, mixe
 NX, K, Q, PERTURB, SIGMA, ESS, SEED = 64, 4, 6, 0.15, 2.0, 63, 2304
 # measured FP64 FMA rate of this GPU model: 152 SMs x 2 FP64 FMA lanes/clk x 2 flops
 FP64_PEAK_GFLOPS_AT_MAX_CLOCK = 152 * 2 * 2 * 2.070
-# DRAM bytes (read + write) per element of k_elem_op<double,4,6,8>, from one ncu capture of the
-# 24^3 case (674.3 MB / 13,824 elements); null once the kernel changes (profiles/k_elem_op_M64_k4q6.md)
-ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6): 674.306560e6 / 13824}
+# DRAM bytes (read + write) per element of the element kernel, from one ncu capture of the 24^3
+# case of the same recipe (13,824 elements); to be dropped when the kernel changes
+ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 674.306560e6 / 13824,   # profiles/k_elem_op_M64_k4q6.md
+                                  (4, 6, "df"): 673.978624e6 / 13824}    # profiles/k_elem_op_df_M64_k4q6.md
+HBM_GBS_MEASURED = 6792.4   # MEASURED_PEAKS.json hbm_gbs (copy, read + write)
 
 
 def workload(n=NX):
@@ -60,6 +62,30 @@ def elem_flops(k, q):
     macs = 2 * interp + 9 * Q ** 3 + K ** 6
     nrt = 3 * (K + 1) * K * K
     return 2 * macs + 6 * K ** 3 + 3 * nrt + K ** 3
+
+
+def roofline(op, nx, kern_ms, emulated):
+    """Roofline object of the fused element kernel. FP64: bound by the FP64 pipe
+    ("alu", peak derived from the unit count and the maximum clock). Double-float:
+    HBM against the measured copy bandwidth (its FP32-pipe floor, 2471 G double-float
+    FMA/s measured, is about equal: both near 1.9 ms at 64^3)."""
+    flops = elem_flops(K, Q) * op.n_elem
+    abytes = elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3)
+    key = (K, Q, "df" if emulated else "f64")
+    traffic = ELEM_TRAFFIC_BYTES_PER_ELEMENT[key] * op.n_elem if key in ELEM_TRAFFIC_BYTES_PER_ELEMENT else None
+    gbs = abytes / (kern_ms * 1e-3) / 1e9
+    gflops = flops / (kern_ms * 1e-3) / 1e9
+    if emulated:
+        return {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS_MEASURED, "unit": "GB/s",
+                "frac": gbs / HBM_GBS_MEASURED, "traffic": traffic, "kernel": "k_elem_op<dfloat,double,4,6,8>",
+                "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
+                "fp64_equivalent_gflops": gflops, "fp64_equivalent_frac_of_fp64_peak": gflops / FP64_PEAK_GFLOPS_AT_MAX_CLOCK}
+    return {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "unit": "GFLOP/s",
+            "frac": gflops / FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "traffic": traffic, "kernel": "k_elem_op<double,double,4,6,8>",
+            "kernel_ms": kern_ms, "flops_per_launch": flops, "algorithmic_bytes_per_launch": abytes,
+            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 FMA probe: 1189 GFLOP/s at 2002 MHz)",
+            "hbm_frac_of_measured": gbs / HBM_GBS_MEASURED}
 
 
 def elem_bytes(k, q, n_elem, n_rt, n_l2, n_vert):
@@ -139,6 +165,34 @@ def oracle_sample(seconds=8.0, n=4):
     return prob.n * reps / el / 1e9, el, reps, prob.n
 
 
+def native_apply(args, nx, vx, vy, vz, alpha, beta, stream):
+    """The same apply with the FP64 element kernel (separate handle), for comparison."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    op = hd.Operator(nx, nx, nx, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=Q,
+                     cycle=args.cycle, fp64_emulation=0, stream=stream)
+    x = torch.from_numpy(synth.uniform(op.n, seed=SEED)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.hd_apply_op(x, y)
+    steps = max(5, args.steps // 10)
+    op.hd_profile(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.hd_apply_op(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.hd_profile(0)
+    launches, kms = op.hd_profile_read()
+    ms = e0.elapsed_time(e1) / steps
+    r = {"value": op.n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms, "steps": steps,
+         "roofline": roofline(op, nx, kms / max(1, launches), False)}
+    op.close()
+    return r
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -165,7 +219,7 @@ def run_ours(args, rank, world, dist):
     vx, vy, vz, alpha, beta = workload(nx)
     t0 = time.perf_counter()
     op = hd.Operator(nx, nx, nx, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=Q,
-                     cycle=args.cycle, stream=stream)
+                     cycle=args.cycle, fp64_emulation=int(args.fp64_emulation), stream=stream)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     n = op.n
@@ -197,19 +251,9 @@ def run_ours(args, rank, world, dist):
     ms_step = ms_total / args.steps
     value = world * n / (ms_step * 1e-3) / 1e9
     # roofline of the fused element kernel (one launch per apply)
-    flops_launch = elem_flops(K, Q) * op.n_elem
     kern_avg_ms = kern_ms / max(1, launches)
-    achieved = flops_launch / (kern_avg_ms * 1e-3) / 1e9
     clocks = clk.summary()
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "unit": "GFLOP/s",
-            "frac": achieved / FP64_PEAK_GFLOPS_AT_MAX_CLOCK,
-            "traffic": (ELEM_TRAFFIC_BYTES_PER_ELEMENT[(K, Q)] * op.n_elem
-                        if (K, Q) in ELEM_TRAFFIC_BYTES_PER_ELEMENT else None),
-            "kernel": "k_elem_op<double,4,6,8>", "kernel_ms": kern_avg_ms,
-            "flops_per_launch": flops_launch,
-            "algorithmic_bytes_per_launch": elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3),
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 FMA probe: 1189 GFLOP/s at 2002 MHz)"}
-    roof["hbm_frac_of_measured"] = roof["algorithmic_bytes_per_launch"] / (kern_avg_ms * 1e-3) / 1e9 / 6792.4
+    roof = roofline(op, nx, kern_avg_ms, bool(args.fp64_emulation))
     # e2e: the same apply through the C ABI with pinned host buffers, copies inside the region
     xh = torch.from_numpy(synth.uniform(n, seed=SEED)).pin_memory()
     yh = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -224,17 +268,21 @@ def run_ours(args, rank, world, dist):
            "ms_per_step": e2e_s * 1e3}
     out = {"metric": METRIC, "value": value, "unit": "GDOF/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "f32x2" if args.fp64_emulation else "f64", "data": "synthetic",
            "config": {"workload": ("M64-perturbed" if nx == NX else "M%d-perturbed (profiling size)" % nx)
                                   + ": grad-div, %d^3 hex elements of the unit cube with interior " % nx +
                                   "vertices moved by U(-0.15h,0.15h) (seed 2304), RT_4 x Q_3 (k=4), q=6, "
                                   "alpha=1, beta=exp(2Z) per element, u.n=0 on all sides",
                       "dofs": n, "n_rt": op.n_rt, "n_l2": op.n_l2, "elements": op.n_elem,
-                      "step": "one fused FP64 block-operator apply (hd_apply_op)",
+                      "step": "one fused block-operator apply (hd_apply_op), FP64 vectors in and out; element "
+                              "kernel in " + ("double-float (FP32 pairs, FP64 parity 1e-12 in the tests)"
+                                              if args.fp64_emulation else "FP64"),
                       "l2": "inputs larger than L2 (x, y: 538 MB each; W^-1 8.6 GB; geometric factors 2.7 GB)",
                       "winv": "dense per-element inverse", "setup_s": setup_s,
                       "schur_cycle": "W" if args.cycle == 2 else "V"},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if args.fp64_emulation and not args.no_native:
+        out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
     # MINRES time to a true relative residual of 1e-8 on the same problem: FP64, and
     # mixed precision (FP32 operator and V-cycle inside an FP64 residual correction)
     if not args.no_solve:
@@ -325,6 +373,9 @@ def main():
     ap.add_argument("--solve-maxit", type=int, default=20000, help="iteration cap of the MINRES solves")
     ap.add_argument("--cycle", type=int, default=2, choices=[1, 2], help="1: V-cycle, 2: W-cycle on S~")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
+    ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
+                    help="1: element kernel in double-float (FP32 pairs, FP64 parity); 0: native FP64")
+    ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison apply")
     ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()

@@ -104,6 +104,10 @@ typedef struct {
   int32_t coarse_max;    /* at most this many cells on the coarsest level; 0 -> 512 */
   int32_t cycle;         /* 0 or 1: V-cycle; 2: W-cycle (two coarse corrections per level
                             whose coarse level is not the coarsest) */
+  int32_t fp64_emulation;/* 0: the element kernel computes in FP64; 1: in double-float (pairs of
+                            FP32 numbers, about 48 significant bits) on the FP32 pipe, with FP64
+                            vectors in and out and the same FP64 results to ~1e-13 relative;
+                            HD_WINV_DENSE only. Setup, lattice kernels and MINRES stay FP64. */
 } hd_problem_desc;
 
 /* MINRES options and report (Sec. 3). */

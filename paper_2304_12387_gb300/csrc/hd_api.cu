@@ -131,6 +131,14 @@ hd_status dalloc(hd_op* h, double** p, int64_t n, const char* what) {
 }
 
 hd_status elem_op(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) {
+  if (h->emul) {
+    switch (h->k) {
+      case 2: return elem_op_df_k2(h, mode, u, q, yu, yq);
+      case 3: return elem_op_df_k3(h, mode, u, q, yu, yq);
+      case 4: return elem_op_df_k4(h, mode, u, q, yu, yq);
+      case 5: return elem_op_df_k5(h, mode, u, q, yu, yq);
+    }
+  }
   switch (h->k) {
     case 2: return elem_op_k2(h, mode, u, q, yu, yq);
     case 3: return elem_op_k3(h, mode, u, q, yu, yq);
@@ -160,10 +168,20 @@ hd_status elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
   return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
 }
 
+// FP64 -> double-float (round-to-nearest hi, remainder lo): setup only
+__global__ void k_split_df(int64_t n, const double* __restrict__ a, dfloat* __restrict__ b) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double v = a[i];
+  float h = __double2float_rn(v);
+  b[i] = dfloat(h, __double2float_rn(v - (double)h));
+}
+
 void destroy_all(hd_op* h) {
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
   cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
   cudaFree(h->f_wdet); cudaFree(h->f_wgldiag);
+  cudaFree(h->x_G); cudaFree(h->x_winv); cudaFree(h->x_cscale);
   cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
   cudaFree(h->d_coarse_inv); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
   cudaFree(h->f_G); cudaFree(h->f_winv); cudaFree(h->f_cscale); cudaFree(h->f_mtinv); cudaFree(h->f_coarse_inv);
@@ -219,6 +237,9 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
   if (h->q != h->k + 1 && h->q != h->k + 2) { delete h; return HD_ERR_INVALID_ARG; }
   if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->fp64_emulation != 0 && d->fp64_emulation != 1) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->fp64_emulation == 1 && d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  h->emul = d->fp64_emulation == 1;
   h->winv_mode = d->winv_mode;
   h->tau = d->tau > 0 ? d->tau : 1.0;
   h->nu = d->nu > 0 ? d->nu : 2;
@@ -298,6 +319,19 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     }
     if (bad) { st = hd_fail(h, HD_ERR_INVALID_ARG, "inverted element (det J <= 0)"); break; }
     if ((st = precond_setup(h)) != HD_OK) break;
+    if (h->emul) {
+      const int64_t ng = E * 6 * nq, nw = E * nl2 * nl2;
+      if (cudaMalloc(&h->x_G, sizeof(dfloat) * (ng > 0 ? ng : 1)) != cudaSuccess ||
+          cudaMalloc(&h->x_winv, sizeof(dfloat) * (nw > 0 ? nw : 1)) != cudaSuccess ||
+          cudaMalloc(&h->x_cscale, sizeof(dfloat) * (E > 0 ? E : 1)) != cudaSuccess) {
+        st = hd_fail(h, HD_ERR_OOM, "double-float copies");
+        break;
+      }
+      if (ng > 0) k_split_df<<<(unsigned)((ng + 255) / 256), 256, 0, s>>>(ng, h->d_G, h->x_G);
+      if (nw > 0) k_split_df<<<(unsigned)((nw + 255) / 256), 256, 0, s>>>(nw, h->d_winv, h->x_winv);
+      if (E > 0) k_split_df<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, h->d_cscale, h->x_cscale);
+      if (cudaGetLastError() != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "double-float split"); break; }
+    }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = hd_cuda_check(h, e, "setup"); break; }
   } while (0);

@@ -6,6 +6,7 @@
 #include <string>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "hdivsp.h"
 
 #define HD_MAXK 5
@@ -88,6 +89,12 @@ struct hd_op {
   double* d_coarse_inv = nullptr;  // dense inverse of the coarsest level (or of A + s 11^T)
   int coarse_n = 0;
   std::vector<LevelT<double>> lv;
+
+  // double-float copies for the emulated-FP64 element kernel (fp64_emulation = 1)
+  bool emul = false;
+  dfloat* x_G = nullptr;
+  dfloat* x_winv = nullptr;
+  dfloat* x_cscale = nullptr;
 
   // FP32 copies for the mixed-precision inner solve
   float* f_G = nullptr;

@@ -11,6 +11,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
+#include "dfloat.cuh"
 #include "hd_internal.h"
 
 namespace hdk {
@@ -24,12 +27,17 @@ struct TabT {
 };
 
 template <typename T>
+inline T tab_cast(double v) { return (T)v; }
+template <>
+inline dfloat tab_cast<dfloat>(double v) { return df_split_host(v); }
+
+template <typename T>
 inline TabT<T> make_tab(const ElemTables& t) {
   TabT<T> o;
-  for (int i = 0; i < HD_MAXQ * (HD_MAXK + 1); ++i) o.BI[i] = (T)t.BI[i];
-  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BH[i] = (T)t.BH[i];
-  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BG[i] = (T)t.BG[i];
-  for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.TT[i] = (T)t.TT[i];
+  for (int i = 0; i < HD_MAXQ * (HD_MAXK + 1); ++i) o.BI[i] = tab_cast<T>(t.BI[i]);
+  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BH[i] = tab_cast<T>(t.BH[i]);
+  for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BG[i] = tab_cast<T>(t.BG[i]);
+  for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.TT[i] = tab_cast<T>(t.TT[i]);
   return o;
 }
 
@@ -328,19 +336,50 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
 // identity); otherwise nothing. y_u receives one atomic add per element and
 // face: a shared face gets exactly two addends on a zeroed vector, so the
 // result does not depend on their order.
-#ifndef HD_ELEM_THREADS
-#define HD_ELEM_THREADS 256
+// Launch configuration per arithmetic type (elements per CTA, threads per CTA),
+// measured on GB300 at k = 4: FP64 is bound by its pipe and prefers 8/256;
+// double-float is latency-bound and gains from more resident warps (8/512);
+// FP32 is HBM-bound and prefers 4/256. The HD_*_EB / HD_*_THREADS macros
+// override them for tuning builds.
+#ifndef HD_F64_EB
+#define HD_F64_EB 8
 #endif
-#ifndef HD_ELEM_EB
-#define HD_ELEM_EB 8
+#ifndef HD_F64_THREADS
+#define HD_F64_THREADS 256
 #endif
+#ifndef HD_DF_EB
+#define HD_DF_EB 8
+#endif
+#ifndef HD_DF_THREADS
+#define HD_DF_THREADS 512
+#endif
+#ifndef HD_F32_EB
+#define HD_F32_EB 4
+#endif
+#ifndef HD_F32_THREADS
+#define HD_F32_THREADS 256
+#endif
+template <typename T>
+struct ElemCfg {
+  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS;
+};
+template <>
+struct ElemCfg<dfloat> {
+  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS;
+};
+template <>
+struct ElemCfg<float> {
+  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS;
+};
 
-template <typename T, int K, int Q, int EB>
-__global__ void __launch_bounds__(HD_ELEM_THREADS)
+// T: arithmetic type (double, float or dfloat); IO: type of the vectors in HBM
+// (double for double and dfloat, float for float).
+template <typename T, typename IO, int K, int Q, int EB>
+__global__ void __launch_bounds__(ElemCfg<T>::THREADS)
 k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem,
           const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
-          const CgArgs<T> cg, const T* __restrict__ u, const T* __restrict__ q, T* __restrict__ yu,
-          T* __restrict__ yq) {
+          const CgArgs<T> cg, const IO* __restrict__ u, const IO* __restrict__ q, IO* __restrict__ yu,
+          IO* __restrict__ yq) {
   using S = Sizes<K, Q>;
   constexpr int NX1 = S::NX1, NRT = S::NRT, NL2 = S::NL2, NQ = S::NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -363,7 +402,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
         bool ess;
         int g = rt_global<K>(L, ex, ey, ez, n, ess);
-        v = ess ? (T)0 : u[g];
+        v = ess ? (T)0 : Cvt<T, IO>::in(u[g]);
       }
       su[t] = v;
     }
@@ -375,7 +414,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       if (e < n_elem) {
         int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
         int i = a % K, j = (a / K) % K, l = a / (K * K);
-        v = q[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))];
+        v = Cvt<T, IO>::in(q[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))]);
       }
       sq[t] = v;
     }
@@ -385,7 +424,9 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   // -- L2 rows: y_q = D u - C q ------------------------------------------------
   const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
   const T* cgres = nullptr;
-  if (use_cg) cgres = local_cg<T, K, Q, EB>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
+  if constexpr (!std::is_same<T, dfloat>::value) {
+    if (use_cg) cgres = local_cg<T, K, Q, EB>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
+  }
   if (mode & (OP_D | OP_C)) {
     for (int t = tid; t < EB * NL2; t += nth) {
       int el = t / NL2, a = t - el * NL2, e = e0 + el;
@@ -407,7 +448,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       }
       int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
       int i = a % K, j = (a / K) % K, l = a / (K * K);
-      yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = v;
+      yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = Cvt<T, IO>::out(v);
     }
   }
   if (use_cg) __syncthreads();
@@ -538,15 +579,16 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
       bool ess;
       int g = rt_global<K>(L, ex, ey, ez, n, ess);
-      T v;
+      IO o;
       if (ess) {
         if (!(mode & OP_M)) continue;
-        v = u[g];
+        o = u[g];
       } else {
-        v = (mode & OP_M) ? su[t] : (T)0;
+        T v = (mode & OP_M) ? su[t] : (T)0;
         if (mode & OP_DT) v += dt_local<T, K>(sq + el * NL2, n);
+        o = Cvt<T, IO>::out(v);
       }
-      atomicAdd(yu + g, v);
+      atomicAdd(yu + g, o);
     }
   }
 }
@@ -742,18 +784,13 @@ __global__ void k_diag_tensor(const ElemTables tab, const int n_elem, const bool
   out[t] = s;
 }
 
-template <int K, int Q>
-constexpr int elem_eb() {
-  return HD_ELEM_EB;
-}
-
-template <typename T, int K, int Q>
+template <typename T, typename IO, int K, int Q>
 hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
-                      const T* u, const T* q, T* yu, T* yq) {
-  constexpr int EB = elem_eb<K, Q>();
+                      const IO* u, const IO* q, IO* yu, IO* yq) {
+  constexpr int EB = ElemCfg<T>::EB;
   using S = Sizes<K, Q>;
   size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
-  auto kern = k_elem_op<T, K, Q, EB>;
+  auto kern = k_elem_op<T, IO, K, Q, EB>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -764,8 +801,8 @@ hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs
   int blocks = (int)((h->n_elem + EB - 1) / EB);
   prof_mark(h, true);
   if (blocks > 0)
-    kern<<<blocks, HD_ELEM_THREADS, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, cg, u, q, yu,
-                                                       yq);
+    kern<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, cg, u, q,
+                                                           yu, yq);
   prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;
@@ -807,6 +844,8 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
 #define HD_DECLARE_K(KK)                                                                          \
   hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,       \
                           double* yq);                                                            \
+  hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,    \
+                             double* yq);                                                         \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,      \
                               float* yq);                                                         \
   hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad);
@@ -823,17 +862,28 @@ HD_DECLARE_K(5)
   hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) { \
     hdk::CgArgs<double> cg{h->winv_mode == HD_WINV_CG ? h->d_wdet : nullptr, h->d_wgldiag, 40, 1e-28};     \
     if (h->q == KK + 1)                                                                                   \
-      return hdk::run_elem_op<double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, yu,  \
-                                                  yq);                                                    \
-    return hdk::run_elem_op<double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, yu, yq); \
+      return hdk::run_elem_op<double, double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, \
+                                                          q, yu, yq);                                     \
+    return hdk::run_elem_op<double, double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, \
+                                                        yu, yq);                                          \
+  }                                                                                                       \
+  hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,            \
+                             double* yq) {                                                                \
+    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0)};                                               \
+    if (h->q == KK + 1)                                                                                   \
+      return hdk::run_elem_op<dfloat, double, KK, KK + 1>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, \
+                                                          q, yu, yq);                                     \
+    return hdk::run_elem_op<dfloat, double, KK, KK + 2>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, q, \
+                                                        yu, yq);                                          \
   }                                                                                                       \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,              \
                               float* yq) {                                                                \
     hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f};                     \
     if (h->q == KK + 1)                                                                                   \
-      return hdk::run_elem_op<float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, yu,   \
-                                                 yq);                                                     \
-    return hdk::run_elem_op<float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, yu, yq); \
+      return hdk::run_elem_op<float, float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, \
+                                                        yu, yq);                                          \
+    return hdk::run_elem_op<float, float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q,  \
+                                                      yu, yq);                                            \
   }                                                                                                       \
   hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad) {                                 \
     if (h->q == KK + 1) return hdk::run_elem_setup<KK, KK + 1>(h, bcoef, d_bad);                          \

@@ -43,3 +43,29 @@ def test_fullsize_sampled_rows(name):
     scale = np.abs(ref).max()
     assert np.abs(got - ref).max() <= 1e-12 * scale, (name, np.abs(got - ref).max() / scale)
     op.close()
+
+
+def test_fullsize_m64_fp64_emulation():
+    """The metric workload with the double-float element kernel, sampled rows at 1e-12."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.sampled import SampledOperator
+    d = fullsize("m64")
+    op = hd.Operator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                     kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"], affine=d["affine"], fp64_emulation=1,
+                     stream=torch.cuda.current_stream())
+    rng = np.random.Generator(np.random.PCG64(78))
+    x = rng.uniform(-1, 1, op.n)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xd)
+    op.hd_apply_op(xd, y)
+    torch.cuda.synchronize()
+    so = SampledOperator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                         kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"])
+    rt = np.concatenate([rng.choice(op.n_rt, 16, replace=False), so.ess[:2], [0, op.n_rt - 1]])
+    l2 = np.concatenate([rng.choice(op.n_l2, 8, replace=False), [0, op.n_l2 - 1]])
+    ref = np.concatenate([so.rt_rows(x, rt), so.l2_rows(x, l2)])
+    got = y[torch.from_numpy(np.concatenate([rt, op.n_rt + l2])).cuda()].cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+    op.close()

@@ -186,3 +186,30 @@ def test_local_cg_winv_mode(name):
     if np.abs(Ct).max() > 0:
         assert close(_host(ct), Ct, RTOL) <= RTOL
     op.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_emulation_mode(name):
+    """Element kernel in double-float arithmetic (FP32 pairs on the FP32 pipe) with
+    FP64 vectors in and out: the same FP64 parity bar as the native kernel."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = inputs(name)
+    prob = oracle_problem(d)
+    op = gpu_operator(d, coarse_max=8, fp64_emulation=1)
+    rng = np.random.Generator(np.random.PCG64(16))
+    x = rng.uniform(-1, 1, prob.n)
+    y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    op.hd_apply_op(_dev(x), y)
+    assert close(_host(y), prob.apply_op(x), RTOL) <= RTOL
+    u = rng.uniform(-1, 1, prob.lat.n_rt)
+    ya = torch.empty(prob.lat.n_rt, dtype=torch.float64, device="cuda")
+    op.hd_apply_A(_dev(u), ya)
+    assert close(_host(ya), prob.apply_A(u), RTOL) <= RTOL
+    q = rng.uniform(-1, 1, prob.lat.n_l2)
+    yc = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
+    op.hd_apply_C(_dev(q), yc)
+    ref = prob.apply_C(q)
+    if np.abs(ref).max() > 0:
+        assert close(_host(yc), ref, RTOL) <= RTOL
+    op.close()
