@@ -1,5 +1,5 @@
 // Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32
-// numbers with |lo| <= ulp(hi)/2, about 48 significant bits. On this GPU the FP32
+// numbers with |lo| < ulp(hi), about 48 significant bits. On this GPU the FP32
 // pipe issues 64 lanes for every FP64 lane, so the element contractions of the
 // FP64 operator run several times faster in double-float while staying within
 // the FP64 parity tolerance. The error-free transformations are the classical
@@ -96,6 +96,17 @@ inline dfloat df_split_host(double v) {
   return dfloat(h, (float)(v - (double)h));
 }
 
+// FP32 -> FP64 exactly with integer operations (zero and FP32 subnormals map to 0,
+// inf/NaN keep their class)
+__device__ __forceinline__ double f2d_exact(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint64_t s = (uint64_t)(b >> 31) << 63;
+  const uint32_t e = (b >> 23) & 0xFF, m = b & 0x7FFFFFu;
+  if (e == 0) return __longlong_as_double((long long)s);
+  if (e == 255) return __longlong_as_double((long long)(s | (0x7FFull << 52) | ((uint64_t)m << 29)));
+  return __longlong_as_double((long long)(s | ((uint64_t)(e - 127 + 1023) << 52) | ((uint64_t)m << 29)));
+}
+
 // element-type conversions used by the templated element kernels
 template <typename T, typename IO>
 struct Cvt;
@@ -108,6 +119,13 @@ template <>
 struct Cvt<float, float> {
   __device__ static float in(float v) { return v; }
   __device__ static float out(float v) { return v; }
+};
+// FP32 arithmetic with FP64 vectors (the inner operator of the mixed-precision
+// solve): truncation to 24 bits on the way in, exact on the way out
+template <>
+struct Cvt<float, double> {
+  __device__ static float in(double v) { return df_from_double(v).hi; }
+  __device__ static double out(float v) { return f2d_exact(v); }
 };
 template <>
 struct Cvt<dfloat, double> {

@@ -158,6 +158,17 @@ hd_status elem_op_f32(hd_op* h, int mode, const float* u, const float* q, float*
   return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
 }
 
+// FP32 arithmetic, FP64 vectors (inner operator of the mixed-precision solve)
+hd_status elem_op_f32io64(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) {
+  switch (h->k) {
+    case 2: return elem_op_f32io64_k2(h, mode, u, q, yu, yq);
+    case 3: return elem_op_f32io64_k3(h, mode, u, q, yu, yq);
+    case 4: return elem_op_f32io64_k4(h, mode, u, q, yu, yq);
+    case 5: return elem_op_f32io64_k5(h, mode, u, q, yu, yq);
+  }
+  return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "k not supported");
+}
+
 hd_status elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
   switch (h->k) {
     case 2: return elem_setup_k2(h, bcoef, d_bad);
@@ -212,6 +223,12 @@ void prof_mark(hd_op* h, bool before) {
 hd_status apply_op_internal(hd_op* h, const double* x, double* y) {
   HD_CK(h, cudaMemsetAsync(y, 0, sizeof(double) * h->n_rt, h->stream));
   return elem_op(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
+}
+
+// y = AA x with the FP32 element kernel reading and writing FP64 vectors
+hd_status apply_op_mixed_internal(hd_op* h, const double* x, double* y) {
+  HD_CK(h, cudaMemsetAsync(y, 0, sizeof(double) * h->n_rt, h->stream));
+  return elem_op_f32io64(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
 }
 
 hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y) {

@@ -120,6 +120,18 @@ struct hd_op {
   // capture of the Lanczos vectors' L2 parts during a solve (training data)
   double* cap_buf = nullptr;
   int cap_every = 1, cap_max = 0, cap_count = 0;
+  // V/W-cycle replayed as CUDA graphs (captured once per input/output pair) on a
+  // private stream ordered after/before the handle's stream with events
+  struct VcGraph {
+    const void* b;
+    void* x;
+    int f32;
+    cudaGraphExec_t exec;
+  };
+  std::vector<VcGraph> vc_graphs;
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t gev[2] = {nullptr, nullptr};
+  bool graphs_off = false;
   // profiling of the fused element kernel
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)

@@ -848,6 +848,8 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
                              double* yq);                                                         \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,      \
                               float* yq);                                                         \
+  hd_status elem_op_f32io64_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, \
+                                  double* yq);                                                    \
   hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad);
 
 HD_DECLARE_K(2)
@@ -884,6 +886,15 @@ HD_DECLARE_K(5)
                                                         yu, yq);                                          \
     return hdk::run_elem_op<float, float, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q,  \
                                                       yu, yq);                                            \
+  }                                                                                                       \
+  hd_status elem_op_f32io64_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,       \
+                                  double* yq) {                                                           \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f};                     \
+    if (h->q == KK + 1)                                                                                   \
+      return hdk::run_elem_op<float, double, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u,  \
+                                                         q, yu, yq);                                      \
+    return hdk::run_elem_op<float, double, KK, KK + 2>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, \
+                                                       yu, yq);                                           \
   }                                                                                                       \
   hd_status elem_setup_k##KK(hd_op* h, const double* bcoef, int* d_bad) {                                 \
     if (h->q == KK + 1) return hdk::run_elem_setup<KK, KK + 1>(h, bcoef, d_bad);                          \

@@ -256,6 +256,7 @@ hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, doub
 
 hd_status apply_op_internal(hd_op* h, const double* x, double* y);
 hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y);
+hd_status apply_op_mixed_internal(hd_op* h, const double* x, double* y);
 
 namespace {
 
@@ -332,13 +333,7 @@ hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p) {
 // y = AA v with the operator in the inner precision (vectors stay FP64)
 static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
   if (!f32) return apply_op_internal(h, v, y);
-  const int64_t n = h->n_rt + h->n_l2;
-  k_d2f<<<nblk(n), TPB, 0, h->stream>>>(n, v, h->fv[0]);
-  hd_status st = apply_op_f32_internal(h, h->fv[0], h->fv[1]);
-  if (st != HD_OK) return st;
-  k_f2d<<<nblk(n), TPB, 0, h->stream>>>(n, h->fv[1], y);
-  HD_LAUNCH_CK(h, "inner apply");
-  return HD_OK;
+  return apply_op_mixed_internal(h, v, y);  // FP32 arithmetic, FP64 vectors
 }
 
 // z_q = V-cycle(r_q) in the inner precision, then the zero-mean projection if singular

@@ -292,19 +292,37 @@ __global__ void k_vc_coarse(int n, const double* __restrict__ Ainv, const T* __r
   if (lane == 0) x[i] = (T)s;
 }
 
-// z -= mean(z): single block, deterministic fixed-order reduction
+// z -= mean(z): deterministic two-pass reduction (fixed per-block chunks, fixed-order final pass)
+constexpr int MEAN_BLOCKS = 512;
 template <typename T>
-__global__ void k_mean(int64_t n, const T* __restrict__ z, double* __restrict__ out) {
-  __shared__ double red[1024];
+__global__ void k_sum_partial(int64_t n, const T* __restrict__ z, double* __restrict__ part) {
+  __shared__ double red[256];
+  int64_t chunk = (n + MEAN_BLOCKS - 1) / MEAN_BLOCKS;
+  int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s += (double)z[i];
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += (double)z[i];
   red[threadIdx.x] = s;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
     __syncthreads();
   }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+__global__ void k_mean_final(int64_t n, const double* __restrict__ part, double* __restrict__ out) {
+  __shared__ double red[MEAN_BLOCKS];
+  red[threadIdx.x] = part[threadIdx.x];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
   if (threadIdx.x == 0) out[0] = red[0] / (double)n;
+}
+template <typename T>
+void launch_mean(hd_op* h, int64_t n, const T* z, double* part_and_out) {
+  k_sum_partial<T><<<MEAN_BLOCKS, 256, 0, h->stream>>>(n, z, part_and_out + 1);
+  k_mean_final<<<1, MEAN_BLOCKS, 0, h->stream>>>(n, part_and_out + 1, part_and_out);
 }
 template <typename T>
 __global__ void k_sub_mean(int64_t n, T* __restrict__ z, const double* __restrict__ mean) {
@@ -366,6 +384,61 @@ const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse
     cur = o2;
   }
   return cur;
+}
+
+// One V/W-cycle on level 0 from b into x, replayed from a CUDA graph captured on
+// first use for this (b, x) pair: a cycle at 64^3 is ~200 small launches, most of
+// them on coarse levels where launch overhead, not the kernels, sets the time.
+template <typename T>
+hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x, int f32) {
+  if (!h->graphs_off && !h->gstream) {
+    if (cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      h->graphs_off = true;
+    }
+  }
+  if (h->graphs_off) {
+    vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+    HD_LAUNCH_CK(h, "vcycle");
+    return HD_OK;
+  }
+  cudaGraphExec_t exec = nullptr;
+  for (auto& g : h->vc_graphs)
+    if (g.b == (const void*)b && g.x == (void*)x && g.f32 == f32) exec = g.exec;
+  if (!exec) {
+    cudaStream_t saved = h->stream;
+    h->stream = h->gstream;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+      e = cudaStreamEndCapture(h->gstream, &graph);
+    }
+    h->stream = saved;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      // capture unavailable here: launch directly from now on
+      cudaGetLastError();
+      h->graphs_off = true;
+      vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+      HD_LAUNCH_CK(h, "vcycle");
+      return HD_OK;
+    }
+    if (h->vc_graphs.size() >= 8) {
+      cudaGraphExecDestroy(h->vc_graphs.front().exec);
+      h->vc_graphs.erase(h->vc_graphs.begin());
+    }
+    h->vc_graphs.push_back({(const void*)b, (void*)x, f32, exec});
+  }
+  HD_CK(h, cudaEventRecord(h->gev[0], h->stream));
+  HD_CK(h, cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+  HD_CK(h, cudaGraphLaunch(exec, h->gstream));
+  HD_CK(h, cudaEventRecord(h->gev[1], h->gstream));
+  HD_CK(h, cudaStreamWaitEvent(h->stream, h->gev[1], 0));
+  return HD_OK;
 }
 
 template <typename T>
@@ -572,6 +645,11 @@ hd_status setup_f32(hd_op* h) {
 }
 
 void precond_free(hd_op* h) {
+  for (auto& g : h->vc_graphs) cudaGraphExecDestroy(g.exec);
+  h->vc_graphs.clear();
+  if (h->gev[0]) cudaEventDestroy(h->gev[0]);
+  if (h->gev[1]) cudaEventDestroy(h->gev[1]);
+  if (h->gstream) cudaStreamDestroy(h->gstream);
   for (size_t l = 0; l < h->lv.size(); ++l) {
     if (l == 0) cudaFree(h->lv[0].wx);
     free_level<double>(h->lv[l], l > 0);
@@ -590,9 +668,7 @@ hd_status schur_apply(hd_op* h, const double* x, double* y) {
 
 hd_status vcycle_apply(hd_op* h, const double* b, double* x) {
   if (h->n_l2 == 0) return HD_OK;
-  vcycle_level<double>(h, h->lv, h->d_coarse_inv, 0, b, x);
-  HD_LAUNCH_CK(h, "vcycle");
-  return HD_OK;
+  return vcycle_graphed<double>(h, h->lv, b, x, 0);
 }
 
 template <typename T>
@@ -600,9 +676,10 @@ static hd_status precond_apply_t(hd_op* h, const T* r, T* z, const T* mtinv, std
                                  const double* cinv) {
   if (h->n_rt > 0) k_diag_scale<T><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->n_rt, mtinv, r, z);
   if (h->n_l2 > 0) {
-    vcycle_level<T>(h, lv, cinv, 0, r + h->n_rt, z + h->n_rt);
+    hd_status sv = vcycle_graphed<T>(h, lv, r + h->n_rt, z + h->n_rt, sizeof(T) == 4);
+    if (sv != HD_OK) return sv;
     if (h->singular) {
-      k_mean<T><<<1, 1024, 0, h->stream>>>(h->n_l2, z + h->n_rt, h->d_red);
+      launch_mean<T>(h, h->n_l2, z + h->n_rt, h->d_red);
       k_sub_mean<T><<<nblk(h->n_l2), TPB, 0, h->stream>>>(h->n_l2, z + h->n_rt, h->d_red);
     }
   }
@@ -665,9 +742,7 @@ hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x) {
   if (h->n_l2 == 0) return HD_OK;
   hd_status st = setup_f32(h);
   if (st != HD_OK) return st;
-  vcycle_level<float>(h, h->lvf, h->d_coarse_inv, 0, b, x);
-  HD_LAUNCH_CK(h, "vcycle f32");
-  return HD_OK;
+  return vcycle_graphed<float>(h, h->lvf, b, x, 1);
 }
 
 // z_u = r_u / (tau M~) on the RT part (identity on essential dofs)
@@ -680,7 +755,7 @@ hd_status diag_scale(hd_op* h, const double* r, double* z) {
 // z -= mean(z) on an L2 vector (pure-Neumann Darcy: the Schur complement's
 // kernel is the constants; Sec. 4.2 orthogonalises after every V-cycle).
 hd_status project_mean(hd_op* h, double* z) {
-  k_mean<double><<<1, 1024, 0, h->stream>>>(h->n_l2, z, h->d_red);
+  launch_mean<double>(h, h->n_l2, z, h->d_red);
   k_sub_mean<double><<<nblk(h->n_l2), TPB, 0, h->stream>>>(h->n_l2, z, h->d_red);
   HD_LAUNCH_CK(h, "project_mean");
   return HD_OK;

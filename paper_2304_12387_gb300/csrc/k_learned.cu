@@ -36,11 +36,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ double block_sum_d(double v, double* sh) {
   v = warp_sum_d(v);
   int w = threadIdx.x >> 5, ln = threadIdx.x & 31;
@@ -477,12 +472,6 @@ hd_status lalloc(hd_op* h, T** p, int64_t n) {
   return HD_OK;
 }
 
-hd_status net_sumsq(hd_op* h, const double* a, const float* w, int64_t n, double* out) {
-  k_sumsq_partial<double><<<RED_BLOCKS, TPB, 0, h->stream>>>(n, a, w, h->net->red);
-  k_final_sum<<<1, RED_BLOCKS, 0, h->stream>>>(h->net->red, out);
-  HD_LAUNCH_CK(h, "sumsq");
-  return HD_OK;
-}
 hd_status net_sumsq_f(hd_op* h, const float* a, int64_t n, double* out) {
   k_sumsq_partial<float><<<RED_BLOCKS, TPB, 0, h->stream>>>(n, a, nullptr, h->net->red);
   k_final_sum<<<1, RED_BLOCKS, 0, h->stream>>>(h->net->red, out);
