@@ -51,6 +51,16 @@ struct CgArgs {
   T tol2;            // stop when ||r||^2 <= tol2 ||b||^2 (per element)
 };
 
+// Sum of products as one FMA chain (one type per arithmetic: double, float or
+// double-float with its renormalised FMA).
+template <typename T>
+struct Acc {
+  T s;
+  __device__ __forceinline__ void init(T b, T x) { s = b * x; }
+  __device__ __forceinline__ void add(T b, T x) { s = fma(b, x, s); }
+  __device__ __forceinline__ T get() const { return s; }
+};
+
 // out[o*SO] = sum_i B[o*NI + i] in[i*SI], o < NO   (B row-major NO x NI)
 template <typename T, int NI, int NO, int SI, int SO>
 __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict__ out, const T* B) {
@@ -59,10 +69,11 @@ __device__ __forceinline__ void contract(const T* __restrict__ in, T* __restrict
   for (int i = 0; i < NI; ++i) x[i] = in[i * SI];
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
-    T s = B[o * NI] * x[0];
+    Acc<T> s;
+    s.init(B[o * NI], x[0]);
 #pragma unroll
-    for (int i = 1; i < NI; ++i) s = fma(B[o * NI + i], x[i], s);
-    out[o * SO] = s;
+    for (int i = 1; i < NI; ++i) s.add(B[o * NI + i], x[i]);
+    out[o * SO] = s.get();
   }
 }
 
@@ -74,10 +85,11 @@ __device__ __forceinline__ void contractT(const T* __restrict__ in, T* __restric
   for (int i = 0; i < NI; ++i) x[i] = in[i * SI];
 #pragma unroll
   for (int o = 0; o < NO; ++o) {
-    T s = B[o] * x[0];
+    Acc<T> s;
+    s.init(B[o], x[0]);
 #pragma unroll
-    for (int i = 1; i < NI; ++i) s = fma(B[i * NO + o], x[i], s);
-    out[o * SO] = s;
+    for (int i = 1; i < NI; ++i) s.add(B[i * NO + o], x[i]);
+    out[o * SO] = s.get();
   }
 }
 
@@ -359,21 +371,45 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
 #ifndef HD_F32_THREADS
 #define HD_F32_THREADS 256
 #endif
+#ifndef HD_F64_PREFETCH
+#define HD_F64_PREFETCH 0
+#endif
+#ifndef HD_DF_PREFETCH
+#define HD_DF_PREFETCH 0
+#endif
+#ifndef HD_F32_PREFETCH
+#define HD_F32_PREFETCH 3
+#endif
+// PREFETCH: bit 1 asks the copy engine to stage the CTA's contiguous G block,
+// bit 2 its W^-1 block, in L2 as the CTA starts (cp.async.bulk.prefetch). The
+// HBM-bound FP32 kernel gains about 10 % at k = 4; the FP64 and double-float
+// kernels, whose loads already overlap their arithmetic, lose.
 template <typename T>
 struct ElemCfg {
-  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS;
+  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH;
 };
 template <>
 struct ElemCfg<dfloat> {
-  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS;
+  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH;
 };
 template <>
 struct ElemCfg<float> {
-  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS;
+  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH;
 };
 
-// T: arithmetic type (double, float or dfloat); IO: type of the vectors in HBM
-// (double for double and dfloat, float for float).
+// L2 prefetch of [p, p + bytes) in 16 KB pieces, one piece per lane; the range
+// is trimmed to whole 16-byte units and skipped when p is not 16-byte aligned.
+__device__ __forceinline__ void prefetch_l2_block(const void* p, size_t bytes, int lane) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+  if (a & 15) return;
+  bytes &= ~(size_t)15;
+  constexpr size_t CH = 16384;
+  for (size_t off = (size_t)lane * CH; off < bytes; off += 32 * CH) {
+    const uint32_t sz = (uint32_t)(bytes - off < CH ? bytes - off : CH);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a + off), "r"(sz) : "memory");
+  }
+}
+
 template <typename T, typename IO, int K, int Q, int EB>
 __global__ void __launch_bounds__(ElemCfg<T>::THREADS)
 k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem,
@@ -392,6 +428,16 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   const int tid = threadIdx.x, nth = blockDim.x;
   const bool needu = (mode & (OP_M | OP_D)) != 0;
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
+  const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
+  if constexpr (ElemCfg<T>::PREFETCH != 0) {
+    if (tid < 32 && e0 < n_elem) {
+      const int ne = (n_elem - e0 < EB) ? n_elem - e0 : EB;
+      if ((ElemCfg<T>::PREFETCH & 1) && (mode & OP_M))
+        prefetch_l2_block(G + (size_t)e0 * 6 * NQ, (size_t)ne * 6 * NQ * sizeof(T), tid);
+      if ((ElemCfg<T>::PREFETCH & 2) && (mode & OP_C) && !use_cg)
+        prefetch_l2_block(winv + (size_t)e0 * NL2 * NL2, (size_t)ne * NL2 * NL2 * sizeof(T), tid);
+    }
+  }
 
   // -- gather -----------------------------------------------------------------
   if (needu) {
@@ -422,33 +468,37 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   __syncthreads();
 
   // -- L2 rows: y_q = D u - C q ------------------------------------------------
-  const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
   const T* cgres = nullptr;
   if constexpr (!std::is_same<T, dfloat>::value) {
     if (use_cg) cgres = local_cg<T, K, Q, EB>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
   }
+  // one L2 row (element-local cell t), given its D u part v
+  auto l2_row = [&](int t, T v) {
+    const int el = t / NL2, a = t - el * NL2, e = e0 + el;
+    if (mode & OP_C) {
+      T s = (T)0;
+      if (use_cg) {
+        s = cgres[el * S::R1 + a];
+      } else {
+        const T* W = winv + (size_t)e * NL2 * NL2;
+        const T* qe = sq + el * NL2;
+        Acc<T> acc;
+        acc.init(W[a], qe[0]);
+#pragma unroll 8
+        for (int b = 1; b < NL2; ++b) acc.add(W[b * NL2 + a], qe[b]);
+        s = acc.get();
+      }
+      s *= cscale[e];
+      v = (mode & OP_CPOS) ? v + s : v - s;
+    }
+    int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+    int i = a % K, j = (a / K) % K, l = a / (K * K);
+    yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = Cvt<T, IO>::out(v);
+  };
   if (mode & (OP_D | OP_C)) {
     for (int t = tid; t < EB * NL2; t += nth) {
-      int el = t / NL2, a = t - el * NL2, e = e0 + el;
-      if (e >= n_elem) continue;
-      T v = (T)0;
-      if (mode & OP_D) v = div_local<T, K>(su + el * NRT, a);
-      if (mode & OP_C) {
-        T s = (T)0;
-        if (use_cg) {
-          s = cgres[el * S::R1 + a];
-        } else {
-          const T* W = winv + (size_t)e * NL2 * NL2;
-          const T* qe = sq + el * NL2;
-#pragma unroll 8
-          for (int b = 0; b < NL2; ++b) s = fma(W[b * NL2 + a], qe[b], s);
-        }
-        s *= cscale[e];
-        v = (mode & OP_CPOS) ? v + s : v - s;
-      }
-      int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
-      int i = a % K, j = (a / K) % K, l = a / (K * K);
-      yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = Cvt<T, IO>::out(v);
+      if (e0 + t / NL2 >= n_elem) continue;
+      l2_row(t, (mode & OP_D) ? div_local<T, K>(su + (t / NL2) * NRT, t % NL2) : (T)0);
     }
   }
   if (use_cg) __syncthreads();
@@ -513,9 +563,13 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       T g00 = g[0], g01 = g[NQ], g02 = g[2 * NQ], g11 = g[3 * NQ], g12 = g[4 * NQ], g22 = g[5 * NQ];
       T* U = s1 + el * S::R1 + p;
       T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
-      U[0] = fma(g00, ux, fma(g01, uy, g02 * uz));
-      U[NQ] = fma(g01, ux, fma(g11, uy, g12 * uz));
-      U[2 * NQ] = fma(g02, ux, fma(g12, uy, g22 * uz));
+      Acc<T> v0, v1, v2;
+      v0.init(g02, uz); v0.add(g01, uy); v0.add(g00, ux);
+      v1.init(g12, uz); v1.add(g11, uy); v1.add(g01, ux);
+      v2.init(g22, uz); v2.add(g12, uy); v2.add(g02, ux);
+      U[0] = v0.get();
+      U[NQ] = v1.get();
+      U[2 * NQ] = v2.get();
     }
     __syncthreads();
     // -- transposed interpolation: stage C^T (z) -------------------------------

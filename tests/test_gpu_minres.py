@@ -95,3 +95,39 @@ def test_wcycle_matches_oracle(name):
     assert st == 0 and abs(info["iterations"] - ir["iterations"]) <= 1, (info, ir["iterations"])
     assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-8 * np.linalg.norm(xr)
     op.close()
+
+
+@pytest.mark.parametrize("name,cycle", [("gd_k4_ragged", 2), ("darcy_k3", 1), ("darcy_neumann", 2), ("c1", 1)])
+def test_fp64_emulation_solver_matches_oracle(name, cycle):
+    """Double-float element kernel and V/W-cycle (fp64_emulation = 1): the V-cycle
+    and preconditioner applies at the FP64 tolerances, MINRES iterations within one
+    of the oracle and the solution within 1e-8."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle.minres import minres
+    from oracle.precond import BlockPrec
+    d = inputs(name)
+    prob = oracle_problem(d)
+    bp = BlockPrec(prob, nu=2, coarse_max=8, cycle=cycle)
+    op = gpu_operator(d, coarse_max=8, cycle=cycle, fp64_emulation=1)
+    rng = np.random.Generator(np.random.PCG64(17))
+    r = rng.uniform(-1, 1, prob.lat.n_l2)
+    z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
+    op.hd_vcycle(torch.from_numpy(r).cuda(), z)
+    torch.cuda.synchronize()
+    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-11) <= 1e-11
+    rr = rng.uniform(-1, 1, prob.n)
+    zz = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+    op.hd_apply_prec(torch.from_numpy(rr).cuda(), zz)
+    torch.cuda.synchronize()
+    assert close(zz.cpu().numpy(), bp.apply(rr), 1e-11) <= 1e-11
+    b = rng.uniform(-1, 1, prob.n)
+    b[prob.ess] = 0.0
+    if bp.singular:
+        b[prob.lat.n_rt:] -= b[prob.lat.n_rt:].mean()
+    xr, ir = minres(prob.apply_op, bp.apply, b, rtol=1e-8, maxit=2000)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_minres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=2000, check_every=4)
+    assert st == 0 and abs(info["iterations"] - ir["iterations"]) <= 1, (info, ir["iterations"])
+    assert np.linalg.norm(x.cpu().numpy() - xr) <= 1e-8 * np.linalg.norm(xr)
+    op.close()
