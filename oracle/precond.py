@@ -14,6 +14,10 @@ V-cycle on the approximate Schur complement (Sec. 2.3-2.4).
     - levels: piecewise-constant aggregation of 2 cells per direction (a trailing
       odd cell is its own aggregate; a direction of length 1 is not coarsened),
       until at most `coarse_max` cells remain;
+    - prolongation: piecewise constant P0 on the aggregates, or, on the first
+      `sa_levels` levels when `smooth` = omega > 0, the smoothed-aggregation
+      prolongator P = (I - omega D_l1^-1 A_l) P0 (one damped l1-Jacobi step
+      applied to P0; omega = 4/3 is the customary choice);
     - Galerkin coarse operators A_{l+1} = P^T A_l P;
     - nu pre- and nu post-sweeps of l1-Jacobi (D_l1 = sum_j |A_ij|, omega = 1),
       zero initial guess on every level, coarse correction added unscaled;
@@ -60,19 +64,28 @@ def aggregation(dims):
     return P, cd
 
 
+def l1_diag(A):
+    """l1-Jacobi diagonal: D_l1 = sum_j |A_ij|."""
+    return np.asarray(abs(A).sum(axis=1)).ravel()
+
+
 class VCycle:
-    def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20, cycle=1):
+    def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20, cycle=1,
+                 smooth=0.0, sa_levels=1):
         self.nu, self.singular, self.cycle = nu, singular, cycle
         self.A, self.P, self.dims, self.dl1 = [A0.tocsr()], [], [tuple(dims)], []
         while np.prod(self.dims[-1]) > coarse_max and len(self.A) < max_levels:
             P, cd = aggregation(self.dims[-1])
             if cd == self.dims[-1]:
                 break
+            if smooth and len(self.P) < sa_levels:
+                A = self.A[-1]
+                P = (P - smooth * sp.diags(1.0 / l1_diag(A)) @ (A @ P)).tocsr()
             self.P.append(P)
             self.A.append((P.T @ self.A[-1] @ P).tocsr())
             self.dims.append(cd)
         for A in self.A:
-            self.dl1.append(np.asarray(abs(A).sum(axis=1)).ravel())
+            self.dl1.append(l1_diag(A))
         Ac = self.A[-1].toarray()
         if singular:
             n = Ac.shape[0]
@@ -115,13 +128,13 @@ def is_singular(prob, Ct):
 class BlockPrec:
     """z = B^-1 r with B = diag(tau M~, S^)."""
 
-    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1):
+    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1, smooth=0.0, sa_levels=1):
         self.prob, self.tau = prob, tau
         self.S, self.Mt, self.Ct = approx_schur(prob)
         self.singular = is_singular(prob, self.Ct)
         lat = prob.lat
         self.vc = VCycle(self.S, (lat.X, lat.Y, lat.Z), nu=nu, coarse_max=coarse_max,
-                         singular=self.singular, cycle=cycle)
+                         singular=self.singular, cycle=cycle, smooth=smooth, sa_levels=sa_levels)
 
     def apply(self, r):
         nrt = self.prob.lat.n_rt
