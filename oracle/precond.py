@@ -24,6 +24,7 @@ V-cycle on the approximate Schur complement (Sec. 2.3-2.4).
     - cycle = 1 (V-cycle) or 2 (W-cycle: the coarse correction is computed
       twice, each time from the current residual, on every level whose coarse
       level is not the coarsest; above the coarsest one exact correction);
+      `w_levels` = k > 0 limits the repetition to levels 0..k-1 (V below);
     - coarsest level: dense Cholesky; when S~ is singular (pure Neumann Darcy
       with gamma = 0) it factors A + s 1 1^T with s = mean(diag A)/n;
     - singular case: the result is projected to zero mean (Sec. 4.2).
@@ -71,8 +72,8 @@ def l1_diag(A):
 
 class VCycle:
     def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20, cycle=1,
-                 smooth=0.0, sa_levels=1):
-        self.nu, self.singular, self.cycle = nu, singular, cycle
+                 smooth=0.0, sa_levels=1, w_levels=0):
+        self.nu, self.singular, self.cycle, self.w_levels = nu, singular, cycle, w_levels
         self.A, self.P, self.dims, self.dl1 = [A0.tocsr()], [], [tuple(dims)], []
         while np.prod(self.dims[-1]) > coarse_max and len(self.A) < max_levels:
             P, cd = aggregation(self.dims[-1])
@@ -103,7 +104,7 @@ class VCycle:
         x = np.zeros_like(b)
         for _ in range(self.nu):
             x = x + (b - A @ x) / d
-        repeats = self.cycle if l + 1 < len(self.A) - 1 else 1
+        repeats = self.cycle if (l + 1 < len(self.A) - 1 and (self.w_levels <= 0 or l < self.w_levels)) else 1
         for _ in range(repeats):
             r = b - A @ x
             x = x + self.P[l] @ self._cycle(l + 1, self.P[l].T @ r)
@@ -128,13 +129,14 @@ def is_singular(prob, Ct):
 class BlockPrec:
     """z = B^-1 r with B = diag(tau M~, S^)."""
 
-    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1, smooth=0.0, sa_levels=1):
+    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1, smooth=0.0, sa_levels=1, w_levels=0):
         self.prob, self.tau = prob, tau
         self.S, self.Mt, self.Ct = approx_schur(prob)
         self.singular = is_singular(prob, self.Ct)
         lat = prob.lat
         self.vc = VCycle(self.S, (lat.X, lat.Y, lat.Z), nu=nu, coarse_max=coarse_max,
-                         singular=self.singular, cycle=cycle, smooth=smooth, sa_levels=sa_levels)
+                         singular=self.singular, cycle=cycle, smooth=smooth, sa_levels=sa_levels,
+                         w_levels=w_levels)
 
     def apply(self, r):
         nrt = self.prob.lat.n_rt

@@ -38,7 +38,8 @@ class ProblemDesc(ctypes.Structure):
                 ("coef1", ctypes.POINTER(ctypes.c_double)), ("ess_mask", ctypes.c_uint32),
                 ("affine", ctypes.c_int32), ("tau", ctypes.c_double), ("winv_mode", ctypes.c_int32),
                 ("nu", ctypes.c_int32), ("coarse_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
-                ("fp64_emulation", ctypes.c_int32)]
+                ("fp64_emulation", ctypes.c_int32), ("smooth_levels", ctypes.c_int32),
+                ("w_levels", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -164,7 +165,7 @@ class Operator:
 
     def __init__(self, nx, ny, nz, k, vx, vy, vz, coef0, coef1, kind=HD_GRAD_DIV, ess_mask=0, q=0,
                  affine=False, tau=0.0, winv_mode=HD_WINV_DENSE, nu=0, coarse_max=0, cycle=1,
-                 fp64_emulation=0, stream=None):
+                 fp64_emulation=0, smooth_levels=0, w_levels=0, stream=None):
         E = nx * ny * nz
         self._keep = []
         arrs = []
@@ -176,7 +177,8 @@ class Operator:
             self._keep.append(a)
             arrs.append(p)
         d = ProblemDesc(kind, nx, ny, nz, k, q, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], ess_mask,
-                        int(affine), tau, winv_mode, nu, coarse_max, cycle, int(fp64_emulation))
+                        int(affine), tau, winv_mode, nu, coarse_max, cycle, int(fp64_emulation),
+                        int(smooth_levels), int(w_levels))
         h = ctypes.c_void_p()
         st = lib().hd_create(ctypes.byref(d), ctypes.byref(h))
         _check(st)

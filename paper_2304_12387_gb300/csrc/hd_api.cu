@@ -264,6 +264,11 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   if (d->cycle < 0 || d->cycle > 2) { delete h; return HD_ERR_INVALID_ARG; }
   h->cycle = d->cycle == 2 ? 2 : 1;
   if (h->coarse_max > 4096) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->smooth_levels < 0) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->smooth_levels > 1) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  h->sa = d->smooth_levels;
+  if (d->w_levels < 0) { delete h; return HD_ERR_INVALID_ARG; }
+  h->w_levels = d->w_levels;
   const int k = h->k;
   LatticeDims& L = h->L;
   L.nx = d->nx; L.ny = d->ny; L.nz = d->nz;
@@ -336,6 +341,7 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     }
     if (bad) { st = hd_fail(h, HD_ERR_INVALID_ARG, "inverted element (det J <= 0)"); break; }
     if ((st = precond_setup(h)) != HD_OK) break;
+    if ((st = sa_setup(h)) != HD_OK) break;
     if (h->emul) {
       const int64_t ng = E * 6 * nq, nw = E * nl2 * nl2;
       if (cudaMalloc(&h->x_G, sizeof(dfloat) * (ng > 0 ? ng : 1)) != cudaSuccess ||

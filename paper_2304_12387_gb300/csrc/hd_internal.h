@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -54,6 +55,23 @@ struct LevelT {
   __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
 };
 
+// A coarse level of the smoothed-aggregation hierarchy: a general stencil on an
+// X x Y x Z cell lattice with NO offsets (33 on the first coarse level: the
+// 3x3x3 box and the six cells two steps away along an axis; 27 below: the box),
+// stored by offset, a[o * n + c] = A(c, c + off_o) (0 where that cell is outside).
+template <typename T>
+struct StLevelT {
+  int X, Y, Z;
+  int fx, fy, fz;      // aggregation factor from the previous (finer) level
+  int no;              // 33 or 27
+  T* a;                // [no][n]
+  T* dinv;             // 1 / sum_o |a[o][c]|  (l1-Jacobi)
+  T* x0;
+  T* x1;
+  T* b;
+  __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
+};
+
 struct MinresState;  // device-side scalars of the MINRES recurrence
 
 struct hd_op {
@@ -65,6 +83,7 @@ struct hd_op {
   double tau;
   int winv_mode, nu, coarse_max;
   int cycle = 1;
+  int w_levels = 0;    // W repetition on levels < w_levels only (0: all)
   bool singular;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -89,6 +108,15 @@ struct hd_op {
   double* d_coarse_inv = nullptr;  // dense inverse of the coarsest level (or of A + s 11^T)
   int coarse_n = 0;
   std::vector<LevelT<double>> lv;
+  // smoothed-aggregation hierarchy (smooth_levels = 1): prolongator values of
+  // level 0 ([4][n_l2]: own aggregate, then the aggregates across the x, y and
+  // z faces), stencil levels 1.., dense inverse of its coarsest level
+  int sa = 0;
+  double* sa_p = nullptr;
+  float* sa_pf = nullptr;
+  std::vector<StLevelT<double>> st;
+  std::vector<StLevelT<float>> stf;
+  double* d_sa_coarse_inv = nullptr;
 
   // double-float copies for the emulated-FP64 element kernel (fp64_emulation = 1)
   bool emul = false;
@@ -125,7 +153,7 @@ struct hd_op {
   struct VcGraph {
     const void* b;
     void* x;
-    int f32;
+    int f32;  // key: 0/1 FP64/FP32 unsmoothed, 2/3 FP64/FP32 smoothed aggregation
     cudaGraphExec_t exec;
   };
   std::vector<VcGraph> vc_graphs;
@@ -178,6 +206,16 @@ hd_status precond_apply_f32(hd_op* h, const float* r, float* z);
 hd_status schur_apply(hd_op* h, const double* x, double* y);
 hd_status vcycle_apply(hd_op* h, const double* b, double* x);
 hd_status setup_f32(hd_op* h);
+// smoothed-aggregation hierarchy (k_amg.cu)
+hd_status sa_setup(hd_op* h);
+hd_status sa_setup_f32(hd_op* h);
+void sa_free(hd_op* h);
+hd_status sa_vcycle(hd_op* h, const double* b, double* x);
+hd_status sa_vcycle_f32(hd_op* h, const float* b, float* x);
+// runs launch() as a cached CUDA graph keyed by (b, x, key) (k_lattice.cu)
+hd_status run_graphed(hd_op* h, const void* b, void* x, int key, const std::function<void()>& launch);
+// dense SPD inverse on the host (row-major; adds s 1 1^T first when singular)
+hd_status dense_spd_inverse(hd_op* h, std::vector<double>& A, int n, bool singular, std::vector<double>& inv);
 void precond_free(hd_op* h);
 hd_status project_mean(hd_op* h, double* z);
 hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x);

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "hd_internal.h"
+#include "k_level7.cuh"
 
 namespace {
 
@@ -175,24 +176,6 @@ __global__ void k_coarsen_mass(LevelT<double> f, LevelT<double> c) {
   c.mass[t] = s;
 }
 
-// residual b - S x at cell (I,J,Z) given the x value there
-template <typename T>
-__device__ __forceinline__ T stencil_res(const LevelT<T>& lv, const T* __restrict__ x, T bc, T xc, int I, int J,
-                                         int Z, int64_t c) {
-  int64_t xl = I + (int64_t)(lv.X + 1) * (J + (int64_t)lv.Y * Z);
-  int64_t yl = I + (int64_t)lv.X * (J + (int64_t)(lv.Y + 1) * Z);
-  int64_t zl = I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z);
-  int64_t XY = (int64_t)lv.X * lv.Y;
-  T r = fma(-lv.diag[c], xc, bc);
-  if (I > 0) r = fma(lv.wx[xl], x[c - 1], r);
-  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], x[c + 1], r);
-  if (J > 0) r = fma(lv.wy[yl], x[c - lv.X], r);
-  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], x[c + lv.X], r);
-  if (Z > 0) r = fma(lv.wz[zl], x[c - XY], r);
-  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], x[c + XY], r);
-  return r;
-}
-
 // same with x replaced by x + P xc (coarse value of each cell's aggregate added)
 template <typename T>
 __device__ __forceinline__ T stencil_res_prolong(const LevelT<T>& lv, const LevelT<T>& cl, const T* __restrict__ x,
@@ -222,23 +205,6 @@ __global__ void k_schur_apply(LevelT<T> lv, const T* __restrict__ x, T* __restri
   if (c >= lv.n()) return;
   int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
   y[c] = -stencil_res<T>(lv, x, (T)0, x[c], I, J, Z, c);
-}
-
-// first pre-smoothing sweep from a zero guess: x = D_l1^-1 b
-template <typename T>
-__global__ void k_vc_scale(LevelT<T> lv, const T* __restrict__ b, T* __restrict__ x) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= lv.n()) return;
-  x[c] = lv.dinv[c] * b[c];
-}
-
-template <typename T>
-__global__ void k_vc_jacobi(LevelT<T> lv, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo) {
-  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
-  T xc = x[c];
-  xo[c] = fma(lv.dinv[c], stencil_res<T>(lv, x, b[c], xc, I, J, Z, c), xc);
 }
 
 template <typename T>
@@ -275,21 +241,6 @@ __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ 
         s += stencil_res<T>(lv, x, b[c], x[c], I, J, Z, c);
       }
   bc[t] = s;
-}
-
-// coarsest level: x = A^-1 b with the stored FP64 dense inverse (n <= a few hundred);
-// FP64 accumulation for either vector type (the coarsest solve stays FP64)
-template <typename T>
-__global__ void k_vc_coarse(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x) {
-  // one warp per output row; the inverse is symmetric, so row i is contiguous
-  int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= n) return;
-  const double* row = Ainv + (int64_t)i * n;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32) s = fma(row[j], (double)b[j], s);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[i] = (T)s;
 }
 
 // z -= mean(z): deterministic two-pass reduction (fixed per-block chunks, fixed-order final pass)
@@ -368,7 +319,7 @@ const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse
   }
   // W-cycle: a second coarse correction from the updated residual, except just
   // above the coarsest level, where the first one is already exact
-  const int repeats = (h->cycle == 2 && l + 1 < last) ? 2 : 1;
+  const int repeats = (h->cycle == 2 && l + 1 < last && (h->w_levels == 0 || l < h->w_levels)) ? 2 : 1;
   const T* xc = nullptr;
   for (int rep = 0; rep < repeats; ++rep) {
     if (rep > 0) k_vc_prolong_add<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, C, xc, cur);
@@ -386,11 +337,14 @@ const T* vcycle_level(hd_op* h, std::vector<LevelT<T>>& lv, const double* coarse
   return cur;
 }
 
-// One V/W-cycle on level 0 from b into x, replayed from a CUDA graph captured on
-// first use for this (b, x) pair: a cycle at 64^3 is ~200 small launches, most of
-// them on coarse levels where launch overhead, not the kernels, sets the time.
-template <typename T>
-hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x, int f32) {
+}  // namespace
+
+// Runs launch() (which enqueues on h->stream) as a CUDA graph captured on first
+// use for this (b, x, key) and replayed on a private stream ordered after and
+// before the handle's stream: a V/W-cycle at 64^3 is ~100-200 small launches,
+// most of them on coarse levels where launch overhead, not the kernels, sets
+// the time. Falls back to direct launches where capture is unavailable.
+hd_status run_graphed(hd_op* h, const void* b, void* x, int key, const std::function<void()>& launch) {
   if (!h->graphs_off && !h->gstream) {
     if (cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming) != cudaSuccess ||
@@ -400,20 +354,20 @@ hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x,
     }
   }
   if (h->graphs_off) {
-    vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+    launch();
     HD_LAUNCH_CK(h, "vcycle");
     return HD_OK;
   }
   cudaGraphExec_t exec = nullptr;
   for (auto& g : h->vc_graphs)
-    if (g.b == (const void*)b && g.x == (void*)x && g.f32 == f32) exec = g.exec;
+    if (g.b == b && g.x == x && g.f32 == key) exec = g.exec;
   if (!exec) {
     cudaStream_t saved = h->stream;
     h->stream = h->gstream;
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+      launch();
       e = cudaStreamEndCapture(h->gstream, &graph);
     }
     h->stream = saved;
@@ -423,7 +377,7 @@ hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x,
       // capture unavailable here: launch directly from now on
       cudaGetLastError();
       h->graphs_off = true;
-      vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x);
+      launch();
       HD_LAUNCH_CK(h, "vcycle");
       return HD_OK;
     }
@@ -431,7 +385,7 @@ hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x,
       cudaGraphExecDestroy(h->vc_graphs.front().exec);
       h->vc_graphs.erase(h->vc_graphs.begin());
     }
-    h->vc_graphs.push_back({(const void*)b, (void*)x, f32, exec});
+    h->vc_graphs.push_back({b, x, key, exec});
   }
   HD_CK(h, cudaEventRecord(h->gev[0], h->stream));
   HD_CK(h, cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
@@ -439,6 +393,14 @@ hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x,
   HD_CK(h, cudaEventRecord(h->gev[1], h->gstream));
   HD_CK(h, cudaStreamWaitEvent(h->stream, h->gev[1], 0));
   return HD_OK;
+}
+
+namespace {
+
+// One V/W-cycle of the unsmoothed hierarchy on level 0 from b into x (graphed)
+template <typename T>
+hd_status vcycle_graphed(hd_op* h, std::vector<LevelT<T>>& lv, const T* b, T* x, int f32) {
+  return run_graphed(h, b, x, f32, [&]() { vcycle_level<T>(h, lv, h->d_coarse_inv, 0, b, x); });
 }
 
 template <typename T>
@@ -490,6 +452,50 @@ hd_status lattice_apply_Bt(hd_op* h, const double* q, double* yu) {
 
 // Builds M~^-1, C~, the level hierarchy and the coarsest inverse. Requires
 // d_mt (diag M summed over elements), d_wdiag and d_cscale from the element setup.
+// Dense SPD inverse on the host for the coarsest level (n <= 4096): Cholesky
+// A = R R^T, then A^-1 = R^-T R^-1 column by column; row-major output. When the
+// level is singular (constants in the kernel) it inverts A + s 1 1^T with
+// s = mean(diag A) / n.
+hd_status dense_spd_inverse(hd_op* h, std::vector<double>& A, int n, bool singular, std::vector<double>& inv) {
+  if (singular) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += A[(size_t)i * n + i];
+    s = (s / n) / n;
+    for (auto& a : A) a += s;
+  }
+  // Cholesky A = R R^T (lower R in place), then A^-1 = R^-T R^-1 column by column
+  std::vector<double> R = A;
+  for (int j = 0; j < n; ++j) {
+    double d = R[(size_t)j * n + j];
+    for (int p = 0; p < j; ++p) d -= R[(size_t)j * n + p] * R[(size_t)j * n + p];
+    if (!(d > 0.0)) return hd_fail(h, HD_ERR_PREC_INDEFINITE, "coarsest Schur level is not positive definite");
+    d = std::sqrt(d);
+    R[(size_t)j * n + j] = d;
+    for (int i = j + 1; i < n; ++i) {
+      double s = R[(size_t)i * n + j];
+      for (int p = 0; p < j; ++p) s -= R[(size_t)i * n + p] * R[(size_t)j * n + p];
+      R[(size_t)i * n + j] = s / d;
+    }
+  }
+  inv.assign((size_t)n * n, 0.0);
+  std::vector<double> col(n);
+  for (int c = 0; c < n; ++c) {
+    for (int i = 0; i < n; ++i) col[i] = (i == c) ? 1.0 : 0.0;
+    for (int i = 0; i < n; ++i) {  // forward: R y = e_c
+      double s = col[i];
+      for (int p = 0; p < i; ++p) s -= R[(size_t)i * n + p] * col[p];
+      col[i] = s / R[(size_t)i * n + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {  // backward: R^T x = y
+      double s = col[i];
+      for (int p = i + 1; p < n; ++p) s -= R[(size_t)p * n + i] * col[p];
+      col[i] = s / R[(size_t)i * n + i];
+    }
+    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = col[i];  // row-major: row i holds (A^-1)_{i,:}
+  }
+  return HD_OK;
+}
+
 hd_status precond_setup(hd_op* h) {
   const LatticeDims& L = h->L;
   // level 0 lives on the fine lattice: its face weights are an RT-sized vector
@@ -564,41 +570,8 @@ hd_status precond_setup(hd_op* h) {
           A[(size_t)id(I, J, Z + 1) * n + c] -= w;
         }
       }
-  if (h->singular) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += A[(size_t)i * n + i];
-    s = (s / n) / n;
-    for (auto& a : A) a += s;
-  }
-  // Cholesky A = R R^T (lower R in place), then A^-1 = R^-T R^-1 column by column
-  std::vector<double> R = A;
-  for (int j = 0; j < n; ++j) {
-    double d = R[(size_t)j * n + j];
-    for (int p = 0; p < j; ++p) d -= R[(size_t)j * n + p] * R[(size_t)j * n + p];
-    if (!(d > 0.0)) return hd_fail(h, HD_ERR_PREC_INDEFINITE, "coarsest Schur level is not positive definite");
-    d = std::sqrt(d);
-    R[(size_t)j * n + j] = d;
-    for (int i = j + 1; i < n; ++i) {
-      double s = R[(size_t)i * n + j];
-      for (int p = 0; p < j; ++p) s -= R[(size_t)i * n + p] * R[(size_t)j * n + p];
-      R[(size_t)i * n + j] = s / d;
-    }
-  }
-  std::vector<double> inv((size_t)n * n), col(n);
-  for (int c = 0; c < n; ++c) {
-    for (int i = 0; i < n; ++i) col[i] = (i == c) ? 1.0 : 0.0;
-    for (int i = 0; i < n; ++i) {  // forward: R y = e_c
-      double s = col[i];
-      for (int p = 0; p < i; ++p) s -= R[(size_t)i * n + p] * col[p];
-      col[i] = s / R[(size_t)i * n + i];
-    }
-    for (int i = n - 1; i >= 0; --i) {  // backward: R^T x = y
-      double s = col[i];
-      for (int p = i + 1; p < n; ++p) s -= R[(size_t)p * n + i] * col[p];
-      col[i] = s / R[(size_t)i * n + i];
-    }
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + c] = col[i];  // row-major: row i holds (A^-1)_{i,:}
-  }
+  std::vector<double> inv;
+  if ((st = dense_spd_inverse(h, A, n, h->singular, inv)) != HD_OK) return st;
   h->coarse_n = n;
   if (cudaMalloc(&h->d_coarse_inv, sizeof(double) * inv.size()) != cudaSuccess)
     return hd_fail(h, HD_ERR_OOM, "coarse inverse");
@@ -640,11 +613,13 @@ hd_status setup_f32(hd_op* h) {
     k_to_f32<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
     HD_LAUNCH_CK(h, "f32 level");
   }
+  if ((st = sa_setup_f32(h)) != HD_OK) return st;
   h->have_f32 = true;
   return HD_OK;
 }
 
 void precond_free(hd_op* h) {
+  sa_free(h);
   for (auto& g : h->vc_graphs) cudaGraphExecDestroy(g.exec);
   h->vc_graphs.clear();
   if (h->gev[0]) cudaEventDestroy(h->gev[0]);
@@ -668,15 +643,19 @@ hd_status schur_apply(hd_op* h, const double* x, double* y) {
 
 hd_status vcycle_apply(hd_op* h, const double* b, double* x) {
   if (h->n_l2 == 0) return HD_OK;
+  if (!h->st.empty()) return sa_vcycle(h, b, x);
   return vcycle_graphed<double>(h, h->lv, b, x, 0);
 }
+
+static hd_status vcycle_any(hd_op* h, const double* b, double* x) { return vcycle_apply(h, b, x); }
+static hd_status vcycle_any(hd_op* h, const float* b, float* x) { return vcycle_apply_f32(h, b, x); }
 
 template <typename T>
 static hd_status precond_apply_t(hd_op* h, const T* r, T* z, const T* mtinv, std::vector<LevelT<T>>& lv,
                                  const double* cinv) {
   if (h->n_rt > 0) k_diag_scale<T><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->n_rt, mtinv, r, z);
   if (h->n_l2 > 0) {
-    hd_status sv = vcycle_graphed<T>(h, lv, r + h->n_rt, z + h->n_rt, sizeof(T) == 4);
+    hd_status sv = vcycle_any(h, r + h->n_rt, z + h->n_rt);
     if (sv != HD_OK) return sv;
     if (h->singular) {
       launch_mean<T>(h, h->n_l2, z + h->n_rt, h->d_red);
@@ -742,6 +721,7 @@ hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x) {
   if (h->n_l2 == 0) return HD_OK;
   hd_status st = setup_f32(h);
   if (st != HD_OK) return st;
+  if (!h->stf.empty()) return sa_vcycle_f32(h, b, x);
   return vcycle_graphed<float>(h, h->lvf, b, x, 1);
 }
 

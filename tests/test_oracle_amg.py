@@ -194,3 +194,29 @@ def test_smoothed_w_cycle_iterations_do_not_grow_with_the_lattice():
     its_ua_v = _pcg_iterations(A, VCycle(A, dims, coarse_max=512).apply)
     assert abs(its[32] - its[16]) <= 1, its
     assert its[32] < its_ua_w < its_ua_v, (its, its_ua_w, its_ua_v)
+
+
+def test_w_recursion_limited_to_the_first_levels():
+    """cycle = 2 with w_levels = 1: level 0 makes two coarse corrections, each one
+    V-cycle of the hierarchy from level 1 down (rebuilt here by hand); w_levels at
+    or above the number of levels is the full W-cycle."""
+    dims = (16, 12, 10)
+    A = block_laplacian(dims, seed=11)
+    kw = dict(coarse_max=8, smooth=OMEGA, sa_levels=1)
+    w1 = VCycle(A, dims, cycle=2, w_levels=1, **kw)
+    v = VCycle(A, dims, cycle=1, **kw)
+    assert w1.n_levels >= 4
+    b = np.random.Generator(np.random.PCG64(12)).standard_normal(A.shape[0])
+    A0, d, P = v.A[0], v.dl1[0], v.P[0]
+    x = np.zeros_like(b)
+    for _ in range(2):
+        x = x + (b - A0 @ x) / d
+    for _ in range(2):
+        x = x + P @ v._cycle(1, P.T @ (b - A0 @ x))
+    for _ in range(2):
+        x = x + (b - A0 @ x) / d
+    assert np.allclose(w1._cycle(0, b), x, rtol=1e-13, atol=1e-13 * np.abs(x).max())
+    full = VCycle(A, dims, cycle=2, **kw)
+    deep = VCycle(A, dims, cycle=2, w_levels=w1.n_levels, **kw)
+    assert np.array_equal(full._cycle(0, b), deep._cycle(0, b))
+    assert not np.allclose(full._cycle(0, b), w1._cycle(0, b))
