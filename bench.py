@@ -219,7 +219,8 @@ def run_ours(args, rank, world, dist):
     vx, vy, vz, alpha, beta = workload(nx)
     t0 = time.perf_counter()
     op = hd.Operator(nx, nx, nx, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=Q,
-                     cycle=args.cycle, fp64_emulation=int(args.fp64_emulation), stream=stream)
+                     cycle=args.cycle, fp64_emulation=int(args.fp64_emulation),
+                     smooth_levels=args.smooth_levels, w_levels=args.w_levels, stream=stream)
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
     n = op.n
@@ -279,7 +280,9 @@ def run_ours(args, rank, world, dist):
                                               if args.fp64_emulation else "FP64"),
                       "l2": "inputs larger than L2 (x, y: 538 MB each; W^-1 8.6 GB; geometric factors 2.7 GB)",
                       "winv": "dense per-element inverse", "setup_s": setup_s,
-                      "schur_cycle": "W" if args.cycle == 2 else "V"},
+                      "schur_cycle": ("W" if args.cycle == 2 else "V") +
+                                     (", smoothed aggregation on the first level" if args.smooth_levels
+                                      else ", plain aggregation")},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if args.fp64_emulation and not args.no_native:
         out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
@@ -372,6 +375,9 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-4, help="inner MINRES tolerance of the mixed solve")
     ap.add_argument("--solve-maxit", type=int, default=20000, help="iteration cap of the MINRES solves")
     ap.add_argument("--cycle", type=int, default=2, choices=[1, 2], help="1: V-cycle, 2: W-cycle on S~")
+    ap.add_argument("--smooth-levels", type=int, default=1, choices=[0, 1],
+                    help="1: smoothed-aggregation prolongator on the first level of the S~ hierarchy")
+    ap.add_argument("--w-levels", type=int, default=0, help="W repetition on the first levels only (0: all)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="1: element kernel in double-float (FP32 pairs, FP64 parity); 0: native FP64")

@@ -55,16 +55,19 @@ struct LevelT {
   __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
 };
 
-// A coarse level of the smoothed-aggregation hierarchy: a general stencil on an
-// X x Y x Z cell lattice with NO offsets (33 on the first coarse level: the
-// 3x3x3 box and the six cells two steps away along an axis; 27 below: the box),
-// stored by offset, a[o * n + c] = A(c, c + off_o) (0 where that cell is outside).
+// A coarse level of the smoothed-aggregation hierarchy: a symmetric stencil on
+// an X x Y x Z cell lattice with NO offsets (33 on the first coarse level: the
+// 3x3x3 box and the six cells two steps away along an axis; 27 below: the box).
+// Stored by offset, a[h * n + c] = A(c, c + off_h) for the centre and the
+// offsets that come later in lattice order (NH = 17 or 14 of them); the
+// mirrored coefficient A(c, c - off_h) is a[h * n + c - off_h]. 0 where the
+// neighbour is outside. During setup a holds all NO offsets.
 template <typename T>
 struct StLevelT {
   int X, Y, Z;
   int fx, fy, fz;      // aggregation factor from the previous (finer) level
   int no;              // 33 or 27
-  T* a;                // [no][n]
+  T* a;                // [NH][n] (setup: [no][n])
   T* dinv;             // 1 / sum_o |a[o][c]|  (l1-Jacobi)
   T* x0;
   T* x1;

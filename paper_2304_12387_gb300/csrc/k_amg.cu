@@ -42,6 +42,11 @@ __host__ __device__ __forceinline__ void st_off(int o, int& dx, int& dy, int& dz
     dz = d == 2 ? v : 0;
   }
 }
+// stored (half) offset h -> full offset index: h = 0 the centre, 1..13 the box
+// offsets after it in lattice order, 14..16 the +2 axis offsets
+__host__ __device__ __forceinline__ int half_full_index(int h) { return h < 14 ? 13 + h : 27 + 2 * (h - 14); }
+__host__ __device__ constexpr int n_half(int no) { return no == 33 ? 17 : 14; }
+
 // index of an offset in the 33-offset list, -1 if it is not there
 __device__ __forceinline__ int st_index(int dx, int dy, int dz) {
   if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
@@ -219,6 +224,14 @@ __global__ void k_ua_galerkin(StLevelT<double> F, CDims c, StLevelT<double> A, i
   for (int o = 0; o < 27; ++o) A.a[o * nc + C] = acc[o];
 }
 
+// keep the centre and the later offsets (setup: full -> half storage)
+__global__ void k_st_compress(StLevelT<double> A, double* __restrict__ half) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = A.n();
+  if (c >= n) return;
+  for (int h = 0; h < n_half(A.no); ++h) half[h * n + c] = A.a[half_full_index(h) * n + c];
+}
+
 __global__ void k_st_dinv(StLevelT<double> A) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = A.n();
@@ -229,17 +242,22 @@ __global__ void k_st_dinv(StLevelT<double> A) {
 }
 
 // -- solve-time kernels of the stencil levels ---------------------------------------
-// (A x)_c; x_at(I, J, Z) supplies the vector value at a lattice cell
+// (A x)_c from the half-stored symmetric stencil; x_at(I, J, Z) supplies the
+// vector value at a lattice cell
 template <typename T, int NO, typename XA>
 __device__ __forceinline__ T st_row(const StLevelT<T>& L, int64_t c, int I, int J, int Z, XA x_at) {
+  constexpr int NH = n_half(NO);
   const int64_t n = L.n();
-  T s = (T)0;
+  T s = L.a[c] * x_at(I, J, Z);
 #pragma unroll
-  for (int o = 0; o < NO; ++o) {
+  for (int h = 1; h < NH; ++h) {
     int dx, dy, dz;
-    st_off(o, dx, dy, dz);
-    const int i = I + dx, j = J + dy, z = Z + dz;
-    if (i >= 0 && i < L.X && j >= 0 && j < L.Y && z >= 0 && z < L.Z) s = fma(L.a[o * n + c], x_at(i, j, z), s);
+    st_off(half_full_index(h), dx, dy, dz);
+    const int64_t d = dx + (int64_t)L.X * (dy + (int64_t)L.Y * dz);
+    if (I + dx >= 0 && I + dx < L.X && J + dy >= 0 && J + dy < L.Y && Z + dz >= 0 && Z + dz < L.Z)
+      s = fma(L.a[h * n + c], x_at(I + dx, J + dy, Z + dz), s);
+    if (I - dx >= 0 && I - dx < L.X && J - dy >= 0 && J - dy < L.Y && Z - dz >= 0 && Z - dz < L.Z)
+      s = fma(L.a[h * n + c - d], x_at(I - dx, J - dy, Z - dz), s);
   }
   return s;
 }
@@ -491,7 +509,9 @@ void sa_cycle0(hd_op* h, LevelT<T>& L, const T* pv, std::vector<StLevelT<T>>& st
 template <typename T>
 hd_status alloc_st(hd_op* h, StLevelT<T>& L, bool coefs) {
   const int64_t n = L.n();
-  if (coefs && cudaMalloc(&L.a, sizeof(T) * n * L.no) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "stencil level");
+  // FP64 setup needs all offsets; the FP32 copy is made from the half storage
+  const int64_t na = sizeof(T) == 8 ? L.no : n_half(L.no);
+  if (coefs && cudaMalloc(&L.a, sizeof(T) * n * na) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "stencil level");
   if (cudaMalloc(&L.dinv, sizeof(T) * n) != cudaSuccess || cudaMalloc(&L.x0, sizeof(T) * n) != cudaSuccess ||
       cudaMalloc(&L.x1, sizeof(T) * n) != cudaSuccess || cudaMalloc(&L.b, sizeof(T) * n) != cudaSuccess)
     return hd_fail(h, HD_ERR_OOM, "stencil level");
@@ -564,6 +584,17 @@ hd_status sa_setup(hd_op* h) {
   if (cudaMalloc(&h->d_sa_coarse_inv, sizeof(double) * inv.size()) != cudaSuccess)
     return hd_fail(h, HD_ERR_OOM, "SA coarse inverse");
   HD_CK(h, cudaMemcpy(h->d_sa_coarse_inv, inv.data(), sizeof(double) * inv.size(), cudaMemcpyHostToDevice));
+  // half storage of the (symmetric) stencils for the solve
+  for (StLevelT<double>& s : h->st) {
+    double* half = nullptr;
+    if (cudaMalloc(&half, sizeof(double) * s.n() * n_half(s.no)) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "stencil level");
+    k_st_compress<<<nblk(s.n()), TPB, 0, h->stream>>>(s, half);
+    HD_LAUNCH_CK(h, "k_st_compress");
+    HD_CK(h, cudaStreamSynchronize(h->stream));
+    cudaFree(s.a);
+    s.a = half;
+  }
   return HD_OK;
 }
 
@@ -578,7 +609,7 @@ hd_status sa_setup_f32(hd_op* h) {
     hd_status st = alloc_st<float>(h, f, true);
     h->stf.push_back(f);
     if (st != HD_OK) return st;
-    k_to_f32_sa<float><<<nblk(d.n() * d.no), TPB, 0, h->stream>>>(d.n() * d.no, d.a, f.a);
+    k_to_f32_sa<float><<<nblk(d.n() * n_half(d.no)), TPB, 0, h->stream>>>(d.n() * n_half(d.no), d.a, f.a);
     k_to_f32_sa<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
   }
   HD_LAUNCH_CK(h, "SA f32");
