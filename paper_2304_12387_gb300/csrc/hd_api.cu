@@ -1,5 +1,6 @@
 // C ABI of the hdivsp library: handle lifetime, host-side setup (1D tables of
 // the interpolation-histopolation basis, index maps) and the apply entry points.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -201,6 +202,9 @@ void destroy_all(hd_op* h) {
   cudaFree(h->d_ms);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
+  for (cudaEvent_t e : h->xev) cudaEventDestroy(e);
+  if (h->xstream[0]) cudaStreamDestroy(h->xstream[0]);
+  if (h->xstream[1]) cudaStreamDestroy(h->xstream[1]);
   learned_free(h);
   precond_free(h);
 }
@@ -486,6 +490,12 @@ hd_status hd_apply_op(hd_handle h, const double* x, double* y) {
   return apply_op_internal(h, x, y);
 }
 
+// Host-buffer apply, pipelined over slabs of element layers along z: the inputs of
+// slab s+1 are copied in (one stream) while slab s is applied (the handle's stream)
+// and the outputs of slab s-1 are copied out (a third stream). In lattice order a
+// slab's inputs and outputs are four contiguous ranges (x-, y-, z-faces, cells);
+// the z-face layer between two slabs receives the two slabs' addends (on zero, so
+// in either order the same sum) and is copied out with the upper slab.
 hd_status hd_apply_op_host(hd_handle h, const double* xh, double* yh) {
   if (!h || !xh || !yh) return HD_ERR_INVALID_ARG;
   const int64_t n = h->n_rt + h->n_l2;
@@ -495,10 +505,59 @@ hd_status hd_apply_op_host(hd_handle h, const double* xh, double* yh) {
   }
   double* dx = h->d_stage;
   double* dy = h->d_stage + n;
-  HD_CK(h, cudaMemcpyAsync(dx, xh, sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
-  hd_status st = apply_op_internal(h, dx, dy);
+  const LatticeDims& L = h->L;
+  const int nz = L.nz, S = std::max(1, std::min(nz, 8));
+  if (!h->xstream[0]) {
+    if (cudaStreamCreateWithFlags(&h->xstream[0], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&h->xstream[1], cudaStreamNonBlocking) != cudaSuccess)
+      return hd_cuda_check(h, cudaGetLastError(), "copy streams");
+  }
+  while ((int)h->xev.size() < 2 * S + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return hd_cuda_check(h, cudaGetLastError(), "copy events");
+    h->xev.push_back(e);
+  }
+  const int K = h->k;
+  const int64_t XY = (int64_t)L.X * L.Y, sx = (int64_t)(L.X + 1) * L.Y, sy = (int64_t)L.X * (L.Y + 1);
+  const int64_t oy = L.n_xf, oz = (int64_t)L.n_xf + L.n_yf, oq = h->n_rt, E2 = (int64_t)L.nx * L.ny;
+  auto copy = [&](double* dst, const double* src, int64_t b, int64_t e, cudaMemcpyKind kind, cudaStream_t s) {
+    return e > b ? cudaMemcpyAsync(dst + b, src + b, sizeof(double) * (e - b), kind, s) : cudaSuccess;
+  };
+  // copies in wait for earlier work on the handle's stream (the staging buffers)
+  HD_CK(h, cudaEventRecord(h->xev[2 * S], h->stream));
+  HD_CK(h, cudaStreamWaitEvent(h->xstream[0], h->xev[2 * S], 0));
+  hd_status st = HD_OK;
+  for (int s = 0; s < S && st == HD_OK; ++s) {
+    const int z0 = (int)((int64_t)s * nz / S), z1 = (int)((int64_t)(s + 1) * nz / S);
+    const int64_t Z0 = (int64_t)z0 * K, Z1 = (int64_t)z1 * K;
+    const int64_t zin = Z0 + (s > 0 ? 1 : 0);  // the layer Z0 came with the slab below
+    HD_CK(h, copy(dx, xh, sx * Z0, sx * Z1, cudaMemcpyHostToDevice, h->xstream[0]));
+    HD_CK(h, copy(dx, xh, oy + sy * Z0, oy + sy * Z1, cudaMemcpyHostToDevice, h->xstream[0]));
+    HD_CK(h, copy(dx, xh, oz + XY * zin, oz + XY * (Z1 + 1), cudaMemcpyHostToDevice, h->xstream[0]));
+    HD_CK(h, copy(dx, xh, oq + XY * Z0, oq + XY * Z1, cudaMemcpyHostToDevice, h->xstream[0]));
+    HD_CK(h, cudaEventRecord(h->xev[s], h->xstream[0]));
+    HD_CK(h, cudaStreamWaitEvent(h->stream, h->xev[s], 0));
+    HD_CK(h, cudaMemsetAsync(dy + sx * Z0, 0, sizeof(double) * sx * (Z1 - Z0), h->stream));
+    HD_CK(h, cudaMemsetAsync(dy + oy + sy * Z0, 0, sizeof(double) * sy * (Z1 - Z0), h->stream));
+    HD_CK(h, cudaMemsetAsync(dy + oz + XY * zin, 0, sizeof(double) * XY * (Z1 + 1 - zin), h->stream));
+    h->e_first = (int64_t)z0 * E2;
+    h->e_end = (int64_t)z1 * E2;
+    st = elem_op(h, OP_M | OP_DT | OP_D | OP_C, dx, dx + h->n_rt, dy, dy + h->n_rt);
+    h->e_first = 0;
+    h->e_end = -1;
+    if (st != HD_OK) break;
+    HD_CK(h, cudaEventRecord(h->xev[S + s], h->stream));
+    HD_CK(h, cudaStreamWaitEvent(h->xstream[1], h->xev[S + s], 0));
+    const int64_t zout = (s == S - 1) ? Z1 + 1 : Z1;  // the top layer leaves with the slab above
+    HD_CK(h, copy(yh, dy, sx * Z0, sx * Z1, cudaMemcpyDeviceToHost, h->xstream[1]));
+    HD_CK(h, copy(yh, dy, oy + sy * Z0, oy + sy * Z1, cudaMemcpyDeviceToHost, h->xstream[1]));
+    HD_CK(h, copy(yh, dy, oz + XY * Z0, oz + XY * zout, cudaMemcpyDeviceToHost, h->xstream[1]));
+    HD_CK(h, copy(yh, dy, oq + XY * Z0, oq + XY * Z1, cudaMemcpyDeviceToHost, h->xstream[1]));
+  }
   if (st != HD_OK) return st;
-  HD_CK(h, cudaMemcpyAsync(yh, dy, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  HD_CK(h, cudaEventRecord(h->xev[2 * S + 1], h->xstream[1]));
+  HD_CK(h, cudaStreamWaitEvent(h->stream, h->xev[2 * S + 1], 0));
   HD_CK(h, cudaStreamSynchronize(h->stream));
   return HD_OK;
 }

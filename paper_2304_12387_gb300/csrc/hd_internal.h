@@ -163,6 +163,11 @@ struct hd_op {
   cudaStream_t gstream = nullptr;
   cudaEvent_t gev[2] = {nullptr, nullptr};
   bool graphs_off = false;
+  // element window of the next element-kernel launch ([e_first, e_end); e_end < 0: all)
+  int64_t e_first = 0, e_end = -1;
+  // streams and events of the pipelined host-buffer apply (copy in, copy out)
+  cudaStream_t xstream[2] = {nullptr, nullptr};
+  std::vector<cudaEvent_t> xev;
   // profiling of the fused element kernel
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)

@@ -412,7 +412,7 @@ __device__ __forceinline__ void prefetch_l2_block(const void* p, size_t bytes, i
 
 template <typename T, typename IO, int K, int Q, int EB>
 __global__ void __launch_bounds__(ElemCfg<T>::THREADS)
-k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem,
+k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem, const int e_first,
           const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
           const CgArgs<T> cg, const IO* __restrict__ u, const IO* __restrict__ q, IO* __restrict__ yu,
           IO* __restrict__ yq) {
@@ -424,7 +424,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   T* sq = su + EB * NRT;              // [EB][NL2]
   T* s1 = sq + EB * NL2;              // [EB][R1]   T1 / point values
   T* s2 = s1 + EB * S::R1;            // [EB][R2]   T2
-  const int e0 = blockIdx.x * EB;
+  const int e0 = e_first + blockIdx.x * EB;  // elements [e_first, n_elem) of this launch
   const int tid = threadIdx.x, nth = blockDim.x;
   const bool needu = (mode & (OP_M | OP_D)) != 0;
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
@@ -852,11 +852,12 @@ hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs
     attr_set = true;
   }
   TabT<T> tab = make_tab<T>(h->tab);
-  int blocks = (int)((h->n_elem + EB - 1) / EB);
+  const int64_t e_end = h->e_end < 0 ? h->n_elem : h->e_end, e_first = h->e_end < 0 ? 0 : h->e_first;
+  int blocks = (int)((e_end - e_first + EB - 1) / EB);
   prof_mark(h, true);
   if (blocks > 0)
-    kern<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(tab, h->L, mode, (int)h->n_elem, G, winv, cs, cg, u, q,
-                                                           yu, yq);
+    kern<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(tab, h->L, mode, (int)e_end, (int)e_first, G, winv, cs,
+                                                           cg, u, q, yu, yq);
   prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;

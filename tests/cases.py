@@ -22,6 +22,8 @@ CASES = {
     "gd_k5": (GRAD_DIV, (1, 2, 1), 5, 6, 0.1, 3, "lognormal1"),
     # k = 3, q = k+1, grad-div, more elements than one CTA batch plus a tail
     "gd_k3": (GRAD_DIV, (3, 3, 2), 3, 4, 0.12, 48, "lognormal1"),
+    # tall grad-div column, 11 element layers: the host-buffer apply's slabs are uneven
+    "gd_tall": (GRAD_DIV, (2, 3, 11), 2, 4, 0.1, 21, "lognormal1"),
 }
 
 
