@@ -251,22 +251,30 @@ __global__ void k_st_dinv(StLevelT<double> A) {
 }
 
 // -- solve-time kernels of the stencil levels ---------------------------------------
-// (A x)_c from the half-stored symmetric stencil; x_at(I, J, Z) supplies the
-// vector value at a lattice cell
+// (A x)_c from the half-stored symmetric stencil; x_at(I, J, Z, k) supplies the
+// vector value at lattice cell (I, J, Z) with linear index k. Which neighbours
+// exist is decided once per cell (flags for steps -2..2 per direction), so that
+// each unrolled offset costs a few flag tests and one index add: these sweeps
+// are otherwise bound by integer address arithmetic rather than by the FP units
+// or HBM. Cell indices fit 32 bits (stencil levels are at most 1/8 of the fine
+// lattice).
 template <typename T, int NO, typename XA>
-__device__ __forceinline__ T st_row(const StLevelT<T>& L, int64_t c, int I, int J, int Z, XA x_at) {
+__device__ __forceinline__ T st_row(const StLevelT<T>& L, int c, int I, int J, int Z, XA x_at) {
   constexpr int NH = n_half(NO);
   const int64_t n = L.n();
-  T s = L.a[c] * x_at(I, J, Z);
+  const int X = L.X, XY = L.X * L.Y;
+  const bool fx[5] = {I >= 2, I >= 1, true, I + 1 < L.X, I + 2 < L.X};
+  const bool fy[5] = {J >= 2, J >= 1, true, J + 1 < L.Y, J + 2 < L.Y};
+  const bool fz[5] = {Z >= 2, Z >= 1, true, Z + 1 < L.Z, Z + 2 < L.Z};
+  T s = L.a[c] * x_at(I, J, Z, c);
 #pragma unroll
   for (int h = 1; h < NH; ++h) {
     int dx, dy, dz;
     st_off(half_full_index(h), dx, dy, dz);
-    const int64_t d = dx + (int64_t)L.X * (dy + (int64_t)L.Y * dz);
-    if (I + dx >= 0 && I + dx < L.X && J + dy >= 0 && J + dy < L.Y && Z + dz >= 0 && Z + dz < L.Z)
-      s = fma(L.a[h * n + c], x_at(I + dx, J + dy, Z + dz), s);
-    if (I - dx >= 0 && I - dx < L.X && J - dy >= 0 && J - dy < L.Y && Z - dz >= 0 && Z - dz < L.Z)
-      s = fma(L.a[h * n + c - d], x_at(I - dx, J - dy, Z - dz), s);
+    const int d = dx + X * dy + XY * dz;
+    const T* ah = L.a + h * n;
+    if (fx[2 + dx] && fy[2 + dy] && fz[2 + dz]) s = fma(ah[c], x_at(I + dx, J + dy, Z + dz, c + d), s);
+    if (fx[2 - dx] && fy[2 - dy] && fz[2 - dz]) s = fma(ah[c - d], x_at(I - dx, J - dy, Z - dz, c - d), s);
   }
   return s;
 }
@@ -285,12 +293,9 @@ __global__ void k_st_scale_jacobi(StLevelT<T> L, const T* __restrict__ b, T* __r
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
   const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
-  auto xa = [&](int i, int j, int z) {
-    const int64_t k = i + (int64_t)L.X * (j + (int64_t)L.Y * z);
-    return L.dinv[k] * b[k];
-  };
-  const T r = b[c] - st_row<T, NO>(L, c, I, J, Z, xa);
-  xo[c] = fma(L.dinv[c], r, xa(I, J, Z));
+  auto xa = [&](int, int, int, int k) { return L.dinv[k] * b[k]; };
+  const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
+  xo[c] = fma(L.dinv[c], r, xa(I, J, Z, (int)c));
 }
 
 template <typename T, int NO>
@@ -298,8 +303,8 @@ __global__ void k_st_jacobi(StLevelT<T> L, const T* __restrict__ b, const T* __r
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
   const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
-  auto xa = [&](int i, int j, int z) { return x[i + (int64_t)L.X * (j + (int64_t)L.Y * z)]; };
-  const T r = b[c] - st_row<T, NO>(L, c, I, J, Z, xa);
+  auto xa = [&](int, int, int, int k) { return x[k]; };
+  const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
   xo[c] = fma(L.dinv[c], r, x[c]);
 }
 
@@ -309,8 +314,8 @@ __global__ void k_st_resid(StLevelT<T> L, const T* __restrict__ b, const T* __re
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
   const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
-  auto xa = [&](int i, int j, int z) { return x[i + (int64_t)L.X * (j + (int64_t)L.Y * z)]; };
-  r[c] = b[c] - st_row<T, NO>(L, c, I, J, Z, xa);
+  auto xa = [&](int, int, int, int k) { return x[k]; };
+  r[c] = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
 }
 
 // b_C = sum over the aggregate of the residual b - A x, one thread per coarse cell
@@ -321,13 +326,13 @@ __global__ void k_st_restrict_small(StLevelT<T> L, CDims cd, const T* __restrict
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
   const int Cx = (int)(C % cd.X), Cy = (int)((C / cd.X) % cd.Y), Cz = (int)(C / ((int64_t)cd.X * cd.Y));
-  auto xa = [&](int i, int j, int z) { return x[i + (int64_t)L.X * (j + (int64_t)L.Y * z)]; };
+  auto xa = [&](int, int, int, int k) { return x[k]; };
   T s = (T)0;
   for (int k = cd.fz * Cz; k < min(cd.fz * Cz + cd.fz, L.Z); ++k)
     for (int j = cd.fy * Cy; j < min(cd.fy * Cy + cd.fy, L.Y); ++j)
       for (int i = cd.fx * Cx; i < min(cd.fx * Cx + cd.fx, L.X); ++i) {
         const int64_t c = i + (int64_t)L.X * (j + (int64_t)L.Y * k);
-        s += b[c] - st_row<T, NO>(L, c, i, j, k, xa);
+        s += b[c] - st_row<T, NO>(L, (int)c, i, j, k, xa);
       }
   bc[C] = s;
 }
@@ -360,12 +365,11 @@ __global__ void k_st_jacobi_prolong(StLevelT<T> L, CDims cd, const T* __restrict
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
   const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
-  auto xa = [&](int i, int j, int z) {
-    return x[i + (int64_t)L.X * (j + (int64_t)L.Y * z)] +
-           e[agg(i, cd.fx) + (int64_t)cd.X * (agg(j, cd.fy) + (int64_t)cd.Y * agg(z, cd.fz))];
+  auto xa = [&](int i, int j, int z, int k) {
+    return x[k] + e[agg(i, cd.fx) + cd.X * (agg(j, cd.fy) + cd.Y * agg(z, cd.fz))];
   };
-  const T xs = xa(I, J, Z);
-  const T r = b[c] - st_row<T, NO>(L, c, I, J, Z, xa);
+  const T xs = xa(I, J, Z, (int)c);
+  const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
   xo[c] = fma(L.dinv[c], r, xs);
 }
 
