@@ -37,9 +37,23 @@ NX, K, Q, PERTURB, SIGMA, ESS, SEED = 64, 4, 6, 0.15, 2.0, 63, 2304
 FP64_PEAK_GFLOPS_AT_MAX_CLOCK = 152 * 2 * 2 * 2.070
 # DRAM bytes (read + write) per element of the element kernel, from one ncu capture of the 24^3
 # case of the same recipe (13,824 elements); to be dropped when the kernel changes
-ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 674.306560e6 / 13824,   # profiles/k_elem_op_M64_k4q6.md
-                                  (4, 6, "df"): 673.978624e6 / 13824}    # profiles/k_elem_op_df_M64_k4q6.md
-HBM_GBS_MEASURED = 6792.4   # MEASURED_PEAKS.json hbm_gbs (copy, read + write)
+ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 674.306560e6 / 13824,   # FP64 kernel
+                                  (4, 6, "df"): 673.752320e6 / 13824}    # double-float kernel
+
+
+def _measured_hbm_gbs(default=6792.4):
+    """HBM copy bandwidth (read + write bytes) measured on this GPU pool, from
+    MEASURED_PEAKS.json beside this file when present; else the value it held when
+    these kernels were measured."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            v = float(json.load(f)["hbm_gbs"])
+        return v if v > 0 else default
+    except (OSError, ValueError, KeyError, TypeError):
+        return default
+
+
+HBM_GBS_MEASURED = _measured_hbm_gbs()
 
 
 def workload(n=NX):
