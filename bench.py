@@ -360,6 +360,38 @@ def run_ours(args, rank, world, dist):
         print(json.dumps(out), flush=True)
 
 
+def run_iterations(args):
+    """Mesh and degree (in)dependence of the iteration counts (Metric 2's study): FP64
+    MINRES to a true relative residual of 1e-8 on the metric recipe (perturbed mesh,
+    beta = exp(2Z), u.n = 0, q = k + 2) at several element counts and degrees, with
+    the plain-aggregation and the smoothed-aggregation W-cycles."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    cases = [(16, 4), (32, 4), (64, 4), (32, 2), (32, 3), (32, 5)]
+    rows = []
+    for nx, k in cases:
+        vx, vy, vz, alpha, beta = workload(nx)
+        row = {"elements": nx, "k": k}
+        for name, sl in (("plain", 0), ("smoothed", 1)):
+            op = hd.Operator(nx, nx, nx, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
+                             cycle=2, fp64_emulation=1, smooth_levels=sl, stream=stream)
+            row["dofs"] = op.n
+            b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
+            b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
+            x = torch.zeros_like(b)
+            st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=args.solve_maxit, check_every=16,
+                                          outer_rtol=1e-8, max_outer=40)
+            row[name] = {"status": int(st), "iterations": info["iterations"], "outer": info["outer"],
+                         "ms": round(info["ms_total"], 1), "true_relres": info["true_relres"]}
+            op.close()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"study": "MINRES iterations vs mesh size and degree", "solver": "FP64 (double-float "
+                      "element kernel), W-cycle, true relative residual 1e-8", "rows": rows}), flush=True)
+
+
 def run_learned(args):
     """Learned Schur preconditioner, evaluated the way it is meant to be used: trained
     on residual/correction pairs from the plain solver on the Darcy recipe (k = 3,
@@ -424,6 +456,8 @@ def main():
                     help="1: smoothed-aggregation prolongator on the first level of the S~ hierarchy")
     ap.add_argument("--w-levels", type=int, default=0, help="W repetition on the first levels only (0: all)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
+    ap.add_argument("--iterations", action="store_true",
+                    help="run the iteration-count study (mesh sizes and degrees) instead")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="1: element kernel in double-float (FP32 pairs, FP64 parity); 0: native FP64")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison apply")
@@ -446,6 +480,8 @@ def main():
         run_reference(args, rank, world)
     elif args.learned:
         run_learned(args)
+    elif args.iterations:
+        run_iterations(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:
