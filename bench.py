@@ -207,6 +207,44 @@ def native_apply(args, nx, vx, vy, vz, alpha, beta, stream):
     return r
 
 
+def affine_apply(args, stream):
+    """Metric 1 on the Cartesian geometry (M64-affine): the unperturbed mesh of the
+    same size and coefficients, q = k + 1, the same element kernel and precision as
+    the main line; a separate handle."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    nx = args.n
+    vx, vy, vz = synth.lattice_vertices(nx, nx, nx)
+    _, _, _, alpha, beta = workload(nx)
+    q = K + 1
+    op = hd.Operator(nx, nx, nx, K, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=q, affine=True,
+                     cycle=args.cycle, fp64_emulation=int(args.fp64_emulation), stream=stream)
+    x = torch.from_numpy(synth.uniform(op.n, seed=SEED)).cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.hd_apply_op(x, y)
+    steps = max(5, args.steps // 10)
+    op.hd_profile(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.hd_apply_op(x, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    op.hd_profile(0)
+    launches, kms = op.hd_profile_read()
+    ms = e0.elapsed_time(e1) / steps
+    kern_ms = kms / max(1, launches)
+    abytes = elem_bytes(K, q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3)
+    r = {"workload": "M%d-affine: the same recipe on the unperturbed mesh, q=%d" % (nx, q),
+         "value": op.n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms, "steps": steps,
+         "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
+         "hbm_frac_of_measured": abytes / (kern_ms * 1e-3) / 1e9 / HBM_GBS_MEASURED}
+    op.close()
+    return r
+
+
 def max_over_ranks(value, dist):
     """Largest value over the ranks (a job takes as long as its slowest rank);
     the value itself without a process group."""
@@ -331,6 +369,8 @@ def run_ours(args, rank, world, dist):
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if args.fp64_emulation and not args.no_native:
         out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
+    if not args.no_affine:
+        out["apply_affine"] = affine_apply(args, stream)
     # MINRES time to a true relative residual of 1e-8 on the same problem: FP64, and
     # mixed precision (FP32 operator and V-cycle inside an FP64 residual correction)
     if not args.no_solve:
@@ -388,8 +428,34 @@ def run_iterations(args):
             op.close()
         rows.append(row)
         print(json.dumps(row), flush=True)
+    # the (1,1)-block scaling tau (tau = 1: the final proposition of Sec. 2.3; tau = 2: Prop. 2's
+    # optimum for exact blocks) on the C1 and C2 shapes, smoothed W-cycle
+    taus = []
+    n1 = 4
+    c1 = dict(nx=n1, k=2, q=3, kind=hd.HD_GRAD_DIV, ess=63, affine=True, rtol=1e-10,
+              v=synth.lattice_vertices(n1, n1, n1), c0=np.ones(n1 ** 3), c1=np.ones(n1 ** 3))
+    n2 = 32
+    c2 = dict(nx=n2, k=3, q=5, kind=hd.HD_DARCY, ess=0, affine=False, rtol=1e-8,
+              v=synth.lattice_vertices(n2, n2, n2, perturb=0.15, seed=SEED),
+              c0=synth.lognormal(n2 ** 3, 2.0, seed=SEED + 1), c1=np.zeros(n2 ** 3))
+    for name, c in (("C1", c1), ("C2", c2)):
+        for tau in (1.0, 2.0):
+            nx = c["nx"]
+            op = hd.Operator(nx, nx, nx, c["k"], *c["v"], c["c0"], c["c1"], kind=c["kind"], ess_mask=c["ess"],
+                             q=c["q"], affine=c["affine"], tau=tau, cycle=2, fp64_emulation=1, smooth_levels=1,
+                             coarse_max=8 if nx < 8 else 0, stream=stream)
+            b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
+            b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
+            x = torch.zeros_like(b)
+            st, info = op.hd_minres_solve(b, x, rtol=c["rtol"], maxit=args.solve_maxit, check_every=16,
+                                          outer_rtol=c["rtol"], max_outer=40)
+            taus.append({"shape": name, "tau": tau, "status": int(st), "iterations": info["iterations"],
+                         "true_relres": info["true_relres"]})
+            print(json.dumps(taus[-1]), flush=True)
+            op.close()
     print(json.dumps({"study": "MINRES iterations vs mesh size and degree", "solver": "FP64 (double-float "
-                      "element kernel), W-cycle, true relative residual 1e-8", "rows": rows}), flush=True)
+                      "element kernel), W-cycle, true relative residual 1e-8", "rows": rows, "tau": taus}),
+          flush=True)
 
 
 def run_learned(args):
@@ -461,6 +527,7 @@ def main():
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
                     help="1: element kernel in double-float (FP32 pairs, FP64 parity); 0: native FP64")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison apply")
+    ap.add_argument("--no-affine", action="store_true", help="skip the apply on the unperturbed (affine) mesh")
     ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
