@@ -75,6 +75,23 @@ struct StLevelT {
   __host__ __device__ int64_t n() const { return (int64_t)X * Y * Z; }
 };
 
+// Lattice coordinates (I, J, Z) of cell c on an X x Y x ... lattice, c = I + X (J + Y Z).
+// 32-bit unsigned division whenever c fits (64-bit integer division costs several
+// times more instructions, and per-cell kernels are otherwise cheap).
+__device__ __forceinline__ void lat_coords(int64_t c, int X, int Y, int& I, int& J, int& Z) {
+  if (c < 0x7fffffffLL) {
+    const unsigned u = (unsigned)c, ux = (unsigned)X, uy = (unsigned)Y, t = u / ux;
+    I = (int)(u - t * ux);
+    J = (int)(t % uy);
+    Z = (int)(t / uy);
+  } else {
+    const int64_t t = c / X;
+    I = (int)(c - t * X);
+    J = (int)(t % Y);
+    Z = (int)(t / Y);
+  }
+}
+
 struct MinresState;  // device-side scalars of the MINRES recurrence
 
 struct hd_op {

@@ -106,7 +106,8 @@ __global__ void k_sa_pvals(LevelT<double> L, int fx, int fy, int fz, double* __r
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = L.n();
   if (i >= n) return;
-  const int I = (int)(i % L.X), J = (int)((i / L.X) % L.Y), Z = (int)(i / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(i, L.X, L.Y, I, J, Z);
   const Face7<double> f = faces7(L, I, J, Z);
   const int so[3] = {out_step(I, L.X, fx), out_step(J, L.Y, fy), out_step(Z, L.Z, fz)};
   const int si[3] = {in_step(I, L.X, fx), in_step(J, L.Y, fy), in_step(Z, L.Z, fz)};
@@ -161,7 +162,8 @@ __global__ void k_sa_galerkin(LevelT<double> L, CDims c, const double* __restric
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nc = A1.n();
   if (C >= nc) return;
-  const int Cx = (int)(C % c.X), Cy = (int)((C / c.X) % c.Y), Cz = (int)(C / ((int64_t)c.X * c.Y));
+  int Cx, Cy, Cz;
+  lat_coords(C, c.X, c.Y, Cx, Cy, Cz);
   const int64_t n = L.n();
   double acc[33];
   for (int o = 0; o < 33; ++o) acc[o] = 0.0;
@@ -205,7 +207,8 @@ __global__ void k_ua_galerkin(StLevelT<double> F, CDims c, StLevelT<double> A, i
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nc = A.n(), n = F.n();
   if (C >= nc) return;
-  const int Cx = (int)(C % c.X), Cy = (int)((C / c.X) % c.Y), Cz = (int)(C / ((int64_t)c.X * c.Y));
+  int Cx, Cy, Cz;
+  lat_coords(C, c.X, c.Y, Cx, Cy, Cz);
   double acc[27];
   for (int o = 0; o < 27; ++o) acc[o] = 0.0;
   for (int Z = c.fz * Cz; Z < min(c.fz * Cz + c.fz, F.Z); ++Z)
@@ -292,7 +295,8 @@ template <typename T, int NO>
 __global__ void k_st_scale_jacobi(StLevelT<T> L, const T* __restrict__ b, T* __restrict__ xo) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   auto xa = [&](int, int, int, int k) { return L.dinv[k] * b[k]; };
   const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
   xo[c] = fma(L.dinv[c], r, xa(I, J, Z, (int)c));
@@ -302,7 +306,8 @@ template <typename T, int NO>
 __global__ void k_st_jacobi(StLevelT<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   auto xa = [&](int, int, int, int k) { return x[k]; };
   const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
   xo[c] = fma(L.dinv[c], r, x[c]);
@@ -313,7 +318,8 @@ template <typename T, int NO>
 __global__ void k_st_resid(StLevelT<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   auto xa = [&](int, int, int, int k) { return x[k]; };
   r[c] = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
 }
@@ -325,7 +331,8 @@ __global__ void k_st_restrict_small(StLevelT<T> L, CDims cd, const T* __restrict
                                     T* __restrict__ bc) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
-  const int Cx = (int)(C % cd.X), Cy = (int)((C / cd.X) % cd.Y), Cz = (int)(C / ((int64_t)cd.X * cd.Y));
+  int Cx, Cy, Cz;
+  lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
   auto xa = [&](int, int, int, int k) { return x[k]; };
   T s = (T)0;
   for (int k = cd.fz * Cz; k < min(cd.fz * Cz + cd.fz, L.Z); ++k)
@@ -342,7 +349,8 @@ template <typename T>
 __global__ void k_agg_sum(int X, int Y, int Z, CDims cd, const T* __restrict__ r, T* __restrict__ bc) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
-  const int Cx = (int)(C % cd.X), Cy = (int)((C / cd.X) % cd.Y), Cz = (int)(C / ((int64_t)cd.X * cd.Y));
+  int Cx, Cy, Cz;
+  lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
   T s = (T)0;
   for (int k = cd.fz * Cz; k < min(cd.fz * Cz + cd.fz, Z); ++k)
     for (int j = cd.fy * Cy; j < min(cd.fy * Cy + cd.fy, Y); ++j)
@@ -354,7 +362,8 @@ template <typename T>
 __global__ void k_st_prolong_add(StLevelT<T> L, CDims cd, const T* __restrict__ e, T* __restrict__ x) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   x[c] += e[agg(I, cd.fx) + (int64_t)cd.X * (agg(J, cd.fy) + (int64_t)cd.Y * agg(Z, cd.fz))];
 }
 
@@ -364,7 +373,8 @@ __global__ void k_st_jacobi_prolong(StLevelT<T> L, CDims cd, const T* __restrict
                                     const T* __restrict__ e, T* __restrict__ xo) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   auto xa = [&](int i, int j, int z, int k) {
     return x[k] + e[agg(i, cd.fx) + cd.X * (agg(j, cd.fy) + cd.Y * agg(z, cd.fz))];
   };
@@ -378,7 +388,8 @@ template <typename T>
 __global__ void k_sa_res0(LevelT<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= L.n()) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   r[c] = stencil_res<T>(L, x, b[c], x[c], I, J, Z, c);
 }
 
@@ -391,7 +402,8 @@ __global__ void k_sa_restrict0(LevelT<T> L, CDims cd, const T* __restrict__ pv, 
                                T* __restrict__ bc) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
-  const int Cc[3] = {(int)(C % cd.X), (int)((C / cd.X) % cd.Y), (int)(C / ((int64_t)cd.X * cd.Y))};
+  int Cc[3];
+  lat_coords(C, cd.X, cd.Y, Cc[0], Cc[1], Cc[2]);
   const int ext[3] = {L.X, L.Y, L.Z}, f[3] = {cd.fx, cd.fy, cd.fz};
   const int64_t str[3] = {1, (int64_t)L.X, (int64_t)L.X * L.Y};
   const int64_t n = L.n();
@@ -431,7 +443,8 @@ __global__ void k_sa_prolong0(LevelT<T> L, CDims cd, const T* __restrict__ pv, c
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = L.n();
   if (c >= n) return;
-  const int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   const int Dx = agg(I, cd.fx), Dy = agg(J, cd.fy), Dz = agg(Z, cd.fz);
   auto ev = [&](int ex, int ey, int ez) { return e[ex + (int64_t)cd.X * (ey + (int64_t)cd.Y * ez)]; };
   T v = pv[c] * ev(Dx, Dy, Dz);

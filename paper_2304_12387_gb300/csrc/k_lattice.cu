@@ -36,7 +36,8 @@ __global__ void k_div(const LatticeDims L, const double* __restrict__ u, double*
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t n = (int64_t)L.X * L.Y * L.Z;
   if (c >= n) return;
-  int I = (int)(c % L.X), J = (int)((c / L.X) % L.Y), Z = (int)(c / ((int64_t)L.X * L.Y));
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
   int64_t xl = I + (int64_t)(L.X + 1) * (J + (int64_t)L.Y * Z);
   int64_t yl = L.n_xf + I + (int64_t)L.X * (J + (int64_t)(L.Y + 1) * Z);
   int64_t yh = yl + L.X;
@@ -116,7 +117,8 @@ template <typename T>
 __global__ void k_level_diag(LevelT<T> lv) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   int64_t xl = I + (int64_t)(lv.X + 1) * (J + (int64_t)lv.Y * Z);
   int64_t yl = I + (int64_t)lv.X * (J + (int64_t)(lv.Y + 1) * Z);
   int64_t zl = I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z);
@@ -158,7 +160,8 @@ __global__ void k_coarsen_z(LevelT<double> f, LevelT<double> c) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t n = (int64_t)c.X * c.Y * (c.Z + 1);
   if (t >= n) return;
-  int Ic = (int)(t % c.X), Jc = (int)((t / c.X) % c.Y), Zc = (int)(t / ((int64_t)c.X * c.Y));
+  int Ic, Jc, Zc;
+  lat_coords(t, c.X, c.Y, Ic, Jc, Zc);
   int Z = min(c.fz * Zc, f.Z);
   double s = 0.0;
   for (int J = c.fy * Jc; J < min(c.fy * Jc + c.fy, f.Y); ++J)
@@ -168,7 +171,8 @@ __global__ void k_coarsen_z(LevelT<double> f, LevelT<double> c) {
 __global__ void k_coarsen_mass(LevelT<double> f, LevelT<double> c) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= c.n()) return;
-  int Ic = (int)(t % c.X), Jc = (int)((t / c.X) % c.Y), Zc = (int)(t / ((int64_t)c.X * c.Y));
+  int Ic, Jc, Zc;
+  lat_coords(t, c.X, c.Y, Ic, Jc, Zc);
   double s = 0.0;
   for (int Z = c.fz * Zc; Z < min(c.fz * Zc + c.fz, f.Z); ++Z)
     for (int J = c.fy * Jc; J < min(c.fy * Jc + c.fy, f.Y); ++J)
@@ -203,7 +207,8 @@ template <typename T>
 __global__ void k_schur_apply(LevelT<T> lv, const T* __restrict__ x, T* __restrict__ y) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   y[c] = -stencil_res<T>(lv, x, (T)0, x[c], I, J, Z, c);
 }
 
@@ -212,7 +217,8 @@ __global__ void k_vc_jacobi_prolong(LevelT<T> lv, LevelT<T> cl, const T* __restr
                                     const T* __restrict__ xcrs, T* __restrict__ xo) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   T xs = x[c] + xcrs[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
   xo[c] = fma(lv.dinv[c], stencil_res_prolong<T>(lv, cl, x, xcrs, b[c], xs, I, J, Z, c), xs);
 }
@@ -222,7 +228,8 @@ template <typename T>
 __global__ void k_vc_prolong_add(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ xcrs, T* __restrict__ x) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   x[c] += xcrs[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
 }
 
@@ -232,7 +239,8 @@ __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ 
                               T* __restrict__ bc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cl.n()) return;
-  int Ic = (int)(t % cl.X), Jc = (int)((t / cl.X) % cl.Y), Zc = (int)(t / ((int64_t)cl.X * cl.Y));
+  int Ic, Jc, Zc;
+  lat_coords(t, cl.X, cl.Y, Ic, Jc, Zc);
   T s = (T)0;
   for (int Z = cl.fz * Zc; Z < min(cl.fz * Zc + cl.fz, lv.Z); ++Z)
     for (int J = cl.fy * Jc; J < min(cl.fy * Jc + cl.fy, lv.Y); ++J)
@@ -690,7 +698,8 @@ __global__ void k_restrict_plain(LevelT<double> lv, LevelT<double> cl, const dou
                                  double* __restrict__ bc) {
   int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= cl.n()) return;
-  int Ic = (int)(t % cl.X), Jc = (int)((t / cl.X) % cl.Y), Zc = (int)(t / ((int64_t)cl.X * cl.Y));
+  int Ic, Jc, Zc;
+  lat_coords(t, cl.X, cl.Y, Ic, Jc, Zc);
   double s = 0.0;
   for (int Z = cl.fz * Zc; Z < min(cl.fz * Zc + cl.fz, lv.Z); ++Z)
     for (int J = cl.fy * Jc; J < min(cl.fy * Jc + cl.fy, lv.Y); ++J)
@@ -701,7 +710,8 @@ __global__ void k_prolong_add(LevelT<double> lv, LevelT<double> cl, const double
                               double* __restrict__ z) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   z[c] += xc[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
 }
 

@@ -36,7 +36,8 @@ template <typename T>
 __global__ void k_vc_jacobi(LevelT<T> lv, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo) {
   int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (c >= lv.n()) return;
-  int I = (int)(c % lv.X), J = (int)((c / lv.X) % lv.Y), Z = (int)(c / ((int64_t)lv.X * lv.Y));
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
   T xc = x[c];
   xo[c] = fma(lv.dinv[c], stencil_res<T>(lv, x, b[c], xc, I, J, Z, c), xc);
 }
