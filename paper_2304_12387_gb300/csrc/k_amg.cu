@@ -27,9 +27,6 @@ namespace {
 constexpr int TPB = 256;
 inline unsigned nblk(int64_t n) { return (unsigned)((n + TPB - 1) / TPB); }
 constexpr double SA_OMEGA = 4.0 / 3.0;
-// stencil levels with at most this many cells restrict with one fused kernel
-// (one thread per coarse cell is too serial on this GPU even on small levels: off)
-constexpr int64_t SMALL_LEVEL = 0;
 // Above this many cells a stencil level runs its sweeps unfused: the fused forms
 // (first two sweeps from zero; prolongation + sweep) recompute D^-1 b or x + P e at
 // every neighbour, which doubles the FP64 operations, and the FP64 pipe (about
@@ -324,26 +321,6 @@ __global__ void k_st_resid(StLevelT<T> L, const T* __restrict__ b, const T* __re
   r[c] = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
 }
 
-// b_C = sum over the aggregate of the residual b - A x, one thread per coarse cell
-// (small levels, where launch count rather than bandwidth sets the time)
-template <typename T, int NO>
-__global__ void k_st_restrict_small(StLevelT<T> L, CDims cd, const T* __restrict__ b, const T* __restrict__ x,
-                                    T* __restrict__ bc) {
-  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
-  int Cx, Cy, Cz;
-  lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
-  auto xa = [&](int, int, int, int k) { return x[k]; };
-  T s = (T)0;
-  for (int k = cd.fz * Cz; k < min(cd.fz * Cz + cd.fz, L.Z); ++k)
-    for (int j = cd.fy * Cy; j < min(cd.fy * Cy + cd.fy, L.Y); ++j)
-      for (int i = cd.fx * Cx; i < min(cd.fx * Cx + cd.fx, L.X); ++i) {
-        const int64_t c = i + (int64_t)L.X * (j + (int64_t)L.Y * k);
-        s += b[c] - st_row<T, NO>(L, (int)c, i, j, k, xa);
-      }
-  bc[C] = s;
-}
-
 // b_C = sum of r over the aggregate of C (plain aggregation; fine lattice X x Y x Z)
 template <typename T>
 __global__ void k_agg_sum(int X, int Y, int Z, CDims cd, const T* __restrict__ r, T* __restrict__ bc) {
@@ -504,15 +481,10 @@ const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, int l, const T* b, T* 
   const T* xc = nullptr;
   for (int rep = 0; rep < repeats; ++rep) {
     if (rep > 0) k_st_prolong_add<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, xc, cur);
-    if (L.n() <= SMALL_LEVEL) {
-      if (w33) k_st_restrict_small<T, 33><<<nblk(C.n()), TPB, 0, h->stream>>>(L, cd, b, cur, C.b);
-      else k_st_restrict_small<T, 27><<<nblk(C.n()), TPB, 0, h->stream>>>(L, cd, b, cur, C.b);
-    } else {
-      T* rtmp = (cur == L.x0) ? L.x1 : L.x0;  // free until the post-smoothing
-      if (w33) k_st_resid<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
-      else k_st_resid<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
-      k_agg_sum<T><<<nblk(C.n()), TPB, 0, h->stream>>>(L.X, L.Y, L.Z, cd, rtmp, C.b);
-    }
+    T* rtmp = (cur == L.x0) ? L.x1 : L.x0;  // free until the post-smoothing
+    if (w33) k_st_resid<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
+    else k_st_resid<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
+    k_agg_sum<T><<<nblk(C.n()), TPB, 0, h->stream>>>(L.X, L.Y, L.Z, cd, rtmp, C.b);
     xc = sa_level<T>(h, st, l + 1, C.b, nullptr);
   }
   T* o = (nu == 1 && out) ? out : ((cur == L.x0) ? L.x1 : L.x0);
