@@ -111,10 +111,12 @@ typedef struct {
   int32_t smooth_levels; /* prolongation of the Schur V-cycle: 0: piecewise constant on the 2x2x2
                             aggregates (unsmoothed aggregation); 1: the first level's prolongator
                             smoothed, P = (I - 4/3 D_l1^-1 S~) P0 (smoothed aggregation; the first
-                            coarse level is a 33-point stencil, the deeper ones 27-point). The
-                            paper's AMG (Sec. 3.2) gives mesh-independent iteration counts;
-                            smoothing restores them for log-normal coefficients. Other values:
-                            HD_ERR_NOT_IMPLEMENTED. The learned Schur preconditioner keeps the
+                            coarse level is a 33-point stencil, the deeper ones 27-point); 2: the
+                            second level's prolongator smoothed in the same way with its own
+                            l1 diagonal (level 2 a 179-point stencil, level 3 81-point, the
+                            deeper ones 27-point). The paper's AMG (Sec. 3.2) gives
+                            mesh-independent iteration counts; smoothing restores them for
+                            log-normal coefficients. Other values: HD_ERR_NOT_IMPLEMENTED. The learned Schur preconditioner keeps the
                             unsmoothed hierarchy for its coarse correction. */
   int32_t w_levels;      /* with cycle = 2: the two coarse corrections are made on levels
                             0..w_levels-1 only, one below (0: on every level); >= 0 */

@@ -269,7 +269,7 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->cycle = d->cycle == 2 ? 2 : 1;
   if (h->coarse_max > 4096) { delete h; return HD_ERR_INVALID_ARG; }
   if (d->smooth_levels < 0) { delete h; return HD_ERR_INVALID_ARG; }
-  if (d->smooth_levels > 1) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  if (d->smooth_levels > 2) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
   h->sa = d->smooth_levels;
   if (d->w_levels < 0) { delete h; return HD_ERR_INVALID_ARG; }
   h->w_levels = d->w_levels;

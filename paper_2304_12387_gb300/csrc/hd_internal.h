@@ -57,16 +57,17 @@ struct LevelT {
 
 // A coarse level of the smoothed-aggregation hierarchy: a symmetric stencil on
 // an X x Y x Z cell lattice with NO offsets (33 on the first coarse level: the
-// 3x3x3 box and the six cells two steps away along an axis; 27 below: the box).
+// 3x3x3 box and the six cells two steps away along an axis; 27 below: the box;
+// 179 and 81 on levels 2 and 3 when level 1's prolongator is smoothed as well).
 // Stored by offset, a[h * n + c] = A(c, c + off_h) for the centre and the
-// offsets that come later in lattice order (NH = 17 or 14 of them); the
+// offsets that come later in lattice order (NH = (NO + 1) / 2 of them); the
 // mirrored coefficient A(c, c - off_h) is a[h * n + c - off_h]. 0 where the
 // neighbour is outside. During setup a holds all NO offsets.
 template <typename T>
 struct StLevelT {
   int X, Y, Z;
   int fx, fy, fz;      // aggregation factor from the previous (finer) level
-  int no;              // 33 or 27
+  int no;              // 27, 33, 81 or 179
   T* a;                // [NH][n] (setup: [no][n])
   T* dinv;             // 1 / sum_o |a[o][c]|  (l1-Jacobi)
   T* x0;
@@ -128,12 +129,14 @@ struct hd_op {
   double* d_coarse_inv = nullptr;  // dense inverse of the coarsest level (or of A + s 11^T)
   int coarse_n = 0;
   std::vector<LevelT<double>> lv;
-  // smoothed-aggregation hierarchy (smooth_levels = 1): prolongator values of
+  // smoothed-aggregation hierarchy (smooth_levels >= 1): prolongator values of
   // level 0 ([4][n_l2]: own aggregate, then the aggregates across the x, y and
   // z faces), stencil levels 1.., dense inverse of its coarsest level
   int sa = 0;
   double* sa_p = nullptr;
   float* sa_pf = nullptr;
+  double* sa_p1 = nullptr;  // smooth_levels = 2: prolongator of level 1 ([11][n_1])
+  float* sa_p1f = nullptr;
   std::vector<StLevelT<double>> st;
   std::vector<StLevelT<float>> stf;
   double* d_sa_coarse_inv = nullptr;

@@ -1,4 +1,4 @@
-// Smoothed-aggregation hierarchy of the Schur V/W-cycle (smooth_levels = 1).
+// Smoothed-aggregation hierarchy of the Schur V/W-cycle (smooth_levels = 1 or 2).
 //
 // The paper applies one AMG V-cycle to the approximate Schur complement S~ and
 // relies on its mesh-independent convergence (Sec. 3.2, Sec. 4). Here:
@@ -12,6 +12,9 @@
 //   level 1: A_1 = P_0^T S~ P_0, a 33-point stencil (3x3x3 box and the six cells
 //            two steps away along an axis), computed per coarse cell from P_0 and
 //            the fine stencil;
+//   level 2: with smooth_levels = 2, P_1 = (I - omega D_l1^-1 A_1) P0 on level 1
+//            as well (at most 11 nonzeros per row, see below) and A_2 = P_1^T A_1
+//            P_1, a 179-point stencil; level 3 its plain aggregation, 81 points;
 //   deeper : plain aggregation, A_{l+1} = P0^T A_l P0, 27-point stencils;
 //   coarsest: dense inverse (host Cholesky), + s 1 1^T when S~ is singular.
 // l1-Jacobi smoothing (D_l1 = sum_j |A_ij|) on every level, nu sweeps before and
@@ -34,32 +37,101 @@ constexpr double SA_OMEGA = 4.0 / 3.0;
 // overhead dominates and fusing wins.
 constexpr int64_t FUSE_MAX = 65536;
 
-// offset o of a stencil level: o < 27 the 3x3x3 box (dx fastest), then +-2 along
-// x, y, z (o = 27 + 2 d + (negative ? 1 : 0))
+// Offset shapes of the stencil levels, by their number of offsets NO:
+//   27 : the 3x3x3 box (plain aggregation of a level whose offsets reach 2 at most
+//        along an axis and 1 across it);
+//   33 : the box and (+-2, 0, 0) with its permutations (P_0^T S~ P_0);
+//   179: the 5x5x5 box and (+-3, a, b), |a|, |b| <= 1, with its permutations
+//        (P_1^T A_1 P_1 when the prolongator of level 1 is smoothed as well);
+//   81 : the box and (+-2, a, b), |a|, |b| <= 1, with its permutations (plain
+//        aggregation of the 179-point level).
+// Offset o < B^3 (B = 3, or 5 for 179) runs over the box, dx fastest. The rest are
+// axial: for 33, o = B^3 + 2 d + (negative); for 81 and 179, o = B^3 + 18 d +
+// 9 (negative) + (a + 1) + 3 (b + 1), with d the axis and (a, b) the offsets
+// across it in the order of the two remaining axes.
+template <int NO>
+struct Shape {
+  static_assert(NO == 27 || NO == 33 || NO == 81 || NO == 179, "stencil shape");
+  static constexpr int R = NO == 179 ? 2 : 1;  // box radius
+  static constexpr int B = 2 * R + 1;
+  static constexpr int NB = B * B * B;
+  static constexpr int NH = (NO + 1) / 2;                         // stored (half) offsets
+};
+__host__ __device__ constexpr int n_half(int no) { return (no + 1) / 2; }
+
+template <int NO>
 __host__ __device__ __forceinline__ void st_off(int o, int& dx, int& dy, int& dz) {
-  if (o < 27) {
-    dx = o % 3 - 1;
-    dy = (o / 3) % 3 - 1;
-    dz = o / 9 - 1;
+  using S = Shape<NO>;
+  if (o < S::NB) {
+    dx = o % S::B - S::R;
+    dy = (o / S::B) % S::B - S::R;
+    dz = o / (S::B * S::B) - S::R;
+    return;
+  }
+  const int a = o - S::NB;
+  int d, v, u = 0, w = 0;
+  if (NO == 33) {
+    d = a >> 1;
+    v = (a & 1) ? -2 : 2;
   } else {
-    const int a = o - 27, d = a >> 1, v = (a & 1) ? -2 : 2;
-    dx = d == 0 ? v : 0;
-    dy = d == 1 ? v : 0;
-    dz = d == 2 ? v : 0;
+    d = a / 18;
+    const int r = a % 18;
+    v = r >= 9 ? -(S::R + 1) : S::R + 1;
+    u = (r % 9) % 3 - 1;
+    w = (r % 9) / 3 - 1;
+  }
+  dx = d == 0 ? v : u;
+  dy = d == 0 ? u : d == 1 ? v : w;
+  dz = d == 2 ? v : w;
+}
+// run-time shape on the host (setup: the dense coarsest matrix)
+inline void st_off_any(int no, int o, int& dx, int& dy, int& dz) {
+  switch (no) {
+    case 27: st_off<27>(o, dx, dy, dz); break;
+    case 33: st_off<33>(o, dx, dy, dz); break;
+    case 81: st_off<81>(o, dx, dy, dz); break;
+    default: st_off<179>(o, dx, dy, dz); break;
   }
 }
-// stored (half) offset h -> full offset index: h = 0 the centre, 1..13 the box
-// offsets after it in lattice order, 14..16 the +2 axis offsets
-__host__ __device__ __forceinline__ int half_full_index(int h) { return h < 14 ? 13 + h : 27 + 2 * (h - 14); }
-__host__ __device__ constexpr int n_half(int no) { return no == 33 ? 17 : 14; }
 
-// index of an offset in the 33-offset list, -1 if it is not there
-__device__ __forceinline__ int st_index(int dx, int dy, int dz) {
-  if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1);
-  if (dy == 0 && dz == 0 && (dx == 2 || dx == -2)) return 27 + (dx < 0);
-  if (dx == 0 && dz == 0 && (dy == 2 || dy == -2)) return 29 + (dy < 0);
-  if (dx == 0 && dy == 0 && (dz == 2 || dz == -2)) return 31 + (dz < 0);
-  return -1;
+// stored (half) offset h -> full offset index: h = 0 the centre, then the box
+// offsets after it in lattice order, then the positive axial offsets
+template <int NO>
+__host__ __device__ __forceinline__ int half_full_index(int h) {
+  using S = Shape<NO>;
+  constexpr int cb = (S::NB - 1) / 2;
+  if (h <= cb) return cb + h;
+  const int j = h - cb - 1;
+  return NO == 33 ? S::NB + 2 * j : S::NB + 18 * (j / 9) + j % 9;
+}
+
+// index of an offset in the list of shape NO, -1 if it is not there
+template <int NO>
+__host__ __device__ __forceinline__ int st_index(int dx, int dy, int dz) {
+  using S = Shape<NO>;
+  if (abs(dx) <= S::R && abs(dy) <= S::R && abs(dz) <= S::R)
+    return (dx + S::R) + S::B * (dy + S::R) + S::B * S::B * (dz + S::R);
+  if (NO == 27) return -1;
+  const int A = S::R + 1;  // the axial step
+  int d, v, u, w;
+  if (abs(dx) == A) { d = 0; v = dx; u = dy; w = dz; }
+  else if (abs(dy) == A) { d = 1; v = dy; u = dx; w = dz; }
+  else if (abs(dz) == A) { d = 2; v = dz; u = dx; w = dy; }
+  else return -1;
+  if (NO == 33) return (u == 0 && w == 0) ? S::NB + 2 * d + (v < 0) : -1;
+  if (abs(u) > 1 || abs(w) > 1) return -1;
+  return S::NB + 18 * d + (v < 0 ? 9 : 0) + (u + 1) + 3 * (w + 1);
+}
+
+// Calls f(std::integral_constant<int, NO>) for a level's run-time shape.
+template <typename F>
+void with_shape(int no, F f) {
+  switch (no) {
+    case 27: f(std::integral_constant<int, 27>{}); break;
+    case 33: f(std::integral_constant<int, 33>{}); break;
+    case 81: f(std::integral_constant<int, 81>{}); break;
+    default: f(std::integral_constant<int, 179>{}); break;
+  }
 }
 
 // -- level 0: the smoothed prolongator ---------------------------------------------
@@ -187,7 +259,7 @@ __global__ void k_sa_galerkin(LevelT<double> L, CDims c, const double* __restric
         if (s == 1) { if (!so[0]) continue; ex = (jI + so[0]) / c.fx; }
         if (s == 2) { if (!so[1]) continue; ey = (jJ + so[1]) / c.fy; }
         if (s == 3) { if (!so[2]) continue; ez = (jZ + so[2]) / c.fz; }
-        const int o = st_index(ex - Cx, ey - Cy, ez - Cz);
+        const int o = st_index<33>(ex - Cx, ey - Cy, ez - Cz);
         if (o < 0) {
           atomicExch(bad, 1);
           continue;
@@ -199,46 +271,49 @@ __global__ void k_sa_galerkin(LevelT<double> L, CDims c, const double* __restric
   for (int o = 0; o < 33; ++o) A1.a[o * nc + C] = acc[o];
 }
 
-// A_{l+1} = P0^T A_l P0 for plain aggregation of a stencil level (27-point result)
+// A_{l+1} = P0^T A_l P0 for plain aggregation of a stencil level of shape NI into
+// one of shape NOUT
+template <int NI, int NOUT>
 __global__ void k_ua_galerkin(StLevelT<double> F, CDims c, StLevelT<double> A, int* __restrict__ bad) {
   const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nc = A.n(), n = F.n();
   if (C >= nc) return;
   int Cx, Cy, Cz;
   lat_coords(C, c.X, c.Y, Cx, Cy, Cz);
-  double acc[27];
-  for (int o = 0; o < 27; ++o) acc[o] = 0.0;
+  double acc[NOUT];
+  for (int o = 0; o < NOUT; ++o) acc[o] = 0.0;
   for (int Z = c.fz * Cz; Z < min(c.fz * Cz + c.fz, F.Z); ++Z)
     for (int J = c.fy * Cy; J < min(c.fy * Cy + c.fy, F.Y); ++J)
       for (int I = c.fx * Cx; I < min(c.fx * Cx + c.fx, F.X); ++I) {
         const int64_t i = I + (int64_t)F.X * (J + (int64_t)F.Y * Z);
-        for (int o = 0; o < F.no; ++o) {
+        for (int o = 0; o < NI; ++o) {
           const double a = F.a[o * n + i];
           if (a == 0.0) continue;
           int dx, dy, dz;
-          st_off(o, dx, dy, dz);
+          st_off<NI>(o, dx, dy, dz);
           const int jI = I + dx, jJ = J + dy, jZ = Z + dz;
           if (jI < 0 || jI >= F.X || jJ < 0 || jJ >= F.Y || jZ < 0 || jZ >= F.Z) {
             atomicExch(bad, 1);
             continue;
           }
-          const int ox = jI / c.fx - Cx, oy = jJ / c.fy - Cy, oz = jZ / c.fz - Cz;
-          if (ox < -1 || ox > 1 || oy < -1 || oy > 1 || oz < -1 || oz > 1) {
+          const int oc = st_index<NOUT>(jI / c.fx - Cx, jJ / c.fy - Cy, jZ / c.fz - Cz);
+          if (oc < 0) {
             atomicExch(bad, 1);
             continue;
           }
-          acc[(ox + 1) + 3 * (oy + 1) + 9 * (oz + 1)] += a;
+          acc[oc] += a;
         }
       }
-  for (int o = 0; o < 27; ++o) A.a[o * nc + C] = acc[o];
+  for (int o = 0; o < NOUT; ++o) A.a[o * nc + C] = acc[o];
 }
 
 // keep the centre and the later offsets (setup: full -> half storage)
+template <int NO>
 __global__ void k_st_compress(StLevelT<double> A, double* __restrict__ half) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t n = A.n();
   if (c >= n) return;
-  for (int h = 0; h < n_half(A.no); ++h) half[h * n + c] = A.a[half_full_index(h) * n + c];
+  for (int h = 0; h < Shape<NO>::NH; ++h) half[h * n + c] = A.a[half_full_index<NO>(h) * n + c];
 }
 
 __global__ void k_st_dinv(StLevelT<double> A) {
@@ -253,28 +328,37 @@ __global__ void k_st_dinv(StLevelT<double> A) {
 // -- solve-time kernels of the stencil levels ---------------------------------------
 // (A x)_c from the half-stored symmetric stencil; x_at(I, J, Z, k) supplies the
 // vector value at lattice cell (I, J, Z) with linear index k. Which neighbours
-// exist is decided once per cell (flags for steps -2..2 per direction), so that
+// exist is decided once per cell (flags for steps -3..3 per direction), so that
 // each unrolled offset costs a few flag tests and one index add: these sweeps
 // are otherwise bound by integer address arithmetic rather than by the FP units
 // or HBM. Cell indices fit 32 bits (stencil levels are at most 1/8 of the fine
 // lattice).
 template <typename T, int NO, typename XA>
 __device__ __forceinline__ T st_row(const StLevelT<T>& L, int c, int I, int J, int Z, XA x_at) {
-  constexpr int NH = n_half(NO);
+  constexpr int NH = Shape<NO>::NH;
   const int64_t n = L.n();
   const int X = L.X, XY = L.X * L.Y;
-  const bool fx[5] = {I >= 2, I >= 1, true, I + 1 < L.X, I + 2 < L.X};
-  const bool fy[5] = {J >= 2, J >= 1, true, J + 1 < L.Y, J + 2 < L.Y};
-  const bool fz[5] = {Z >= 2, Z >= 1, true, Z + 1 < L.Z, Z + 2 < L.Z};
+  const bool fx[7] = {I >= 3, I >= 2, I >= 1, true, I + 1 < L.X, I + 2 < L.X, I + 3 < L.X};
+  const bool fy[7] = {J >= 3, J >= 2, J >= 1, true, J + 1 < L.Y, J + 2 < L.Y, J + 3 < L.Y};
+  const bool fz[7] = {Z >= 3, Z >= 2, Z >= 1, true, Z + 1 < L.Z, Z + 2 < L.Z, Z + 3 < L.Z};
   T s = L.a[c] * x_at(I, J, Z, c);
 #pragma unroll
   for (int h = 1; h < NH; ++h) {
     int dx, dy, dz;
-    st_off(half_full_index(h), dx, dy, dz);
+    st_off<NO>(half_full_index<NO>(h), dx, dy, dz);
     const int d = dx + X * dy + XY * dz;
     const T* ah = L.a + h * n;
-    if (fx[2 + dx] && fy[2 + dy] && fz[2 + dz]) s = fma(ah[c], x_at(I + dx, J + dy, Z + dz, c + d), s);
-    if (fx[2 - dx] && fy[2 - dy] && fz[2 - dz]) s = fma(ah[c - d], x_at(I - dx, J - dy, Z - dz, c - d), s);
+    const bool okp = fx[3 + dx] && fy[3 + dy] && fz[3 + dz];
+    const bool okm = fx[3 - dx] && fy[3 - dy] && fz[3 - dz];
+    // every load is issued unconditionally, at the own cell where the neighbour
+    // is missing (a branch per offset would keep the loads from overlapping).
+    // The stored coefficient towards a missing +d neighbour is an exact zero;
+    // the mirrored one is selected away.
+    const T ap = ah[c];
+    T am = ah[okm ? c - d : c];
+    am = okm ? am : (T)0;
+    s = fma(ap, x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c), s);
+    s = fma(am, x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c), s);
   }
   return s;
 }
@@ -309,6 +393,136 @@ __global__ void k_st_jacobi(StLevelT<T> L, const T* __restrict__ b, const T* __r
   const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
   xo[c] = fma(L.dinv[c], r, x[c]);
 }
+
+// The wide shapes (81 and 179 offsets) sit on small levels: one thread per cell
+// leaves a few waves of threads that each walk a long serial chain of loads.
+// There a block of G warps takes 32 consecutive cells and warp w the stored
+// offsets h with h % G == w (the centre with warp 0); the G partial sums meet in
+// shared memory in a fixed order and warp 0 finishes the cell.
+template <int NO>
+struct SplitG {  // 8 and 4 measured best (16 warps per 32 cells: slower)
+  static constexpr int G = NO == 179 ? 8 : 4;
+};
+
+// Warp W's part of (A x)_c: the stored offsets h = W, W + G, ... (the centre with
+// warp 0). The offsets are known at compile time, so all loads are issued first
+// and the products added afterwards, in the order +d, -d per offset.
+template <typename T, int NO, int W, typename XA>
+__device__ __forceinline__ T st_row_part(const StLevelT<T>& L, int c, int I, int J, int Z, XA x_at) {
+  constexpr int NH = Shape<NO>::NH, G = SplitG<NO>::G;
+  constexpr int H0 = W == 0 ? G : W;
+  constexpr int CNT = H0 < NH ? (NH - 1 - H0) / G + 1 : 0;
+  constexpr int NV = CNT > 0 ? 2 * CNT : 1;
+  const int64_t n = L.n();
+  const int X = L.X, XY = L.X * L.Y;
+  const bool fx[7] = {I >= 3, I >= 2, I >= 1, true, I + 1 < L.X, I + 2 < L.X, I + 3 < L.X};
+  const bool fy[7] = {J >= 3, J >= 2, J >= 1, true, J + 1 < L.Y, J + 2 < L.Y, J + 3 < L.Y};
+  const bool fz[7] = {Z >= 3, Z >= 2, Z >= 1, true, Z + 1 < L.Z, Z + 2 < L.Z, Z + 3 < L.Z};
+  T av[NV], xv[NV];
+#pragma unroll
+  for (int j = 0; j < CNT; ++j) {
+    const int h = H0 + G * j;
+    int dx, dy, dz;
+    st_off<NO>(half_full_index<NO>(h), dx, dy, dz);
+    const int d = dx + X * dy + XY * dz;
+    const T* ah = L.a + h * n;
+    const bool okp = fx[3 + dx] && fy[3 + dy] && fz[3 + dz];
+    const bool okm = fx[3 - dx] && fy[3 - dy] && fz[3 - dz];
+    // missing neighbours: loads at the own cell; the stored +d coefficient is an
+    // exact zero there and the mirrored one is selected away
+    av[2 * j] = ah[c];
+    const T am = ah[okm ? c - d : c];
+    av[2 * j + 1] = okm ? am : (T)0;
+    xv[2 * j] = x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c);
+    xv[2 * j + 1] = x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c);
+  }
+  T s = W == 0 ? L.a[c] * x_at(I, J, Z, c) : (T)0;
+#pragma unroll
+  for (int j = 0; j < 2 * CNT; ++j) s = fma(av[j], xv[j], s);
+  return s;
+}
+
+template <typename T, int NO, typename XA>
+__device__ __forceinline__ T st_row_part_any(const StLevelT<T>& L, int c, int I, int J, int Z, int w, XA x_at) {
+  switch (w) {  // uniform per warp
+    case 0: return st_row_part<T, NO, 0>(L, c, I, J, Z, x_at);
+    case 1: return st_row_part<T, NO, 1>(L, c, I, J, Z, x_at);
+    case 2: return st_row_part<T, NO, 2>(L, c, I, J, Z, x_at);
+    case 3: return st_row_part<T, NO, 3>(L, c, I, J, Z, x_at);
+  }
+  if constexpr (SplitG<NO>::G > 4) {
+    switch (w) {
+      case 4: return st_row_part<T, NO, 4>(L, c, I, J, Z, x_at);
+      case 5: return st_row_part<T, NO, 5>(L, c, I, J, Z, x_at);
+      case 6: return st_row_part<T, NO, 6>(L, c, I, J, Z, x_at);
+      case 7: return st_row_part<T, NO, 7>(L, c, I, J, Z, x_at);
+    }
+  }
+  return (T)0;
+}
+
+// (A x)_c for the cell of this lane, complete in warp 0 (other warps: undefined).
+// Every thread of the block must call it (it holds a block barrier).
+template <typename T, int NO, typename XA>
+__device__ __forceinline__ T st_row_split(const StLevelT<T>& L, bool live, int c, int I, int J, int Z, XA x_at) {
+  constexpr int G = SplitG<NO>::G;
+  __shared__ T part[G][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  part[w][lane] = live ? st_row_part_any<T, NO>(L, c, I, J, Z, w, x_at) : (T)0;
+  __syncthreads();
+  T t = (T)0;
+  if (w == 0)
+    for (int g = 0; g < G; ++g) t += part[g][lane];
+  return t;
+}
+
+#define HD_SPLIT_CELL                                                 \
+  const int64_t c64 = (int64_t)blockIdx.x * 32 + (threadIdx.x & 31); \
+  const bool live = c64 < L.n();                                      \
+  const int c = live ? (int)c64 : 0;                                  \
+  int I = 0, J = 0, Z = 0;                                            \
+  if (live) lat_coords(c, L.X, L.Y, I, J, Z);                         \
+  const bool fin = live && threadIdx.x < 32;
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(32 * SplitG<NO>::G)
+    k_st_jacobi_split(StLevelT<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ xo) {
+  HD_SPLIT_CELL
+  auto xa = [&](int, int, int, int k) { return x[k]; };
+  const T ax = st_row_split<T, NO>(L, live, c, I, J, Z, xa);
+  if (fin) xo[c] = fma(L.dinv[c], b[c] - ax, x[c]);
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(32 * SplitG<NO>::G)
+    k_st_resid_split(StLevelT<T> L, const T* __restrict__ b, const T* __restrict__ x, T* __restrict__ r) {
+  HD_SPLIT_CELL
+  auto xa = [&](int, int, int, int k) { return x[k]; };
+  const T ax = st_row_split<T, NO>(L, live, c, I, J, Z, xa);
+  if (fin) r[c] = b[c] - ax;
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(32 * SplitG<NO>::G)
+    k_st_scale_jacobi_split(StLevelT<T> L, const T* __restrict__ b, T* __restrict__ xo) {
+  HD_SPLIT_CELL
+  auto xa = [&](int, int, int, int k) { return L.dinv[k] * b[k]; };
+  const T ax = st_row_split<T, NO>(L, live, c, I, J, Z, xa);
+  if (fin) xo[c] = fma(L.dinv[c], b[c] - ax, xa(I, J, Z, c));
+}
+
+template <typename T, int NO>
+__global__ void __launch_bounds__(32 * SplitG<NO>::G)
+    k_st_jacobi_prolong_split(StLevelT<T> L, CDims cd, const T* __restrict__ b, const T* __restrict__ x,
+                              const T* __restrict__ e, T* __restrict__ xo) {
+  HD_SPLIT_CELL
+  auto xa = [&](int i, int j, int z, int k) {
+    return x[k] + e[agg(i, cd.fx) + cd.X * (agg(j, cd.fy) + cd.Y * agg(z, cd.fz))];
+  };
+  const T ax = st_row_split<T, NO>(L, live, c, I, J, Z, xa);
+  if (fin) xo[c] = fma(L.dinv[c], b[c] - ax, xa(I, J, Z, c));
+}
+#undef HD_SPLIT_CELL
 
 // r = b - A x on a stencil level (fine-parallel half of the restriction)
 template <typename T, int NO>
@@ -424,11 +638,265 @@ __global__ void k_sa_prolong0(LevelT<T> L, CDims cd, const T* __restrict__ pv, c
   lat_coords(c, L.X, L.Y, I, J, Z);
   const int Dx = agg(I, cd.fx), Dy = agg(J, cd.fy), Dz = agg(Z, cd.fz);
   auto ev = [&](int ex, int ey, int ez) { return e[ex + (int64_t)cd.X * (ey + (int64_t)cd.Y * ez)]; };
-  T v = pv[c] * ev(Dx, Dy, Dz);
+  // no branches: a missing slot (no step out of the aggregate) holds an exact
+  // zero and points at the own aggregate
   const int sx = out_step(I, L.X, cd.fx), sy = out_step(J, L.Y, cd.fy), sz = out_step(Z, L.Z, cd.fz);
-  if (sx) v = fma(pv[n + c], ev(agg(I + sx, cd.fx), Dy, Dz), v);
-  if (sy) v = fma(pv[2 * n + c], ev(Dx, agg(J + sy, cd.fy), Dz), v);
-  if (sz) v = fma(pv[3 * n + c], ev(Dx, Dy, agg(Z + sz, cd.fz)), v);
+  const T p0 = pv[c], p1 = pv[n + c], p2 = pv[2 * n + c], p3 = pv[3 * n + c];
+  const T e0 = ev(Dx, Dy, Dz), e1 = ev(agg(I + sx, cd.fx), Dy, Dz), e2 = ev(Dx, agg(J + sy, cd.fy), Dz),
+          e3 = ev(Dx, Dy, agg(Z + sz, cd.fz));
+  T v = p0 * e0;
+  v = fma(p1, e1, v);
+  v = fma(p2, e2, v);
+  v = fma(p3, e3, v);
+  x[c] += v;
+}
+
+// -- level 1 -> 2 with a smoothed prolongator (smooth_levels = 2) --------------------
+// P_1 = (I - omega D_l1^-1 A_1) P0 on the 33-point level 1. Along a direction with
+// factor 2, let s = +1 for an odd fine coordinate and -1 for an even one (the side
+// on which the cell's aggregate has its other cell). A fine cell's row of P_1 then
+// has at most 11 nonzeros: slots 0..7, the aggregates agg + (b0 sx, b1 sy, b2 sz)
+// for bits b of the slot (slot 0 is the own aggregate), reached through the box
+// offsets and the axial steps towards s; slots 8 + d, the aggregate at -s along d
+// alone, reached through the axial step of 2 away from s. Stored as [11][n1].
+constexpr int P1_SLOTS = 11;
+
+struct AxisPos {  // fine coordinate along one direction: aggregate and side
+  int a, s;
+};
+__device__ __forceinline__ AxisPos axis_pos(int I, int f) { return AxisPos{I >> (f - 1), f == 2 ? ((I & 1) ? 1 : -1) : 0}; }
+
+// slot of the aggregate at offset D from the cell's own, -1 if the row has none
+__device__ __forceinline__ int p1_slot(const int D[3], const int s[3]) {
+  int bits = 0, far = -1;
+  for (int d = 0; d < 3; ++d) {
+    if (D[d] == 0) continue;
+    if (s[d] != 0 && D[d] == s[d]) {
+      bits |= 1 << d;
+    } else if (s[d] != 0 && D[d] == -s[d] && far < 0) {
+      far = d;
+    } else {
+      return -1;
+    }
+  }
+  if (far >= 0) return bits ? -1 : 8 + far;
+  return bits;
+}
+// coarse cell t of slot k for a fine cell with aggregate a and sides s; false when
+// the slot has no aggregate inside the coarse lattice ce
+__device__ __forceinline__ bool p1_target(int k, const int a[3], const int s[3], const int ce[3], int t[3]) {
+  for (int d = 0; d < 3; ++d) t[d] = a[d];
+  if (k < 8) {
+    for (int d = 0; d < 3; ++d)
+      if ((k >> d) & 1) {
+        if (!s[d]) return false;
+        t[d] += s[d];
+      }
+  } else {
+    const int d = k - 8;
+    if (!s[d]) return false;
+    t[d] -= s[d];
+  }
+  for (int d = 0; d < 3; ++d)
+    if (t[d] < 0 || t[d] >= ce[d]) return false;
+  return true;
+}
+
+// P_1 from the full-storage 33-point level (its l1 inverse diagonal included)
+__global__ void k_sa_pvals1(StLevelT<double> A1, CDims cd, double* __restrict__ p1, int* __restrict__ bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = A1.n();
+  if (i >= n) return;
+  int I, J, Z;
+  lat_coords(i, A1.X, A1.Y, I, J, Z);
+  const AxisPos px = axis_pos(I, cd.fx), py = axis_pos(J, cd.fy), pz = axis_pos(Z, cd.fz);
+  const int s[3] = {px.s, py.s, pz.s};
+  double acc[P1_SLOTS];
+  for (int k = 0; k < P1_SLOTS; ++k) acc[k] = 0.0;
+  acc[0] = 1.0;
+  const double wd = SA_OMEGA * A1.dinv[i];
+  for (int o = 0; o < 33; ++o) {
+    const double a = A1.a[o * n + i];
+    if (a == 0.0) continue;
+    int dx, dy, dz;
+    st_off<33>(o, dx, dy, dz);
+    const int jI = I + dx, jJ = J + dy, jZ = Z + dz;
+    if (jI < 0 || jI >= A1.X || jJ < 0 || jJ >= A1.Y || jZ < 0 || jZ >= A1.Z) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    const int D[3] = {(jI >> (cd.fx - 1)) - px.a, (jJ >> (cd.fy - 1)) - py.a, (jZ >> (cd.fz - 1)) - pz.a};
+    const int k = p1_slot(D, s);
+    if (k < 0) {
+      atomicExch(bad, 1);
+      continue;
+    }
+    acc[k] -= wd * a;
+  }
+  for (int k = 0; k < P1_SLOTS; ++k) p1[k * n + i] = acc[k];
+}
+
+// Enumerates the fine cells i with a slot for coarse cell C in their row of P_1
+// and calls fn(i, I, J, Z, slot). Per direction with factor 2 the candidates are
+// 2C-2 .. 2C+3 (the aggregate, one layer on each side through the box slots and a
+// second layer through the axial slot); factor 1 leaves C itself.
+template <typename F>
+__device__ __forceinline__ void for_support1(int X, int Y, int Zn, const CDims& cd, int Cx, int Cy, int Cz, F fn) {
+  const int x0 = cd.fx == 2 ? max(2 * Cx - 2, 0) : Cx, x1 = cd.fx == 2 ? min(2 * Cx + 3, X - 1) : Cx;
+  const int y0 = cd.fy == 2 ? max(2 * Cy - 2, 0) : Cy, y1 = cd.fy == 2 ? min(2 * Cy + 3, Y - 1) : Cy;
+  const int z0 = cd.fz == 2 ? max(2 * Cz - 2, 0) : Cz, z1 = cd.fz == 2 ? min(2 * Cz + 3, Zn - 1) : Cz;
+  for (int Z = z0; Z <= z1; ++Z)
+    for (int J = y0; J <= y1; ++J)
+      for (int I = x0; I <= x1; ++I) {
+        const AxisPos px = axis_pos(I, cd.fx), py = axis_pos(J, cd.fy), pz = axis_pos(Z, cd.fz);
+        const int s[3] = {px.s, py.s, pz.s};
+        const int D[3] = {Cx - px.a, Cy - py.a, Cz - pz.a};
+        const int k = p1_slot(D, s);
+        if (k >= 0) fn(I + X * (J + Y * Z), I, J, Z, k);
+      }
+}
+
+// A_2 = P_1^T A_1 P_1 (179-point), one thread per coarse cell C: for every fine i
+// in the support of column C, every neighbour j of i and every slot of row j
+template <int NOUT>
+__global__ void k_sa_galerkin1(StLevelT<double> A1, CDims cd, const double* __restrict__ p1, StLevelT<double> A2,
+                               int* __restrict__ bad) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = A2.n();
+  if (C >= nc) return;
+  int Cx, Cy, Cz;
+  lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
+  const int64_t n = A1.n();
+  const int ce[3] = {cd.X, cd.Y, cd.Z};
+  double acc[NOUT];
+  for (int o = 0; o < NOUT; ++o) acc[o] = 0.0;
+  for_support1(A1.X, A1.Y, A1.Z, cd, Cx, Cy, Cz, [&](int i, int I, int J, int Z, int k) {
+    const double p = p1[k * n + i];
+    if (p == 0.0) return;
+    for (int o = 0; o < 33; ++o) {
+      const double a = A1.a[o * n + i];
+      if (a == 0.0) continue;
+      int dx, dy, dz;
+      st_off<33>(o, dx, dy, dz);
+      const int jI = I + dx, jJ = J + dy, jZ = Z + dz;
+      if (jI < 0 || jI >= A1.X || jJ < 0 || jJ >= A1.Y || jZ < 0 || jZ >= A1.Z) {
+        atomicExch(bad, 1);
+        continue;
+      }
+      const int j = jI + A1.X * (jJ + A1.Y * jZ);
+      const AxisPos qx = axis_pos(jI, cd.fx), qy = axis_pos(jJ, cd.fy), qz = axis_pos(jZ, cd.fz);
+      const int ja[3] = {qx.a, qy.a, qz.a}, js[3] = {qx.s, qy.s, qz.s};
+      for (int t = 0; t < P1_SLOTS; ++t) {
+        int e[3];
+        if (!p1_target(t, ja, js, ce, e)) continue;
+        const double q = p1[t * n + j];
+        if (q == 0.0) continue;
+        const int oc = st_index<NOUT>(e[0] - Cx, e[1] - Cy, e[2] - Cz);
+        if (oc < 0) {
+          atomicExch(bad, 1);
+          continue;
+        }
+        acc[oc] = fma(p * a, q, acc[oc]);
+      }
+    }
+  });
+  for (int o = 0; o < NOUT; ++o) A2.a[o * nc + C] = acc[o];
+}
+
+// b_C = (P_1^T r)_C, one thread per coarse cell (neighbouring threads then read
+// neighbouring aggregates). The support is enumerated directly: per direction
+// with factor 2 the positions 2C-1 .. 2C+2 through the box slots (bit 1 at the
+// two outer ones), then 2C-2 / 2C+3 through the axial slot with the other two
+// directions inside the aggregate; 64 + 24 fine cells. Each row of four is
+// loaded before it is added; a missing cell reads the aggregate's first cell
+// with weight zero.
+template <typename T>
+__global__ void k_sa_restrict1(StLevelT<T> L, CDims cd, const T* __restrict__ p1, const T* __restrict__ r,
+                               T* __restrict__ bc) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
+  int Cx, Cy, Cz;
+  lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
+  const int64_t n = L.n();
+  const int64_t sy = L.X, sz = (int64_t)L.X * L.Y;
+  // position q = 0..3 of the box part along a direction: fine coordinate, slot bit
+  auto box_pos = [](int f, int ce, int extent, int q, int& x, int& bit) {
+    if (f == 2) {
+      x = 2 * ce - 1 + q;
+      bit = (q == 0 || q == 3);
+      return x >= 0 && x < extent;
+    }
+    x = ce;
+    bit = 0;
+    return q == 1;
+  };
+  const int64_t i0 = (cd.fx == 2 ? 2 * Cx : Cx) + sy * (cd.fy == 2 ? 2 * Cy : Cy) + sz * (cd.fz == 2 ? 2 * Cz : Cz);
+  T s = (T)0;
+  for (int row = 0; row < 16; ++row) {
+    int y, z, by, bz;
+    const bool okr = box_pos(cd.fy, Cy, L.Y, row & 3, y, by) & box_pos(cd.fz, Cz, L.Z, row >> 2, z, bz);
+    T pw[4], rv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int x, bx;
+      const bool ok = okr & box_pos(cd.fx, Cx, L.X, q, x, bx);
+      const int64_t i = ok ? x + sy * y + sz * z : i0;
+      const T p = p1[(ok ? (bx | (by << 1) | (bz << 2)) : 0) * n + i];
+      pw[q] = ok ? p : (T)0;
+      rv[q] = r[i];
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) s = fma(pw[q], rv[q], s);
+  }
+  // axial cells, direction d: (side, lateral bits u, v) over the other two
+  // directions in the order (d + 1) % 3, (d + 2) % 3
+  auto axial = [&](int d, int fd, int cdd, int extd, int fa, int ca, int exta, int fb, int cb, int extb, int64_t sdd,
+                   int64_t sa, int64_t sb) {
+    T pw[8], rv[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int side = k >> 2, u = k & 1, v = (k >> 1) & 1;
+      const int pd = side ? 2 * cdd + 3 : 2 * cdd - 2;
+      const int pa = fa == 2 ? 2 * ca + u : ca, pb = fb == 2 ? 2 * cb + v : cb;
+      const bool ok = fd == 2 && pd >= 0 && pd < extd && (fa == 2 || u == 0) && pa < exta && (fb == 2 || v == 0) &&
+                      pb < extb;
+      const int64_t i = ok ? sdd * pd + sa * pa + sb * pb : i0;
+      const T p = p1[(8 + d) * n + i];
+      pw[k] = ok ? p : (T)0;
+      rv[k] = r[i];
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s = fma(pw[k], rv[k], s);
+  };
+  axial(0, cd.fx, Cx, L.X, cd.fy, Cy, L.Y, cd.fz, Cz, L.Z, 1, sy, sz);
+  axial(1, cd.fy, Cy, L.Y, cd.fz, Cz, L.Z, cd.fx, Cx, L.X, sy, sz, 1);
+  axial(2, cd.fz, Cz, L.Z, cd.fx, Cx, L.X, cd.fy, Cy, L.Y, sz, 1, sy);
+  bc[C] = s;
+}
+
+// x += P_1 e. A slot without an aggregate holds an exact zero, so its target is
+// only clamped into the coarse lattice (no branch per slot).
+template <typename T>
+__global__ void k_sa_prolong1(StLevelT<T> L, CDims cd, const T* __restrict__ p1, const T* __restrict__ e,
+                              T* __restrict__ x) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = L.n();
+  if (c >= n) return;
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
+  const AxisPos px = axis_pos(I, cd.fx), py = axis_pos(J, cd.fy), pz = axis_pos(Z, cd.fz);
+  // coarse coordinate a + m s per direction, clamped, for m = -1, 0, 1
+  auto cl = [](int v, int hi) { return min(max(v, 0), hi - 1); };
+  const int xs[3] = {cl(px.a - px.s, cd.X), px.a, cl(px.a + px.s, cd.X)};
+  const int ys[3] = {cl(py.a - py.s, cd.Y), py.a, cl(py.a + py.s, cd.Y)};
+  const int zs[3] = {cl(pz.a - pz.s, cd.Z), pz.a, cl(pz.a + pz.s, cd.Z)};
+  auto ev = [&](int ix, int iy, int iz) { return e[xs[ix] + cd.X * (ys[iy] + cd.Y * zs[iz])]; };
+  T v = (T)0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v = fma(p1[k * n + c], ev(1 + (k & 1), 1 + ((k >> 1) & 1), 1 + (k >> 2)), v);
+  v = fma(p1[8 * n + c], ev(0, 1, 1), v);
+  v = fma(p1[9 * n + c], ev(1, 0, 1), v);
+  v = fma(p1[10 * n + c], ev(1, 1, 0), v);
   x[c] += v;
 }
 
@@ -444,9 +912,10 @@ CDims cdims_of(const StLevelT<T>& c) {
 }
 
 // -- the cycle ----------------------------------------------------------------------
-// levels >= 1: st[l - 1]; the last one is solved densely
+// levels >= 1: st[l - 1]; the last one is solved densely. p1: the smoothed
+// prolongator from level 1 to level 2 (nullptr: plain aggregation there too).
 template <typename T>
-const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, int l, const T* b, T* out) {
+const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, const T* p1, int l, const T* b, T* out) {
   StLevelT<T>& L = st[l - 1];
   const int last = (int)st.size();
   if (l == last) {
@@ -457,20 +926,34 @@ const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, int l, const T* b, T* 
   StLevelT<T>& C = st[l];
   const CDims cd = cdims_of(C);
   const int nu = h->nu;
-  const bool w33 = L.no == 33;
+  const bool smoothed = l == 1 && p1 != nullptr;
+  const unsigned g = nblk(L.n());
+  cudaStream_t sm = h->stream;
+  // wide shapes: 32 cells per block of SplitG warps
+  const unsigned gs = (unsigned)((L.n() + 31) / 32);
   auto jacobi = [&](const T* x, T* xo) {
-    if (w33) k_st_jacobi<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, x, xo);
-    else k_st_jacobi<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, x, xo);
+    with_shape(L.no, [&](auto t) {
+      constexpr int NO = decltype(t)::value;
+      if constexpr (NO >= 81) k_st_jacobi_split<T, NO><<<gs, 32 * SplitG<NO>::G, 0, sm>>>(L, b, x, xo);
+      else k_st_jacobi<T, NO><<<g, TPB, 0, sm>>>(L, b, x, xo);
+    });
+  };
+  auto prolong = [&](const T* xc, T* x) {
+    if (smoothed) k_sa_prolong1<T><<<g, TPB, 0, sm>>>(L, cd, p1, xc, x);
+    else k_st_prolong_add<T><<<g, TPB, 0, sm>>>(L, cd, xc, x);
   };
   T* cur = L.x0;
   int s0 = 1;
   const bool fuse = L.n() <= FUSE_MAX;
   if (nu >= 2 && fuse) {  // the first two sweeps fused
-    if (w33) k_st_scale_jacobi<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur);
-    else k_st_scale_jacobi<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur);
+    with_shape(L.no, [&](auto t) {
+      constexpr int NO = decltype(t)::value;
+      if constexpr (NO >= 81) k_st_scale_jacobi_split<T, NO><<<gs, 32 * SplitG<NO>::G, 0, sm>>>(L, b, cur);
+      else k_st_scale_jacobi<T, NO><<<g, TPB, 0, sm>>>(L, b, cur);
+    });
     s0 = 2;
   } else {
-    k_st_scale<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur);
+    k_st_scale<T><<<g, TPB, 0, sm>>>(L, b, cur);
   }
   for (int s = s0; s < nu; ++s) {
     T* o = (cur == L.x0) ? L.x1 : L.x0;
@@ -480,19 +963,27 @@ const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, int l, const T* b, T* 
   const int repeats = (h->cycle == 2 && l + 1 < last && (h->w_levels == 0 || l < h->w_levels)) ? 2 : 1;
   const T* xc = nullptr;
   for (int rep = 0; rep < repeats; ++rep) {
-    if (rep > 0) k_st_prolong_add<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, xc, cur);
+    if (rep > 0) prolong(xc, cur);
     T* rtmp = (cur == L.x0) ? L.x1 : L.x0;  // free until the post-smoothing
-    if (w33) k_st_resid<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
-    else k_st_resid<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, rtmp);
-    k_agg_sum<T><<<nblk(C.n()), TPB, 0, h->stream>>>(L.X, L.Y, L.Z, cd, rtmp, C.b);
-    xc = sa_level<T>(h, st, l + 1, C.b, nullptr);
+    with_shape(L.no, [&](auto t) {
+      constexpr int NO = decltype(t)::value;
+      if constexpr (NO >= 81) k_st_resid_split<T, NO><<<gs, 32 * SplitG<NO>::G, 0, sm>>>(L, b, cur, rtmp);
+      else k_st_resid<T, NO><<<g, TPB, 0, sm>>>(L, b, cur, rtmp);
+    });
+    if (smoothed) k_sa_restrict1<T><<<nblk(C.n()), TPB, 0, sm>>>(L, cd, p1, rtmp, C.b);
+    else k_agg_sum<T><<<nblk(C.n()), TPB, 0, sm>>>(L.X, L.Y, L.Z, cd, rtmp, C.b);
+    xc = sa_level<T>(h, st, p1, l + 1, C.b, nullptr);
   }
   T* o = (nu == 1 && out) ? out : ((cur == L.x0) ? L.x1 : L.x0);
-  if (fuse) {
-    if (w33) k_st_jacobi_prolong<T, 33><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, b, cur, xc, o);
-    else k_st_jacobi_prolong<T, 27><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, b, cur, xc, o);
+  if (fuse && !smoothed) {
+    with_shape(L.no, [&](auto t) {
+      constexpr int NO = decltype(t)::value;
+      if constexpr (NO >= 81)
+        k_st_jacobi_prolong_split<T, NO><<<gs, 32 * SplitG<NO>::G, 0, sm>>>(L, cd, b, cur, xc, o);
+      else k_st_jacobi_prolong<T, NO><<<g, TPB, 0, sm>>>(L, cd, b, cur, xc, o);
+    });
   } else {
-    k_st_prolong_add<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, xc, cur);
+    prolong(xc, cur);
     jacobi(cur, o);
   }
   cur = o;
@@ -506,7 +997,8 @@ const T* sa_level(hd_op* h, std::vector<StLevelT<T>>& st, int l, const T* b, T* 
 
 // level 0 (7-point lattice) with the smoothed transfers to level 1
 template <typename T>
-void sa_cycle0(hd_op* h, LevelT<T>& L, const T* pv, std::vector<StLevelT<T>>& st, const T* b, T* out) {
+void sa_cycle0(hd_op* h, LevelT<T>& L, const T* pv, std::vector<StLevelT<T>>& st, const T* p1, const T* b,
+               T* out) {
   const CDims cd = cdims_of(st[0]);
   const int nu = h->nu;
   T* cur = L.x0;
@@ -523,7 +1015,7 @@ void sa_cycle0(hd_op* h, LevelT<T>& L, const T* pv, std::vector<StLevelT<T>>& st
     if (rep > 0) k_sa_prolong0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, xc, cur);
     k_sa_res0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, L.b);
     k_sa_restrict0<T><<<nblk(st[0].n()), TPB, 0, h->stream>>>(L, cd, pv, L.b, st[0].b);
-    xc = sa_level<T>(h, st, 1, st[0].b, nullptr);
+    xc = sa_level<T>(h, st, p1, 1, st[0].b, nullptr);
   }
   k_sa_prolong0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, xc, cur);
   for (int s = 0; s < nu; ++s) {
@@ -568,19 +1060,38 @@ hd_status sa_setup(hd_op* h) {
   if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "flag");
   HD_CK(h, cudaMemsetAsync(d_bad, 0, sizeof(int), h->stream));
   hd_status st = HD_OK;
+  const bool two = h->sa >= 2;
   for (size_t l = 1; l < h->lv.size() && st == HD_OK; ++l) {
     const LevelT<double>& g = h->lv[l];  // same lattice dimensions as the unsmoothed level
     StLevelT<double> s{};
     s.X = g.X; s.Y = g.Y; s.Z = g.Z; s.fx = g.fx; s.fy = g.fy; s.fz = g.fz;
-    s.no = (l == 1) ? 33 : 27;
+    // shapes: 33 on level 1; with the second smoothed level 179 on level 2 and 81
+    // on level 3; 27 elsewhere
+    s.no = (l == 1) ? 33 : (two && l == 2) ? 179 : (two && l == 3) ? 81 : 27;
     st = alloc_st<double>(h, s, true);
     h->st.push_back(s);
     if (st != HD_OK) break;
     const StLevelT<double>& S = h->st.back();
     const CDims cd = cdims_of(S);
-    if (l == 1) k_sa_galerkin<<<nblk(S.n()), TPB, 0, h->stream>>>(L0, cd, h->sa_p, S, d_bad);
-    else k_ua_galerkin<<<nblk(S.n()), TPB, 0, h->stream>>>(h->st[h->st.size() - 2], cd, S, d_bad);
-    k_st_dinv<<<nblk(S.n()), TPB, 0, h->stream>>>(S);
+    const unsigned gc = nblk(S.n());
+    if (l == 1) {
+      k_sa_galerkin<<<gc, TPB, 0, h->stream>>>(L0, cd, h->sa_p, S, d_bad);
+    } else if (two && l == 2) {
+      const StLevelT<double>& A1 = h->st[0];
+      if (cudaMalloc(&h->sa_p1, sizeof(double) * P1_SLOTS * A1.n()) != cudaSuccess) {
+        st = hd_fail(h, HD_ERR_OOM, "SA prolongator of level 1");
+        break;
+      }
+      k_sa_pvals1<<<nblk(A1.n()), TPB, 0, h->stream>>>(A1, cd, h->sa_p1, d_bad);
+      k_sa_galerkin1<179><<<gc, TPB, 0, h->stream>>>(A1, cd, h->sa_p1, S, d_bad);
+    } else {
+      const StLevelT<double>& F = h->st[h->st.size() - 2];
+      if (F.no == 179) k_ua_galerkin<179, 81><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+      else if (F.no == 81) k_ua_galerkin<81, 27><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+      else if (F.no == 33) k_ua_galerkin<33, 27><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+      else k_ua_galerkin<27, 27><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+    }
+    k_st_dinv<<<gc, TPB, 0, h->stream>>>(S);
     if (cudaGetLastError() != cudaSuccess) st = hd_fail(h, HD_ERR_CUDA, "SA Galerkin");
   }
   int bad = 0;
@@ -602,7 +1113,7 @@ hd_status sa_setup(hd_op* h) {
         const int r = I + c.X * (J + c.Y * Z);
         for (int o = 0; o < c.no; ++o) {
           int dx, dy, dz;
-          st_off(o, dx, dy, dz);
+          st_off_any(c.no, o, dx, dy, dz);
           const int i = I + dx, j = J + dy, z = Z + dz;
           if (i < 0 || i >= c.X || j < 0 || j >= c.Y || z < 0 || z >= c.Z) continue;
           A[(size_t)r * n + (i + c.X * (j + c.Y * z))] += a[(size_t)o * n + r];
@@ -617,7 +1128,7 @@ hd_status sa_setup(hd_op* h) {
     double* half = nullptr;
     if (cudaMalloc(&half, sizeof(double) * s.n() * n_half(s.no)) != cudaSuccess)
       return hd_fail(h, HD_ERR_OOM, "stencil level");
-    k_st_compress<<<nblk(s.n()), TPB, 0, h->stream>>>(s, half);
+    with_shape(s.no, [&](auto t) { k_st_compress<decltype(t)::value><<<nblk(s.n()), TPB, 0, h->stream>>>(s, half); });
     HD_LAUNCH_CK(h, "k_st_compress");
     HD_CK(h, cudaStreamSynchronize(h->stream));
     cudaFree(s.a);
@@ -631,6 +1142,11 @@ hd_status sa_setup_f32(hd_op* h) {
   const int64_t n0 = h->lv[0].n();
   if (cudaMalloc(&h->sa_pf, sizeof(float) * 4 * n0) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA f32");
   k_to_f32_sa<float><<<nblk(4 * n0), TPB, 0, h->stream>>>(4 * n0, h->sa_p, h->sa_pf);
+  if (h->sa_p1) {
+    const int64_t np = P1_SLOTS * h->st[0].n();
+    if (cudaMalloc(&h->sa_p1f, sizeof(float) * np) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA f32");
+    k_to_f32_sa<float><<<nblk(np), TPB, 0, h->stream>>>(np, h->sa_p1, h->sa_p1f);
+  }
   for (const StLevelT<double>& d : h->st) {
     StLevelT<float> f{};
     f.X = d.X; f.Y = d.Y; f.Z = d.Z; f.fx = d.fx; f.fy = d.fy; f.fz = d.fz; f.no = d.no;
@@ -651,16 +1167,20 @@ void sa_free(hd_op* h) {
   h->stf.clear();
   cudaFree(h->sa_p);
   cudaFree(h->sa_pf);
+  cudaFree(h->sa_p1);
+  cudaFree(h->sa_p1f);
   cudaFree(h->d_sa_coarse_inv);
   h->sa_p = nullptr;
   h->sa_pf = nullptr;
+  h->sa_p1 = nullptr;
+  h->sa_p1f = nullptr;
   h->d_sa_coarse_inv = nullptr;
 }
 
 hd_status sa_vcycle(hd_op* h, const double* b, double* x) {
-  return run_graphed(h, b, x, 2, [&]() { sa_cycle0<double>(h, h->lv[0], h->sa_p, h->st, b, x); });
+  return run_graphed(h, b, x, 2, [&]() { sa_cycle0<double>(h, h->lv[0], h->sa_p, h->st, h->sa_p1, b, x); });
 }
 
 hd_status sa_vcycle_f32(hd_op* h, const float* b, float* x) {
-  return run_graphed(h, b, x, 3, [&]() { sa_cycle0<float>(h, h->lvf[0], h->sa_pf, h->stf, b, x); });
+  return run_graphed(h, b, x, 3, [&]() { sa_cycle0<float>(h, h->lvf[0], h->sa_pf, h->stf, h->sa_p1f, b, x); });
 }

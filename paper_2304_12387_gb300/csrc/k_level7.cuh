@@ -14,13 +14,21 @@ __device__ __forceinline__ T stencil_res(const LevelT<T>& lv, const T* __restric
   int64_t yl = I + (int64_t)lv.X * (J + (int64_t)(lv.Y + 1) * Z);
   int64_t zl = I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z);
   int64_t XY = (int64_t)lv.X * lv.Y;
+  // Face weights exist for boundary faces too, so all six are loaded; a missing
+  // neighbour reads x at the own cell and gets a zero weight. No branch: the
+  // loads overlap instead of waiting one after another.
+  const bool ml = I > 0, mh = I < lv.X - 1, nl = J > 0, nh = J < lv.Y - 1, ol = Z > 0, oh = Z < lv.Z - 1;
+  const T w0 = lv.wx[xl], w1 = lv.wx[xl + 1], w2 = lv.wy[yl], w3 = lv.wy[yl + lv.X], w4 = lv.wz[zl],
+          w5 = lv.wz[zl + XY];
+  const T x0 = x[ml ? c - 1 : c], x1 = x[mh ? c + 1 : c], x2 = x[nl ? c - lv.X : c], x3 = x[nh ? c + lv.X : c],
+          x4 = x[ol ? c - XY : c], x5 = x[oh ? c + XY : c];
   T r = fma(-lv.diag[c], xc, bc);
-  if (I > 0) r = fma(lv.wx[xl], x[c - 1], r);
-  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], x[c + 1], r);
-  if (J > 0) r = fma(lv.wy[yl], x[c - lv.X], r);
-  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], x[c + lv.X], r);
-  if (Z > 0) r = fma(lv.wz[zl], x[c - XY], r);
-  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], x[c + XY], r);
+  r = fma(ml ? w0 : (T)0, x0, r);
+  r = fma(mh ? w1 : (T)0, x1, r);
+  r = fma(nl ? w2 : (T)0, x2, r);
+  r = fma(nh ? w3 : (T)0, x3, r);
+  r = fma(ol ? w4 : (T)0, x4, r);
+  r = fma(oh ? w5 : (T)0, x5, r);
   return r;
 }
 

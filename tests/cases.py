@@ -24,6 +24,9 @@ CASES = {
     "gd_k3": (GRAD_DIV, (3, 3, 2), 3, 4, 0.12, 48, "lognormal1"),
     # tall grad-div column, 11 element layers: the host-buffer apply's slabs are uneven
     "gd_tall": (GRAD_DIV, (2, 3, 11), 2, 4, 0.1, 21, "lognormal1"),
+    # one element layer in y (a lattice 2 cells thick): a coarse level of extent 1 that
+    # the next aggregation leaves unsplit
+    "gd_flat": (GRAD_DIV, (4, 1, 5), 2, 4, 0.1, 12, "lognormal1"),
 }
 
 

@@ -1,6 +1,7 @@
-"""Smoothed-aggregation hierarchy (smooth_levels = 1) against the oracle running the
-same spec: the V/W-cycle and preconditioner applies within 1e-11, MINRES iteration
-counts within one and solutions within 1e-8; the FP32 copy within FP32 rounding."""
+"""Smoothed-aggregation hierarchy (smooth_levels = 1: the first prolongator smoothed;
+2: the first two) against the oracle running the same spec: the V/W-cycle and
+preconditioner applies within 1e-11, MINRES iteration counts within one and
+solutions within 1e-8; the FP32 copy within FP32 rounding."""
 import numpy as np
 import pytest
 
@@ -10,25 +11,28 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 OMEGA = 4.0 / 3.0
-NAMES = ["gd_k4_ragged", "darcy_k3", "darcy_neumann", "c1", "gd_k5", "darcy_gamma"]
+NAMES = ["gd_k4_ragged", "darcy_k3", "darcy_neumann", "c1", "gd_k5", "darcy_gamma", "gd_tall", "gd_flat"]
 
 
 def _setup(name, cycle, w_levels=0, smooth_levels=1):
     from oracle.precond import BlockPrec
     d = inputs(name)
     prob = oracle_problem(d)
-    bp = BlockPrec(prob, nu=2, coarse_max=8, cycle=cycle, smooth=OMEGA if smooth_levels else 0.0, sa_levels=1,
-                   w_levels=w_levels)
+    bp = BlockPrec(prob, nu=2, coarse_max=8, cycle=cycle, smooth=OMEGA if smooth_levels else 0.0,
+                   sa_levels=max(smooth_levels, 1), w_levels=w_levels)
     op = gpu_operator(d, coarse_max=8, cycle=cycle, smooth_levels=smooth_levels, w_levels=w_levels)
     return d, prob, bp, op
 
 
+@pytest.mark.parametrize("smooth_levels", [1, 2])
 @pytest.mark.parametrize("cycle,w_levels", [(1, 0), (2, 0), (2, 1), (2, 2)])
 @pytest.mark.parametrize("name", NAMES)
-def test_smoothed_cycle_and_preconditioner_match_oracle(name, cycle, w_levels):
+def test_smoothed_cycle_and_preconditioner_match_oracle(name, cycle, w_levels, smooth_levels):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    d, prob, bp, op = _setup(name, cycle, w_levels)
+    d, prob, bp, op = _setup(name, cycle, w_levels, smooth_levels)
+    if smooth_levels == 2:
+        assert bp.vc.n_levels >= 3  # the second prolongator exists
     rng = np.random.Generator(np.random.PCG64(21))
     r = rng.uniform(-1, 1, prob.lat.n_l2)
     z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
@@ -48,13 +52,15 @@ def test_smoothed_cycle_and_preconditioner_match_oracle(name, cycle, w_levels):
     op.close()
 
 
-@pytest.mark.parametrize("name,cycle,w_levels", [("gd_k4_ragged", 2, 2), ("darcy_k3", 2, 0), ("darcy_neumann", 2, 2),
-                                                 ("c1", 1, 0), ("darcy_gamma", 1, 0)])
-def test_smoothed_minres_matches_oracle(name, cycle, w_levels):
+@pytest.mark.parametrize("name,cycle,w_levels,smooth_levels",
+                         [("gd_k4_ragged", 2, 2, 1), ("darcy_k3", 2, 0, 1), ("darcy_neumann", 2, 2, 1),
+                          ("c1", 1, 0, 1), ("darcy_gamma", 1, 0, 1), ("gd_k4_ragged", 2, 0, 2),
+                          ("darcy_neumann", 2, 0, 2), ("darcy_k3", 1, 0, 2)])
+def test_smoothed_minres_matches_oracle(name, cycle, w_levels, smooth_levels):
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from oracle.minres import minres
-    d, prob, bp, op = _setup(name, cycle, w_levels)
+    d, prob, bp, op = _setup(name, cycle, w_levels, smooth_levels)
     b = np.random.Generator(np.random.PCG64(22)).uniform(-1, 1, prob.n)
     b[prob.ess] = 0.0
     if bp.singular:
@@ -79,7 +85,7 @@ def test_smooth_levels_argument_checks():
     import paper_2304_12387_gb300 as hd
     d = inputs("c1")
     with pytest.raises(hd.HdError) as e:
-        gpu_operator(d, smooth_levels=2)
+        gpu_operator(d, smooth_levels=3)
     assert e.value.status == hd.HD_ERR_NOT_IMPLEMENTED
     with pytest.raises(hd.HdError) as e:
         gpu_operator(d, smooth_levels=-1)

@@ -220,3 +220,160 @@ def test_w_recursion_limited_to_the_first_levels():
     deep = VCycle(A, dims, cycle=2, w_levels=w1.n_levels, **kw)
     assert np.array_equal(full._cycle(0, b), deep._cycle(0, b))
     assert not np.allclose(full._cycle(0, b), w1._cycle(0, b))
+
+
+# -- smoothed prolongator on the second level as well (sa_levels = 2) ----------------
+
+def _block_laplacian_fast(m, block=4, sigma=2.0, shift=1e-3, seed=0):
+    """block_laplacian on an m^3 lattice, assembled with array operations (same
+    definition: harmonic-mean face weights of log-normal per-block coefficients)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    nb = -(-m // block)
+    kap = np.exp(sigma * rng.standard_normal(nb ** 3))
+    c = np.arange(m ** 3)
+    I, J, K = c % m, (c // m) % m, c // (m * m)
+    coef = kap[I // block + nb * (J // block + nb * (K // block))]
+    diag = shift * rng.uniform(0.5, 1.5, m ** 3)
+    rows, cols, vals = [], [], []
+    for di, dj, dk in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        a = c[(I + di < m) & (J + dj < m) & (K + dk < m)]
+        b = a + di + m * (dj + m * dk)
+        w = 2.0 * coef[a] * coef[b] / (coef[a] + coef[b])
+        rows += [a, b]; cols += [b, a]; vals += [-w, -w]
+        np.add.at(diag, a, w); np.add.at(diag, b, w)
+    rows, cols = np.concatenate(rows + [c]), np.concatenate(cols + [c])
+    return sp.csr_matrix((np.concatenate(vals + [diag]), (rows, cols)), shape=(m ** 3, m ** 3))
+
+
+def _offsets(A, dims, radius_margin):
+    """Offsets of the rows of A whose cell lies at least radius_margin from every side."""
+    X, Y, Z = dims
+    A = A.tocoo()
+    keep = np.abs(A.data) > 0
+    r, c = A.row[keep], A.col[keep]
+    xyz = lambda i: np.stack([i % X, (i // X) % Y, i // (X * Y)])
+    pr = xyz(r)
+    inner = np.all((pr >= radius_margin) & (pr < np.array(dims)[:, None] - radius_margin), axis=0)
+    return {tuple(o) for o in (xyz(c) - pr).T[inner]}
+
+
+def _shape(box, axial, lateral):
+    """The box of radius `box` and the cells `axial` steps away along an axis whose
+    offsets across it are at most `lateral`."""
+    out = set(itertools.product(range(-box, box + 1), repeat=3))
+    for d in range(3):
+        for v in (axial, -axial):
+            for u, w in itertools.product(range(-lateral, lateral + 1), repeat=2):
+                o = [u, w]
+                o.insert(d, v)
+                out.add(tuple(o))
+    return out
+
+
+def test_second_smoothed_prolongator_entries_brute_force():
+    """P_1[i, C] = [i in C] - omega / D_l1(A_1)[i] * sum_{j in C} A_1[i, j] on the
+    first coarse level (A_1 = P_0^T A P_0 with the smoothed P_0), by loops."""
+    dims = (10, 8, 6)
+    A = lattice_laplacian(dims, seed=21)
+    vc = VCycle(A, dims, coarse_max=1, smooth=OMEGA, sa_levels=2, max_levels=3)
+    assert vc.n_levels == 3
+    A1 = vc.A[1].toarray()
+    P1 = vc.P[1].toarray()
+    Q, _ = aggregation(vc.dims[1])
+    Q = Q.toarray()
+    dl1 = np.abs(A1).sum(axis=1)
+    for i in range(A1.shape[0]):
+        for C in range(Q.shape[1]):
+            members = np.nonzero(Q[:, C])[0]
+            expect = Q[i, C] - OMEGA / dl1[i] * A1[i, members].sum()
+            assert abs(P1[i, C] - expect) <= 1e-14 * max(1.0, abs(expect))
+    # sa_levels = 1 leaves the second prolongator piecewise constant
+    vc1 = VCycle(A, dims, coarse_max=1, smooth=OMEGA, sa_levels=1, max_levels=3)
+    assert set(np.unique(vc1.P[1].toarray())) <= {0.0, 1.0}
+    assert np.array_equal(vc1.P[0].toarray(), vc.P[0].toarray())
+
+
+def test_second_prolongator_row_pattern():
+    """A row of P_1 has nonzeros only at the aggregates agg(i) + (b_x s_x, b_y s_y,
+    b_z s_z), b in {0,1}^3, and agg(i) - s_d e_d, where s = +1 on an odd and -1 on
+    an even fine coordinate: at most 11 per row (the slots the kernels store)."""
+    dims = (16, 14, 12)
+    A = lattice_laplacian(dims, seed=22)
+    vc = VCycle(A, dims, coarse_max=1, smooth=OMEGA, sa_levels=2, max_levels=3)
+    P1 = vc.P[1].tocoo()
+    (X, Y, Z), (cx, cy, _) = vc.dims[1], vc.dims[2]
+    keep = np.abs(P1.data) > 0
+    most = 0
+    for i, C in zip(P1.row[keep], P1.col[keep]):
+        f = np.array([i % X, (i // X) % Y, i // (X * Y)])
+        s = np.where(f % 2 == 1, 1, -1)
+        D = np.array([C % cx, (C // cx) % cy, C // (cx * cy)]) - f // 2
+        box = all(D[d] in (0, s[d]) for d in range(3))
+        far = sum(D[d] == -s[d] for d in range(3)) == 1 and sum(D != 0) == 1
+        assert box or far, (i, C, D, s)
+    counts = np.bincount(P1.row[keep], minlength=P1.shape[0])
+    assert counts.max() == 11
+
+
+def test_second_smoothed_level_shapes():
+    """Interior stencils: level 1 the 33-point shape, level 2 the 5x5x5 box plus
+    the cells 3 steps away along an axis with at most 1 across (179), level 3 the
+    3x3x3 box plus 2 steps along an axis with at most 1 across (81), level 4 the
+    3x3x3 box."""
+    m = 48
+    A = lattice_laplacian((m, m, m), seed=23)
+    vc = VCycle(A, (m, m, m), coarse_max=1, smooth=OMEGA, sa_levels=2, max_levels=5)
+    assert vc.n_levels == 5
+    s33 = _shape(1, 2, 0)
+    s179, s81, s27 = _shape(2, 3, 1), _shape(1, 2, 1), _shape(1, 1, 1)
+    assert (len(s33), len(s179), len(s81), len(s27)) == (33, 179, 81, 27)
+    assert _offsets(vc.A[1], vc.dims[1], 2) == s33
+    assert _offsets(vc.A[2], vc.dims[2], 3) == s179
+    assert _offsets(vc.A[3], vc.dims[3], 2) == s81
+    assert _offsets(vc.A[4], vc.dims[4], 1) == s27
+
+
+def test_second_level_two_grid_correction_is_an_A_orthogonal_projector():
+    """E = I - P_1 (P_1^T A_1 P_1)^-1 P_1^T A_1 on the first coarse level."""
+    dims = (12, 10, 8)
+    A = lattice_laplacian(dims, seed=24)
+    vc = VCycle(A, dims, coarse_max=1, smooth=OMEGA, sa_levels=2, max_levels=3)
+    A1, P1, A2 = vc.A[1].toarray(), vc.P[1].toarray(), vc.A[2].toarray()
+    E = np.eye(A1.shape[0]) - P1 @ np.linalg.solve(A2, P1.T @ A1)
+    assert np.abs(E @ E - E).max() < 1e-10
+    AE = A1 @ E
+    assert np.abs(AE - AE.T).max() < 1e-10 * np.abs(A1).max()
+    Q = aggregation(vc.dims[1])[0].toarray()
+    Ebad = np.eye(A1.shape[0]) - P1 @ np.linalg.solve(Q.T @ A1 @ Q, P1.T @ A1)
+    assert np.abs(Ebad @ Ebad - Ebad).max() > 1e-3
+
+
+@pytest.mark.parametrize("cycle", [1, 2])
+@pytest.mark.parametrize("singular", [False, True])
+def test_second_smoothed_cycle_symmetric_positive(cycle, singular):
+    dims = (12, 10, 9)
+    A = lattice_laplacian(dims, seed=25, singular=singular)
+    vc = VCycle(A, dims, coarse_max=8, smooth=OMEGA, sa_levels=2, cycle=cycle, singular=singular)
+    assert vc.n_levels >= 4
+    if singular:
+        assert np.abs(vc.A[2] @ np.ones(vc.A[2].shape[0])).max() < 1e-10 * abs(vc.A[2]).max()
+    rng = np.random.Generator(np.random.PCG64(26))
+    x, y = rng.standard_normal((2, A.shape[0]))
+    if singular:
+        x -= x.mean(); y -= y.mean()
+    Vx, Vy = vc.apply(x), vc.apply(y)
+    assert abs(x @ Vy - y @ Vx) < 1e-11 * np.linalg.norm(x) * np.linalg.norm(Vy)
+    assert x @ Vx > 0
+
+
+def test_second_smoothed_w_cycle_iterations_flat():
+    """Log-normal block coefficients: with both prolongators smoothed, PCG needs the
+    same iterations (within one) on 32^3 and 64^3 cells, and fewer than with the
+    first one smoothed alone on 64^3 (whose count grows)."""
+    its2, its1 = {}, {}
+    for m in (32, 64):
+        A = _block_laplacian_fast(m, seed=27)
+        its2[m] = _pcg_iterations(A, VCycle(A, (m,) * 3, coarse_max=512, smooth=OMEGA, sa_levels=2, cycle=2).apply)
+        its1[m] = _pcg_iterations(A, VCycle(A, (m,) * 3, coarse_max=512, smooth=OMEGA, sa_levels=1, cycle=2).apply)
+    assert abs(its2[64] - its2[32]) <= 1, its2
+    assert its2[64] <= its1[64] - 2, (its1, its2)
