@@ -364,8 +364,8 @@ def run_ours(args, rank, world, dist):
                       "l2": "inputs larger than L2 (x, y: 538 MB each; W^-1 8.6 GB; geometric factors 2.7 GB)",
                       "winv": "dense per-element inverse", "setup_s": setup_s,
                       "schur_cycle": ("W" if args.cycle == 2 else "V") +
-                                     (", smoothed aggregation on the first level" if args.smooth_levels
-                                      else ", plain aggregation")},
+                                     {0: ", plain aggregation", 1: ", smoothed aggregation on the first level",
+                                      2: ", smoothed aggregation on the first two levels"}[args.smooth_levels]},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if args.fp64_emulation and not args.no_native:
         out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
@@ -404,27 +404,30 @@ def run_iterations(args):
     """Mesh and degree (in)dependence of the iteration counts (Metric 2's study): FP64
     MINRES to a true relative residual of 1e-8 on the metric recipe (perturbed mesh,
     beta = exp(2Z), u.n = 0, q = k + 2) at several element counts and degrees, with
-    the plain-aggregation and the smoothed-aggregation W-cycles."""
+    the plain-aggregation W-cycle and the smoothed-aggregation W-cycles with one and
+    with two smoothed levels; mixed precision beside FP64 for the last."""
     import torch
     import paper_2304_12387_gb300 as hd
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     stream = torch.cuda.current_stream()
-    cases = [(16, 4), (32, 4), (64, 4), (32, 2), (32, 3), (32, 5)]
+    cases = [(16, 4), (32, 4), (64, 4), (96, 4), (32, 2), (32, 3), (32, 5)]
     rows = []
     for nx, k in cases:
         vx, vy, vz, alpha, beta = workload(nx)
         row = {"elements": nx, "k": k}
-        for name, sl in (("plain", 0), ("smoothed", 1)):
+        for name, sl in (("plain", 0), ("smoothed1", 1), ("smoothed2", 2)):
             op = hd.Operator(nx, nx, nx, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
                              cycle=2, fp64_emulation=1, smooth_levels=sl, stream=stream)
             row["dofs"] = op.n
             b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
             b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
-            x = torch.zeros_like(b)
-            st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=args.solve_maxit, check_every=16,
-                                          outer_rtol=1e-8, max_outer=40)
-            row[name] = {"status": int(st), "iterations": info["iterations"], "outer": info["outer"],
-                         "ms": round(info["ms_total"], 1), "true_relres": info["true_relres"]}
+            for prec in ((0, 1) if sl == 2 else (0,)):
+                x = torch.zeros_like(b)
+                st, info = op.hd_minres_solve(b, x, rtol=1e-4 if prec else 1e-8, maxit=args.solve_maxit,
+                                              check_every=16, precision=prec, outer_rtol=1e-8, max_outer=40)
+                row[name + ("_mixed" if prec else "")] = {
+                    "status": int(st), "iterations": info["iterations"], "outer": info["outer"],
+                    "ms": round(info["ms_total"], 1), "true_relres": info["true_relres"]}
             op.close()
         rows.append(row)
         print(json.dumps(row), flush=True)
@@ -442,7 +445,7 @@ def run_iterations(args):
         for tau in (1.0, 2.0):
             nx = c["nx"]
             op = hd.Operator(nx, nx, nx, c["k"], *c["v"], c["c0"], c["c1"], kind=c["kind"], ess_mask=c["ess"],
-                             q=c["q"], affine=c["affine"], tau=tau, cycle=2, fp64_emulation=1, smooth_levels=1,
+                             q=c["q"], affine=c["affine"], tau=tau, cycle=2, fp64_emulation=1, smooth_levels=2,
                              coarse_max=8 if nx < 8 else 0, stream=stream)
             b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
             b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
@@ -518,8 +521,9 @@ def main():
     ap.add_argument("--inner-rtol", type=float, default=1e-4, help="inner MINRES tolerance of the mixed solve")
     ap.add_argument("--solve-maxit", type=int, default=20000, help="iteration cap of the MINRES solves")
     ap.add_argument("--cycle", type=int, default=2, choices=[1, 2], help="1: V-cycle, 2: W-cycle on S~")
-    ap.add_argument("--smooth-levels", type=int, default=1, choices=[0, 1],
-                    help="1: smoothed-aggregation prolongator on the first level of the S~ hierarchy")
+    ap.add_argument("--smooth-levels", type=int, default=2, choices=[0, 1, 2],
+                    help="smoothed-aggregation prolongators on the first 1 or 2 levels of the S~ hierarchy "
+                         "(0: plain aggregation)")
     ap.add_argument("--w-levels", type=int, default=0, help="W repetition on the first levels only (0: all)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
     ap.add_argument("--iterations", action="store_true",
