@@ -461,6 +461,49 @@ def run_iterations(args):
           flush=True)
 
 
+def run_winv_study(args):
+    """W^-1 alternatives (Sec. 3.1 and its mass-inverse table): on perturbed meshes of about
+    1.7 M L2 DOFs for k = 2..5, the setup of the W^-1 data and 100 applications of W^-1
+    (hd_apply_C, FP64) by the stored explicit inverse (batched gemv), the fused local CG in
+    the Gauss-Legendre nodal basis and the same CG in the histopolation basis."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    rows = []
+    for k, nx in ((2, 60), (3, 40), (4, 30), (5, 24)):
+        vx, vy, vz, alpha, beta = workload(nx)
+        row = {"k": k, "elements": nx ** 3, "l2_dofs": (nx * k) ** 3}
+        ref = None
+        for name, mode in (("inverse", hd.HD_WINV_DENSE), ("cg_gl", hd.HD_WINV_CG), ("cg_hist", hd.HD_WINV_CG_HIST)):
+            op = hd.Operator(nx, nx, nx, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
+                             winv_mode=mode, stream=stream)
+            st = op.hd_get_setup_times()
+            q = torch.from_numpy(synth.uniform(op.n_l2, seed=SEED + 9)).cuda()
+            y = torch.empty_like(q)
+            for _ in range(3):
+                op.hd_apply_C(q, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(100):
+                op.hd_apply_C(q, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            yh = y.cpu().numpy()
+            if ref is None:
+                ref = yh
+            row[name] = {"setup_ms": round(st["winv"], 3), "solve_x100_ms": round(ms, 3),
+                         "total_ms": round(st["winv"] + ms, 3), "gdof_s": round(op.n_l2 * 100 / ms / 1e6, 3),
+                         "max_rel_diff_vs_inverse": float(np.abs(yh - ref).max() / np.abs(ref).max())}
+            op.close()
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"study": "W^-1 setup and 100 applications, FP64, perturbed mesh, q = k + 2",
+                      "rows": rows}), flush=True)
+
+
 def run_learned(args):
     """Learned Schur preconditioner, evaluated the way it is meant to be used: trained
     on residual/correction pairs from the plain solver on the Darcy recipe (k = 3,
@@ -526,6 +569,8 @@ def main():
                          "(0: plain aggregation)")
     ap.add_argument("--w-levels", type=int, default=0, help="W repetition on the first levels only (0: all)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
+    ap.add_argument("--winv-study", action="store_true",
+                    help="W^-1 by explicit inverse vs local CG (GL and histopolation bases): setup and 100 applies")
     ap.add_argument("--iterations", action="store_true",
                     help="run the iteration-count study (mesh sizes and degrees) instead")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
@@ -553,6 +598,8 @@ def main():
         run_learned(args)
     elif args.iterations:
         run_iterations(args)
+    elif args.winv_study:
+        run_winv_study(args)
     else:
         run_ours(args, rank, world, dist)
     if dist:

@@ -70,9 +70,12 @@ enum { HD_GRAD_DIV = 0, HD_DARCY = 1 };
 enum {
   HD_WINV_DENSE = 0, /* explicit per-element inverse (the inverse + gemv approach of Sec. 3.1),
                         k^6 doubles per element, computed at setup */
-  HD_WINV_CG = 1     /* fused local CG in the Gauss-Legendre nodal basis (Sec. 2.5, 3.1):
+  HD_WINV_CG = 1,    /* fused local CG in the Gauss-Legendre nodal basis (Sec. 2.5, 3.1):
                         Jacobi-preconditioned, per-element relative residual 1e-14 (cap 40
                         iterations), no stored inverse */
+  HD_WINV_CG_HIST = 2 /* the same fused CG on W in the histopolation basis itself, without the
+                        change of basis (the comparison of Sec. 3.1; cap 100 iterations). The
+                        FP64 operator only: the FP32 inner operator keeps the GL-basis CG */
 };
 
 /* essential-boundary side bits */
@@ -99,7 +102,7 @@ typedef struct {
   uint32_t ess_mask;     /* HD_SIDE_* bits: sides where u.n is essential */
   int32_t affine;        /* caller states the mesh is affine (only selects the default q) */
   double tau;            /* (1,1) preconditioner scaling tau M~; 0 -> 1 */
-  int32_t winv_mode;     /* HD_WINV_DENSE or HD_WINV_CG */
+  int32_t winv_mode;     /* HD_WINV_DENSE, HD_WINV_CG or HD_WINV_CG_HIST */
   int32_t nu;            /* l1-Jacobi sweeps before and after the coarse correction; 0 -> 2 */
   int32_t coarse_max;    /* at most this many cells on the coarsest level; 0 -> 512 */
   int32_t cycle;         /* 0 or 1: V-cycle; 2: W-cycle (two coarse corrections per level
@@ -174,6 +177,13 @@ hd_status hd_set_stream(hd_handle h, void* stream);
 
 /* -- sizes and index maps ----------------------------------------------- */
 hd_status hd_get_sizes(hd_handle h, int64_t* n_rt, int64_t* n_l2, int64_t* n_elem);
+/* Setup phase times of hd_create in milliseconds (the setup Sec. 3.1 times apart from
+ * the solve): ms[0] geometric factors, ms[1] the W^-1 data (dense per-element
+ * inverses, or the Jacobi diagonals of the local CG), ms[2] diag(M), ms[3] the Schur
+ * preconditioner hierarchies, ms[4] the double-float copies, ms[5] hd_create in
+ * total (host clock). ms[0..2] are CUDA-event times. Writes the first n (0..6)
+ * entries to the host array ms; HD_ERR_INVALID_ARG otherwise. */
+hd_status hd_get_setup_times(hd_handle h, double* ms, int32_t n);
 /* Signed element-to-RT-dof map of Algorithm 1 (element_map, rt_local_to_global
  * and the orientations folded in): host_out has n_elem * 3(k+1)k^2 int32 entries,
  * row e lists the global id g of each local dof, stored as g when local and global

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhdivsp.so")
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_CUDA, HD_ERR_OOM, HD_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 HD_ERR_PREC_INDEFINITE, HD_ERR_NAN, HD_ERR_STAGNATION, HD_ERR_BOUNDS, HD_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 HD_GRAD_DIV, HD_DARCY = 0, 1
-HD_WINV_DENSE, HD_WINV_CG = 0, 1
+HD_WINV_DENSE, HD_WINV_CG, HD_WINV_CG_HIST = 0, 1, 2
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_OOM",
                 4: "HD_ERR_NOT_CONVERGED", 5: "HD_ERR_PREC_INDEFINITE", 6: "HD_ERR_NAN",
                 7: "HD_ERR_STAGNATION", 8: "HD_ERR_BOUNDS", 9: "HD_ERR_NOT_IMPLEMENTED"}
@@ -73,6 +73,7 @@ _SIGS = {
     "hd_set_stream": [_H, _VP],
     "hd_get_sizes": [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                      ctypes.POINTER(ctypes.c_int64)],
+    "hd_get_setup_times": [_H, ctypes.POINTER(ctypes.c_double), ctypes.c_int32],
     "hd_get_e2d_map": [_H, _VP],
     "hd_get_ess_dofs": [_H, _VP, ctypes.POINTER(ctypes.c_int64)],
     "hd_lattice_e2d_map": [ctypes.c_int32] * 4 + [_VP],
@@ -191,6 +192,13 @@ class Operator:
         self.n = self.n_rt + self.n_l2
         if stream is not None:
             self.set_stream(stream)
+
+    def hd_get_setup_times(self):
+        """Setup phase times of hd_create in ms: geometric factors, W^-1 data, diag(M),
+        Schur preconditioner hierarchies, double-float copies, total."""
+        ms = (ctypes.c_double * 6)()
+        _check(lib().hd_get_setup_times(self.h, ms, 6), self.h)
+        return {k: ms[i] for i, k in enumerate(("geometry", "winv", "diag_m", "schur", "double_float", "total"))}
 
     def close(self):
         if getattr(self, "h", None):

@@ -1,6 +1,7 @@
 // C ABI of the hdivsp library: handle lifetime, host-side setup (1D tables of
 // the interpolation-histopolation basis, index maps) and the apply entry points.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -243,6 +244,7 @@ hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y) {
 extern "C" {
 
 hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
+  const auto t_create = std::chrono::steady_clock::now();
   if (!d || !out) return HD_ERR_INVALID_ARG;
   *out = nullptr;
   hd_op* h = new (std::nothrow) hd_op();
@@ -257,7 +259,10 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->k = d->k;
   h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
   if (h->q != h->k + 1 && h->q != h->k + 2) { delete h; return HD_ERR_INVALID_ARG; }
-  if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG && d->winv_mode != HD_WINV_CG_HIST) {
+    delete h;
+    return HD_ERR_INVALID_ARG;
+  }
   if (d->fp64_emulation != 0 && d->fp64_emulation != 1) { delete h; return HD_ERR_INVALID_ARG; }
   if (d->fp64_emulation == 1 && d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
   h->emul = d->fp64_emulation == 1;
@@ -344,8 +349,12 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
       break;
     }
     if (bad) { st = hd_fail(h, HD_ERR_INVALID_ARG, "inverted element (det J <= 0)"); break; }
+    auto t_pre = std::chrono::steady_clock::now();
     if ((st = precond_setup(h)) != HD_OK) break;
     if ((st = sa_setup(h)) != HD_OK) break;
+    if (cudaStreamSynchronize(s) != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "setup"); break; }
+    auto t_emul = std::chrono::steady_clock::now();
+    h->setup_ms[3] = std::chrono::duration<float, std::milli>(t_emul - t_pre).count();
     if (h->emul) {
       const int64_t ng = E * 6 * nq, nw = E * nl2 * nl2;
       if (cudaMalloc(&h->x_G, sizeof(dfloat) * (ng > 0 ? ng : 1)) != cudaSuccess ||
@@ -361,6 +370,9 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = hd_cuda_check(h, e, "setup"); break; }
+    const auto t_end = std::chrono::steady_clock::now();
+    h->setup_ms[4] = std::chrono::duration<float, std::milli>(t_end - t_emul).count();
+    h->setup_ms[5] = std::chrono::duration<float, std::milli>(t_end - t_create).count();
   } while (0);
   cudaFree(d_b);
   cudaFree(d_bad);
@@ -387,6 +399,12 @@ const char* hd_last_error(hd_handle h) { return h ? h->err.c_str() : "null handl
 hd_status hd_set_stream(hd_handle h, void* stream) {
   if (!h) return HD_ERR_INVALID_ARG;
   h->stream = (cudaStream_t)stream;
+  return HD_OK;
+}
+
+hd_status hd_get_setup_times(hd_handle h, double* ms, int32_t n) {
+  if (!h || !ms || n < 0 || n > 6) return HD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; ++i) ms[i] = h->setup_ms[i];
   return HD_OK;
 }
 

@@ -103,6 +103,9 @@ struct hd_op {
   int64_t n_rt, n_l2, n_elem;
   double tau;
   int winv_mode, nu, coarse_max;
+  // setup phase times in ms (hd_get_setup_times): geometric factors, W^-1 data,
+  // diag(M), Schur preconditioner hierarchies, double-float copies, hd_create total
+  float setup_ms[6] = {0, 0, 0, 0, 0, 0};
   int cycle = 1;
   int w_levels = 0;    // W repetition on levels < w_levels only (0: all)
   bool singular;

@@ -46,9 +46,10 @@ inline TabT<T> make_tab(const ElemTables& t) {
 template <typename T>
 struct CgArgs {
   const T* wdet;     // [E][Q^3] w_p / det J, or null: use the dense W_e^-1
-  const T* diag;     // [E][K^3] Jacobi diagonal of W_e in the GL nodal basis
+  const T* diag;     // [E][K^3] Jacobi diagonal of W_e in the basis the CG works in
   int maxit;
   T tol2;            // stop when ||r||^2 <= tol2 ||b||^2 (per element)
+  int hist;          // 0: CG in the GL nodal basis (Sec. 2.5); 1: in the histopolation basis
 };
 
 // Sum of products as one FMA chain (one type per arithmetic: double, float or
@@ -195,29 +196,31 @@ __device__ __forceinline__ void apply_tt(const TabT<T>& tab, const T* in, int in
   __syncthreads();
 }
 
-// w = W_GL p for EB elements: GL nodal -> quadrature points (three stages with
-// BG), times w_p / det J, and back (three transposed stages). Scratch s1.
-template <typename T, int K, int Q, int EB>
+// w = W p for EB elements in the GL nodal basis (GLB: tables BG) or the
+// histopolation basis (tables BH): basis -> quadrature points (three stages),
+// times w_p / det J, and back (three transposed stages). Scratch s1.
+template <typename T, int K, int Q, int EB, bool GLB>
 __device__ __forceinline__ void apply_wgl(const TabT<T>& tab, const T* p, int vstride, T* w, T* s1, int s1stride,
                                           const T* __restrict__ wdet, int e0, int n_elem) {
   constexpr int KK = K * K, NQ = Q * Q * Q;
   const int tid = threadIdx.x, nth = blockDim.x;
+  const T* B = GLB ? tab.BG : tab.BH;
   T* t1b = s1;                       // [Q K K]
   T* t2b = s1 + Q * KK;              // [Q Q K]
   T* vb = s1 + Q * KK + Q * Q * K;   // [Q^3]
   for (int t = tid; t < EB * KK; t += nth) {
     int el = t / KK, r = t - el * KK;
-    contract<T, K, Q, 1, 1>(p + el * vstride + K * r, t1b + el * s1stride + Q * r, tab.BG);
+    contract<T, K, Q, 1, 1>(p + el * vstride + K * r, t1b + el * s1stride + Q * r, B);
   }
   __syncthreads();
   for (int t = tid; t < EB * Q * K; t += nth) {
     int el = t / (Q * K), r = t - el * Q * K, px = r % Q, m3 = r / Q;
-    contract<T, K, Q, Q, Q>(t1b + el * s1stride + px + Q * K * m3, t2b + el * s1stride + px + Q * Q * m3, tab.BG);
+    contract<T, K, Q, Q, Q>(t1b + el * s1stride + px + Q * K * m3, t2b + el * s1stride + px + Q * Q * m3, B);
   }
   __syncthreads();
   for (int t = tid; t < EB * Q * Q; t += nth) {
     int el = t / (Q * Q), r = t - el * Q * Q;
-    contract<T, K, Q, Q * Q, Q * Q>(t2b + el * s1stride + r, vb + el * s1stride + r, tab.BG);
+    contract<T, K, Q, Q * Q, Q * Q>(t2b + el * s1stride + r, vb + el * s1stride + r, B);
   }
   __syncthreads();
   for (int t = tid; t < EB * NQ; t += nth) {
@@ -227,17 +230,17 @@ __device__ __forceinline__ void apply_wgl(const TabT<T>& tab, const T* p, int vs
   __syncthreads();
   for (int t = tid; t < EB * Q * Q; t += nth) {
     int el = t / (Q * Q), r = t - el * Q * Q;
-    contractT<T, Q, K, Q * Q, Q * Q>(vb + el * s1stride + r, t2b + el * s1stride + r, tab.BG);
+    contractT<T, Q, K, Q * Q, Q * Q>(vb + el * s1stride + r, t2b + el * s1stride + r, B);
   }
   __syncthreads();
   for (int t = tid; t < EB * Q * K; t += nth) {
     int el = t / (Q * K), r = t - el * Q * K, px = r % Q, m3 = r / Q;
-    contractT<T, Q, K, Q, Q>(t2b + el * s1stride + px + Q * Q * m3, t1b + el * s1stride + px + Q * K * m3, tab.BG);
+    contractT<T, Q, K, Q, Q>(t2b + el * s1stride + px + Q * Q * m3, t1b + el * s1stride + px + Q * K * m3, B);
   }
   __syncthreads();
   for (int t = tid; t < EB * KK; t += nth) {
     int el = t / KK, r = t - el * KK;
-    contractT<T, Q, K, 1, 1>(t1b + el * s1stride + Q * r, w + el * vstride + K * r, tab.BG);
+    contractT<T, Q, K, 1, 1>(t1b + el * s1stride + Q * r, w + el * vstride + K * r, B);
   }
   __syncthreads();
 }
@@ -251,9 +254,11 @@ __device__ __forceinline__ T warp_allsum(T v) {
 
 // W_e^-1 q_e for EB elements by the local CG of Sec. 2.5: b = TT^T q (GL nodal
 // right-hand side), Jacobi-preconditioned CG on W_GL from a = 0, result TT a in
-// s1 (returned). One warp per element for the vector operations; the loop runs
-// until every element of the CTA meets its tolerance or maxit is reached.
-template <typename T, int K, int Q, int EB>
+// s1 (returned). GLB = false: the same CG on W in the histopolation basis itself
+// (b = q, result a; the comparison of the two bases in Sec. 3.1). One warp per
+// element for the vector operations; the loop runs until every element of the
+// CTA meets its tolerance or maxit is reached.
+template <typename T, int K, int Q, int EB, bool GLB>
 __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* s2, int s2stride,
                        const CgArgs<T>& cg, int e0, int n_elem) {
   constexpr int NL2 = K * K * K;
@@ -266,7 +271,12 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
   T* R = s2 + NL2;
   T* P = s2 + 2 * NL2;
   T* W = s2 + 3 * NL2;
-  apply_tt<T, K, EB, true>(tab, sq, NL2, s1, s1 + NL2, R, s1stride, s2stride);  // r = b = TT^T q
+  if (GLB) {
+    apply_tt<T, K, EB, true>(tab, sq, NL2, s1, s1 + NL2, R, s1stride, s2stride);  // r = b = TT^T q
+  } else {
+    for (int t = threadIdx.x; t < EB * NL2; t += blockDim.x) R[(t / NL2) * s2stride + t % NL2] = sq[t];
+    __syncthreads();
+  }
   for (int el = warp; el < EB; el += nw) {
     const int e = e0 + el;
     const T* D = cg.diag + (size_t)(e < n_elem ? e : 0) * NL2;
@@ -289,7 +299,7 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
   }
   __syncthreads();
   for (int it = 0; it < cg.maxit; ++it) {
-    apply_wgl<T, K, Q, EB>(tab, P, s2stride, W, s1, s1stride, cg.wdet, e0, n_elem);
+    apply_wgl<T, K, Q, EB, GLB>(tab, P, s2stride, W, s1, s1stride, cg.wdet, e0, n_elem);
     for (int el = warp; el < EB; el += nw) {
       if (!sc_active[el]) continue;
       T pw = 0;
@@ -333,7 +343,13 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
     __syncthreads();
   }
   T* out = s1 + 2 * NL2;
-  apply_tt<T, K, EB, false>(tab, A, s2stride, s1, s1 + NL2, out, s1stride, s1stride);  // TT a
+  if (GLB) {
+    apply_tt<T, K, EB, false>(tab, A, s2stride, s1, s1 + NL2, out, s1stride, s1stride);  // TT a
+  } else {
+    for (int t = threadIdx.x; t < EB * NL2; t += blockDim.x)
+      out[(t / NL2) * s1stride + t % NL2] = A[(t / NL2) * s2stride + t % NL2];
+    __syncthreads();
+  }
   return out;
 }
 
@@ -470,7 +486,11 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   // -- L2 rows: y_q = D u - C q ------------------------------------------------
   const T* cgres = nullptr;
   if constexpr (!std::is_same<T, dfloat>::value) {
-    if (use_cg) cgres = local_cg<T, K, Q, EB>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
+    if (use_cg) {
+      if constexpr (std::is_same<T, double>::value)  // the histopolation-basis CG: FP64 only
+        if (cg.hist) cgres = local_cg<T, K, Q, EB, false>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
+      if (!cgres) cgres = local_cg<T, K, Q, EB, true>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
+    }
   }
   // one L2 row (element-local cell t), given its D u part v
   auto l2_row = [&](int t, T v) {
@@ -866,15 +886,21 @@ hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs
 template <int K, int Q>
 hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
   constexpr int NQ = Q * Q * Q, NRT = 3 * (K + 1) * K * K;
+  // phase times (setup_ms[0..2]): geometric factors; W^-1 data (dense inverses, or
+  // the Jacobi diagonals of the local CG); diag(M)
+  cudaEvent_t ev[4];
+  for (auto& x : ev) cudaEventCreate(&x);
+  cudaEventRecord(ev[0], h->stream);
   int64_t n = h->n_elem * NQ;
   if (n > 0) k_geom<Q><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
       h->tab, h->L, (int)h->n_elem, h->d_vx, h->d_vy, h->d_vz, bcoef, h->d_G, h->d_wdet, d_bad);
   HD_LAUNCH_CK(h, "k_geom");
+  cudaEventRecord(ev[1], h->stream);
   if (h->n_elem > 0) {
     constexpr int NL2 = K * K * K;
     unsigned nb = (unsigned)((h->n_elem * NL2 + 255) / 256);
     k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, true, h->d_wdet, h->d_wgldiag);
-    if (h->winv_mode == HD_WINV_CG)
+    if (h->winv_mode != HD_WINV_DENSE)  // the dense path gets diag(W_e) from k_winv
       k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, false, h->d_wdet, h->d_wdiag);
     HD_LAUNCH_CK(h, "k_diag_tensor");
   }
@@ -886,10 +912,15 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
                                                                  h->d_wdiag);
     HD_LAUNCH_CK(h, "k_winv");
   }
+  cudaEventRecord(ev[2], h->stream);
   int64_t m = h->n_elem * NRT;
   if (m > 0) k_diagM<K, Q><<<(unsigned)((m + 255) / 256), 256, 0, h->stream>>>(h->tab, h->L, (int)h->n_elem,
                                                                           h->d_G, h->d_mt);
   HD_LAUNCH_CK(h, "k_diagM");
+  cudaEventRecord(ev[3], h->stream);
+  if (cudaEventSynchronize(ev[3]) == cudaSuccess)
+    for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&h->setup_ms[i], ev[i], ev[i + 1]);
+  for (auto& x : ev) cudaEventDestroy(x);
   return HD_OK;
 }
 
@@ -912,12 +943,16 @@ HD_DECLARE_K(3)
 HD_DECLARE_K(4)
 HD_DECLARE_K(5)
 
-// FP64: the dense W_e^-1, or the local CG to a relative residual of 1e-14 (HD_WINV_CG).
+// FP64: the dense W_e^-1, or the local CG to a relative residual of 1e-14 in the GL nodal
+// basis (HD_WINV_CG, at most 40 iterations) or the histopolation basis (HD_WINV_CG_HIST,
+// at most 100: its Jacobi-scaled W is worse conditioned).
 // FP32 (inner solves): the dense W_e^-1 in FP32 when the handle has one (faster on
 // this GPU than the CG's barrier-bound iterations), else the local CG to 1e-6.
 #define HD_DEFINE_K(KK)                                                                                   \
   hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) { \
-    hdk::CgArgs<double> cg{h->winv_mode == HD_WINV_CG ? h->d_wdet : nullptr, h->d_wgldiag, 40, 1e-28};     \
+    const bool hi = h->winv_mode == HD_WINV_CG_HIST;                                                      \
+    hdk::CgArgs<double> cg{h->winv_mode != HD_WINV_DENSE ? h->d_wdet : nullptr, hi ? h->d_wdiag : h->d_wgldiag, \
+                           hi ? 100 : 40, 1e-28, hi ? 1 : 0};                                             \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<double, double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, \
                                                           q, yu, yq);                                     \
@@ -926,7 +961,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,            \
                              double* yq) {                                                                \
-    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0)};                                               \
+    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0};                                            \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<dfloat, double, KK, KK + 1>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, \
                                                           q, yu, yq);                                     \
@@ -935,7 +970,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,              \
                               float* yq) {                                                                \
-    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f};                     \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0};                  \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<float, float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, \
                                                         yu, yq);                                          \
@@ -944,7 +979,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_f32io64_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,       \
                                   double* yq) {                                                           \
-    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f};                     \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0};                  \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<float, double, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u,  \
                                                          q, yu, yq);                                      \

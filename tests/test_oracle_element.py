@@ -175,3 +175,28 @@ def test_gl_mass_diagonal_on_parallelepiped():
     WGL = S.T @ W @ S
     off = WGL - np.diag(np.diag(WGL))
     assert np.abs(off).max() < 1e-13 * np.abs(WGL).max()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_gl_basis_is_better_conditioned_on_a_perturbed_element(k):
+    """Sec. 3.1: the local CG changes to the Gauss-Legendre nodal basis because the
+    Jacobi-scaled L2 mass is better conditioned there than in the histopolation basis
+    (on a perturbed, non-affine element: close to 1 against several units)."""
+    V = _one_element(0.15, seed=11)
+    W = element.element_matrices(V, k, k + 2, np.array([1.0]), np.array([1.0]), want=("W",))["W"][0]
+    g, _ = basis1d.gl_points(k)
+    xi = basis1d.gll_nodes(k)
+    t, w = np.polynomial.legendre.leggauss(k + 2)
+    S1 = np.zeros((k, k))
+    for j in range(k):
+        a, b = xi[j], xi[j + 1]
+        x = 0.5 * (b - a) * t + 0.5 * (a + b)
+        S1[j] = basis1d.lagrange(g, x) @ (0.5 * (b - a) * w)
+    S = np.kron(S1, np.kron(S1, S1))
+
+    def scaled_cond(A):
+        d = 1.0 / np.sqrt(np.diag(A))
+        return np.linalg.cond(A * np.outer(d, d))
+
+    k_hist, k_gl = scaled_cond(W), scaled_cond(S.T @ W @ S)
+    assert k_gl < 1.5 < k_hist, (k_gl, k_hist)
