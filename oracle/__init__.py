@@ -23,6 +23,8 @@ Modules
   precond   diag(M), diag(W), the approximate Schur complement (Eq. approx-schur)
             and the geometric V-cycle spec that stands in for AMG.
   minres    preconditioned MINRES (Paige & Saunders 1975) in FP64.
+  gmres     restarted right-preconditioned GMRES (Saad & Schultz 1986) for the
+            block-triangular preconditioner of the remark in Sec. 2.3.
   sampled   single rows of the block operator at any mesh size (element-local).
   conv      reference 3D convolution forward/backward for the learned Schur
             preconditioner.

@@ -144,3 +144,18 @@ class BlockPrec:
         zu = np.where(self.prob.free, ru / (self.tau * self.Mt), ru)
         zq = self.vc.apply(rq)
         return np.concatenate([zu, zq])
+
+
+class BlockTriPrec(BlockPrec):
+    """z = P^-1 r with the block upper-triangular P = [[tau M~, D^T], [0, -S^]]
+    (the remark on block-triangular preconditioners in Sec. 2.3), for GMRES:
+    z_q = -S^-1 r_q (the V/W-cycle of BlockPrec), then
+    z_u = (r_u - D^T z_q) / (tau M~) on free dofs and z_u = r_u on essential dofs
+    (D has no columns for them, so D^T z_q vanishes there)."""
+
+    def apply(self, r):
+        nrt = self.prob.lat.n_rt
+        ru, rq = r[:nrt], r[nrt:]
+        zq = -self.vc.apply(rq)
+        zu = np.where(self.prob.free, (ru - self.prob.apply_Bt(zq)) / (self.tau * self.Mt), ru)
+        return np.concatenate([zu, zq])
