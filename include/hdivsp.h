@@ -240,6 +240,39 @@ hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3
 hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
                           const hd_solve_opts* opts, hd_solve_info* info);
 
+/* -- GMRES with block preconditioners ----------------------------------------- */
+/* The remark on block-triangular preconditioners in Sec. 2.3: with exact blocks,
+ * P = [[M, D^T], [0, -S]] gives GMRES convergence in two iterations; with the
+ * approximations tau M~ and the Schur V/W-cycle S^,
+ *   z = P^-1 r:  z_q = -S^-1 r_q,  z_u = (r_u - D^T z_q) / (tau M~)
+ * (identity on essential dofs, zero-mean z_q in the singular case). The
+ * preconditioned operator is not symmetric, hence GMRES (right-preconditioned,
+ * restarted, Saad & Schultz 1986) instead of MINRES. */
+enum {
+  HD_GMRES_BLOCK_DIAG = 0, /* the block-diagonal preconditioner of hd_minres_solve */
+  HD_GMRES_BLOCK_TRI = 1   /* the block upper-triangular one above */
+};
+typedef struct {
+  double rtol;      /* stop when ||b - AA x||_2 <= rtol ||b||_2; the recurrence estimates the
+                       true residual (right preconditioning) and every restart and the exit
+                       recompute it in FP64 */
+  int32_t maxit;    /* Arnoldi steps in total (>= 1) */
+  int32_t restart;  /* steps before a restart, 1..128; the basis takes restart + 1 device
+                       vectors of n_rt + n_l2 doubles (allocated on the first call and kept) */
+  int32_t prec;     /* HD_GMRES_BLOCK_DIAG or HD_GMRES_BLOCK_TRI */
+  int32_t use_x0;   /* 1: start from x, else from zero */
+} hd_gmres_opts;
+/* GMRES on AA x = b (device vectors of n_rt + n_l2 doubles, owned by the caller) with
+ * the handle's operator (FP64 or double-float element kernel) and FP64 V/W-cycle.
+ * Arnoldi by classical Gram-Schmidt, a second pass when the norm drops below 1e-3 of
+ * its value; fixed-order reductions (deterministic). info->iterations = Arnoldi
+ * steps, info->outer = restart cycles, info->eta_ratio = the last estimate / ||b||,
+ * info->true_relres the FP64 true residual at exit. HD_ERR_NOT_CONVERGED when maxit
+ * runs out, HD_ERR_NAN on a breakdown, HD_ERR_OOM when the basis does not fit,
+ * HD_ERR_NOT_IMPLEMENTED with the learned Schur preconditioner enabled. */
+hd_status hd_gmres_solve(hd_handle h, const double* b, double* x, const hd_gmres_opts* opts,
+                         hd_solve_info* info);
+
 /* -- profiling ------------------------------------------------------------- */
 /* enable != 0: record a CUDA event pair on the handle's stream around every
  * launch of the fused element kernel (up to 4096 launches, then recording

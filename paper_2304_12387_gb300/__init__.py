@@ -19,6 +19,7 @@ HD_OK, HD_ERR_INVALID_ARG, HD_ERR_CUDA, HD_ERR_OOM, HD_ERR_NOT_CONVERGED = 0, 1,
 HD_ERR_PREC_INDEFINITE, HD_ERR_NAN, HD_ERR_STAGNATION, HD_ERR_BOUNDS, HD_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 HD_GRAD_DIV, HD_DARCY = 0, 1
 HD_WINV_DENSE, HD_WINV_CG, HD_WINV_CG_HIST = 0, 1, 2
+HD_GMRES_BLOCK_DIAG, HD_GMRES_BLOCK_TRI = 0, 1
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_OOM",
                 4: "HD_ERR_NOT_CONVERGED", 5: "HD_ERR_PREC_INDEFINITE", 6: "HD_ERR_NAN",
                 7: "HD_ERR_STAGNATION", 8: "HD_ERR_BOUNDS", 9: "HD_ERR_NOT_IMPLEMENTED"}
@@ -46,6 +47,11 @@ class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("outer_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+
+
+class GmresOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("restart", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -90,6 +96,7 @@ _SIGS = {
     "hd_get_diagonals": [_H, _VP, _VP],
     "hd_get_level": [_H, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)],
     "hd_minres_solve": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_gmres_solve": [_H, _VP, _VP, ctypes.POINTER(GmresOpts), ctypes.POINTER(SolveInfo)],
     "hd_minres_solve_noalloc": [_H, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
     "hd_profile": [_H, ctypes.c_int32],
     "hd_profile_read": [_H, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)],
@@ -279,6 +286,15 @@ class Operator:
         return st, {"iterations": info.iterations, "outer": info.outer, "eta_ratio": info.eta_ratio,
                     "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status,
                     "fallback": info.fallback}
+
+    def hd_gmres_solve(self, b, x, rtol=1e-8, maxit=1000, restart=64, prec=1, use_x0=False):
+        """Restarted right-preconditioned GMRES on AA x = b; prec = HD_GMRES_BLOCK_TRI (1,
+        the block upper-triangular preconditioner) or HD_GMRES_BLOCK_DIAG (0)."""
+        o = GmresOpts(rtol, maxit, restart, prec, int(use_x0))
+        info = SolveInfo()
+        st = lib().hd_gmres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        return st, {"iterations": info.iterations, "cycles": info.outer, "estimate_ratio": info.eta_ratio,
+                    "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status}
 
     # -- learned Schur preconditioner ----------------------------------------
     def hd_learned_init(self, nc=32, seed=2304, delta=1e-3):

@@ -201,6 +201,11 @@ void destroy_all(hd_op* h) {
   for (double* p : h->mv) cudaFree(p);
   for (float* p : h->fv) cudaFree(p);
   cudaFree(h->d_ms);
+  cudaFree(h->gm_V);
+  cudaFree(h->gm_w);
+  cudaFree(h->gm_part);
+  cudaFree(h->gm_dots);
+  if (h->gm_host) cudaFreeHost(h->gm_host);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);
   for (cudaEvent_t e : h->xev) cudaEventDestroy(e);

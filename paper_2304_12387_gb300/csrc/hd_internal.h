@@ -166,6 +166,14 @@ struct hd_op {
   double* d_stage = nullptr;    // 2 (n_rt + n_l2) staging for *_host calls
   // MINRES work vectors (allocated on first solve)
   std::vector<double*> mv;
+  // GMRES (hd_gmres_solve): basis [gm_m + 1][n], work vectors w, z, t [3][n], dot
+  // partials and results, pinned host copy
+  double* gm_V = nullptr;
+  int gm_m = 0;
+  double* gm_w = nullptr;
+  double* gm_part = nullptr;
+  double* gm_dots = nullptr;
+  double* gm_host = nullptr;
   MinresState* d_ms = nullptr;
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
   // Schur-block preconditioner: 0 = V-cycle, 1 = learned network + coarse correction
