@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
 
 class GmresOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("restart", ctypes.c_int32),
-                ("prec", ctypes.c_int32), ("use_x0", ctypes.c_int32)]
+                ("prec", ctypes.c_int32), ("use_x0", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("inner_rtol", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -287,10 +288,12 @@ class Operator:
                     "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status,
                     "fallback": info.fallback}
 
-    def hd_gmres_solve(self, b, x, rtol=1e-8, maxit=1000, restart=64, prec=1, use_x0=False):
+    def hd_gmres_solve(self, b, x, rtol=1e-8, maxit=1000, restart=64, prec=1, use_x0=False, precision=0,
+                       inner_rtol=1e-4):
         """Restarted right-preconditioned GMRES on AA x = b; prec = HD_GMRES_BLOCK_TRI (1,
-        the block upper-triangular preconditioner) or HD_GMRES_BLOCK_DIAG (0)."""
-        o = GmresOpts(rtol, maxit, restart, prec, int(use_x0))
+        the block upper-triangular preconditioner) or HD_GMRES_BLOCK_DIAG (0); precision 1:
+        FP32 operator and V-cycle inside the cycles, FP64 residual at every restart."""
+        o = GmresOpts(rtol, maxit, restart, prec, int(use_x0), precision, inner_rtol)
         info = SolveInfo()
         st = lib().hd_gmres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
         return st, {"iterations": info.iterations, "cycles": info.outer, "estimate_ratio": info.eta_ratio,

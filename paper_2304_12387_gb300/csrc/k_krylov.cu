@@ -760,13 +760,13 @@ static hd_status ensure_gmres(hd_op* h, int m) {
 // triangular (prec 1). tmp: n doubles of scratch. The q part of v is copied into
 // tmp's q part first: the V-cycle replays a CUDA graph cached per (input, output)
 // pointer pair, and the Arnoldi vectors would otherwise each need a new capture.
-static hd_status gmres_prec(hd_op* h, int prec, const double* v, double* z, double* tmp) {
+static hd_status gmres_prec(hd_op* h, int prec, bool f32, const double* v, double* z, double* tmp) {
   hd_status st;
   if ((st = diag_scale(h, v, z)) != HD_OK) return st;  // prec 1 overwrites z_u below
   if (h->n_l2 == 0) return HD_OK;
   double* rq = tmp + h->n_rt;
   HD_CK(h, cudaMemcpyAsync(rq, v + h->n_rt, sizeof(double) * h->n_l2, cudaMemcpyDeviceToDevice, h->stream));
-  if ((st = inner_vcycle(h, false, rq, z + h->n_rt)) != HD_OK) return st;  // s = S^-1 r_q
+  if ((st = inner_vcycle(h, f32, rq, z + h->n_rt)) != HD_OK) return st;  // s = S^-1 r_q
   if (prec == 0) return HD_OK;
   if ((st = lattice_apply_Bt(h, z + h->n_rt, tmp)) != HD_OK) return st;  // D^T s
   cudaStream_t s = h->stream;
@@ -800,10 +800,17 @@ static hd_status gm_update(hd_op* h, const double* V, int64_t n, int nv, double*
   return HD_OK;
 }
 
+// precision = 1: the Arnoldi steps apply the operator and the V-cycle in FP32 (FP64
+// vectors, FP64 Gram-Schmidt), a cycle ends once its estimate has fallen by
+// inner_rtol, and every restart recomputes the residual with the FP64 operator: the
+// FP64 residual correction of the mixed MINRES solve, with GMRES cycles as the
+// inner solver.
 hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o, hd_solve_info* info) {
   const int m = o->restart;
   hd_status st = ensure_gmres(h, m);
   if (st != HD_OK) return st;
+  const bool f32 = o->precision == 1;
+  if (f32 && (st = ensure_f32_work(h)) != HD_OK) return st;
   const int64_t n = h->n_rt + h->n_l2;
   cudaStream_t s = h->stream;
   double *V = h->gm_V, *w = h->gm_w, *z = h->gm_w + n, *tmp = h->gm_w + 2 * n;
@@ -838,8 +845,8 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
     const int mc = std::min(m, o->maxit - its);
     while (j < mc) {
       double* Vj = V + (int64_t)j * n;
-      if ((st = gmres_prec(h, o->prec, Vj, z, tmp)) != HD_OK) return st;
-      if ((st = apply_op_internal(h, z, w)) != HD_OK) return st;
+      if ((st = gmres_prec(h, o->prec, f32, Vj, z, tmp)) != HD_OK) return st;
+      if ((st = inner_apply(h, f32, z, w)) != HD_OK) return st;
       // classical Gram-Schmidt: h = V^T w (with ||w||^2 before), w -= V h
       if ((st = gm_mdot(h, V, n, j + 1, true, w, hostd)) != HD_OK) return st;
       const double before = hostd[j + 1];
@@ -878,7 +885,7 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
       ++j;
       ++its;
       est = std::fabs(g[j]);
-      if (est <= o->rtol * bn || hn == 0.0) break;
+      if (est <= o->rtol * bn || hn == 0.0 || (f32 && est <= o->inner_rtol * rn)) break;
     }
     // y = H(0:j, 0:j)^-1 g, x += P^-1 V y
     for (int i = j - 1; i >= 0; --i) {
@@ -889,7 +896,7 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
     HD_CK(h, cudaMemcpyAsync(h->gm_dots, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
     k_gm_combine<<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, tmp);
     HD_LAUNCH_CK(h, "gmres combine");
-    if ((st = gmres_prec(h, o->prec, tmp, z, w)) != HD_OK) return st;
+    if ((st = gmres_prec(h, o->prec, f32, tmp, z, w)) != HD_OK) return st;
     k_add<<<nblk(n), TPB, 0, s>>>(n, z, x);
     HD_LAUNCH_CK(h, "gmres update x");
   }
@@ -915,8 +922,11 @@ extern "C" hd_status hd_gmres_solve(hd_handle h, const double* b, double* x, con
                                     hd_solve_info* info) {
   if (!h || !b || !x || !o) return HD_ERR_INVALID_ARG;
   if (o->restart < 1 || o->restart > GM_MAX_RESTART || o->maxit < 1 || !(o->rtol >= 0.0) ||
-      (o->prec != HD_GMRES_BLOCK_DIAG && o->prec != HD_GMRES_BLOCK_TRI))
-    return hd_fail(h, HD_ERR_INVALID_ARG, "hd_gmres_solve: restart 1..128, maxit >= 1, rtol >= 0, prec 0 or 1");
+      (o->prec != HD_GMRES_BLOCK_DIAG && o->prec != HD_GMRES_BLOCK_TRI) || (o->precision != 0 && o->precision != 1) ||
+      (o->precision == 1 && !(o->inner_rtol > 0.0 && o->inner_rtol < 1.0)))
+    return hd_fail(h, HD_ERR_INVALID_ARG,
+                   "hd_gmres_solve: restart 1..128, maxit >= 1, rtol >= 0, prec 0 or 1, precision 0 or 1 "
+                   "(1: 0 < inner_rtol < 1)");
   if (h->schur_mode != 0) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "hd_gmres_solve: V-cycle Schur preconditioner only");
   return gmres_run(h, b, x, o, info);
 }

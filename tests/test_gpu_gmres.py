@@ -90,10 +90,32 @@ def test_gmres_arguments_and_non_convergence():
     d, prob, bp, op, b = _setup("darcy_k3", True)
     bt = torch.from_numpy(b).cuda()
     x = torch.zeros_like(bt)
-    for kw in (dict(restart=0), dict(restart=129), dict(prec=2), dict(maxit=0)):
+    for kw in (dict(restart=0), dict(restart=129), dict(prec=2), dict(maxit=0), dict(precision=2),
+               dict(precision=1, inner_rtol=0.0), dict(precision=1, inner_rtol=1.0)):
         st, _ = op.hd_gmres_solve(bt, x, **kw)
         assert st == hd.HD_ERR_INVALID_ARG, kw
     st, info = op.hd_gmres_solve(bt, x, rtol=1e-12, maxit=3, restart=64, prec=hd.HD_GMRES_BLOCK_TRI)
     assert st == hd.HD_ERR_NOT_CONVERGED and info["iterations"] == 3
     assert 0 < info["true_relres"] < 1
+    op.close()
+
+
+@pytest.mark.parametrize("name", ["gd_k4_ragged", "darcy_k3", "darcy_neumann", "gd_flat"])
+def test_mixed_precision_gmres_reaches_the_fp64_solution(name):
+    """precision = 1: FP32 operator and V-cycle inside the cycles, FP64 residual at
+    every restart: the true relative residual 1e-8 is reached and the solution
+    agrees with the oracle's FP64 GMRES."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.gmres import gmres
+    d, prob, bp, op, b = _setup(name, True)
+    xr, ir = gmres(prob.apply_op, bp.apply, b, rtol=1e-10, maxit=2000, restart=64)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_gmres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=2000, restart=32,
+                                 prec=hd.HD_GMRES_BLOCK_TRI, precision=1, inner_rtol=1e-4)
+    assert st == 0 and info["true_relres"] <= 1e-8 and info["cycles"] >= 2, info
+    xs = x.cpu().numpy()
+    assert np.linalg.norm(b - prob.apply_op(xs)) <= 1e-8 * np.linalg.norm(b)
+    assert np.linalg.norm(xs - xr) <= 1e-6 * np.linalg.norm(xr)
     op.close()
