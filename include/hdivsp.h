@@ -261,10 +261,10 @@ typedef struct {
                        vectors of n_rt + n_l2 doubles (allocated on the first call and kept) */
   int32_t prec;     /* HD_GMRES_BLOCK_DIAG or HD_GMRES_BLOCK_TRI */
   int32_t use_x0;   /* 1: start from x, else from zero */
-  int32_t precision;/* 0: FP64 operator and V-cycle; 1: both in FP32 inside the Arnoldi steps
-                       (FP64 vectors and Gram-Schmidt), every restart recomputing the residual
-                       with the FP64 operator (a residual correction with GMRES cycles as the
-                       inner solver) */
+  int32_t precision;/* 0: FP64 throughout; 1: every cycle in FP32 (basis, Gram-Schmidt,
+                       operator, V-cycle), every restart recomputing the residual with the FP64
+                       operator and adding the cycle's correction to the FP64 solution (a
+                       residual correction with GMRES cycles as the inner solver) */
   double inner_rtol;/* precision 1: a cycle ends once its estimate has fallen below inner_rtol
                        times the cycle's starting residual (0 < inner_rtol < 1) */
 } hd_gmres_opts;

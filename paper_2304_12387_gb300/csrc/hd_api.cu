@@ -205,6 +205,8 @@ void destroy_all(hd_op* h) {
   cudaFree(h->gm_w);
   cudaFree(h->gm_part);
   cudaFree(h->gm_dots);
+  cudaFree(h->gm_Vf);
+  cudaFree(h->gm_wf);
   if (h->gm_host) cudaFreeHost(h->gm_host);
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   for (cudaEvent_t e : h->prof_ev) cudaEventDestroy(e);

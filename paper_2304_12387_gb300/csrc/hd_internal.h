@@ -174,6 +174,9 @@ struct hd_op {
   double* gm_part = nullptr;
   double* gm_dots = nullptr;
   double* gm_host = nullptr;
+  float* gm_Vf = nullptr;  // mixed precision: FP32 basis [gm_mf + 1][n] and work [3][n]
+  int gm_mf = 0;
+  float* gm_wf = nullptr;
   MinresState* d_ms = nullptr;
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
   // Schur-block preconditioner: 0 = V-cycle, 1 = learned network + coarse correction
@@ -238,6 +241,7 @@ hd_status launch_elem_setup(hd_op* h);   // geometric factors, W_e^-1, diag(W), 
 // lattice kernels (k_lattice.cu)
 hd_status lattice_apply_B(hd_op* h, const double* u, double* yq);
 hd_status lattice_apply_Bt(hd_op* h, const double* q, double* yu);
+hd_status lattice_apply_Bt_f32(hd_op* h, const float* q, float* yu);
 hd_status lattice_ess_identity(hd_op* h, const double* x, double* y);
 hd_status precond_setup(hd_op* h);
 hd_status precond_apply(hd_op* h, const double* r, double* z);
@@ -259,6 +263,9 @@ void precond_free(hd_op* h);
 hd_status project_mean(hd_op* h, double* z);
 hd_status vcycle_apply_f32(hd_op* h, const float* b, float* x);
 hd_status diag_scale(hd_op* h, const double* r, double* z);
+hd_status diag_scale_f32(hd_op* h, const float* r, float* z);
+hd_status project_mean_f32(hd_op* h, float* z);
+hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y);
 hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn);
 // z += P_1 V_1 P_1^T r: the coarse correction of the V-cycle hierarchy (nothing with one level)
 hd_status coarse_correction(hd_op* h, const double* r, double* z);

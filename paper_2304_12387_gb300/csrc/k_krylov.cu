@@ -644,24 +644,34 @@ extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, doubl
 // before the pass; the Hessenberg least-squares problem by Givens rotations on the
 // host (one small copy per step). All reductions run over fixed blocks in a fixed
 // order, so a solve is deterministic.
+//
+// FP64 (precision 0): basis, operator and V-cycle in FP64 (the operator in the
+// handle's element arithmetic). Mixed (precision 1): the cycles run entirely in FP32
+// (basis, Gram-Schmidt, operator, V-cycle), each ends once its estimate has fallen
+// by inner_rtol, and every restart recomputes the residual with the FP64 operator
+// and adds the cycle's correction to the FP64 solution: iterative refinement with
+// GMRES cycles as the inner solver. Gram-Schmidt on an FP64 basis is bound by the
+// FP64 pipe on this GPU (one FMA per value read); in FP32 it streams at HBM speed.
 namespace {
 constexpr int GM_MAX_RESTART = 128;
 constexpr int GM_CH = 8;  // basis vectors per sweep of the multi-dot
 
 // partial[k * DOT_BLOCKS + b] = block b's chunk of V_k . w for k < nv, and with
-// self_dot also w . w at k = nv (V_k = V + k ldv)
-__global__ void k_gm_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, int nv, bool self_dot,
-                          const double* __restrict__ w, double* __restrict__ partial) {
+// self_dot also w . w at k = nv (V_k = V + k ldv). Per-thread sums in T, the
+// block sums in FP64.
+template <typename T>
+__global__ void k_gm_mdot(int64_t n, const T* __restrict__ V, int64_t ldv, int nv, bool self_dot,
+                          const T* __restrict__ w, double* __restrict__ partial) {
   __shared__ double sh[32];
   const int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   const int ntot = nv + (self_dot ? 1 : 0);
   for (int k0 = 0; k0 < ntot; k0 += GM_CH) {
-    double acc[GM_CH];
+    T acc[GM_CH];
 #pragma unroll
-    for (int c = 0; c < GM_CH; ++c) acc[c] = 0.0;
+    for (int c = 0; c < GM_CH; ++c) acc[c] = (T)0;
     for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
+      const T wi = w[i];
 #pragma unroll
       for (int c = 0; c < GM_CH; ++c) {
         const int k = k0 + c;
@@ -672,7 +682,7 @@ __global__ void k_gm_mdot(int64_t n, const double* __restrict__ V, int64_t ldv, 
 #pragma unroll
     for (int c = 0; c < GM_CH; ++c) {
       if (k0 + c >= ntot) break;  // uniform over the block
-      const double s = block_sum(acc[c], sh);
+      const double s = block_sum((double)acc[c], sh);
       if (threadIdx.x == 0) partial[(k0 + c) * DOT_BLOCKS + blockIdx.x] = s;
     }
   }
@@ -686,102 +696,139 @@ __global__ void k_gm_final(const double* __restrict__ partial, double* __restric
 }
 
 // w -= sum_k h[k] V_k (k < nv), and partial[b] = block b's chunk of the new w . w
-__global__ void k_gm_update_norm(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                                 const double* __restrict__ hcoef, double* __restrict__ w,
-                                 double* __restrict__ partial) {
+template <typename T>
+__global__ void k_gm_update_norm(int64_t n, const T* __restrict__ V, int64_t ldv, int nv,
+                                 const double* __restrict__ hcoef, T* __restrict__ w, double* __restrict__ partial) {
   __shared__ double sh[32];
-  __shared__ double hs[GM_MAX_RESTART + 1];
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = hcoef[k];
+  __shared__ T hs[GM_MAX_RESTART + 1];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)hcoef[k];
   __syncthreads();
   const int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-  double acc = 0.0;
+  T acc = (T)0;
   for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-    double s = w[i];
+    T s = w[i];
     for (int k = 0; k < nv; ++k) s = fma(-hs[k], V[k * ldv + i], s);
     w[i] = s;
     acc = fma(s, s, acc);
   }
-  acc = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+  const double b = block_sum((double)acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = b;
 }
 
 // u = sum_k y[k] V_k (k < nv)
-__global__ void k_gm_combine(int64_t n, const double* __restrict__ V, int64_t ldv, int nv,
-                             const double* __restrict__ y, double* __restrict__ u) {
-  __shared__ double ys[GM_MAX_RESTART];
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = y[k];
+template <typename T>
+__global__ void k_gm_combine(int64_t n, const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ y,
+                             T* __restrict__ u) {
+  __shared__ T ys[GM_MAX_RESTART];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = (T)y[k];
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double s = 0.0;
+  T s = (T)0;
   for (int k = 0; k < nv; ++k) s = fma(ys[k], V[k * ldv + i], s);
   u[i] = s;
 }
 
-__global__ void k_gm_scale(int64_t n, double a, const double* __restrict__ x, double* __restrict__ y) {
+// y = a x (in y's type)
+template <typename S, typename T>
+__global__ void k_gm_scale(int64_t n, double a, const S* __restrict__ x, T* __restrict__ y) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = a * x[i];
+  if (i < n) y[i] = (T)(a * (double)x[i]);
 }
 
 // triangular preconditioner, RT part: z_u = mtinv (r_u + D^T s) with s = S^-1 r_q
 // (so that z_q = -s); mtinv = 1 and (D^T s) = 0 on essential dofs
-__global__ void k_gm_tri_u(int64_t n_rt, const double* __restrict__ mtinv, const double* __restrict__ ru,
-                           const double* __restrict__ dts, double* __restrict__ zu) {
+template <typename T>
+__global__ void k_gm_tri_u(int64_t n_rt, const T* __restrict__ mtinv, const T* __restrict__ ru,
+                           const T* __restrict__ dts, T* __restrict__ zu) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n_rt) zu[i] = mtinv[i] * (ru[i] + dts[i]);
 }
-__global__ void k_gm_neg(int64_t n, double* __restrict__ x) {
+template <typename T>
+__global__ void k_gm_neg(int64_t n, T* __restrict__ x) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) x[i] = -x[i];
 }
+// x += (double) z
+__global__ void k_gm_add_f(int64_t n, const float* __restrict__ z, double* __restrict__ x) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += (double)z[i];
+}
 }  // namespace
 
-static hd_status ensure_gmres(hd_op* h, int m) {
-  const int64_t n = h->n_rt + h->n_l2;
-  if (h->gm_V && h->gm_m >= m) return HD_OK;
-  cudaFree(h->gm_V);
-  h->gm_V = nullptr;
-  h->gm_m = 0;
-  if (cudaMalloc(&h->gm_V, sizeof(double) * (size_t)(m + 1) * (size_t)(n > 0 ? n : 1)) != cudaSuccess)
-    return hd_fail(h, HD_ERR_OOM, "GMRES basis");
-  h->gm_m = m;
+static hd_status ensure_gmres(hd_op* h, int m, bool f32) {
+  const int64_t n = h->n_rt + h->n_l2, nn = n > 0 ? n : 1;
   if (!h->gm_w) {
-    if (cudaMalloc(&h->gm_w, sizeof(double) * 3 * (n > 0 ? n : 1)) != cudaSuccess ||
+    if (cudaMalloc(&h->gm_w, sizeof(double) * 3 * nn) != cudaSuccess ||
         cudaMalloc(&h->gm_part, sizeof(double) * (GM_MAX_RESTART + 2) * DOT_BLOCKS) != cudaSuccess ||
         cudaMalloc(&h->gm_dots, sizeof(double) * (GM_MAX_RESTART + 2)) != cudaSuccess ||
         cudaMallocHost(&h->gm_host, sizeof(double) * (GM_MAX_RESTART + 2)) != cudaSuccess)
       return hd_fail(h, HD_ERR_OOM, "GMRES work");
   }
+  if (!f32 && !(h->gm_V && h->gm_m >= m)) {
+    cudaFree(h->gm_V);
+    h->gm_V = nullptr;
+    h->gm_m = 0;
+    if (cudaMalloc(&h->gm_V, sizeof(double) * (size_t)(m + 1) * (size_t)nn) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "GMRES basis");
+    h->gm_m = m;
+  }
+  if (f32) {
+    if (!h->gm_wf && cudaMalloc(&h->gm_wf, sizeof(float) * 3 * nn) != cudaSuccess)
+      return hd_fail(h, HD_ERR_OOM, "GMRES FP32 work");
+    if (!(h->gm_Vf && h->gm_mf >= m)) {
+      cudaFree(h->gm_Vf);
+      h->gm_Vf = nullptr;
+      h->gm_mf = 0;
+      if (cudaMalloc(&h->gm_Vf, sizeof(float) * (size_t)(m + 1) * (size_t)nn) != cudaSuccess)
+        return hd_fail(h, HD_ERR_OOM, "GMRES FP32 basis");
+      h->gm_mf = m;
+    }
+  }
   return HD_OK;
 }
 
-// z = P^-1 v: block-diagonal (prec 0: the MINRES preconditioner) or block upper
-// triangular (prec 1). tmp: n doubles of scratch. The q part of v is copied into
+// z = P^-1 v in T: block-diagonal (prec 0: the MINRES preconditioner) or block upper
+// triangular (prec 1). tmp: n values of scratch. The q part of v is copied into
 // tmp's q part first: the V-cycle replays a CUDA graph cached per (input, output)
 // pointer pair, and the Arnoldi vectors would otherwise each need a new capture.
-static hd_status gmres_prec(hd_op* h, int prec, bool f32, const double* v, double* z, double* tmp) {
+template <typename T>
+static hd_status gmres_prec(hd_op* h, int prec, const T* v, T* z, T* tmp) {
+  constexpr bool F = std::is_same<T, float>::value;
   hd_status st;
-  if ((st = diag_scale(h, v, z)) != HD_OK) return st;  // prec 1 overwrites z_u below
+  if constexpr (F) st = diag_scale_f32(h, v, z);  // prec 1 overwrites z_u below
+  else st = diag_scale(h, v, z);
+  if (st != HD_OK) return st;
   if (h->n_l2 == 0) return HD_OK;
-  double* rq = tmp + h->n_rt;
-  HD_CK(h, cudaMemcpyAsync(rq, v + h->n_rt, sizeof(double) * h->n_l2, cudaMemcpyDeviceToDevice, h->stream));
-  if ((st = inner_vcycle(h, f32, rq, z + h->n_rt)) != HD_OK) return st;  // s = S^-1 r_q
+  T* rq = tmp + h->n_rt;
+  HD_CK(h, cudaMemcpyAsync(rq, v + h->n_rt, sizeof(T) * h->n_l2, cudaMemcpyDeviceToDevice, h->stream));
+  if constexpr (F) {  // s = S^-1 r_q
+    if ((st = vcycle_apply_f32(h, rq, z + h->n_rt)) != HD_OK) return st;
+    if (h->singular && (st = project_mean_f32(h, z + h->n_rt)) != HD_OK) return st;
+  } else {
+    if ((st = inner_vcycle(h, false, rq, z + h->n_rt)) != HD_OK) return st;
+  }
   if (prec == 0) return HD_OK;
-  if ((st = lattice_apply_Bt(h, z + h->n_rt, tmp)) != HD_OK) return st;  // D^T s
+  if constexpr (F) st = lattice_apply_Bt_f32(h, z + h->n_rt, tmp);  // D^T s
+  else st = lattice_apply_Bt(h, z + h->n_rt, tmp);
+  if (st != HD_OK) return st;
   cudaStream_t s = h->stream;
-  k_gm_tri_u<<<nblk(h->n_rt), TPB, 0, s>>>(h->n_rt, h->d_mtinv, v, tmp, z);
-  k_gm_neg<<<nblk(h->n_l2), TPB, 0, s>>>(h->n_l2, z + h->n_rt);
+  const T* mtinv;
+  if constexpr (F) mtinv = h->f_mtinv;
+  else mtinv = h->d_mtinv;
+  k_gm_tri_u<T><<<nblk(h->n_rt), TPB, 0, s>>>(h->n_rt, mtinv, v, tmp, z);
+  k_gm_neg<T><<<nblk(h->n_l2), TPB, 0, s>>>(h->n_l2, z + h->n_rt);
   HD_LAUNCH_CK(h, "gmres triangular preconditioner");
   return HD_OK;
 }
 
 // dots[k] = V_k . w (k < nv) and, with self_dot, dots[nv] = w . w; copied to the host
-static hd_status gm_mdot(hd_op* h, const double* V, int64_t n, int nv, bool self_dot, const double* w,
-                         double* host) {
+template <typename T>
+static hd_status gm_mdot(hd_op* h, const T* V, int64_t n, int nv, bool self_dot, const T* w, double* host) {
   cudaStream_t s = h->stream;
   const int nd = nv + (self_dot ? 1 : 0);
-  k_gm_mdot<<<DOT_BLOCKS, TPB, 0, s>>>(n, V, n, nv, self_dot, w, h->gm_part);
+  k_gm_mdot<T><<<DOT_BLOCKS, TPB, 0, s>>>(n, V, n, nv, self_dot, w, h->gm_part);
   k_gm_final<<<nd, DOT_BLOCKS, 0, s>>>(h->gm_part, h->gm_dots);
   HD_LAUNCH_CK(h, "gmres dots");
   HD_CK(h, cudaMemcpyAsync(host, h->gm_dots, sizeof(double) * nd, cudaMemcpyDeviceToHost, s));
@@ -790,9 +837,10 @@ static hd_status gm_mdot(hd_op* h, const double* V, int64_t n, int nv, bool self
 }
 
 // w -= V h (h = the dots just computed, still on the device); returns ||w||^2
-static hd_status gm_update(hd_op* h, const double* V, int64_t n, int nv, double* w, double* nrm2) {
+template <typename T>
+static hd_status gm_update(hd_op* h, const T* V, int64_t n, int nv, T* w, double* nrm2) {
   cudaStream_t s = h->stream;
-  k_gm_update_norm<<<DOT_BLOCKS, TPB, 0, s>>>(n, V, n, nv, h->gm_dots, w, h->gm_part);
+  k_gm_update_norm<T><<<DOT_BLOCKS, TPB, 0, s>>>(n, V, n, nv, h->gm_dots, w, h->gm_part);
   k_gm_final<<<1, DOT_BLOCKS, 0, s>>>(h->gm_part, h->gm_dots + GM_MAX_RESTART + 1);
   HD_LAUNCH_CK(h, "gmres update");
   HD_CK(h, cudaMemcpyAsync(nrm2, h->gm_dots + GM_MAX_RESTART + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -800,105 +848,131 @@ static hd_status gm_update(hd_op* h, const double* V, int64_t n, int nv, double*
   return HD_OK;
 }
 
-// precision = 1: the Arnoldi steps apply the operator and the V-cycle in FP32 (FP64
-// vectors, FP64 Gram-Schmidt), a cycle ends once its estimate has fallen by
-// inner_rtol, and every restart recomputes the residual with the FP64 operator: the
-// FP64 residual correction of the mixed MINRES solve, with GMRES cycles as the
-// inner solver.
-hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o, hd_solve_info* info) {
+// One GMRES cycle in T on the residual r (FP64, norm rn): at most mc steps, ending
+// at est <= stop; on exit the correction P^-1 V y has been added to x.
+template <typename T>
+static hd_status gmres_cycle(hd_op* h, const hd_gmres_opts* o, const double* r, double rn, int mc, double stop,
+                             T* V, T* w, T* z, T* tmp, double* x, int* steps, double* est_out) {
   const int m = o->restart;
-  hd_status st = ensure_gmres(h, m);
-  if (st != HD_OK) return st;
-  const bool f32 = o->precision == 1;
-  if (f32 && (st = ensure_f32_work(h)) != HD_OK) return st;
   const int64_t n = h->n_rt + h->n_l2;
   cudaStream_t s = h->stream;
-  double *V = h->gm_V, *w = h->gm_w, *z = h->gm_w + n, *tmp = h->gm_w + 2 * n;
+  hd_status st;
+  constexpr bool F = std::is_same<T, float>::value;
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m);
+  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+  double* hostd = h->gm_host;
+  k_gm_scale<double, T><<<nblk(n), TPB, 0, s>>>(n, 1.0 / rn, r, V);
+  HD_LAUNCH_CK(h, "gmres restart");
+  g[0] = rn;
+  int j = 0;
+  double est = rn;
+  while (j < mc) {
+    T* Vj = V + (int64_t)j * n;
+    if ((st = gmres_prec<T>(h, o->prec, Vj, z, tmp)) != HD_OK) return st;
+    if constexpr (F) st = apply_op_f32_internal(h, z, w);
+    else st = apply_op_internal(h, z, w);
+    if (st != HD_OK) return st;
+    // classical Gram-Schmidt: h = V^T w (with ||w||^2 before), w -= V h
+    if ((st = gm_mdot<T>(h, V, n, j + 1, true, w, hostd)) != HD_OK) return st;
+    const double before = hostd[j + 1];
+    for (int i = 0; i <= j; ++i) Hat(i, j) = hostd[i];
+    double nrm2 = 0;
+    if ((st = gm_update<T>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
+    // Orthogonalise once more only on severe cancellation (more than three digits
+    // lost). With the 1/sqrt(2) test of the two-pass method the second pass ran at
+    // every step on the metric workload and changed neither the step count nor the
+    // final residual (52 steps, 9.0e-9 at 64^3) while costing a quarter of the time;
+    // the true residual is recomputed at every restart and at the exit in any case.
+    if (nrm2 < 1e-6 * before) {
+      if ((st = gm_mdot<T>(h, V, n, j + 1, false, w, hostd)) != HD_OK) return st;
+      for (int i = 0; i <= j; ++i) Hat(i, j) += hostd[i];
+      if ((st = gm_update<T>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
+    }
+    const double hn = std::sqrt(std::max(nrm2, 0.0));
+    Hat(j + 1, j) = hn;
+    if (hn > 0.0) {
+      k_gm_scale<T, T><<<nblk(n), TPB, 0, s>>>(n, 1.0 / hn, w, V + (int64_t)(j + 1) * n);
+      HD_LAUNCH_CK(h, "gmres normalise");
+    }
+    for (int i = 0; i < j; ++i) {  // previous rotations on the new column
+      const double a = Hat(i, j), c = Hat(i + 1, j);
+      Hat(i, j) = cs[i] * a + sn[i] * c;
+      Hat(i + 1, j) = -sn[i] * a + cs[i] * c;
+    }
+    const double d = std::hypot(Hat(j, j), Hat(j + 1, j));
+    if (!(d > 0.0) || !std::isfinite(d))
+      return hd_fail(h, HD_ERR_NAN, "GMRES breakdown (zero or non-finite Hessenberg column)");
+    cs[j] = Hat(j, j) / d;
+    sn[j] = Hat(j + 1, j) / d;
+    Hat(j, j) = d;
+    Hat(j + 1, j) = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    ++j;
+    est = std::fabs(g[j]);
+    if (est <= stop || hn == 0.0) break;
+  }
+  // y = H(0:j, 0:j)^-1 g, x += P^-1 V y
+  for (int i = j - 1; i >= 0; --i) {
+    double t = g[i];
+    for (int l = i + 1; l < j; ++l) t -= Hat(i, l) * y[l];
+    y[i] = t / Hat(i, i);
+  }
+  HD_CK(h, cudaMemcpyAsync(h->gm_dots, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
+  k_gm_combine<T><<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, tmp);
+  HD_LAUNCH_CK(h, "gmres combine");
+  if ((st = gmres_prec<T>(h, o->prec, tmp, z, w)) != HD_OK) return st;
+  if constexpr (F) k_gm_add_f<<<nblk(n), TPB, 0, s>>>(n, z, x);
+  else k_add<<<nblk(n), TPB, 0, s>>>(n, z, x);
+  HD_LAUNCH_CK(h, "gmres update x");
+  *steps = j;
+  *est_out = est;
+  return HD_OK;
+}
+
+hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o, hd_solve_info* info) {
+  const int m = o->restart;
+  const bool f32 = o->precision == 1;
+  hd_status st = ensure_gmres(h, m, f32);
+  if (st != HD_OK) return st;
+  if (f32 && (st = setup_f32(h)) != HD_OK) return st;
+  const int64_t n = h->n_rt + h->n_l2;
+  cudaStream_t s = h->stream;
+  double* r = h->gm_w;  // FP64 residual; the rest of gm_w is the FP64 cycle's work
   cudaEvent_t e0, e1;
   HD_CK(h, cudaEventCreate(&e0));
   HD_CK(h, cudaEventCreate(&e1));
   HD_CK(h, cudaEventRecord(e0, s));
   if (!o->use_x0) HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
-  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), y(m);
-  auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
-  double* hostd = h->gm_host;
   int its = 0, cycles = 0;
   double bn = 0, rn = 0, est = 0;
   hd_status status = HD_ERR_NOT_CONVERGED;
   for (;;) {
-    // true residual r = b - AA x into V_0 (then normalised)
-    if ((st = apply_op_internal(h, x, w)) != HD_OK) return st;
-    if ((st = residual_norms(h, b, w, &rn, &bn)) != HD_OK) return st;
+    // true residual r = b - AA x in FP64
+    if ((st = apply_op_internal(h, x, r)) != HD_OK) return st;
+    if ((st = residual_norms(h, b, r, &rn, &bn)) != HD_OK) return st;
     if (bn == 0.0 || rn <= o->rtol * bn) {
       status = HD_OK;
       break;
     }
     if (its >= o->maxit) break;
-    k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, w);  // w = b - AA x
-    k_gm_scale<<<nblk(n), TPB, 0, s>>>(n, 1.0 / rn, w, V);
-    HD_LAUNCH_CK(h, "gmres restart");
+    k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, r);  // r = b - AA x
+    HD_LAUNCH_CK(h, "gmres residual");
     ++cycles;
-    std::fill(H.begin(), H.end(), 0.0);
-    std::fill(g.begin(), g.end(), 0.0);
-    g[0] = rn;
-    int j = 0;
     const int mc = std::min(m, o->maxit - its);
-    while (j < mc) {
-      double* Vj = V + (int64_t)j * n;
-      if ((st = gmres_prec(h, o->prec, f32, Vj, z, tmp)) != HD_OK) return st;
-      if ((st = inner_apply(h, f32, z, w)) != HD_OK) return st;
-      // classical Gram-Schmidt: h = V^T w (with ||w||^2 before), w -= V h
-      if ((st = gm_mdot(h, V, n, j + 1, true, w, hostd)) != HD_OK) return st;
-      const double before = hostd[j + 1];
-      for (int i = 0; i <= j; ++i) Hat(i, j) = hostd[i];
-      double nrm2 = 0;
-      if ((st = gm_update(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
-      // Orthogonalise once more only on severe cancellation (more than three digits
-      // lost). With the 1/sqrt(2) test of the two-pass method the second pass ran at
-      // every step on the metric workload and changed neither the step count nor the
-      // final residual (52 steps, 9.0e-9 at 64^3) while costing a quarter of the time;
-      // the true residual is recomputed at every restart and at the exit in any case.
-      if (nrm2 < 1e-6 * before) {
-        if ((st = gm_mdot(h, V, n, j + 1, false, w, hostd)) != HD_OK) return st;
-        for (int i = 0; i <= j; ++i) Hat(i, j) += hostd[i];
-        if ((st = gm_update(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
-      }
-      const double hn = std::sqrt(std::max(nrm2, 0.0));
-      Hat(j + 1, j) = hn;
-      if (hn > 0.0) {
-        k_gm_scale<<<nblk(n), TPB, 0, s>>>(n, 1.0 / hn, w, V + (int64_t)(j + 1) * n);
-        HD_LAUNCH_CK(h, "gmres normalise");
-      }
-      for (int i = 0; i < j; ++i) {  // previous rotations on the new column
-        const double a = Hat(i, j), c = Hat(i + 1, j);
-        Hat(i, j) = cs[i] * a + sn[i] * c;
-        Hat(i + 1, j) = -sn[i] * a + cs[i] * c;
-      }
-      const double d = std::hypot(Hat(j, j), Hat(j + 1, j));
-      if (!(d > 0.0) || !std::isfinite(d)) return hd_fail(h, HD_ERR_NAN, "GMRES breakdown (zero or non-finite Hessenberg column)");
-      cs[j] = Hat(j, j) / d;
-      sn[j] = Hat(j + 1, j) / d;
-      Hat(j, j) = d;
-      Hat(j + 1, j) = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      ++j;
-      ++its;
-      est = std::fabs(g[j]);
-      if (est <= o->rtol * bn || hn == 0.0 || (f32 && est <= o->inner_rtol * rn)) break;
+    int steps = 0;
+    if (f32) {
+      const double stop = std::max(o->rtol * bn, o->inner_rtol * rn);
+      float* wf = h->gm_wf;
+      st = gmres_cycle<float>(h, o, r, rn, mc, stop, h->gm_Vf, wf, wf + n, wf + 2 * n, x, &steps, &est);
+    } else {
+      // the FP64 cycle's w, z, t: gm_w's second and third vectors and the basis's last one
+      double* V = h->gm_V;
+      st = gmres_cycle<double>(h, o, r, rn, mc, o->rtol * bn, V, h->gm_w + n, h->gm_w + 2 * n,
+                               V + (int64_t)m * n, x, &steps, &est);
     }
-    // y = H(0:j, 0:j)^-1 g, x += P^-1 V y
-    for (int i = j - 1; i >= 0; --i) {
-      double t = g[i];
-      for (int l = i + 1; l < j; ++l) t -= Hat(i, l) * y[l];
-      y[i] = t / Hat(i, i);
-    }
-    HD_CK(h, cudaMemcpyAsync(h->gm_dots, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-    k_gm_combine<<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, tmp);
-    HD_LAUNCH_CK(h, "gmres combine");
-    if ((st = gmres_prec(h, o->prec, f32, tmp, z, w)) != HD_OK) return st;
-    k_add<<<nblk(n), TPB, 0, s>>>(n, z, x);
-    HD_LAUNCH_CK(h, "gmres update x");
+    if (st != HD_OK) return st;
+    its += steps;
   }
   HD_CK(h, cudaEventRecord(e1, s));
   HD_CK(h, cudaEventSynchronize(e1));

@@ -53,11 +53,12 @@ __global__ void k_div(const LatticeDims L, const double* __restrict__ u, double*
 }
 
 // (D^T q)_face = q_low - q_high (a missing cell contributes 0); 0 on essential faces
-__global__ void k_divT(const LatticeDims L, const double* __restrict__ q, double* __restrict__ yu) {
+template <typename T>
+__global__ void k_divT(const LatticeDims L, const T* __restrict__ q, T* __restrict__ yu) {
   int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t n = (int64_t)L.n_xf + L.n_yf + (int64_t)L.X * L.Y * (L.Z + 1);
   if (g >= n) return;
-  double v = 0.0;
+  T v = (T)0;
   if (!face_is_ess(L, g)) {
     if (g < L.n_xf) {
       int I = (int)(g % (L.X + 1));
@@ -453,8 +454,14 @@ hd_status lattice_apply_B(hd_op* h, const double* u, double* yq) {
 }
 
 hd_status lattice_apply_Bt(hd_op* h, const double* q, double* yu) {
-  if (h->n_rt > 0) k_divT<<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->L, q, yu);
+  if (h->n_rt > 0) k_divT<double><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->L, q, yu);
   HD_LAUNCH_CK(h, "k_divT");
+  return HD_OK;
+}
+
+hd_status lattice_apply_Bt_f32(hd_op* h, const float* q, float* yu) {
+  if (h->n_rt > 0) k_divT<float><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->L, q, yu);
+  HD_LAUNCH_CK(h, "k_divT f32");
   return HD_OK;
 }
 
@@ -748,5 +755,18 @@ hd_status project_mean(hd_op* h, double* z) {
   launch_mean<double>(h, h->n_l2, z, h->d_red);
   k_sub_mean<double><<<nblk(h->n_l2), TPB, 0, h->stream>>>(h->n_l2, z, h->d_red);
   HD_LAUNCH_CK(h, "project_mean");
+  return HD_OK;
+}
+
+// FP32 copies of the two above (the FP32 vectors of the mixed-precision GMRES)
+hd_status diag_scale_f32(hd_op* h, const float* r, float* z) {
+  if (h->n_rt > 0) k_diag_scale<float><<<nblk(h->n_rt), TPB, 0, h->stream>>>(h->n_rt, h->f_mtinv, r, z);
+  HD_LAUNCH_CK(h, "diag_scale f32");
+  return HD_OK;
+}
+hd_status project_mean_f32(hd_op* h, float* z) {
+  launch_mean<float>(h, h->n_l2, z, h->d_red);
+  k_sub_mean<float><<<nblk(h->n_l2), TPB, 0, h->stream>>>(h->n_l2, z, h->d_red);
+  HD_LAUNCH_CK(h, "project_mean f32");
   return HD_OK;
 }
