@@ -378,7 +378,10 @@ def run_ours(args, rank, world, dist):
         ess = torch.from_numpy(op.hd_get_ess_dofs()).cuda()
         b[ess] = 0.0
         sols = {}
+        solvers = set(args.solvers.split(","))
         for key, prec, rtol in (("minres_fp64", 0, 1e-8), ("minres_mixed", 1, args.inner_rtol)):
+            if "minres" not in solvers:
+                break
             xs = torch.zeros_like(b)
             st, info = op.hd_minres_solve(b, xs, rtol=rtol, maxit=args.solve_maxit, check_every=16,
                                           precision=prec, outer_rtol=1e-8, max_outer=40)
@@ -386,34 +389,40 @@ def run_ours(args, rank, world, dist):
             out[key] = {"status": int(st), "iterations": info["iterations"], "outer": info["outer"],
                         "ms": info["ms_total"], "true_relres": info["true_relres"], "inner_rtol": rtol,
                         "ms_per_iteration": info["ms_total"] / max(1, info["iterations"])}
-        d = float(torch.linalg.vector_norm(sols["minres_mixed"] - sols["minres_fp64"]) /
-                  torch.linalg.vector_norm(sols["minres_fp64"]))
-        out["minres_mixed"]["rel_diff_vs_fp64_solution"] = d
-        out["minres_mixed"]["speedup_vs_fp64"] = out["minres_fp64"]["ms"] / out["minres_mixed"]["ms"]
-        # GMRES with the block upper-triangular preconditioner (the remark in Sec. 2.3), FP64,
-        # to the same true relative residual
-        xs = torch.zeros_like(b)
-        st, info = op.hd_gmres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
-                                     prec=hd.HD_GMRES_BLOCK_TRI)
-        out["gmres_tri_fp64"] = {
-            "status": int(st), "iterations": info["iterations"], "restart": args.gmres_restart,
-            "cycles": info["cycles"], "ms": info["ms_total"], "true_relres": info["true_relres"],
-            "ms_per_iteration": info["ms_total"] / max(1, info["iterations"]),
-            "rel_diff_vs_minres_fp64_solution": float(torch.linalg.vector_norm(xs - sols["minres_fp64"]) /
-                                                      torch.linalg.vector_norm(sols["minres_fp64"])),
-            "speedup_vs_minres_fp64": out["minres_fp64"]["ms"] / info["ms_total"]}
-        # the same with the operator and the V-cycle in FP32 inside the cycles (FP64 residual at
-        # every restart)
-        xs = torch.zeros_like(b)
-        st, info = op.hd_gmres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
-                                     prec=hd.HD_GMRES_BLOCK_TRI, precision=1, inner_rtol=args.gmres_inner_rtol)
-        out["gmres_tri_mixed"] = {
-            "status": int(st), "iterations": info["iterations"], "restart": args.gmres_restart,
-            "inner_rtol": args.gmres_inner_rtol, "cycles": info["cycles"], "ms": info["ms_total"],
-            "true_relres": info["true_relres"], "ms_per_iteration": info["ms_total"] / max(1, info["iterations"]),
-            "rel_diff_vs_minres_fp64_solution": float(torch.linalg.vector_norm(xs - sols["minres_fp64"]) /
-                                                      torch.linalg.vector_norm(sols["minres_fp64"])),
-            "speedup_vs_minres_fp64": out["minres_fp64"]["ms"] / info["ms_total"]}
+        if "minres" in solvers:
+            d = float(torch.linalg.vector_norm(sols["minres_mixed"] - sols["minres_fp64"]) /
+                      torch.linalg.vector_norm(sols["minres_fp64"]))
+            out["minres_mixed"]["rel_diff_vs_fp64_solution"] = d
+            out["minres_mixed"]["speedup_vs_fp64"] = out["minres_fp64"]["ms"] / out["minres_mixed"]["ms"]
+        def vs_minres(xs, ms):
+            if "minres_fp64" not in sols:
+                return {}
+            ref = sols["minres_fp64"]
+            return {"rel_diff_vs_minres_fp64_solution": float(torch.linalg.vector_norm(xs - ref) /
+                                                              torch.linalg.vector_norm(ref)),
+                    "speedup_vs_minres_fp64": out["minres_fp64"]["ms"] / ms}
+
+        if "gmres" in solvers:
+            # GMRES with the block upper-triangular preconditioner (the remark in Sec. 2.3), FP64,
+            # to the same true relative residual
+            xs = torch.zeros_like(b)
+            st, info = op.hd_gmres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
+                                         prec=hd.HD_GMRES_BLOCK_TRI)
+            out["gmres_tri_fp64"] = {
+                "status": int(st), "iterations": info["iterations"], "restart": args.gmres_restart,
+                "cycles": info["cycles"], "ms": info["ms_total"], "true_relres": info["true_relres"],
+                "ms_per_iteration": info["ms_total"] / max(1, info["iterations"]),
+                **vs_minres(xs, info["ms_total"])}
+            # the same with every cycle in FP32 (basis, Gram-Schmidt, operator, V-cycle) and the FP64
+            # residual at every restart
+            xs = torch.zeros_like(b)
+            st, info = op.hd_gmres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
+                                         prec=hd.HD_GMRES_BLOCK_TRI, precision=1, inner_rtol=args.gmres_inner_rtol)
+            out["gmres_tri_mixed"] = {
+                "status": int(st), "iterations": info["iterations"], "restart": args.gmres_restart,
+                "inner_rtol": args.gmres_inner_rtol, "cycles": info["cycles"], "ms": info["ms_total"],
+                "true_relres": info["true_relres"], "ms_per_iteration": info["ms_total"] / max(1, info["iterations"]),
+                **vs_minres(xs, info["ms_total"])}
     if rank == 0 and world == 1 and not args.no_cpu:
         gd, el, reps, ndof = oracle_sample(seconds=8.0)
         out["cpu_baseline"] = {"value": gd, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
@@ -607,6 +616,8 @@ def main():
     ap.add_argument("--w-levels", type=int, default=0, help="W repetition on the first levels only (0: all)")
     ap.add_argument("--learned", action="store_true", help="run the learned-preconditioner study instead")
     ap.add_argument("--gmres-restart", type=int, default=32, help="GMRES restart length (block-triangular solve)")
+    ap.add_argument("--solvers", default="minres,gmres",
+                    help="comma-separated solves of the timed line: minres (FP64 and mixed), gmres (FP64 and mixed)")
     ap.add_argument("--gmres-inner-rtol", type=float, default=1e-3,
                     help="per-cycle reduction of the mixed-precision GMRES before its FP64 residual")
     ap.add_argument("--winv-study", action="store_true",

@@ -656,9 +656,45 @@ namespace {
 constexpr int GM_MAX_RESTART = 128;
 constexpr int GM_CH = 8;  // basis vectors per sweep of the multi-dot
 
+// One sweep of the multi-dot over G vectors fixed at compile time: vector c is
+// V_{k0 + c}, or w itself at index nv (the self-dot). Two elements per iteration.
+template <typename T, int G>
+__device__ __forceinline__ void gm_mdot_group(int64_t lo, int64_t hi, const T* __restrict__ V, int64_t ldv, int nv,
+                                              int k0, const T* __restrict__ w, double* __restrict__ partial,
+                                              double* sh) {
+  const T* vp[G];
+#pragma unroll
+  for (int c = 0; c < G; ++c) vp[c] = (k0 + c < nv) ? V + (int64_t)(k0 + c) * ldv : w;
+  T acc[G];
+#pragma unroll
+  for (int c = 0; c < G; ++c) acc[c] = (T)0;
+  int64_t i = lo + threadIdx.x;
+  for (; i + blockDim.x < hi; i += 2 * blockDim.x) {
+    const T w0 = w[i], w1 = w[i + blockDim.x];
+    T a0[G], a1[G];
+#pragma unroll
+    for (int c = 0; c < G; ++c) {
+      a0[c] = vp[c][i];
+      a1[c] = vp[c][i + blockDim.x];
+    }
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c] = fma(a1[c], w1, fma(a0[c], w0, acc[c]));
+  }
+  if (i < hi) {
+    const T w0 = w[i];
+#pragma unroll
+    for (int c = 0; c < G; ++c) acc[c] = fma(vp[c][i], w0, acc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < G; ++c) {
+    const double s = block_sum((double)acc[c], sh);
+    if (threadIdx.x == 0) partial[(k0 + c) * DOT_BLOCKS + blockIdx.x] = s;
+  }
+}
+
 // partial[k * DOT_BLOCKS + b] = block b's chunk of V_k . w for k < nv, and with
 // self_dot also w . w at k = nv (V_k = V + k ldv). Per-thread sums in T, the
-// block sums in FP64.
+// block sums in FP64. Sweeps of at most GM_CH vectors, each sized at compile time.
 template <typename T>
 __global__ void k_gm_mdot(int64_t n, const T* __restrict__ V, int64_t ldv, int nv, bool self_dot,
                           const T* __restrict__ w, double* __restrict__ partial) {
@@ -667,23 +703,15 @@ __global__ void k_gm_mdot(int64_t n, const T* __restrict__ V, int64_t ldv, int n
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
   const int ntot = nv + (self_dot ? 1 : 0);
   for (int k0 = 0; k0 < ntot; k0 += GM_CH) {
-    T acc[GM_CH];
-#pragma unroll
-    for (int c = 0; c < GM_CH; ++c) acc[c] = (T)0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const T wi = w[i];
-#pragma unroll
-      for (int c = 0; c < GM_CH; ++c) {
-        const int k = k0 + c;
-        if (k < nv) acc[c] = fma(V[k * ldv + i], wi, acc[c]);
-        else if (k == nv && self_dot) acc[c] = fma(wi, wi, acc[c]);
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < GM_CH; ++c) {
-      if (k0 + c >= ntot) break;  // uniform over the block
-      const double s = block_sum((double)acc[c], sh);
-      if (threadIdx.x == 0) partial[(k0 + c) * DOT_BLOCKS + blockIdx.x] = s;
+    switch (min(GM_CH, ntot - k0)) {  // uniform over the grid
+      case 1: gm_mdot_group<T, 1>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 2: gm_mdot_group<T, 2>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 3: gm_mdot_group<T, 3>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 4: gm_mdot_group<T, 4>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 5: gm_mdot_group<T, 5>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 6: gm_mdot_group<T, 6>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      case 7: gm_mdot_group<T, 7>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
+      default: gm_mdot_group<T, GM_CH>(lo, hi, V, ldv, nv, k0, w, partial, sh); break;
     }
   }
 }

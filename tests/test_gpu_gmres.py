@@ -119,3 +119,44 @@ def test_mixed_precision_gmres_reaches_the_fp64_solution(name):
     assert np.linalg.norm(b - prob.apply_op(xs)) <= 1e-8 * np.linalg.norm(b)
     assert np.linalg.norm(xs - xr) <= 1e-6 * np.linalg.norm(xr)
     op.close()
+
+
+def test_gmres_edge_cases():
+    """b = 0 gives x = 0 in no steps; a starting guess that already meets the
+    tolerance returns at once; restart = 1 (minimal-residual steps from the true
+    residual each time) still converges, as the oracle's GMRES(1) does."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.gmres import gmres
+    d, prob, bp, op, b = _setup("darcy_gamma", True)
+    bt = torch.from_numpy(b).cuda()
+    z = torch.zeros_like(bt)
+    x = torch.full_like(bt, 3.0)
+    st, info = op.hd_gmres_solve(z, x, rtol=1e-8, maxit=100, restart=16, prec=hd.HD_GMRES_BLOCK_TRI)
+    assert st == 0 and info["iterations"] == 0 and float(x.abs().max()) == 0.0
+    x = torch.zeros_like(bt)
+    st, info = op.hd_gmres_solve(bt, x, rtol=1e-10, maxit=500, restart=32, prec=hd.HD_GMRES_BLOCK_TRI)
+    assert st == 0
+    st, info = op.hd_gmres_solve(bt, x, rtol=1e-8, maxit=500, restart=32, prec=hd.HD_GMRES_BLOCK_TRI, use_x0=True)
+    assert st == 0 and info["iterations"] == 0 and info["true_relres"] <= 1e-8
+    xr, ir = gmres(prob.apply_op, bp.apply, b, rtol=1e-6, maxit=5000, restart=1)
+    x = torch.zeros_like(bt)
+    st, info = op.hd_gmres_solve(bt, x, rtol=1e-6, maxit=5000, restart=1, prec=hd.HD_GMRES_BLOCK_TRI)
+    assert ir["converged"] and st == 0 and info["cycles"] == info["iterations"]
+    assert abs(info["iterations"] - ir["iterations"]) <= max(2, ir["iterations"] // 50), (info, ir["iterations"])
+    op.close()
+
+
+def test_mixed_gmres_block_diagonal():
+    """precision = 1 with the block-diagonal preconditioner also reaches the true 1e-8."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    d, prob, bp, op, b = _setup("darcy_k3", False)
+    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
+    st, info = op.hd_gmres_solve(torch.from_numpy(b).cuda(), x, rtol=1e-8, maxit=3000, restart=32,
+                                 prec=hd.HD_GMRES_BLOCK_DIAG, precision=1, inner_rtol=1e-3)
+    assert st == 0 and info["true_relres"] <= 1e-8
+    assert np.linalg.norm(b - prob.apply_op(x.cpu().numpy())) <= 1e-8 * np.linalg.norm(b)
+    op.close()

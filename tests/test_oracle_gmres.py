@@ -87,3 +87,17 @@ def test_block_triangular_gmres_needs_fewer_iterations_than_minres():
     x, ig = gmres(prob.apply_op, BlockTriPrec(prob, **kw).apply, b, rtol=1e-8, maxit=2000, restart=50)
     assert ig["converged"] and ig["true_relres"] <= 1e-8
     assert ig["iterations"] < 0.8 * im["iterations"], (ig["iterations"], im["iterations"])
+
+
+def test_gmres_zero_rhs_and_restart_one():
+    """b = 0 returns x = 0 with no steps; GMRES(1) on an SPD system is the
+    minimal-residual iteration and converges (slowly) to the dense solution."""
+    rng = np.random.Generator(np.random.PCG64(34))
+    Q, _ = np.linalg.qr(rng.standard_normal((12, 12)))
+    A = Q @ np.diag(np.linspace(1.0, 4.0, 12)) @ Q.T
+    x, info = gmres(lambda v: A @ v, lambda r: r, np.zeros(12), rtol=1e-8, maxit=10)
+    assert info["iterations"] == 0 and np.all(x == 0)
+    b = rng.standard_normal(12)
+    x, info = gmres(lambda v: A @ v, lambda r: r, b, rtol=1e-10, maxit=500, restart=1)
+    assert info["converged"] and info["cycles"] == info["iterations"]
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-8, atol=1e-9)
