@@ -207,6 +207,36 @@ def native_apply(args, nx, vx, vy, vz, alpha, beta, stream):
     return r
 
 
+def f32_apply(args, op, nx):
+    """The FP32 operator of the mixed-precision solves (FP32 element kernel, FP32 vectors),
+    on the main line's handle: GDOF/s and its HBM roofline. Algorithmic bytes per apply:
+    4 (2N + E (6 q^3 + k^6 + 1)) (FP32 vectors in and out, FP32 G, W_e^-1 and c_e)."""
+    import torch
+    n = op.n
+    x = torch.from_numpy(synth.uniform(n, seed=SEED)).float().cuda()
+    y = torch.empty_like(x)
+    for _ in range(3):
+        op.hd_apply_op_f32(x, y)
+    steps = max(5, args.steps // 10)
+    op.hd_profile(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        op.hd_apply_op_f32(x, y)
+    e1.record()
+    torch.cuda.synchronize()
+    op.hd_profile(0)
+    launches, kms = op.hd_profile_read()
+    kms = kms / max(1, launches)
+    E = nx ** 3
+    alg = 4 * (2 * n + E * (6 * Q ** 3 + K ** 6 + 1))
+    peak = _measured_hbm_gbs()
+    return {"value": n / (e0.elapsed_time(e1) / steps * 1e-3) / 1e9, "unit": "GDOF/s",
+            "ms_per_step": e0.elapsed_time(e1) / steps, "steps": steps, "kernel_ms": kms,
+            "algorithmic_bytes_per_launch": alg, "hbm_frac_of_measured": alg / (kms * 1e-3) / 1e9 / peak}
+
+
 def affine_apply(args, stream):
     """Metric 1 on the Cartesian geometry (M64-affine): the unperturbed mesh of the
     same size and coefficients, q = k + 1, the same element kernel and precision as
@@ -367,6 +397,7 @@ def run_ours(args, rank, world, dist):
                                      {0: ", plain aggregation", 1: ", smoothed aggregation on the first level",
                                       2: ", smoothed aggregation on the first two levels"}[args.smooth_levels]},
            "roofline": roof, "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    out["apply_fp32_inner"] = f32_apply(args, op, nx)
     if args.fp64_emulation and not args.no_native:
         out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
     if not args.no_affine:
