@@ -967,9 +967,16 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
   const int64_t n = h->n_rt + h->n_l2;
   cudaStream_t s = h->stream;
   double* r = h->gm_w;  // FP64 residual; the rest of gm_w is the FP64 cycle's work
-  cudaEvent_t e0, e1;
-  HD_CK(h, cudaEventCreate(&e0));
-  HD_CK(h, cudaEventCreate(&e1));
+  struct Events {  // destroyed on every return path
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Events() {
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+    }
+  } ev;
+  HD_CK(h, cudaEventCreate(&ev.a));
+  HD_CK(h, cudaEventCreate(&ev.b));
+  cudaEvent_t e0 = ev.a, e1 = ev.b;
   HD_CK(h, cudaEventRecord(e0, s));
   if (!o->use_x0) HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
   int its = 0, cycles = 0;
@@ -1006,8 +1013,6 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
   HD_CK(h, cudaEventSynchronize(e1));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   if (info) {
     info->iterations = its;
     info->outer = cycles;
