@@ -602,8 +602,14 @@ def run_learned(args):
         b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 9)).cuda()
         x = torch.zeros_like(b)
         st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=5000, check_every=16)
-        return {"status": int(st), "iterations": info["iterations"], "ms": info["ms_total"],
-                "fallback": info["fallback"], "true_relres": info["true_relres"]}
+        r = {"status": int(st), "iterations": info["iterations"], "ms": info["ms_total"],
+             "fallback": info["fallback"], "true_relres": info["true_relres"]}
+        # GMRES with the block-triangular preconditioner, the same Schur part, to a true 1e-8
+        x = torch.zeros_like(b)
+        st, info = op.hd_gmres_solve(b, x, rtol=1e-8, maxit=5000, restart=32, prec=hd.HD_GMRES_BLOCK_TRI)
+        r["gmres_tri"] = {"status": int(st), "iterations": info["iterations"], "ms": info["ms_total"],
+                          "true_relres": info["true_relres"]}
+        return r
 
     out = {"metric": "learned Schur preconditioner vs plain hierarchy: FP64 MINRES to rtol 1e-8",
            "config": {"workload": "Darcy, gamma=0, k=3, q=5, perturbed +-15% h, eps=exp(2Z), natural BC; "

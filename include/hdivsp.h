@@ -275,7 +275,8 @@ typedef struct {
  * steps, info->outer = restart cycles, info->eta_ratio = the last estimate / ||b||,
  * info->true_relres the FP64 true residual at exit. HD_ERR_NOT_CONVERGED when maxit
  * runs out, HD_ERR_NAN on a breakdown, HD_ERR_OOM when the basis does not fit,
- * HD_ERR_NOT_IMPLEMENTED with the learned Schur preconditioner enabled. */
+ * HD_ERR_NOT_IMPLEMENTED for precision 1 with the learned Schur preconditioner enabled (it
+ * replaces S^-1 in precision 0). */
 hd_status hd_gmres_solve(hd_handle h, const double* b, double* x, const hd_gmres_opts* opts,
                          hd_solve_info* info);
 

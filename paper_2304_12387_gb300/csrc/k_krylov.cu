@@ -1034,6 +1034,7 @@ extern "C" hd_status hd_gmres_solve(hd_handle h, const double* b, double* x, con
     return hd_fail(h, HD_ERR_INVALID_ARG,
                    "hd_gmres_solve: restart 1..128, maxit >= 1, rtol >= 0, prec 0 or 1, precision 0 or 1 "
                    "(1: 0 < inner_rtol < 1)");
-  if (h->schur_mode != 0) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "hd_gmres_solve: V-cycle Schur preconditioner only");
+  if (h->schur_mode != 0 && o->precision != 0)  // the FP32 cycles have no learned Schur preconditioner
+    return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "hd_gmres_solve: the learned Schur preconditioner is FP64 only");
   return gmres_run(h, b, x, o, info);
 }
