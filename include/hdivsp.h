@@ -261,7 +261,8 @@ typedef struct {
                        vectors of n_rt + n_l2 doubles (allocated on the first call and kept) */
   int32_t prec;     /* HD_GMRES_BLOCK_DIAG or HD_GMRES_BLOCK_TRI */
   int32_t use_x0;   /* 1: start from x, else from zero */
-  int32_t precision;/* 0: FP64 throughout; 1: every cycle in FP32 (basis, Gram-Schmidt,
+  int32_t precision;/* 0: FP64 operator and V-cycle, the basis and Gram-Schmidt in double-float
+                       (FP32 pairs, ~48 bits); 1: every cycle in FP32 (basis, Gram-Schmidt,
                        operator, V-cycle), every restart recomputing the residual with the FP64
                        operator and adding the cycle's correction to the FP64 solution (a
                        residual correction with GMRES cycles as the inner solver) */

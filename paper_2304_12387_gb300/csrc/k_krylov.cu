@@ -12,6 +12,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "hd_internal.h"
 
 namespace {
@@ -645,8 +646,8 @@ extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, doubl
 // host (one small copy per step). All reductions run over fixed blocks in a fixed
 // order, so a solve is deterministic.
 //
-// FP64 (precision 0): basis, operator and V-cycle in FP64 (the operator in the
-// handle's element arithmetic). Mixed (precision 1): the cycles run entirely in FP32
+// FP64 (precision 0): operator and V-cycle in FP64 (the operator in the handle's
+// element arithmetic), the basis and Gram-Schmidt in double-float. Mixed (precision 1): the cycles run entirely in FP32
 // (basis, Gram-Schmidt, operator, V-cycle), each ends once its estimate has fallen
 // by inner_rtol, and every restart recomputes the residual with the FP64 operator
 // and adds the cycle's correction to the FP64 solution: iterative refinement with
@@ -655,6 +656,19 @@ extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, doubl
 namespace {
 constexpr int GM_MAX_RESTART = 128;
 constexpr int GM_CH = 8;  // basis vectors per sweep of the multi-dot
+
+// conversions of the basis types (double, float, double-float pairs) to and from FP64
+__device__ __forceinline__ double to_dbl(double v) { return v; }
+__device__ __forceinline__ double to_dbl(float v) { return (double)v; }
+__device__ __forceinline__ double to_dbl(dfloat v) { return df_to_double(v); }
+template <typename T>
+__device__ __forceinline__ T from_dbl(double v);
+template <>
+__device__ __forceinline__ double from_dbl<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ float from_dbl<float>(double v) { return (float)v; }
+template <>
+__device__ __forceinline__ dfloat from_dbl<dfloat>(double v) { return df_from_double(v); }
 
 // One sweep of the multi-dot over G vectors fixed at compile time: vector c is
 // V_{k0 + c}, or w itself at index nv (the self-dot). Two elements per iteration.
@@ -687,7 +701,7 @@ __device__ __forceinline__ void gm_mdot_group(int64_t lo, int64_t hi, const T* _
   }
 #pragma unroll
   for (int c = 0; c < G; ++c) {
-    const double s = block_sum((double)acc[c], sh);
+    const double s = block_sum(to_dbl(acc[c]), sh);
     if (threadIdx.x == 0) partial[(k0 + c) * DOT_BLOCKS + blockIdx.x] = s;
   }
 }
@@ -729,7 +743,7 @@ __global__ void k_gm_update_norm(int64_t n, const T* __restrict__ V, int64_t ldv
                                  const double* __restrict__ hcoef, T* __restrict__ w, double* __restrict__ partial) {
   __shared__ double sh[32];
   __shared__ T hs[GM_MAX_RESTART + 1];
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)hcoef[k];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = from_dbl<T>(hcoef[k]);
   __syncthreads();
   const int64_t chunk = (n + DOT_BLOCKS - 1) / DOT_BLOCKS;
   const int64_t lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
@@ -740,7 +754,7 @@ __global__ void k_gm_update_norm(int64_t n, const T* __restrict__ V, int64_t ldv
     w[i] = s;
     acc = fma(s, s, acc);
   }
-  const double b = block_sum((double)acc, sh);
+  const double b = block_sum(to_dbl(acc), sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = b;
 }
 
@@ -749,7 +763,7 @@ template <typename T>
 __global__ void k_gm_combine(int64_t n, const T* __restrict__ V, int64_t ldv, int nv, const double* __restrict__ y,
                              T* __restrict__ u) {
   __shared__ T ys[GM_MAX_RESTART];
-  for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = (T)y[k];
+  for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = from_dbl<T>(y[k]);
   __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -762,7 +776,7 @@ __global__ void k_gm_combine(int64_t n, const T* __restrict__ V, int64_t ldv, in
 template <typename S, typename T>
 __global__ void k_gm_scale(int64_t n, double a, const S* __restrict__ x, T* __restrict__ y) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) y[i] = (T)(a * (double)x[i]);
+  if (i < n) y[i] = from_dbl<T>(a * to_dbl(x[i]));
 }
 
 // triangular preconditioner, RT part: z_u = mtinv (r_u + D^T s) with s = S^-1 r_q
@@ -876,50 +890,64 @@ static hd_status gm_update(hd_op* h, const T* V, int64_t n, int nv, T* w, double
   return HD_OK;
 }
 
-// One GMRES cycle in T on the residual r (FP64, norm rn): at most mc steps, ending
-// at est <= stop; on exit the correction P^-1 V y has been added to x.
-template <typename T>
+// One GMRES cycle on the residual r (FP64, norm rn): at most mc steps, ending at
+// est <= stop; on exit the correction P^-1 V y has been added to x. TB: the basis
+// and Gram-Schmidt type; TV: the type of the operator and preconditioner vectors.
+// With TB != TV (a double-float basis for the FP64 solve) V_j is converted to TV in
+// vconv before the preconditioner and the operator's result back to TB in w.
+template <typename TB, typename TV>
 static hd_status gmres_cycle(hd_op* h, const hd_gmres_opts* o, const double* r, double rn, int mc, double stop,
-                             T* V, T* w, T* z, T* tmp, double* x, int* steps, double* est_out) {
+                             TB* V, TB* w, TV* z, TV* tmp, TV* vconv, double* x, int* steps, double* est_out) {
   const int m = o->restart;
   const int64_t n = h->n_rt + h->n_l2;
   cudaStream_t s = h->stream;
   hd_status st;
-  constexpr bool F = std::is_same<T, float>::value;
+  constexpr bool F = std::is_same<TV, float>::value;
+  constexpr bool SAME = std::is_same<TB, TV>::value;
   std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m);
   auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
   double* hostd = h->gm_host;
-  k_gm_scale<double, T><<<nblk(n), TPB, 0, s>>>(n, 1.0 / rn, r, V);
+  auto apply = [&](const TV* in, TV* out) -> hd_status {
+    if constexpr (F) return apply_op_f32_internal(h, in, out);
+    else return apply_op_internal(h, in, out);
+  };
+  k_gm_scale<double, TB><<<nblk(n), TPB, 0, s>>>(n, 1.0 / rn, r, V);
   HD_LAUNCH_CK(h, "gmres restart");
   g[0] = rn;
   int j = 0;
   double est = rn;
   while (j < mc) {
-    T* Vj = V + (int64_t)j * n;
-    if ((st = gmres_prec<T>(h, o->prec, Vj, z, tmp)) != HD_OK) return st;
-    if constexpr (F) st = apply_op_f32_internal(h, z, w);
-    else st = apply_op_internal(h, z, w);
-    if (st != HD_OK) return st;
+    TB* Vj = V + (int64_t)j * n;
+    if constexpr (SAME) {
+      if ((st = gmres_prec<TV>(h, o->prec, Vj, z, tmp)) != HD_OK) return st;
+      if ((st = apply(z, w)) != HD_OK) return st;
+    } else {
+      k_gm_scale<TB, TV><<<nblk(n), TPB, 0, s>>>(n, 1.0, Vj, vconv);
+      if ((st = gmres_prec<TV>(h, o->prec, vconv, z, tmp)) != HD_OK) return st;
+      if ((st = apply(z, vconv)) != HD_OK) return st;
+      k_gm_scale<TV, TB><<<nblk(n), TPB, 0, s>>>(n, 1.0, vconv, w);
+      HD_LAUNCH_CK(h, "gmres basis conversion");
+    }
     // classical Gram-Schmidt: h = V^T w (with ||w||^2 before), w -= V h
-    if ((st = gm_mdot<T>(h, V, n, j + 1, true, w, hostd)) != HD_OK) return st;
+    if ((st = gm_mdot<TB>(h, V, n, j + 1, true, w, hostd)) != HD_OK) return st;
     const double before = hostd[j + 1];
     for (int i = 0; i <= j; ++i) Hat(i, j) = hostd[i];
     double nrm2 = 0;
-    if ((st = gm_update<T>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
+    if ((st = gm_update<TB>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
     // Orthogonalise once more only on severe cancellation (more than three digits
     // lost). With the 1/sqrt(2) test of the two-pass method the second pass ran at
     // every step on the metric workload and changed neither the step count nor the
     // final residual (52 steps, 9.0e-9 at 64^3) while costing a quarter of the time;
     // the true residual is recomputed at every restart and at the exit in any case.
     if (nrm2 < 1e-6 * before) {
-      if ((st = gm_mdot<T>(h, V, n, j + 1, false, w, hostd)) != HD_OK) return st;
+      if ((st = gm_mdot<TB>(h, V, n, j + 1, false, w, hostd)) != HD_OK) return st;
       for (int i = 0; i <= j; ++i) Hat(i, j) += hostd[i];
-      if ((st = gm_update<T>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
+      if ((st = gm_update<TB>(h, V, n, j + 1, w, &nrm2)) != HD_OK) return st;
     }
     const double hn = std::sqrt(std::max(nrm2, 0.0));
     Hat(j + 1, j) = hn;
     if (hn > 0.0) {
-      k_gm_scale<T, T><<<nblk(n), TPB, 0, s>>>(n, 1.0 / hn, w, V + (int64_t)(j + 1) * n);
+      k_gm_scale<TB, TB><<<nblk(n), TPB, 0, s>>>(n, 1.0 / hn, w, V + (int64_t)(j + 1) * n);
       HD_LAUNCH_CK(h, "gmres normalise");
     }
     for (int i = 0; i < j; ++i) {  // previous rotations on the new column
@@ -947,9 +975,18 @@ static hd_status gmres_cycle(hd_op* h, const hd_gmres_opts* o, const double* r, 
     y[i] = t / Hat(i, i);
   }
   HD_CK(h, cudaMemcpyAsync(h->gm_dots, y.data(), sizeof(double) * j, cudaMemcpyHostToDevice, s));
-  k_gm_combine<T><<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, tmp);
+  TV* u;
+  if constexpr (SAME) {
+    k_gm_combine<TB><<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, tmp);
+    u = tmp;
+    if ((st = gmres_prec<TV>(h, o->prec, u, z, w)) != HD_OK) return st;
+  } else {
+    k_gm_combine<TB><<<nblk(n), TPB, 0, s>>>(n, V, n, j, h->gm_dots, w);
+    k_gm_scale<TB, TV><<<nblk(n), TPB, 0, s>>>(n, 1.0, w, vconv);
+    u = vconv;
+    if ((st = gmres_prec<TV>(h, o->prec, u, z, tmp)) != HD_OK) return st;
+  }
   HD_LAUNCH_CK(h, "gmres combine");
-  if ((st = gmres_prec<T>(h, o->prec, tmp, z, w)) != HD_OK) return st;
   if constexpr (F) k_gm_add_f<<<nblk(n), TPB, 0, s>>>(n, z, x);
   else k_add<<<nblk(n), TPB, 0, s>>>(n, z, x);
   HD_LAUNCH_CK(h, "gmres update x");
@@ -999,12 +1036,18 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
     if (f32) {
       const double stop = std::max(o->rtol * bn, o->inner_rtol * rn);
       float* wf = h->gm_wf;
-      st = gmres_cycle<float>(h, o, r, rn, mc, stop, h->gm_Vf, wf, wf + n, wf + 2 * n, x, &steps, &est);
+      st = gmres_cycle<float, float>(h, o, r, rn, mc, stop, h->gm_Vf, wf, wf + n, wf + 2 * n, nullptr, x, &steps,
+                                     &est);
     } else {
-      // the FP64 cycle's w, z, t: gm_w's second and third vectors and the basis's last one
-      double* V = h->gm_V;
-      st = gmres_cycle<double>(h, o, r, rn, mc, o->rtol * bn, V, h->gm_w + n, h->gm_w + 2 * n,
-                               V + (int64_t)m * n, x, &steps, &est);
+      // Double-float basis and Gram-Schmidt (FP32 pairs, ~48 bits) in the basis memory
+      // (8 bytes a value either way): on an FP64 basis these passes are bound by the FP64
+      // pipe (one FMA per value read); with the two conversions per step the solve is
+      // 2.6 % faster at 64^3 (832 against 854 ms, the same 52 steps). The basis's last
+      // vector is the cycle's w (written in place when it becomes V_m); the FP64
+      // residual buffer converts V_j and holds the operator's result.
+      dfloat* V = reinterpret_cast<dfloat*>(h->gm_V);
+      st = gmres_cycle<dfloat, double>(h, o, r, rn, mc, o->rtol * bn, V, V + (int64_t)m * n, h->gm_w + n,
+                                       h->gm_w + 2 * n, r, x, &steps, &est);
     }
     if (st != HD_OK) return st;
     its += steps;

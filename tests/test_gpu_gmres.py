@@ -160,3 +160,25 @@ def test_mixed_gmres_block_diagonal():
     assert st == 0 and info["true_relres"] <= 1e-8
     assert np.linalg.norm(b - prob.apply_op(x.cpu().numpy())) <= 1e-8 * np.linalg.norm(b)
     op.close()
+
+
+def test_gmres_with_the_learned_schur_preconditioner():
+    """The learned Schur preconditioner replaces S^-1 inside FP64 block-triangular GMRES
+    (no symmetry needed): the true 1e-8 is reached; the FP32 cycles refuse it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    d = inputs("darcy_k3")
+    prob = oracle_problem(d)
+    op = gpu_operator(d, coarse_max=8, cycle=2)
+    op.hd_learned_init(seed=5)
+    op.hd_set_schur_prec(1)
+    b = np.random.Generator(np.random.PCG64(43)).uniform(-1, 1, prob.n)
+    bt = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bt)
+    st, info = op.hd_gmres_solve(bt, x, rtol=1e-8, maxit=3000, restart=32, prec=hd.HD_GMRES_BLOCK_TRI)
+    assert st == 0 and info["true_relres"] <= 1e-8, info
+    assert np.linalg.norm(b - prob.apply_op(x.cpu().numpy())) <= 1e-8 * np.linalg.norm(b)
+    st, _ = op.hd_gmres_solve(bt, x, rtol=1e-8, maxit=100, restart=32, prec=hd.HD_GMRES_BLOCK_TRI, precision=1)
+    assert st == hd.HD_ERR_NOT_IMPLEMENTED
+    op.close()
