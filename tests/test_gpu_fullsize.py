@@ -106,3 +106,30 @@ def test_fullsize_m64_smoothed_hierarchy():
         op.close()
     assert its[1] < 0.8 * its[0], its
     assert its[2] < 0.9 * its[1], its
+
+
+def test_fullsize_m64_gmres():
+    """The metric workload with block-triangular GMRES (FP64 with the double-float basis,
+    and mixed precision): both reach a true relative residual of 1e-8, their solutions
+    agree with FP64 MINRES's, and they need fewer than half its steps."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    d = fullsize("m64")
+    op = hd.Operator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                     kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"], affine=d["affine"], fp64_emulation=1,
+                     cycle=2, smooth_levels=2, stream=torch.cuda.current_stream())
+    rhs = torch.from_numpy(np.random.Generator(np.random.PCG64(81)).uniform(-1, 1, op.n)).cuda()
+    rhs[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
+    xm = torch.zeros_like(rhs)
+    st, mi = op.hd_minres_solve(rhs, xm, rtol=1e-8, maxit=5000, check_every=16, outer_rtol=1e-8, max_outer=10)
+    assert st == 0
+    for prec in (0, 1):
+        x = torch.zeros_like(rhs)
+        st, gi = op.hd_gmres_solve(rhs, x, rtol=1e-8, maxit=2000, restart=32, prec=hd.HD_GMRES_BLOCK_TRI,
+                                   precision=prec, inner_rtol=1e-3)
+        assert st == 0 and gi["true_relres"] <= 1e-8, gi
+        assert 2 * gi["iterations"] < mi["iterations"], (gi, mi)
+        rel = float(torch.linalg.vector_norm(x - xm) / torch.linalg.vector_norm(xm))
+        assert rel <= 1e-6, rel
+    op.close()
