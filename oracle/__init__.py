@@ -25,6 +25,9 @@ Modules
   minres    preconditioned MINRES (Paige & Saunders 1975) in FP64.
   gmres     restarted right-preconditioned GMRES (Saad & Schultz 1986) for the
             block-triangular preconditioner of the remark in Sec. 2.3.
+  conditioning  condition numbers on single elements: the diagonally scaled L2 mass
+            in three bases (Sec. 2.5) and the transformed versus the untransformed
+            Schur complement.
   sampled   single rows of the block operator at any mesh size (element-local).
   conv      reference 3D convolution forward/backward for the learned Schur
             preconditioner.
