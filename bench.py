@@ -541,8 +541,9 @@ def run_iterations(args):
 def run_winv_study(args):
     """W^-1 alternatives (Sec. 3.1 and its mass-inverse table): on perturbed meshes of about
     1.7 M L2 DOFs for k = 2..5, the setup of the W^-1 data and 100 applications of W^-1
-    (hd_apply_C, FP64) by the stored explicit inverse (batched gemv), the fused local CG in
-    the Gauss-Legendre nodal basis and the same CG in the histopolation basis."""
+    (hd_apply_C, FP64) by the stored explicit inverse (batched gemv), the stored Cholesky
+    factors (two triangular solves), the fused local CG in the Gauss-Legendre nodal basis
+    and the same CG in the histopolation basis."""
     import torch
     import paper_2304_12387_gb300 as hd
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -552,7 +553,8 @@ def run_winv_study(args):
         vx, vy, vz, alpha, beta = workload(nx)
         row = {"k": k, "elements": nx ** 3, "l2_dofs": (nx * k) ** 3}
         ref = None
-        for name, mode in (("inverse", hd.HD_WINV_DENSE), ("cg_gl", hd.HD_WINV_CG), ("cg_hist", hd.HD_WINV_CG_HIST)):
+        for name, mode in (("inverse", hd.HD_WINV_DENSE), ("cholesky", hd.HD_WINV_CHOL), ("cg_gl", hd.HD_WINV_CG),
+                           ("cg_hist", hd.HD_WINV_CG_HIST)):
             op = hd.Operator(nx, nx, nx, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
                              winv_mode=mode, stream=stream)
             st = op.hd_get_setup_times()
@@ -658,7 +660,8 @@ def main():
     ap.add_argument("--gmres-inner-rtol", type=float, default=1e-3,
                     help="per-cycle reduction of the mixed-precision GMRES before its FP64 residual")
     ap.add_argument("--winv-study", action="store_true",
-                    help="W^-1 by explicit inverse vs local CG (GL and histopolation bases): setup and 100 applies")
+                    help="W^-1 by explicit inverse, Cholesky and local CG (GL and histopolation bases): setup "
+                         "and 100 applies")
     ap.add_argument("--iterations", action="store_true",
                     help="run the iteration-count study (mesh sizes and degrees) instead")
     ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],

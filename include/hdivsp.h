@@ -73,9 +73,13 @@ enum {
   HD_WINV_CG = 1,    /* fused local CG in the Gauss-Legendre nodal basis (Sec. 2.5, 3.1):
                         Jacobi-preconditioned, per-element relative residual 1e-14 (cap 40
                         iterations), no stored inverse */
-  HD_WINV_CG_HIST = 2 /* the same fused CG on W in the histopolation basis itself, without the
+  HD_WINV_CG_HIST = 2,/* the same fused CG on W in the histopolation basis itself, without the
                         change of basis (the comparison of Sec. 3.1; cap 100 iterations). The
                         FP64 operator only: the FP32 inner operator keeps the GL-basis CG */
+  HD_WINV_CHOL = 3    /* the per-element Cholesky factor W_e = L L^T computed at setup (the
+                        factorisation approach of Sec. 3.1), k^6 doubles per element; every
+                        apply solves two triangular systems per element. FP64 operator only (the
+                        FP32 inner operator keeps the GL-basis CG) */
 };
 
 /* essential-boundary side bits */
@@ -102,7 +106,7 @@ typedef struct {
   uint32_t ess_mask;     /* HD_SIDE_* bits: sides where u.n is essential */
   int32_t affine;        /* caller states the mesh is affine (only selects the default q) */
   double tau;            /* (1,1) preconditioner scaling tau M~; 0 -> 1 */
-  int32_t winv_mode;     /* HD_WINV_DENSE, HD_WINV_CG or HD_WINV_CG_HIST */
+  int32_t winv_mode;     /* HD_WINV_DENSE, HD_WINV_CG, HD_WINV_CG_HIST or HD_WINV_CHOL */
   int32_t nu;            /* l1-Jacobi sweeps before and after the coarse correction; 0 -> 2 */
   int32_t coarse_max;    /* at most this many cells on the coarsest level; 0 -> 512 */
   int32_t cycle;         /* 0 or 1: V-cycle; 2: W-cycle (two coarse corrections per level

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libhdivsp.so")
 HD_OK, HD_ERR_INVALID_ARG, HD_ERR_CUDA, HD_ERR_OOM, HD_ERR_NOT_CONVERGED = 0, 1, 2, 3, 4
 HD_ERR_PREC_INDEFINITE, HD_ERR_NAN, HD_ERR_STAGNATION, HD_ERR_BOUNDS, HD_ERR_NOT_IMPLEMENTED = 5, 6, 7, 8, 9
 HD_GRAD_DIV, HD_DARCY = 0, 1
-HD_WINV_DENSE, HD_WINV_CG, HD_WINV_CG_HIST = 0, 1, 2
+HD_WINV_DENSE, HD_WINV_CG, HD_WINV_CG_HIST, HD_WINV_CHOL = 0, 1, 2, 3
 HD_GMRES_BLOCK_DIAG, HD_GMRES_BLOCK_TRI = 0, 1
 STATUS_NAMES = {0: "HD_OK", 1: "HD_ERR_INVALID_ARG", 2: "HD_ERR_CUDA", 3: "HD_ERR_OOM",
                 4: "HD_ERR_NOT_CONVERGED", 5: "HD_ERR_PREC_INDEFINITE", 6: "HD_ERR_NAN",

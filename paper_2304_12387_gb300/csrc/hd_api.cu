@@ -193,6 +193,7 @@ __global__ void k_split_df(int64_t n, const double* __restrict__ a, dfloat* __re
 void destroy_all(hd_op* h) {
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
   cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
+  cudaFree(h->d_wchol);
   cudaFree(h->f_wdet); cudaFree(h->f_wgldiag);
   cudaFree(h->x_G); cudaFree(h->x_winv); cudaFree(h->x_cscale);
   cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
@@ -266,7 +267,8 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->k = d->k;
   h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
   if (h->q != h->k + 1 && h->q != h->k + 2) { delete h; return HD_ERR_INVALID_ARG; }
-  if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG && d->winv_mode != HD_WINV_CG_HIST) {
+  if (d->winv_mode != HD_WINV_DENSE && d->winv_mode != HD_WINV_CG && d->winv_mode != HD_WINV_CG_HIST &&
+      d->winv_mode != HD_WINV_CHOL) {
     delete h;
     return HD_ERR_INVALID_ARG;
   }
@@ -328,6 +330,7 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     if ((st = dalloc(h, &h->d_G, E * 6 * nq, "geometric factors")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_wdet, E * nq, "wdet")) != HD_OK) break;
     if (h->winv_mode == HD_WINV_DENSE && (st = dalloc(h, &h->d_winv, E * nl2 * nl2, "W inverse")) != HD_OK) break;
+    if (h->winv_mode == HD_WINV_CHOL && (st = dalloc(h, &h->d_wchol, E * nl2 * nl2, "W Cholesky")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_wgldiag, E * nl2, "GL-basis W diagonal")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_wdiag, E * nl2, "W diagonal")) != HD_OK) break;
     if ((st = dalloc(h, &h->d_cscale, E, "cscale")) != HD_OK) break;

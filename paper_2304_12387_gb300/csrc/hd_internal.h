@@ -123,6 +123,7 @@ struct hd_op {
   double* d_winv = nullptr;     // [E][k^3][k^3] unweighted W_e^-1 (dense mode)
   double* d_wdiag = nullptr;    // [E][k^3] diag(W_e) (unweighted)
   double* d_wgldiag = nullptr;  // [E][k^3] diag of W_e in the GL nodal basis (local CG)
+  double* d_wchol = nullptr;    // HD_WINV_CHOL: [E][k^3][k^3] Cholesky factor of W_e (reciprocal diagonal)
   float* f_wdet = nullptr;      // FP32 copies for the inner solve
   float* f_wgldiag = nullptr;
   double* d_cscale = nullptr;   // [E] c_e: C_e = c_e W_e^-1

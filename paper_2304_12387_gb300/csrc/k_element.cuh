@@ -50,6 +50,7 @@ struct CgArgs {
   int maxit;
   T tol2;            // stop when ||r||^2 <= tol2 ||b||^2 (per element)
   int hist;          // 0: CG in the GL nodal basis (Sec. 2.5); 1: in the histopolation basis
+  int chol;          // 1 (and wdet null): W_e^-1 q_e by the stored Cholesky factor passed as winv
 };
 
 // Sum of products as one FMA chain (one type per arithmetic: double, float or
@@ -353,6 +354,44 @@ __device__ T* local_cg(const TabT<T>& tab, const T* sq, T* s1, int s1stride, T* 
   return out;
 }
 
+// W_e^-1 q_e for EB elements by the Cholesky factor of W_e (the factorisation
+// approach of Sec. 3.1: W_e = L L^T stored [NL2][NL2] row-major, zero above the
+// diagonal, the diagonal entries stored as their reciprocals). One warp per
+// element: forward L y = q by rows (a warp sum per row), back L^T z = y by the
+// columns of L^T, which are the rows of L (an axpy per step): every read of L is a
+// contiguous row. Result in s1 (returned).
+template <typename T, int K, int EB>
+__device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1stride, int e0, int n_elem) {
+  constexpr int NL2 = K * K * K;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int el = warp; el < EB; el += nw) {
+    const int e = e0 + el;
+    T* y = s1 + el * s1stride;
+    for (int i = lane; i < NL2; i += 32) y[i] = sq[el * NL2 + i];
+    __syncwarp();
+    if (e >= n_elem) continue;
+    const T* L = Lg + (size_t)e * NL2 * NL2;
+    for (int i = 0; i < NL2; ++i) {
+      T sum = (T)0;
+      for (int j = lane; j < i; j += 32) sum = fma(L[i * NL2 + j], y[j], sum);
+      sum = warp_allsum(sum);
+      const T yi = (y[i] - sum) * L[i * NL2 + i];
+      __syncwarp();
+      if (lane == 0) y[i] = yi;
+      __syncwarp();
+    }
+    for (int i = NL2 - 1; i >= 0; --i) {
+      const T zi = y[i] * L[i * NL2 + i];
+      __syncwarp();
+      if (lane == 0) y[i] = zi;
+      for (int j = lane; j < i; j += 32) y[j] = fma(-L[i * NL2 + j], zi, y[j]);
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  return s1;
+}
+
 // ---------------------------------------------------------------------------
 // Fused block-operator kernel: EB elements per CTA.
 //   OP_M : y_u += M_e u_e (sum factorisation: interpolation to the Q^3 points,
@@ -445,6 +484,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   const bool needu = (mode & (OP_M | OP_D)) != 0;
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
   const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
+  const bool use_chol = (mode & OP_C) && !use_cg && cg.chol != 0;
   if constexpr (ElemCfg<T>::PREFETCH != 0) {
     if (tid < 32 && e0 < n_elem) {
       const int ne = (n_elem - e0 < EB) ? n_elem - e0 : EB;
@@ -491,13 +531,15 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         if (cg.hist) cgres = local_cg<T, K, Q, EB, false>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
       if (!cgres) cgres = local_cg<T, K, Q, EB, true>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
     }
+    if constexpr (std::is_same<T, double>::value)  // the Cholesky factor: FP64 only
+      if (use_chol) cgres = local_chol<T, K, EB>(winv, sq, s1, S::R1, e0, n_elem);
   }
   // one L2 row (element-local cell t), given its D u part v
   auto l2_row = [&](int t, T v) {
     const int el = t / NL2, a = t - el * NL2, e = e0 + el;
     if (mode & OP_C) {
       T s = (T)0;
-      if (use_cg) {
+      if (use_cg || use_chol) {
         s = cgres[el * S::R1 + a];
       } else {
         const T* W = winv + (size_t)e * NL2 * NL2;
@@ -521,7 +563,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       l2_row(t, (mode & OP_D) ? div_local<T, K>(su + (t / NL2) * NRT, t % NL2) : (T)0);
     }
   }
-  if (use_cg) __syncthreads();
+  if (use_cg || use_chol) __syncthreads();
 
   if (mode & OP_M) {
     // -- interpolation to the points: stage A (contract along x) ----------------
@@ -729,7 +771,7 @@ struct WinvSmem {
   static constexpr int TOTAL = OFF_COL + NL2;
 };
 
-template <int K, int Q>
+template <int K, int Q, bool CHOL = false>
 __global__ void __launch_bounds__(128)
 k_winv(const ElemTables tab, const int n_elem, const double* __restrict__ wdet,
        double* __restrict__ winv, double* __restrict__ wdiag) {
@@ -776,6 +818,29 @@ k_winv(const ElemTables tab, const int n_elem, const double* __restrict__ wdet,
   }
   __syncthreads();
   for (int t = tid; t < NL2; t += nth) wdiag[(size_t)e * NL2 + t] = A[t * NL2 + t];
+  if constexpr (CHOL) {
+    // W_e = L L^T (right-looking, in place in the lower triangle; SPD: no pivoting);
+    // stored with zeros above the diagonal and the reciprocal on it
+    for (int p = 0; p < NL2; ++p) {
+      __syncthreads();
+      const double d = sqrt(A[p * NL2 + p]);
+      for (int i = p + 1 + tid; i < NL2; i += nth) A[i * NL2 + p] /= d;
+      __syncthreads();
+      if (tid == 0) A[p * NL2 + p] = d;
+      const int m = NL2 - p - 1;  // trailing lower triangle, row-wise
+      for (int t = tid; t < m * m; t += nth) {
+        const int i = p + 1 + t / m, j = p + 1 + t % m;
+        if (j <= i) A[i * NL2 + j] = fma(-A[i * NL2 + p], A[j * NL2 + p], A[i * NL2 + j]);
+      }
+    }
+    __syncthreads();
+    double* out = winv + (size_t)e * NL2 * NL2;
+    for (int t = tid; t < NL2 * NL2; t += nth) {
+      const int i = t / NL2, j = t % NL2;
+      out[t] = j < i ? A[t] : (j == i ? 1.0 / A[t] : 0.0);
+    }
+    return;
+  }
   // Gauss-Jordan elimination in place (W_e is SPD: no pivoting). After step p,
   // column p holds column p of the inverse.
   for (int p = 0; p < NL2; ++p) {
@@ -900,7 +965,7 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
     constexpr int NL2 = K * K * K;
     unsigned nb = (unsigned)((h->n_elem * NL2 + 255) / 256);
     k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, true, h->d_wdet, h->d_wgldiag);
-    if (h->winv_mode != HD_WINV_DENSE)  // the dense path gets diag(W_e) from k_winv
+    if (h->winv_mode == HD_WINV_CG || h->winv_mode == HD_WINV_CG_HIST)  // else diag(W_e) comes from k_winv
       k_diag_tensor<K, Q><<<nb, 256, 0, h->stream>>>(h->tab, (int)h->n_elem, false, h->d_wdet, h->d_wdiag);
     HD_LAUNCH_CK(h, "k_diag_tensor");
   }
@@ -911,6 +976,15 @@ hd_status run_elem_setup(hd_op* h, const double* bcoef, int* d_bad) {
     k_winv<K, Q><<<(unsigned)h->n_elem, 128, smem, h->stream>>>(h->tab, (int)h->n_elem, h->d_wdet, h->d_winv,
                                                                  h->d_wdiag);
     HD_LAUNCH_CK(h, "k_winv");
+  }
+  if (h->winv_mode == HD_WINV_CHOL && h->n_elem > 0) {
+    size_t smem = (size_t)WinvSmem<K, Q>::TOTAL * sizeof(double);
+    cudaError_t err =
+        cudaFuncSetAttribute(k_winv<K, Q, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return hd_cuda_check(h, err, "cudaFuncSetAttribute(k_winv chol)");
+    k_winv<K, Q, true><<<(unsigned)h->n_elem, 128, smem, h->stream>>>(h->tab, (int)h->n_elem, h->d_wdet,
+                                                                       h->d_wchol, h->d_wdiag);
+    HD_LAUNCH_CK(h, "k_winv chol");
   }
   cudaEventRecord(ev[2], h->stream);
   int64_t m = h->n_elem * NRT;
@@ -950,18 +1024,19 @@ HD_DECLARE_K(5)
 // this GPU than the CG's barrier-bound iterations), else the local CG to 1e-6.
 #define HD_DEFINE_K(KK)                                                                                   \
   hd_status elem_op_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) { \
-    const bool hi = h->winv_mode == HD_WINV_CG_HIST;                                                      \
-    hdk::CgArgs<double> cg{h->winv_mode != HD_WINV_DENSE ? h->d_wdet : nullptr, hi ? h->d_wdiag : h->d_wgldiag, \
-                           hi ? 100 : 40, 1e-28, hi ? 1 : 0};                                             \
+    const bool hi = h->winv_mode == HD_WINV_CG_HIST, ch = h->winv_mode == HD_WINV_CHOL;                   \
+    const bool cgm = h->winv_mode == HD_WINV_CG || hi;                                                    \
+    hdk::CgArgs<double> cg{cgm ? h->d_wdet : nullptr, hi ? h->d_wdiag : h->d_wgldiag, hi ? 100 : 40, 1e-28, \
+                           hi ? 1 : 0, ch ? 1 : 0};                                                       \
+    const double* wi = ch ? h->d_wchol : h->d_winv;                                                       \
     if (h->q == KK + 1)                                                                                   \
-      return hdk::run_elem_op<double, double, KK, KK + 1>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, \
-                                                          q, yu, yq);                                     \
-    return hdk::run_elem_op<double, double, KK, KK + 2>(h, mode, h->d_G, h->d_winv, h->d_cscale, cg, u, q, \
-                                                        yu, yq);                                          \
+      return hdk::run_elem_op<double, double, KK, KK + 1>(h, mode, h->d_G, wi, h->d_cscale, cg, u, q, yu, \
+                                                          yq);                                            \
+    return hdk::run_elem_op<double, double, KK, KK + 2>(h, mode, h->d_G, wi, h->d_cscale, cg, u, q, yu, yq); \
   }                                                                                                       \
   hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,            \
                              double* yq) {                                                                \
-    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0};                                            \
+    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0, 0};                                         \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<dfloat, double, KK, KK + 1>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, \
                                                           q, yu, yq);                                     \
@@ -970,7 +1045,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_f32_k##KK(hd_op* h, int mode, const float* u, const float* q, float* yu,              \
                               float* yq) {                                                                \
-    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0};                  \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0, 0};               \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<float, float, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u, q, \
                                                         yu, yq);                                          \
@@ -979,7 +1054,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_f32io64_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,       \
                                   double* yq) {                                                           \
-    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0};                  \
+    hdk::CgArgs<float> cg{h->f_winv ? nullptr : h->f_wdet, h->f_wgldiag, 20, 1e-12f, 0, 0};               \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<float, double, KK, KK + 1>(h, mode, h->f_G, h->f_winv, h->f_cscale, cg, u,  \
                                                          q, yu, yq);                                      \

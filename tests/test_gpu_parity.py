@@ -179,19 +179,21 @@ def test_f32_operator_close(pair):
     assert close(_host(y).astype(np.float64), prob.apply_op(x), 1e-4) <= 1e-4
 
 
-@pytest.mark.parametrize("basis", ["gl", "hist"])
+@pytest.mark.parametrize("basis", ["gl", "hist", "chol"])
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_local_cg_winv_mode(name, basis):
     """W^-1 by the fused local CG in the Gauss-Legendre nodal basis (the paper's
-    matrix-free method, Sec. 2.5 and 3.1), or in the histopolation basis itself (the
-    comparison of Sec. 3.1), instead of stored dense inverses: same operator to 1e-12."""
+    matrix-free method, Sec. 2.5 and 3.1), in the histopolation basis itself (the
+    comparison of Sec. 3.1), or by per-element Cholesky factors (the factorisation
+    approach of Sec. 3.1), instead of stored dense inverses: same operator to 1e-12."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2304_12387_gb300 as hd
     from oracle.precond import approx_schur
     d = inputs(name)
     prob = oracle_problem(d)
-    op = gpu_operator(d, coarse_max=8, winv_mode=hd.HD_WINV_CG if basis == "gl" else hd.HD_WINV_CG_HIST)
+    op = gpu_operator(d, coarse_max=8, winv_mode={"gl": hd.HD_WINV_CG, "hist": hd.HD_WINV_CG_HIST,
+                                                  "chol": hd.HD_WINV_CHOL}[basis])
     rng = np.random.Generator(np.random.PCG64(15))
     x = rng.uniform(-1, 1, prob.n)
     y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
