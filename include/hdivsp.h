@@ -139,6 +139,9 @@ typedef struct {
                             FP64 outer residual correction (see hd_minres_solve) */
   double outer_rtol;     /* precision = 1: target true relative residual ||b-AAx||/||b|| */
   int32_t max_outer;     /* precision = 1: at most this many outer corrections */
+  int32_t resume;        /* 1: continue the recurrence kept on the handle (see hd_checkpoint_minres)
+                            for up to maxit more iterations; rtol, use_x0 are those of the stopped
+                            solve, x receives its iterate first; plain FP64 path only */
 } hd_solve_opts;
 
 typedef struct {
@@ -244,6 +247,24 @@ hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3
 hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
                           const hd_solve_opts* opts, hd_solve_info* info);
 
+/* -- MINRES checkpoints ------------------------------------------------------ */
+/* A plain FP64 solve (precision 0, max_outer <= 1, V-cycle Schur block) that stops at
+ * its iteration cap keeps its recurrence on the handle: the iterate x, the Lanczos
+ * vectors v_j, r_{j-1}, r_j, the direction vectors w_{j-1}, w_j and the device
+ * scalars (Givens rotation, eta, iteration count). Any later solve on the handle
+ * replaces it. A solve with opts.resume = 1 continues it exactly where it stopped:
+ * with the same kernels, N iterations then a resume of M give the same x, bit for
+ * bit, as N + M iterations in one call, and info.iterations counts from the start.
+ *
+ * hd_checkpoint_minres writes the kept recurrence to `path` (a header, then six
+ * FP64 vectors of n_rt + n_l2 entries; host byte order); HD_ERR_INVALID_ARG when
+ * the handle keeps none or the file cannot be written. hd_resume_minres reads such
+ * a file into a handle of the same problem size (n_rt, n_l2, k), after which a solve
+ * with opts.resume = 1 continues it; HD_ERR_INVALID_ARG for a missing, foreign,
+ * truncated or differently sized file (the handle keeps no recurrence then). */
+hd_status hd_checkpoint_minres(hd_handle h, const char* path);
+hd_status hd_resume_minres(hd_handle h, const char* path);
+
 /* -- GMRES with block preconditioners ----------------------------------------- */
 /* The remark on block-triangular preconditioners in Sec. 2.3: with exact blocks,
  * P = [[M, D^T], [0, -S]] gives GMRES convergence in two iterations; with the
@@ -345,6 +366,14 @@ hd_status hd_learned_train(hd_handle h, const hd_train_opts* opts, hd_train_info
  * block in hd_apply_prec and hd_minres_solve (FP64 solves fall back to the
  * V-cycle if MINRES breaks down: info.fallback). */
 hd_status hd_set_schur_prec(hd_handle h, int32_t mode);
+/* on = 1: hd_set_schur_prec(h, 1); on = 0: back to the V-cycle */
+hd_status hd_enable_learned(hd_handle h, int32_t on);
+/* The network (nc, delta, W1, W2 in the layout above; FP32, host byte order) to a
+ * file and back. hd_learned_load initialises the network when the handle has none
+ * (or another delta); HD_ERR_INVALID_ARG for a missing, foreign or truncated file.
+ * Training runs as one call, so no optimiser state is kept. */
+hd_status hd_learned_save(hd_handle h, const char* path);
+hd_status hd_learned_load(hd_handle h, const char* path);
 
 /* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);

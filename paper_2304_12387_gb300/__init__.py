@@ -46,7 +46,7 @@ class ProblemDesc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("maxit", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("outer_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32)]
+                ("outer_rtol", ctypes.c_double), ("max_outer", ctypes.c_int32), ("resume", ctypes.c_int32)]
 
 
 class GmresOpts(ctypes.Structure):
@@ -109,6 +109,11 @@ _SIGS = {
     "hd_learned_grad": [_H, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)],
     "hd_learned_train": [_H, ctypes.POINTER(TrainOpts), ctypes.POINTER(TrainInfo)],
     "hd_set_schur_prec": [_H, ctypes.c_int32],
+    "hd_enable_learned": [_H, ctypes.c_int32],
+    "hd_learned_save": [_H, ctypes.c_char_p],
+    "hd_learned_load": [_H, ctypes.c_char_p],
+    "hd_checkpoint_minres": [_H, ctypes.c_char_p],
+    "hd_resume_minres": [_H, ctypes.c_char_p],
     "hd_apply_op_f32": [_H, _VP, _VP],
     "hd_apply_prec_f32": [_H, _VP, _VP],
 }
@@ -276,10 +281,12 @@ class Operator:
         return nl.value, tuple(dims)
 
     def hd_minres_solve(self, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8, precision=0,
-                        outer_rtol=0.0, max_outer=1, raise_on_error=False):
+                        outer_rtol=0.0, max_outer=1, raise_on_error=False, resume=False):
         """MINRES on AA x = b. max_outer > 1 or precision = 1 wraps it in an FP64
-        residual correction that stops at ||b - AA x|| <= outer_rtol ||b||."""
-        o = SolveOpts(rtol, maxit, int(use_x0), check_every, precision, outer_rtol, max_outer)
+        residual correction that stops at ||b - AA x|| <= outer_rtol ||b||. resume:
+        continue the recurrence that the handle keeps (a stopped solve or
+        hd_resume_minres) for up to maxit more iterations."""
+        o = SolveOpts(rtol, maxit, int(use_x0), check_every, precision, outer_rtol, max_outer, int(resume))
         info = SolveInfo()
         st = lib().hd_minres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
         if raise_on_error:
@@ -335,3 +342,23 @@ class Operator:
 
     def hd_set_schur_prec(self, mode):
         _check(lib().hd_set_schur_prec(self.h, int(mode)), self.h)
+
+    def hd_enable_learned(self, on):
+        _check(lib().hd_enable_learned(self.h, int(bool(on))), self.h)
+
+    def hd_learned_save(self, path):
+        """Returns the status (HD_OK or HD_ERR_INVALID_ARG)."""
+        return lib().hd_learned_save(self.h, os.fsencode(path))
+
+    def hd_learned_load(self, path):
+        return lib().hd_learned_load(self.h, os.fsencode(path))
+
+    # -- MINRES checkpoints ----------------------------------------------------
+    def hd_checkpoint_minres(self, path):
+        """Writes the recurrence that a stopped plain FP64 solve left on the handle;
+        returns the status."""
+        return lib().hd_checkpoint_minres(self.h, os.fsencode(path))
+
+    def hd_resume_minres(self, path):
+        """Loads a checkpoint; the next hd_minres_solve(..., resume=True) continues it."""
+        return lib().hd_resume_minres(self.h, os.fsencode(path))

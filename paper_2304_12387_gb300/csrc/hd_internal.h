@@ -179,6 +179,11 @@ struct hd_op {
   int gm_mf = 0;
   float* gm_wf = nullptr;
   MinresState* d_ms = nullptr;
+  // MINRES recurrence kept after a plain FP64 solve stopped at its iteration cap:
+  // mr_it iterations done (0: none kept); mr_map[i] = index in mv of rpp, rp, y, z,
+  // v, vn, wpp, wp, wn; x copied to mv[9]
+  int mr_it = 0;
+  int mr_map[9] = {0, 1, 2, 3, 4, 5, 6, 7, 8};
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
   // Schur-block preconditioner: 0 = V-cycle, 1 = learned network + coarse correction
   int schur_mode = 0;

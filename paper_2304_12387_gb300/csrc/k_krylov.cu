@@ -359,34 +359,47 @@ static hd_status inner_vcycle(hd_op* h, bool f32, const double* rq, double* zq) 
 
 // MINRES on AA x = b (x0 = x when use_x0). The Lanczos vectors, inner products and
 // Givens scalars are FP64; with f32 the operator and the V-cycle run in FP32.
+// it0 > 0: continue a recurrence kept on the handle after it0 iterations (its
+// vectors in h->mv by h->mr_map, its scalars in h->d_ms, x given). keep: when the
+// iteration cap stops the recurrence, record where its vectors are and copy x to
+// h->mv[9], so that hd_checkpoint_minres / a resumed solve can continue it.
 static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bool use_x0, double rtol, int maxit,
-                              int check, int* iters, MinresState* hs_out) {
+                              int check, int* iters, MinresState* hs_out, int it0 = 0, bool keep = false) {
   const int64_t n = h->n_rt + h->n_l2;
-  double *rpp = h->mv[0], *rp = h->mv[1], *y = h->mv[2], *z = h->mv[3], *v = h->mv[4], *vn = h->mv[5];
-  double *wpp = h->mv[6], *wp = h->mv[7], *wn = h->mv[8];
+  double* slot[9];  // rpp, rp, y, z, v, vn, wpp, wp, wn
+  for (int i = 0; i < 9; ++i) slot[i] = h->mv[it0 > 0 ? h->mr_map[i] : i];
+  double *rpp = slot[0], *rp = slot[1], *y = slot[2], *z = slot[3], *v = slot[4], *vn = slot[5];
+  double *wpp = slot[6], *wp = slot[7], *wn = slot[8];
   cudaStream_t s = h->stream;
   hd_status st;
-  if (use_x0) {
+  h->mr_it = 0;
+  if (it0 > 0) {
+    // the kept state: x from its copy, everything else where the stopped solve left it
+    HD_CK(h, cudaMemcpyAsync(x, h->mv[9], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  } else if (use_x0) {
     if ((st = apply_op_internal(h, x, rp)) != HD_OK) return st;
     k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, rp);
   } else {
     HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
     HD_CK(h, cudaMemcpyAsync(rp, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   }
-  HD_CK(h, cudaMemsetAsync(wp, 0, sizeof(double) * n, s));
-  HD_CK(h, cudaMemsetAsync(wpp, 0, sizeof(double) * n, s));
-  HD_CK(h, cudaMemsetAsync(rpp, 0, sizeof(double) * n, s));
-  // z = B^-1 r: the u part by M~ scaling, the q part by the V-cycle
-  if ((st = diag_scale(h, rp, z)) != HD_OK) return st;
-  if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, rp + h->n_rt, z + h->n_rt)) != HD_OK) return st;
-  k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
-  k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, rtol);
-  k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, h->d_ms, v);
-  HD_LAUNCH_CK(h, "minres init");
+  if (it0 == 0) {
+    HD_CK(h, cudaMemsetAsync(wp, 0, sizeof(double) * n, s));
+    HD_CK(h, cudaMemsetAsync(wpp, 0, sizeof(double) * n, s));
+    HD_CK(h, cudaMemsetAsync(rpp, 0, sizeof(double) * n, s));
+    // z = B^-1 r: the u part by M~ scaling, the q part by the V-cycle
+    if ((st = diag_scale(h, rp, z)) != HD_OK) return st;
+    if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, rp + h->n_rt, z + h->n_rt)) != HD_OK) return st;
+    k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
+    k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, rtol);
+    k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, h->d_ms, v);
+    HD_LAUNCH_CK(h, "minres init");
+  }
   if (check < 1) check = 1;
   MinresState hs;
   int it;
-  for (it = 1; it <= maxit; ++it) {
+  const int it_end = it0 + maxit;
+  for (it = it0 + 1; it <= it_end; ++it) {
     if ((st = inner_apply(h, f32, v, y)) != HD_OK) return st;
     k_mr_lanczos1<<<DOT_BLOCKS, TPB, 0, s>>>(n, it, h->d_ms, v, y, rpp, h->d_red);
     k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red);
@@ -405,7 +418,7 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
     double* t = rpp; rpp = rp; rp = y; y = t;
     t = wpp; wpp = wp; wp = wn; wn = t;
     t = v; v = vn; vn = t;
-    if (it % check == 0 || it == maxit) {
+    if (it % check == 0 || it == it_end) {
       HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
       HD_CK(h, cudaStreamSynchronize(s));
       if (hs.done_at >= 0) break;
@@ -413,9 +426,20 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
   }
   HD_CK(h, cudaMemcpyAsync(&hs, h->d_ms, sizeof(MinresState), cudaMemcpyDeviceToHost, s));
   HD_CK(h, cudaStreamSynchronize(s));
-  *iters = hs.done_at >= 0 ? hs.done_at : maxit;
+  *iters = hs.done_at >= 0 ? hs.done_at : it_end;
   if (hs_out) *hs_out = hs;
-  if (hs.done_at < 0) return HD_ERR_NOT_CONVERGED;
+  if (hs.done_at < 0) {
+    if (keep) {
+      const double* now[9] = {rpp, rp, y, z, v, vn, wpp, wp, wn};
+      for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j)
+          if (now[i] == h->mv[j]) h->mr_map[i] = j;
+      HD_CK(h, cudaMemcpyAsync(h->mv[9], x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+      HD_CK(h, cudaStreamSynchronize(s));
+      h->mr_it = it_end;
+    }
+    return HD_ERR_NOT_CONVERGED;
+  }
   return hs.status;
 }
 
@@ -426,6 +450,13 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
   hd_status st = ensure_minres(h);
   if (st != HD_OK) return st;
   const bool f32 = o->precision == 1;
+  const int it0 = h->mr_it;
+  if (o->resume) {
+    if (f32 || o->max_outer > 1 || h->schur_mode != 0)
+      return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "resume: plain FP64 MINRES only (precision 0, max_outer <= 1, V-cycle)");
+    if (it0 == 0) return hd_fail(h, HD_ERR_INVALID_ARG, "resume: no stopped MINRES recurrence on this handle");
+  }
+  h->mr_it = 0;  // any solve overwrites the kept recurrence
   if (f32 && (st = ensure_f32_work(h)) != HD_OK) return st;
   const int64_t n = h->n_rt + h->n_l2;
   cudaStream_t s = h->stream;
@@ -441,7 +472,8 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
   int fallback = 0;
   if (!refine) {
     outer = 1;
-    status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs);
+    status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs,
+                          o->resume ? it0 : 0, h->schur_mode == 0);
     if (h->schur_mode == 1 && (status == HD_ERR_PREC_INDEFINITE || status == HD_ERR_NAN)) {
       // the learned Schur preconditioner broke down: solve again with the V-cycle
       fallback = 1;
@@ -612,10 +644,91 @@ hd_status minres_run_ws(hd_op* h, double* ws, const double* b, double* x, const 
 
 }  // namespace
 
+// ---- MINRES checkpoints ----------------------------------------------------------
+// File: header, the device state word, then x, v, r_{j-1}, r_j, w_{j-1}, w_j (FP64,
+// n_rt + n_l2 each, host byte order).
+struct MinresCkptHeader {
+  char magic[8];
+  int64_t n_rt, n_l2;
+  int32_t k, it;
+  int32_t state_bytes, reserved;
+};
+static const char kMinresMagic[8] = {'H', 'D', 'M', 'I', 'N', 'R', 'S', '1'};
+static const int kCkptSlots[5] = {4, 0, 1, 6, 7};  // v, rpp, rp, wpp, wp in mr_map order
+
+extern "C" hd_status hd_checkpoint_minres(hd_handle h, const char* path) {
+  if (!h || !path) return HD_ERR_INVALID_ARG;
+  if (h->mr_it == 0) return hd_fail(h, HD_ERR_INVALID_ARG, "checkpoint: no stopped MINRES recurrence on this handle");
+  const int64_t n = h->n_rt + h->n_l2;
+  MinresState ms;
+  HD_CK(h, cudaMemcpyAsync(&ms, h->d_ms, sizeof ms, cudaMemcpyDeviceToHost, h->stream));
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  std::vector<double> buf((size_t)n);
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return hd_fail(h, HD_ERR_INVALID_ARG, std::string("checkpoint: cannot open ") + path);
+  MinresCkptHeader hd{};
+  std::memcpy(hd.magic, kMinresMagic, sizeof hd.magic);
+  hd.n_rt = h->n_rt;
+  hd.n_l2 = h->n_l2;
+  hd.k = h->k;
+  hd.it = h->mr_it;
+  hd.state_bytes = (int32_t)sizeof(MinresState);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(&ms, sizeof ms, 1, f) == 1;
+  cudaError_t ce = cudaSuccess;
+  for (int i = 0; ok && i < 6; ++i) {
+    const double* src = i == 0 ? h->mv[9] : h->mv[h->mr_map[kCkptSlots[i - 1]]];
+    ce = cudaMemcpyAsync(buf.data(), src, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(h->stream);
+    ok = ce == cudaSuccess && std::fwrite(buf.data(), sizeof(double), (size_t)n, f) == (size_t)n;
+  }
+  ok = std::fclose(f) == 0 && ok;
+  if (ce != cudaSuccess) return hd_cuda_check(h, ce, "checkpoint copy");
+  return ok ? HD_OK : hd_fail(h, HD_ERR_INVALID_ARG, std::string("checkpoint: write failed: ") + path);
+}
+
+extern "C" hd_status hd_resume_minres(hd_handle h, const char* path) {
+  if (!h || !path) return HD_ERR_INVALID_ARG;
+  hd_status st = ensure_minres(h);
+  if (st != HD_OK) return st;
+  h->mr_it = 0;  // a refused file leaves no recurrence on the handle
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return hd_fail(h, HD_ERR_INVALID_ARG, std::string("resume: cannot open ") + path);
+  const int64_t n = h->n_rt + h->n_l2;
+  MinresCkptHeader hd{};
+  MinresState ms{};
+  std::string err;
+  if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, kMinresMagic, sizeof hd.magic) != 0)
+    err = "not a MINRES checkpoint";
+  else if (hd.n_rt != h->n_rt || hd.n_l2 != h->n_l2 || hd.k != h->k)
+    err = "checkpoint of another problem size";
+  else if (hd.state_bytes != (int32_t)sizeof(MinresState) || hd.it < 1)
+    err = "checkpoint of another library version";
+  else if (std::fread(&ms, sizeof ms, 1, f) != 1 || ms.done_at != -1)
+    err = "checkpoint without a running recurrence";
+  std::vector<double> buf[6];
+  for (int i = 0; err.empty() && i < 6; ++i) {
+    buf[i].resize((size_t)n);
+    if (std::fread(buf[i].data(), sizeof(double), (size_t)n, f) != (size_t)n) err = "truncated checkpoint";
+  }
+  if (err.empty() && std::fgetc(f) != EOF) err = "trailing bytes after the checkpoint";
+  std::fclose(f);
+  if (!err.empty()) return hd_fail(h, HD_ERR_INVALID_ARG, "resume: " + err + ": " + path);
+  for (int i = 0; i < 9; ++i) h->mr_map[i] = i;
+  for (int i = 0; i < 6; ++i) {
+    double* dst = i == 0 ? h->mv[9] : h->mv[kCkptSlots[i - 1]];
+    HD_CK(h, cudaMemcpyAsync(dst, buf[i].data(), sizeof(double) * n, cudaMemcpyHostToDevice, h->stream));
+  }
+  HD_CK(h, cudaMemcpyAsync(h->d_ms, &ms, sizeof ms, cudaMemcpyHostToDevice, h->stream));
+  HD_CK(h, cudaStreamSynchronize(h->stream));
+  h->mr_it = hd.it;
+  return HD_OK;
+}
+
 extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, double* x, const hd_solve_opts* o,
                                              hd_solve_info* info) {
   if (!h || !b || !x || !o || b == x || o->maxit < 1 || !(o->rtol > 0)) return HD_ERR_INVALID_ARG;
   if (o->precision != 0) return hd_fail(h, HD_ERR_INVALID_ARG, "hd_minres_solve_noalloc: FP64 only (precision = 0)");
+  if (o->resume) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "hd_minres_solve_noalloc: no resume (use hd_minres_solve)");
   const int64_t n = h->n_rt + h->n_l2;
   if (n > HD_NOALLOC_MAX_DOFS) {
     char msg[160];

@@ -17,6 +17,7 @@
 #include <cuda_fp16.h>
 
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -838,6 +839,61 @@ hd_status hd_set_schur_prec(hd_handle h, int32_t mode) {
   if (mode == 1 && !h->net) return hd_fail(h, HD_ERR_INVALID_ARG, "learned preconditioner not initialised");
   h->schur_mode = mode;
   return HD_OK;
+}
+
+hd_status hd_enable_learned(hd_handle h, int32_t on) {
+  if (!h || (on != 0 && on != 1)) return HD_ERR_INVALID_ARG;
+  return hd_set_schur_prec(h, on);
+}
+
+// Network file: magic, channels, taps, delta, then W1 and W2 (FP32, host byte order).
+struct NetFileHeader {
+  char magic[8];
+  int32_t nc, taps;
+  double delta;
+};
+static const char kNetMagic[8] = {'H', 'D', 'L', 'N', 'E', 'T', '0', '1'};
+
+hd_status hd_learned_save(hd_handle h, const char* path) {
+  if (!h || !path) return HD_ERR_INVALID_ARG;
+  if (!h->net) return hd_fail(h, HD_ERR_INVALID_ARG, "learned preconditioner not initialised");
+  std::vector<float> w1(NC * NT), w2(NC * NC * NT);
+  hd_status st = hd_learned_get_weights(h, w1.data(), w2.data());
+  if (st != HD_OK) return st;
+  NetFileHeader hd{};
+  std::memcpy(hd.magic, kNetMagic, sizeof hd.magic);
+  hd.nc = NC;
+  hd.taps = NT;
+  hd.delta = h->net->delta;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return hd_fail(h, HD_ERR_INVALID_ARG, std::string("learned save: cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof hd, 1, f) == 1 && std::fwrite(w1.data(), 4, w1.size(), f) == w1.size() &&
+            std::fwrite(w2.data(), 4, w2.size(), f) == w2.size();
+  ok = std::fclose(f) == 0 && ok;
+  return ok ? HD_OK : hd_fail(h, HD_ERR_INVALID_ARG, std::string("learned save: write failed: ") + path);
+}
+
+hd_status hd_learned_load(hd_handle h, const char* path) {
+  if (!h || !path) return HD_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return hd_fail(h, HD_ERR_INVALID_ARG, std::string("learned load: cannot open ") + path);
+  NetFileHeader hd{};
+  std::vector<float> w1(NC * NT), w2(NC * NC * NT);
+  std::string err;
+  if (std::fread(&hd, sizeof hd, 1, f) != 1 || std::memcmp(hd.magic, kNetMagic, sizeof hd.magic) != 0)
+    err = "not a learned-preconditioner file";
+  else if (hd.nc != NC || hd.taps != NT || !(hd.delta >= 0))
+    err = "network of another shape";
+  else if (std::fread(w1.data(), 4, w1.size(), f) != w1.size() || std::fread(w2.data(), 4, w2.size(), f) != w2.size())
+    err = "truncated file";
+  else if (std::fgetc(f) != EOF)
+    err = "trailing bytes after the weights";
+  std::fclose(f);
+  if (!err.empty()) return hd_fail(h, HD_ERR_INVALID_ARG, "learned load: " + err + ": " + path);
+  hd_status st = HD_OK;
+  if (!h->net || h->net->delta != hd.delta) st = hd_learned_init(h, NC, 0, hd.delta);
+  if (st != HD_OK) return st;
+  return hd_learned_set_weights(h, w1.data(), w2.data());
 }
 
 }  // extern "C"
