@@ -14,8 +14,9 @@ defining sparse product, and MINRES in FP64. It shares no code with the CUDA pat
 Modules
   basis1d   1D Gauss-Lobatto / Gauss-Legendre points, Lagrange interpolation and
             histopolation bases (Sec. 2.1).
-  lattice   global numbering of the refined (subcell) lattice, the signed
-            element-to-dof map and essential dofs (Algorithm 1's arrays).
+  lattice   global numbering of the refined (subcell) lattice, the 24 element
+            rotations, the signed element-to-dof maps, essential dofs and the
+            divergence by Algorithm 1.
   element   reference RT/L2 bases, trilinear geometry, Piola maps and element
             matrices M_e, W_e, B_e by full quadrature (Eq. matrices).
   assembly  global CSR M, D, W^{-1}; the transformed block operator (Eq.

@@ -17,6 +17,10 @@ Essential (u.n prescribed) RT dofs are eliminated as a constrained identity: the
 rows and columns of M and the columns of D belonging to them are dropped and the
 diagonal of AA is 1 there, so (AA x)_ess = x_ess.
 
+Elements may carry rotation codes (oracle.lattice): element matrices are then
+computed in each element's own reference frame and assembled through the rotated
+signed maps, and D is built by Algorithm 1 from those maps.
+
 Everything is assembled with scipy.sparse from element matrices computed by full
 quadrature (oracle.element); (2,2) blocks use dense per-element inverses
 (numpy.linalg.inv). This is the plain definition; it is slow by design.
@@ -25,7 +29,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import element
-from .lattice import Lattice
+from .lattice import Lattice, algorithm1_divergence
 
 GRAD_DIV, DARCY = 0, 1
 
@@ -39,8 +43,9 @@ class Problem:
     """A discretised grad-div or Darcy problem on a structured hex mesh."""
 
     def __init__(self, nx, ny, nz, k, vx, vy, vz, coef0, coef1, kind=GRAD_DIV,
-                 ess_mask=0, q=None, affine=False, batch=64):
+                 ess_mask=0, q=None, affine=False, batch=64, rot=None):
         self.lat = Lattice(nx, ny, nz, k)
+        self.rot = None if rot is None else np.asarray(rot, dtype=np.int64)
         self.k, self.kind = k, kind
         self.q = default_q(k, affine) if q is None else q
         self.vx, self.vy, self.vz = (np.asarray(v, dtype=np.float64) for v in (vx, vy, vz))
@@ -63,9 +68,12 @@ class Problem:
         lat, k, q = self.lat, self.k, self.q
         E = lat.n_elem
         nloc, wloc = lat.n_rt_loc, lat.n_l2_loc
-        self.e2d = lat.e2d_map()
-        self.e2l = lat.e2l2_map()
+        self.e2d = lat.e2d_map(self.rot)
+        self.e2l = lat.e2l2_map(self.rot)
         V = element.element_vertices(lat.nx, lat.ny, lat.nz, self.vx, self.vy, self.vz)
+        if self.rot is not None:
+            V = element.rotate_vertices(V, self.rot)
+        self.V = V
         Me = np.zeros((E, nloc, nloc))
         We = np.zeros((E, wloc, wloc))           # unweighted or alpha-weighted L2 mass
         Ce = np.zeros((E, wloc, wloc))           # the (2,2) block C (AA has -C)
@@ -93,8 +101,12 @@ class Problem:
         M = sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())),
                           shape=(lat.n_rt, lat.n_rt)).tocsr()
         self.M_full = M
-        r, c, v = lat.divergence_incidence()
-        self.D_full = sp.coo_matrix((v, (r, c)), shape=(lat.n_l2, lat.n_rt)).tocsr()
+        if self.rot is None:
+            r, c, v = lat.divergence_incidence()
+            self.D_full = sp.coo_matrix((v, (r, c)), shape=(lat.n_l2, lat.n_rt)).tocsr()
+        else:
+            ip, ix, dv = algorithm1_divergence(lat, self.e2d, self.e2l)
+            self.D_full = sp.csr_matrix((dv, ix, ip), shape=(lat.n_l2, lat.n_rt))
         # constrained versions: drop essential rows/cols of M, essential cols of D
         Pf = sp.diags(self.free.astype(np.float64))
         Pe = sp.diags((~self.free).astype(np.float64))

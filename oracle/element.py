@@ -21,7 +21,7 @@ no sum factorisation.
 """
 import numpy as np
 
-from . import basis1d
+from . import basis1d, lattice
 
 
 def element_vertices(nx, ny, nz, vx, vy, vz, elems=None):
@@ -41,6 +41,24 @@ def element_vertices(nx, ny, nz, vx, vy, vz, elems=None):
                 V[:, c, b, a, 1] = vy[vid]
                 V[:, c, b, a, 2] = vz[vid]
     return V
+
+
+def rotate_vertices(V, rot):
+    """Corner coordinates V[e, c, b, a, dim] in each element's own reference frame:
+    with the rotation code rot[e] (oracle.lattice), the reference corner (a, b, c)
+    is the lattice-aligned corner eta = 1/2 + R ((a, b, c) - 1/2), so the element's
+    trilinear map is the lattice-aligned one composed with xi -> eta."""
+    out = np.empty_like(V)
+    for e in range(V.shape[0]):
+        perm, sgn = lattice.rotation(int(rot[e]))
+        for c in range(2):
+            for b in range(2):
+                for a in range(2):
+                    eta = [0, 0, 0]
+                    for d, t in enumerate((a, b, c)):
+                        eta[perm[d]] = t if sgn[d] > 0 else 1 - t
+                    out[e, c, b, a] = V[e, eta[2], eta[1], eta[0]]
+    return out
 
 
 def quad_rule(q):

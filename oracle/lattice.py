@@ -21,11 +21,57 @@ local and global orientations) but not a convention; this module fixes one:
 
 The signed map stores the global id g where the local and global orientations
 agree and ~g = -1-g where they are opposite (sigma_loc * sigma_glob of
-Algorithm 1). On this lattice all elements are unrotated, so every sign is +1.
+Algorithm 1).
+
+Element rotations. An element's reference axes need not be the lattice axes:
+its reference cube may be placed by any of the 24 proper symmetries R of the
+cube, xi -> eta = 1/2 + R (xi - 1/2) (eta: the lattice-aligned coordinates of
+the element). R sends reference axis d to lattice axis perm[d] with sign
+sgn[d]; a node index t in [0, k] along axis d becomes t or k - t, an interval
+index t in [0, k) becomes t or k - 1 - t, and the RT basis function of
+reference component d has the orientation sgn[d] against the global +axis
+(the Piola map u = J u_hat / det J with J = J_lattice R). The rotation code is
+4 p + t: p indexes the 6 permutations of (0, 1, 2) in lexicographic order, t the
+4 sign patterns with det R = +1 in increasing order of the bit pattern
+[sgn0 < 0] + 2 [sgn1 < 0] + 4 [sgn2 < 0]; code 0 is the identity.
 """
+import itertools
+
 import numpy as np
 
 SIDE_X0, SIDE_X1, SIDE_Y0, SIDE_Y1, SIDE_Z0, SIDE_Z1 = 1, 2, 4, 8, 16, 32
+
+
+def _parity(perm):
+    inv = sum(1 for a in range(3) for b in range(a + 1, 3) if perm[a] > perm[b])
+    return -1 if inv % 2 else 1
+
+
+def rotation(code):
+    """(perm, sgn) of the cube symmetry with the given code (module doc)."""
+    if not 0 <= code < 24:
+        raise ValueError("rotation code must be in 0..23")
+    perm = list(itertools.permutations(range(3)))[code // 4]
+    pats = []
+    for bits in range(8):
+        sgn = tuple(-1 if bits >> d & 1 else 1 for d in range(3))
+        if _parity(perm) * sgn[0] * sgn[1] * sgn[2] == 1:
+            pats.append(sgn)
+    return perm, pats[code % 4]
+
+
+def rotation_matrix(code):
+    """R with R e_d = sgn[d] e_perm[d] (columns are the images of the reference axes)."""
+    perm, sgn = rotation(code)
+    R = np.zeros((3, 3))
+    for d in range(3):
+        R[perm[d], d] = sgn[d]
+    return R
+
+
+def _to_lattice(t, s, n):
+    """Index t along a reference axis with sign s, on an axis of n positions."""
+    return t if s > 0 else n - 1 - t
 
 
 class Lattice:
@@ -84,34 +130,69 @@ class Lattice:
         ez = e // (self.nx * self.ny)
         return ex, ey, ez
 
-    def e2d_map(self):
-        """Signed element-to-RT-dof map, shape (E, 3(k+1)k^2), int64."""
+    def local_to_lattice(self, rot, idx, node_axis):
+        """Lattice-aligned indices (along x, y, z) of the local subcell entity with
+        reference indices idx; idx[node_axis] is a node index in [0, k] (an RT face)
+        and the others interval indices in [0, k); node_axis None for a cell."""
+        perm, sgn = rotation(rot)
+        k = self.k
+        L = [0, 0, 0]
+        for c in range(3):
+            n = k + 1 if c == node_axis else k
+            L[perm[c]] = _to_lattice(idx[c], sgn[c], n)
+        return L
+
+    def e2d_map(self, rot=None):
+        """Signed element-to-RT-dof map, shape (E, 3(k+1)k^2), int64; rot: rotation
+        code per element (None: all 0)."""
         k = self.k
         loc = self.local_rt()
+        rot = np.zeros(self.n_elem, dtype=np.int64) if rot is None else np.asarray(rot)
+        face = (self.xface, self.yface, self.zface)
         m = np.zeros((self.n_elem, len(loc)), dtype=np.int64)
         for e in range(self.n_elem):
             ex, ey, ez = self.elem_coords(e)
-            ox, oy, oz = ex * k, ey * k, ez * k
+            perm, sgn = rotation(int(rot[e]))
             for n, (d, i, j, l) in enumerate(loc):
-                if d == 0:
-                    g = self.xface(ox + i, oy + j, oz + l)
-                elif d == 1:
-                    g = self.yface(ox + i, oy + j, oz + l)
-                else:
-                    g = self.zface(ox + i, oy + j, oz + l)
-                m[e, n] = g  # orientation +1 everywhere on an unrotated lattice
+                L = self.local_to_lattice(int(rot[e]), (i, j, l), d)
+                g = face[perm[d]](ex * k + L[0], ey * k + L[1], ez * k + L[2])
+                m[e, n] = g if sgn[d] > 0 else -1 - g
         return m
 
-    def e2l2_map(self):
-        """Element-to-L2-dof map, shape (E, k^3)."""
+    def e2l2_map(self, rot=None):
+        """Element-to-L2-dof map, shape (E, k^3); rot as for e2d_map."""
         k = self.k
         loc = self.local_l2()
+        rot = np.zeros(self.n_elem, dtype=np.int64) if rot is None else np.asarray(rot)
         m = np.zeros((self.n_elem, len(loc)), dtype=np.int64)
         for e in range(self.n_elem):
             ex, ey, ez = self.elem_coords(e)
             for n, (a, b, c) in enumerate(loc):
-                m[e, n] = self.cell(ex * k + a, ey * k + b, ez * k + c)
+                L = self.local_to_lattice(int(rot[e]), (a, b, c), None)
+                m[e, n] = self.cell(ex * k + L[0], ey * k + L[1], ez * k + L[2])
         return m
+
+    def volume_to_face(self):
+        """For each local L2 dof, its 2d local subcell faces as (local RT id, sigma_loc):
+        the low then the high face along reference axes 0, 1, 2; sigma_loc = -1 on the
+        low face (the basis function points into the subcell) and +1 on the high face."""
+        k = self.k
+        off = (0, (k + 1) * k * k, 2 * (k + 1) * k * k)
+        out = []
+        for (a, b, c) in self.local_l2():
+            faces = []
+            for d in range(3):
+                for hi in (0, 1):
+                    i, j, l = a + (hi if d == 0 else 0), b + (hi if d == 1 else 0), c + (hi if d == 2 else 0)
+                    if d == 0:
+                        jl = off[0] + i + (k + 1) * (j + k * l)
+                    elif d == 1:
+                        jl = off[1] + i + k * (j + (k + 1) * l)
+                    else:
+                        jl = off[2] + i + k * (j + k * l)
+                    faces.append((jl, 1 if hi else -1))
+            out.append(faces)
+        return out
 
     def ess_dofs(self, side_mask):
         """Ascending global ids of the RT dofs on the domain sides in side_mask."""
@@ -152,3 +233,32 @@ class Lattice:
             cols += [lo, hi]
             vals += [-np.ones(len(c)), np.ones(len(c))]
         return np.concatenate(rows), np.concatenate(cols), np.concatenate(vals)
+
+
+def algorithm1_divergence(lat, e2d, e2l):
+    """The discrete divergence D in CSR form by Algorithm 1 (Sec. 3.2): row i (an L2
+    dof, a subcell volume) has 2d = 6 entries at I[i] = 6 i; for each subcell face of
+    the volume, the local RT dof j_loc and its reference orientation sigma_loc, the
+    global dof j and the orientation sigma_glob of j relative to j_loc (both read from
+    the signed map), and the entry sigma_loc * sigma_glob. element_map and
+    l2_global_to_local are the inverse of the element-to-L2 map e2l.
+    Returns (indptr, indices, data)."""
+    N = lat.n_l2
+    element_map = np.zeros(N, dtype=np.int64)
+    l2_global_to_local = np.zeros(N, dtype=np.int64)
+    for e in range(e2l.shape[0]):
+        for a in range(e2l.shape[1]):
+            element_map[e2l[e, a]] = e
+            l2_global_to_local[e2l[e, a]] = a
+    v2f = lat.volume_to_face()
+    indptr = 6 * np.arange(N + 1, dtype=np.int64)
+    indices = np.zeros(6 * N, dtype=np.int64)
+    data = np.zeros(6 * N)
+    for i in range(N):
+        e, iloc = element_map[i], l2_global_to_local[i]
+        for f, (jloc, sigma_loc) in enumerate(v2f[iloc]):
+            s = e2d[e, jloc]
+            j, sigma_glob = (s, 1) if s >= 0 else (-1 - s, -1)
+            indices[6 * i + f] = j
+            data[6 * i + f] = sigma_loc * sigma_glob
+    return indptr, indices, data

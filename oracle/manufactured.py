@@ -34,7 +34,7 @@ def rt_load(prob, f_fn, qf=None):
     lat, k = prob.lat, prob.k
     qf = k + 2 if qf is None else qf
     pts, w = element.quad_rule(qf)
-    V = element.element_vertices(lat.nx, lat.ny, lat.nz, prob.vx, prob.vy, prob.vz)
+    V = prob.V
     J = element.jacobian(V, pts)
     Xp = element.physical_points(V, pts)
     Phi, _ = element.rt_basis(k, pts)
@@ -52,7 +52,7 @@ def l2_errors(prob, u_h, q_h, u_fn, qe=None):
     lat, k = prob.lat, prob.k
     qe = k + 3 if qe is None else qe
     pts, w = element.quad_rule(qe)
-    V = element.element_vertices(lat.nx, lat.ny, lat.nz, prob.vx, prob.vy, prob.vz)
+    V = prob.V
     J = element.jacobian(V, pts)
     detJ = np.linalg.det(J)
     Xp = element.physical_points(V, pts)
