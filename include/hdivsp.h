@@ -127,6 +127,14 @@ typedef struct {
                             unsmoothed hierarchy for its coarse correction. */
   int32_t w_levels;      /* with cycle = 2: the two coarse corrections are made on levels
                             0..w_levels-1 only, one below (0: on every level); >= 0 */
+  const int8_t* elem_rotation; /* NULL (every element lattice-aligned) or n_elem rotation codes
+                            0..23: element e places its reference cube by that proper symmetry
+                            of the cube (Algorithm 1's local orientations; code convention at
+                            hd_lattice_e2d_map_rot). The global RT and L2 bases, hence every
+                            operator, do not depend on the codes: the kernels compute each
+                            element in its lattice-aligned frame, and the codes shape only the
+                            element-local numbering and signs of hd_get_e2d_map and
+                            hd_get_e2l_map. A code outside 0..23: HD_ERR_INVALID_ARG. */
 } hd_problem_desc;
 
 /* MINRES options and report (Sec. 3). */
@@ -198,6 +206,10 @@ hd_status hd_get_setup_times(hd_handle h, double* ms, int32_t n);
  * i + (k+1)(j + k l), then y-component i + k (j + (k+1) l), then z-component
  * i + k (j + k l). */
 hd_status hd_get_e2d_map(hd_handle h, int32_t* host_out);
+/* Element-to-L2-dof map (Algorithm 1's element_map and l2_global_to_local, inverted):
+ * host_out has n_elem * k^3 int32 entries, row e lists the lattice cell id of each
+ * local L2 dof a + k (b + k c) of element e in its own (possibly rotated) frame. */
+hd_status hd_get_e2l_map(hd_handle h, int32_t* host_out);
 /* Essential RT dofs in ascending order; *n in: capacity of host_out, out: count
  * (host_out may be NULL to query the count). */
 hd_status hd_get_ess_dofs(hd_handle h, int64_t* host_out, int64_t* n);
@@ -207,6 +219,22 @@ hd_status hd_get_ess_dofs(hd_handle h, int64_t* host_out, int64_t* n);
  * essential dofs (hd_lattice_ess_dofs; *n out: count; out may be NULL).
  * Return HD_ERR_INVALID_ARG on bad sizes or when the id range exceeds int32. */
 hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out);
+/* The same maps for rotated elements (Algorithm 1 with non-trivial sigma_loc * sigma_glob).
+ * rot: NULL or nx*ny*nz codes 0..23 (host). Element e with code r maps its reference
+ * coordinates xi to the lattice-aligned ones eta = 1/2 + R (xi - 1/2), where R sends
+ * reference axis d to lattice axis perm[d] with sign sgn[d]; r = 4 p + t, p the index of
+ * perm among the 6 permutations of (0,1,2) in lexicographic order, t the index of sgn
+ * among the 4 sign patterns with det R = +1, in increasing order of
+ * [sgn0 < 0] + 2 [sgn1 < 0] + 4 [sgn2 < 0] (r = 0: identity). Along reference axis d
+ * a node index t in [0,k] becomes t or k - t and an interval index t in [0,k) becomes t
+ * or k - 1 - t (sgn[d] = +1 or -1); the RT dofs of reference component d lie on the
+ * faces normal to lattice axis perm[d] and carry the orientation sgn[d] (stored as
+ * -1-g when it is -1). hd_lattice_e2l_map writes nx*ny*nz * k^3 cell ids, local order
+ * a + k (b + k c). A code outside 0..23 or bad sizes: HD_ERR_INVALID_ARG. */
+hd_status hd_lattice_e2d_map_rot(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot,
+                                 int32_t* out);
+hd_status hd_lattice_e2l_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot,
+                             int32_t* out);
 hd_status hd_lattice_ess_dofs(int32_t nx, int32_t ny, int32_t nz, int32_t k, uint32_t ess_mask,
                               int64_t* out, int64_t* n);
 

@@ -40,7 +40,7 @@ class ProblemDesc(ctypes.Structure):
                 ("affine", ctypes.c_int32), ("tau", ctypes.c_double), ("winv_mode", ctypes.c_int32),
                 ("nu", ctypes.c_int32), ("coarse_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
                 ("fp64_emulation", ctypes.c_int32), ("smooth_levels", ctypes.c_int32),
-                ("w_levels", ctypes.c_int32)]
+                ("w_levels", ctypes.c_int32), ("elem_rotation", ctypes.POINTER(ctypes.c_int8))]
 
 
 class SolveOpts(ctypes.Structure):
@@ -84,6 +84,9 @@ _SIGS = {
     "hd_get_e2d_map": [_H, _VP],
     "hd_get_ess_dofs": [_H, _VP, ctypes.POINTER(ctypes.c_int64)],
     "hd_lattice_e2d_map": [ctypes.c_int32] * 4 + [_VP],
+    "hd_lattice_e2d_map_rot": [ctypes.c_int32] * 4 + [_VP, _VP],
+    "hd_lattice_e2l_map": [ctypes.c_int32] * 4 + [_VP, _VP],
+    "hd_get_e2l_map": [_H, _VP],
     "hd_lattice_ess_dofs": [ctypes.c_int32] * 4 + [ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int64)],
     "hd_apply_A": [_H, _VP, _VP],
     "hd_apply_B": [_H, _VP, _VP],
@@ -166,6 +169,32 @@ def hd_lattice_e2d_map(nx, ny, nz, k):
     return out
 
 
+def _rot_codes(rot, E):
+    """Rotation codes as a contiguous int8 array of length E (None stays None)."""
+    if rot is None:
+        return None
+    r = np.ascontiguousarray(rot, dtype=np.int64)
+    if r.shape != (E,):
+        raise ValueError("elem_rotation needs one code per element")
+    if (r < -128).any() or (r > 127).any():
+        raise ValueError("rotation codes must fit int8 (valid codes: 0..23)")
+    return np.ascontiguousarray(r.astype(np.int8))
+
+
+def hd_lattice_e2d_map_rot(nx, ny, nz, k, rot):
+    rot = _rot_codes(rot, nx * ny * nz)
+    out = np.zeros((nx * ny * nz, 3 * (k + 1) * k * k), dtype=np.int32)
+    _check(lib().hd_lattice_e2d_map_rot(nx, ny, nz, k, _ptr(rot), out.ctypes.data))
+    return out
+
+
+def hd_lattice_e2l_map(nx, ny, nz, k, rot=None):
+    rot = _rot_codes(rot, nx * ny * nz)
+    out = np.zeros((nx * ny * nz, k ** 3), dtype=np.int32)
+    _check(lib().hd_lattice_e2l_map(nx, ny, nz, k, _ptr(rot), out.ctypes.data))
+    return out
+
+
 def hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask):
     n = ctypes.c_int64(0)
     _check(lib().hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask, None, ctypes.byref(n)))
@@ -179,9 +208,11 @@ class Operator:
 
     def __init__(self, nx, ny, nz, k, vx, vy, vz, coef0, coef1, kind=HD_GRAD_DIV, ess_mask=0, q=0,
                  affine=False, tau=0.0, winv_mode=HD_WINV_DENSE, nu=0, coarse_max=0, cycle=1,
-                 fp64_emulation=0, smooth_levels=0, w_levels=0, stream=None):
+                 fp64_emulation=0, smooth_levels=0, w_levels=0, elem_rotation=None, stream=None):
         E = nx * ny * nz
         self._keep = []
+        rot = _rot_codes(elem_rotation, E)
+        self._keep.append(rot)
         arrs = []
         for a, n in ((vx, None), (vy, None), (vz, None), (coef0, E), (coef1, E)):
             a = np.asarray(a, dtype=np.float64)
@@ -192,7 +223,8 @@ class Operator:
             arrs.append(p)
         d = ProblemDesc(kind, nx, ny, nz, k, q, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], ess_mask,
                         int(affine), tau, winv_mode, nu, coarse_max, cycle, int(fp64_emulation),
-                        int(smooth_levels), int(w_levels))
+                        int(smooth_levels), int(w_levels),
+                        None if rot is None else rot.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
         h = ctypes.c_void_p()
         st = lib().hd_create(ctypes.byref(d), ctypes.byref(h))
         _check(st)
@@ -265,6 +297,11 @@ class Operator:
     def hd_get_e2d_map(self):
         out = np.zeros((self.n_elem, 3 * (self.k + 1) * self.k ** 2), dtype=np.int32)
         _check(lib().hd_get_e2d_map(self.h, out.ctypes.data), self.h)
+        return out
+
+    def hd_get_e2l_map(self):
+        out = np.zeros((self.n_elem, self.k ** 3), dtype=np.int32)
+        _check(lib().hd_get_e2l_map(self.h, out.ctypes.data), self.h)
         return out
 
     def hd_get_ess_dofs(self):

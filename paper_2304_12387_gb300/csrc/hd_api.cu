@@ -263,6 +263,14 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   if (d->k < 2 || d->k > HD_MAXK) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
   if (!d->vx || !d->vy || !d->vz || !d->coef0 || !d->coef1) { delete h; return HD_ERR_INVALID_ARG; }
   if (d->ess_mask > 63) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->elem_rotation) {
+    // codes only renumber element-local dofs: kept for the exported maps
+    const int64_t E = (int64_t)d->nx * d->ny * d->nz;
+    for (int64_t e = 0; e < E; ++e)
+      if (d->elem_rotation[e] < 0 || d->elem_rotation[e] > 23) { delete h; return HD_ERR_INVALID_ARG; }
+    h->rot.assign(d->elem_rotation, d->elem_rotation + E);
+  }
+  h->desc.elem_rotation = nullptr;   // the caller's array is only read here
   h->kind = d->kind;
   h->k = d->k;
   h->q = d->q ? d->q : (d->affine ? d->k + 1 : d->k + 2);
@@ -426,31 +434,94 @@ hd_status hd_get_sizes(hd_handle h, int64_t* n_rt, int64_t* n_l2, int64_t* n_ele
   return HD_OK;
 }
 
-hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out) {
-  if (!out || nx < 1 || ny < 1 || nz < 1 || k < 1) return HD_ERR_INVALID_ARG;
+// Rotation code r = 4 p + t of a proper cube symmetry: perm = the p-th permutation of
+// (0,1,2) in lexicographic order; sgn = the t-th of the sign patterns with
+// parity(perm) * sgn0 * sgn1 * sgn2 = +1, counted in increasing order of the bit
+// pattern [sgn0 < 0] + 2 [sgn1 < 0] + 4 [sgn2 < 0].
+static void cube_rotation(int r, int perm[3], int sgn[3]) {
+  static const int kPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  static const int kParity[6] = {1, -1, -1, 1, 1, -1};
+  const int p = r / 4, t = r % 4;
+  for (int d = 0; d < 3; ++d) perm[d] = kPerm[p][d];
+  int seen = 0;
+  for (int bits = 0; bits < 8; ++bits) {
+    const int s0 = (bits & 1) ? -1 : 1, s1 = (bits & 2) ? -1 : 1, s2 = (bits & 4) ? -1 : 1;
+    if (kParity[p] * s0 * s1 * s2 != 1) continue;
+    if (seen++ == t) {
+      sgn[0] = s0; sgn[1] = s1; sgn[2] = s2;
+      return;
+    }
+  }
+}
+
+static bool lattice_sizes_ok(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot) {
+  if (nx < 1 || ny < 1 || nz < 1 || k < 1) return false;
   const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k, Z = (int64_t)nz * k;
-  const int64_t nxf = (X + 1) * Y * Z, nyf = X * (Y + 1) * Z, nzf = X * Y * (Z + 1);
-  if (nxf + nyf + nzf >= ((int64_t)1 << 31)) return HD_ERR_INVALID_ARG;
+  if ((X + 1) * Y * Z + X * (Y + 1) * Z + X * Y * (Z + 1) >= ((int64_t)1 << 31)) return false;
+  if (rot)
+    for (int64_t e = 0, E = (int64_t)nx * ny * nz; e < E; ++e)
+      if (rot[e] < 0 || rot[e] > 23) return false;
+  return true;
+}
+
+hd_status hd_lattice_e2d_map_rot(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot,
+                                 int32_t* out) {
+  if (!out || !lattice_sizes_ok(nx, ny, nz, k, rot)) return HD_ERR_INVALID_ARG;
+  const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k, Z = (int64_t)nz * k;
+  const int64_t nxf = (X + 1) * Y * Z, nyf = X * (Y + 1) * Z;
   const int nloc = 3 * (k + 1) * k * k;
   const int64_t E = (int64_t)nx * ny * nz;
   for (int64_t e = 0; e < E; ++e) {
-    int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
+    const int64_t org[3] = {(e % nx) * k, ((e / nx) % ny) * k, (e / ((int64_t)nx * ny)) * k};
+    int perm[3], sgn[3];
+    cube_rotation(rot ? rot[e] : 0, perm, sgn);
     int32_t* row = out + e * nloc;
     int n = 0;
-    for (int l = 0; l < k; ++l)
-      for (int j = 0; j < k; ++j)
-        for (int i = 0; i <= k; ++i) row[n++] = (int32_t)((ex * k + i) + (X + 1) * ((ey * k + j) + Y * (ez * k + l)));
-    for (int l = 0; l < k; ++l)
-      for (int j = 0; j <= k; ++j)
-        for (int i = 0; i < k; ++i)
-          row[n++] = (int32_t)(nxf + (ex * k + i) + X * ((ey * k + j) + (Y + 1) * (ez * k + l)));
-    for (int l = 0; l <= k; ++l)
-      for (int j = 0; j < k; ++j)
-        for (int i = 0; i < k; ++i)
-          row[n++] = (int32_t)(nxf + nyf + (ex * k + i) + X * ((ey * k + j) + Y * (ez * k + l)));
-    // every element is unrotated: local and global orientation agree (sign +1)
+    for (int d = 0; d < 3; ++d) {          // reference component d: node index along axis d
+      int ext[3] = {k, k, k};
+      ext[d] = k + 1;
+      for (int t2 = 0; t2 < ext[2]; ++t2)
+        for (int t1 = 0; t1 < ext[1]; ++t1)
+          for (int t0 = 0; t0 < ext[0]; ++t0) {
+            const int t[3] = {t0, t1, t2};
+            int64_t L[3];
+            for (int c = 0; c < 3; ++c) L[perm[c]] = org[perm[c]] + (sgn[c] > 0 ? t[c] : ext[c] - 1 - t[c]);
+            int64_t g;
+            if (perm[d] == 0) g = L[0] + (X + 1) * (L[1] + Y * L[2]);
+            else if (perm[d] == 1) g = nxf + L[0] + X * (L[1] + (Y + 1) * L[2]);
+            else g = nxf + nyf + L[0] + X * (L[1] + Y * L[2]);
+            row[n++] = (int32_t)(sgn[d] > 0 ? g : -1 - g);
+          }
+    }
   }
   return HD_OK;
+}
+
+hd_status hd_lattice_e2l_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot, int32_t* out) {
+  if (!out || !lattice_sizes_ok(nx, ny, nz, k, rot)) return HD_ERR_INVALID_ARG;
+  const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k;
+  const int64_t E = (int64_t)nx * ny * nz;
+  const int nloc = k * k * k;
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t org[3] = {(e % nx) * k, ((e / nx) % ny) * k, (e / ((int64_t)nx * ny)) * k};
+    int perm[3], sgn[3];
+    cube_rotation(rot ? rot[e] : 0, perm, sgn);
+    int32_t* row = out + e * nloc;
+    int n = 0;
+    for (int c2 = 0; c2 < k; ++c2)
+      for (int c1 = 0; c1 < k; ++c1)
+        for (int c0 = 0; c0 < k; ++c0) {
+          const int t[3] = {c0, c1, c2};
+          int64_t L[3];
+          for (int c = 0; c < 3; ++c) L[perm[c]] = org[perm[c]] + (sgn[c] > 0 ? t[c] : k - 1 - t[c]);
+          row[n++] = (int32_t)(L[0] + X * (L[1] + Y * L[2]));
+        }
+  }
+  return HD_OK;
+}
+
+hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out) {
+  return hd_lattice_e2d_map_rot(nx, ny, nz, k, nullptr, out);
 }
 
 hd_status hd_lattice_ess_dofs(int32_t nx, int32_t ny, int32_t nz, int32_t k, uint32_t m, int64_t* out, int64_t* n) {
@@ -482,7 +553,12 @@ hd_status hd_lattice_ess_dofs(int32_t nx, int32_t ny, int32_t nz, int32_t k, uin
 
 hd_status hd_get_e2d_map(hd_handle h, int32_t* out) {
   if (!h || !out) return HD_ERR_INVALID_ARG;
-  return hd_lattice_e2d_map(h->L.nx, h->L.ny, h->L.nz, h->k, out);
+  return hd_lattice_e2d_map_rot(h->L.nx, h->L.ny, h->L.nz, h->k, h->rot.empty() ? nullptr : h->rot.data(), out);
+}
+
+hd_status hd_get_e2l_map(hd_handle h, int32_t* out) {
+  if (!h || !out) return HD_ERR_INVALID_ARG;
+  return hd_lattice_e2l_map(h->L.nx, h->L.ny, h->L.nz, h->k, h->rot.empty() ? nullptr : h->rot.data(), out);
 }
 
 hd_status hd_get_ess_dofs(hd_handle h, int64_t* out, int64_t* n) {

@@ -98,6 +98,7 @@ struct MinresState;  // device-side scalars of the MINRES recurrence
 struct hd_op {
   // problem
   hd_problem_desc desc;
+  std::vector<int8_t> rot;   // element rotation codes (empty: all lattice-aligned)
   int kind, k, q;
   LatticeDims L;
   int64_t n_rt, n_l2, n_elem;

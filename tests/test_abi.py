@@ -41,6 +41,28 @@ def test_e2d_map_bit_exact(dims, k):
     assert np.array_equal(got.astype(np.int64), ref)
 
 
+@pytest.mark.parametrize("dims,k", [((1, 1, 1), 2), ((2, 3, 1), 3), ((3, 2, 2), 4), ((1, 2, 1), 5)])
+def test_rotated_maps_bit_exact(dims, k):
+    """Algorithm 1's signed maps for rotated elements: every one of the 24 codes."""
+    lat = Lattice(*dims, k)
+    E = lat.n_elem
+    for shift in range(0, 24, E):
+        rot = (np.arange(E) + shift) % 24
+        got = hd.hd_lattice_e2d_map_rot(*dims, k, rot)
+        assert np.array_equal(got.astype(np.int64), lat.e2d_map(rot))
+        got = hd.hd_lattice_e2l_map(*dims, k, rot)
+        assert np.array_equal(got.astype(np.int64), lat.e2l2_map(rot))
+    assert np.array_equal(hd.hd_lattice_e2l_map(*dims, k).astype(np.int64), lat.e2l2_map())
+
+
+def test_bad_rotation_codes_are_rejected():
+    for bad in (24, -1, 100):
+        with pytest.raises(hd.HdError):
+            hd.hd_lattice_e2d_map_rot(2, 1, 1, 2, [0, bad])
+        with pytest.raises(hd.HdError):
+            hd.hd_lattice_e2l_map(2, 1, 1, 2, [bad, 3])
+
+
 @pytest.mark.parametrize("mask", [0, 1, 2, 5, 12, 48, 63, 42])
 def test_ess_dofs_bit_exact(mask):
     lat = Lattice(3, 2, 2, 3)
