@@ -78,6 +78,25 @@ def elem_flops(k, q):
     return 2 * macs + 6 * K ** 3 + 3 * nrt + K ** 3
 
 
+def elem_flops_affine(k, q):
+    """The same count for the affine fast path: the geometric factor is one 3x3 matrix per
+    element scaled by w_p (the weight product and three scalings per point), and W_e^-1 is
+    det J (H^-1 x H^-1 x H^-1), three k x k contractions (3 k^4 MACs) and one scaling."""
+    K, Q = k, q
+    interp = (K * K * Q * (K + 1) + Q * K * Q * K + Q * Q * Q * K
+              + (K + 1) * K * Q * K + Q * K * Q * (K + 1) + Q * Q * Q * K
+              + K * (K + 1) * Q * K + Q * (K + 1) * Q * K + Q * Q * Q * (K + 1))
+    macs = 2 * interp + 9 * Q ** 3 + 3 * K ** 4
+    nrt = 3 * (K + 1) * K * K
+    return 2 * macs + 5 * Q ** 3 + K ** 3 + 6 * K ** 3 + 3 * nrt + K ** 3
+
+
+def elem_bytes_affine(n_elem, n_rt, n_l2):
+    """Algorithmic DRAM bytes of one affine fast-path apply: read x, write y and 8
+    doubles per element (the constant geometric factor and det J)."""
+    return 8 * (2 * (n_rt + n_l2) + 8 * n_elem)
+
+
 def roofline(op, nx, kern_ms, emulated):
     """Roofline object of the fused element kernel. FP64: bound by the FP64 pipe
     ("alu", peak derived from the unit count and the maximum clock). Double-float:
@@ -266,11 +285,15 @@ def affine_apply(args, stream):
     launches, kms = op.hd_profile_read()
     ms = e0.elapsed_time(e1) / steps
     kern_ms = kms / max(1, launches)
-    abytes = elem_bytes(K, q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3)
+    abytes = elem_bytes_affine(op.n_elem, op.n_rt, op.n_l2)
+    flops = elem_flops_affine(K, q) * op.n_elem
     r = {"workload": "M%d-affine: the same recipe on the unperturbed mesh, q=%d" % (nx, q),
          "value": op.n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms, "steps": steps,
+         "kernel": "k_elem_op<%s,double,%d,%d,8,affine>" % ("dfloat" if args.fp64_emulation else "double", K, q),
          "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
-         "hbm_frac_of_measured": abytes / (kern_ms * 1e-3) / 1e9 / HBM_GBS_MEASURED}
+         "element_data": "affine fast path: 64 B per element (constant geometric factor, det J)",
+         "hbm_frac_of_measured": abytes / (kern_ms * 1e-3) / 1e9 / HBM_GBS_MEASURED,
+         "fp64_equivalent_gflops": flops / (kern_ms * 1e-3) / 1e9}
     op.close()
     return r
 

@@ -125,6 +125,75 @@ void build_tables(int k, int q, ElemTables& t) {
       for (size_t i = 0; i < gs.size(); ++i) s += ws[i] * lag(gk, m, a + (b - a) * gs[i]);
       t.TT[j * k + m] = (b - a) * s;
     }
+  // 1D histopolation mass (exact: q >= k points for degree 2k-2) and its inverse by
+  // Gauss-Jordan elimination with partial pivoting
+  double A[HD_MAXK][2 * HD_MAXK];
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) {
+      double s = 0.0;
+      for (int p = 0; p < q; ++p) s += gw[p] * t.BH[p * k + a] * t.BH[p * k + b];
+      A[a][b] = s;
+      A[a][k + b] = a == b ? 1.0 : 0.0;
+    }
+  for (int c = 0; c < k; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < k; ++r)
+      if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+    for (int j = 0; j < 2 * k; ++j) std::swap(A[c][j], A[piv][j]);
+    const double d = A[c][c];
+    for (int j = 0; j < 2 * k; ++j) A[c][j] /= d;
+    for (int r = 0; r < k; ++r)
+      if (r != c) {
+        const double f = A[r][c];
+        for (int j = 0; j < 2 * k; ++j) A[r][j] -= f * A[c][j];
+      }
+  }
+  for (int a = 0; a < k; ++a)
+    for (int b = 0; b < k; ++b) t.HI[a * k + b] = A[a][k + b];
+}
+
+// Affine fast path: every element a parallelepiped (its trilinear map has no bilinear or
+// trilinear part, to 1e-14 of the element's edge length). Then J is constant, the
+// geometric factor at point p is w_p times one symmetric 3x3 matrix, and W_e^-1 =
+// det J (H^-1 x H^-1 x H^-1): 8 values per element instead of 6 q^3 + k^6. Fills
+// ga[E][8] and returns true, or returns false at the first element that is not affine.
+static bool affine_factors(const hd_problem_desc* d, const double* bco, std::vector<double>& ga) {
+  const int64_t nx = d->nx, ny = d->ny, nz = d->nz, E = nx * ny * nz;
+  ga.assign((size_t)E * 8, 0.0);
+  for (int64_t e = 0; e < E; ++e) {
+    const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / (nx * ny);
+    double v[8][3];
+    for (int c = 0; c < 8; ++c) {
+      const int64_t id = (ex + (c & 1)) + (nx + 1) * ((ey + ((c >> 1) & 1)) + (ny + 1) * (ez + (c >> 2)));
+      v[c][0] = d->vx[id]; v[c][1] = d->vy[id]; v[c][2] = d->vz[id];
+    }
+    double J[3][3], h = 0.0;  // J[i][a] = d x_i / d xi_a
+    for (int i = 0; i < 3; ++i) {
+      J[i][0] = v[1][i] - v[0][i];
+      J[i][1] = v[2][i] - v[0][i];
+      J[i][2] = v[4][i] - v[0][i];
+      for (int a = 0; a < 3; ++a) h = std::max(h, std::fabs(J[i][a]));
+    }
+    for (int i = 0; i < 3; ++i) {
+      const double t01 = v[3][i] - v[1][i] - v[2][i] + v[0][i], t02 = v[5][i] - v[1][i] - v[4][i] + v[0][i],
+                   t12 = v[6][i] - v[2][i] - v[4][i] + v[0][i],
+                   t012 = v[7][i] - v[3][i] - v[5][i] - v[6][i] + v[1][i] + v[2][i] + v[4][i] - v[0][i];
+      const double tol = 1e-14 * h;
+      if (std::fabs(t01) > tol || std::fabs(t02) > tol || std::fabs(t12) > tol || std::fabs(t012) > tol)
+        return false;
+    }
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    if (!(det > 0.0)) return false;
+    auto jtj = [&](int a, int b) { return J[0][a] * J[0][b] + J[1][a] * J[1][b] + J[2][a] * J[2][b]; };
+    const double f = bco[e] / det;
+    double* g = ga.data() + (size_t)e * 8;
+    g[0] = f * jtj(0, 0); g[1] = f * jtj(0, 1); g[2] = f * jtj(0, 2);
+    g[3] = f * jtj(1, 1); g[4] = f * jtj(1, 2); g[5] = f * jtj(2, 2);
+    g[6] = det;
+  }
+  return true;
 }
 
 hd_status dalloc(hd_op* h, double** p, int64_t n, const char* what) {
@@ -196,6 +265,7 @@ void destroy_all(hd_op* h) {
   cudaFree(h->d_wchol);
   cudaFree(h->f_wdet); cudaFree(h->f_wgldiag);
   cudaFree(h->x_G); cudaFree(h->x_winv); cudaFree(h->x_cscale);
+  cudaFree(h->d_Ga); cudaFree(h->x_Ga);
   cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
   cudaFree(h->d_coarse_inv); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
   cudaFree(h->f_G); cudaFree(h->f_winv); cudaFree(h->f_cscale); cudaFree(h->f_mtinv); cudaFree(h->f_coarse_inv);
@@ -373,6 +443,21 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     if (cudaStreamSynchronize(s) != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "setup"); break; }
     auto t_emul = std::chrono::steady_clock::now();
     h->setup_ms[3] = std::chrono::duration<float, std::milli>(t_emul - t_pre).count();
+    // the affine fast path of the FP64 and double-float applies (dense W^-1 mode, q = k+1)
+    std::vector<double> ga;
+    if (d->affine && h->q == k + 1 && h->winv_mode == HD_WINV_DENSE && E > 0 && affine_factors(d, bco.data(), ga)) {
+      if ((st = dalloc(h, &h->d_Ga, E * 8, "affine factors")) != HD_OK) break;
+      if (cudaMemcpyAsync(h->d_Ga, ga.data(), E * 64, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        st = hd_fail(h, HD_ERR_CUDA, "upload");
+        break;
+      }
+      if (h->emul) {
+        if (cudaMalloc(&h->x_Ga, sizeof(dfloat) * E * 8) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "affine factors"); break; }
+        k_split_df<<<(unsigned)((E * 8 + 255) / 256), 256, 0, s>>>(E * 8, h->d_Ga, h->x_Ga);
+      }
+      // ga is read by the copy above: wait before it goes out of scope
+      if (cudaStreamSynchronize(s) != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "affine factors"); break; }
+    }
     if (h->emul) {
       const int64_t ng = E * 6 * nq, nw = E * nl2 * nl2;
       if (cudaMalloc(&h->x_G, sizeof(dfloat) * (ng > 0 ? ng : 1)) != cudaSuccess ||

@@ -26,6 +26,8 @@ struct ElemTables {
                                        //   nodes (the nodal basis of the local CG) at the q points
   double TT[HD_MAXK * HD_MAXK];        // TT[j*k+m] = integral of L_m over subcell j: GL-nodal
                                        //   coefficients -> histopolation coefficients
+  double HI[HD_MAXK * HD_MAXK];        // inverse of the 1D histopolation mass H[a][b] = int h_a h_b
+                                       //   (affine elements: W_e^-1 = det J  HI x HI x HI)
 };
 
 // Mesh/lattice constants passed to kernels.
@@ -125,6 +127,8 @@ struct hd_op {
   double* d_wdiag = nullptr;    // [E][k^3] diag(W_e) (unweighted)
   double* d_wgldiag = nullptr;  // [E][k^3] diag of W_e in the GL nodal basis (local CG)
   double* d_wchol = nullptr;    // HD_WINV_CHOL: [E][k^3][k^3] Cholesky factor of W_e (reciprocal diagonal)
+  double* d_Ga = nullptr;       // affine meshes: [E][8] b_e (J^T J)_{ab} / det J (00,01,02,11,12,22), det J, 0
+  dfloat* x_Ga = nullptr;       //   and its double-float copy (the FP64 apply's affine fast path)
   float* f_wdet = nullptr;      // FP32 copies for the inner solve
   float* f_wgldiag = nullptr;
   double* d_cscale = nullptr;   // [E] c_e: C_e = c_e W_e^-1

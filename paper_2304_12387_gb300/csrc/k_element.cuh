@@ -24,6 +24,8 @@ struct TabT {
   T BH[HD_MAXQ * HD_MAXK];
   T BG[HD_MAXQ * HD_MAXK];
   T TT[HD_MAXK * HD_MAXK];
+  T GW[HD_MAXQ];             // 1D Gauss-Legendre weights on [0,1]
+  T HI[HD_MAXK * HD_MAXK];   // inverse 1D histopolation mass
 };
 
 template <typename T>
@@ -38,6 +40,8 @@ inline TabT<T> make_tab(const ElemTables& t) {
   for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BH[i] = tab_cast<T>(t.BH[i]);
   for (int i = 0; i < HD_MAXQ * HD_MAXK; ++i) o.BG[i] = tab_cast<T>(t.BG[i]);
   for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.TT[i] = tab_cast<T>(t.TT[i]);
+  for (int i = 0; i < HD_MAXQ; ++i) o.GW[i] = tab_cast<T>(t.gw[i]);
+  for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.HI[i] = tab_cast<T>(t.HI[i]);
   return o;
 }
 
@@ -399,6 +403,10 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 //   OP_DT: y_u += own-cell D^T q
 //   OP_D : y_q  = D u on the element's cells
 //   OP_C : y_q -= c_e W_e^-1 q  (OP_CPOS: +)
+// AFF (affine meshes, q = k+1): Ga[e][8] holds b_e J^T J / det J (6 entries) and
+// det J; the point factor is w_p times that matrix, and W_e^-1 q = det J
+// (H^-1 x H^-1 x H^-1) q by three K x K contractions, so the kernel reads 64 B of
+// element data instead of 8 (6 Q^3 + K^6) B.
 // Essential faces: with OP_M the owning element adds u_g (constrained
 // identity); otherwise nothing. y_u receives one atomic add per element and
 // face: a shared face gets exactly two addends on a zeroed vector, so the
@@ -465,12 +473,12 @@ __device__ __forceinline__ void prefetch_l2_block(const void* p, size_t bytes, i
   }
 }
 
-template <typename T, typename IO, int K, int Q, int EB>
+template <typename T, typename IO, int K, int Q, int EB, bool AFF = false>
 __global__ void __launch_bounds__(ElemCfg<T>::THREADS)
 k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem, const int e_first,
           const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
           const CgArgs<T> cg, const IO* __restrict__ u, const IO* __restrict__ q, IO* __restrict__ yu,
-          IO* __restrict__ yq) {
+          IO* __restrict__ yq, const T* __restrict__ Ga) {
   using S = Sizes<K, Q>;
   constexpr int NX1 = S::NX1, NRT = S::NRT, NL2 = S::NL2, NQ = S::NQ;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -483,9 +491,9 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   const int tid = threadIdx.x, nth = blockDim.x;
   const bool needu = (mode & (OP_M | OP_D)) != 0;
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
-  const bool use_cg = (mode & OP_C) && cg.wdet != nullptr;
-  const bool use_chol = (mode & OP_C) && !use_cg && cg.chol != 0;
-  if constexpr (ElemCfg<T>::PREFETCH != 0) {
+  const bool use_cg = !AFF && (mode & OP_C) && cg.wdet != nullptr;
+  const bool use_chol = !AFF && (mode & OP_C) && !use_cg && cg.chol != 0;
+  if constexpr (ElemCfg<T>::PREFETCH != 0 && !AFF) {
     if (tid < 32 && e0 < n_elem) {
       const int ne = (n_elem - e0 < EB) ? n_elem - e0 : EB;
       if ((ElemCfg<T>::PREFETCH & 1) && (mode & OP_M))
@@ -525,7 +533,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
 
   // -- L2 rows: y_q = D u - C q ------------------------------------------------
   const T* cgres = nullptr;
-  if constexpr (!std::is_same<T, dfloat>::value) {
+  if constexpr (!std::is_same<T, dfloat>::value && !AFF) {
     if (use_cg) {
       if constexpr (std::is_same<T, double>::value)  // the histopolation-basis CG: FP64 only
         if (cg.hist) cgres = local_cg<T, K, Q, EB, false>(tab, sq, s1, S::R1, s2, S::R2, cg, e0, n_elem);
@@ -534,12 +542,34 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
     if constexpr (std::is_same<T, double>::value)  // the Cholesky factor: FP64 only
       if (use_chol) cgres = local_chol<T, K, EB>(winv, sq, s1, S::R1, e0, n_elem);
   }
+  if constexpr (AFF) {
+    if (mode & OP_C) {  // H^-1 along x (sq -> s1), y (s1 -> s2), z (s2 -> s1)
+      constexpr int KK = K * K;
+      for (int t = tid; t < EB * KK; t += nth) {
+        const int el = t / KK, r = t - el * KK;
+        contract<T, K, K, 1, 1>(sq + el * NL2 + K * r, s1 + el * S::R1 + K * r, tab.HI);
+      }
+      __syncthreads();
+      for (int t = tid; t < EB * KK; t += nth) {
+        const int el = t / KK, r = t - el * KK, i = r % K, l = r / K;
+        contract<T, K, K, K, K>(s1 + el * S::R1 + i + KK * l, s2 + el * S::R2 + i + KK * l, tab.HI);
+      }
+      __syncthreads();
+      for (int t = tid; t < EB * KK; t += nth) {
+        const int el = t / KK, r = t - el * KK;
+        contract<T, K, K, KK, KK>(s2 + el * S::R2 + r, s1 + el * S::R1 + r, tab.HI);
+      }
+      __syncthreads();
+    }
+  }
   // one L2 row (element-local cell t), given its D u part v
   auto l2_row = [&](int t, T v) {
     const int el = t / NL2, a = t - el * NL2, e = e0 + el;
     if (mode & OP_C) {
       T s = (T)0;
-      if (use_cg || use_chol) {
+      if constexpr (AFF) {
+        s = s1[el * S::R1 + a] * Ga[(size_t)e * 8 + 6];
+      } else if (use_cg || use_chol) {
         s = cgres[el * S::R1 + a];
       } else {
         const T* W = winv + (size_t)e * NL2 * NL2;
@@ -563,7 +593,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       l2_row(t, (mode & OP_D) ? div_local<T, K>(su + (t / NL2) * NRT, t % NL2) : (T)0);
     }
   }
-  if (use_cg || use_chol) __syncthreads();
+  if (use_cg || use_chol || (AFF && (mode & OP_C))) __syncthreads();
 
   if (mode & OP_M) {
     // -- interpolation to the points: stage A (contract along x) ----------------
@@ -621,10 +651,19 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
     for (int t = tid; t < EB * NQ; t += nth) {
       int el = t / NQ, p = t - el * NQ, e = e0 + el;
       if (e >= n_elem) continue;
-      const T* g = G + (size_t)e * 6 * NQ + p;
-      T g00 = g[0], g01 = g[NQ], g02 = g[2 * NQ], g11 = g[3 * NQ], g12 = g[4 * NQ], g22 = g[5 * NQ];
+      T g00, g01, g02, g11, g12, g22;
       T* U = s1 + el * S::R1 + p;
       T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
+      if constexpr (AFF) {
+        const T* g = Ga + (size_t)e * 8;
+        g00 = g[0]; g01 = g[1]; g02 = g[2]; g11 = g[3]; g12 = g[4]; g22 = g[5];
+        const int px = p % Q, py = (p / Q) % Q, pz = p / (Q * Q);
+        const T w = tab.GW[px] * tab.GW[py] * tab.GW[pz];
+        ux = ux * w; uy = uy * w; uz = uz * w;
+      } else {
+        const T* g = G + (size_t)e * 6 * NQ + p;
+        g00 = g[0]; g01 = g[NQ]; g02 = g[2 * NQ]; g11 = g[3 * NQ]; g12 = g[4 * NQ]; g22 = g[5 * NQ];
+      }
       Acc<T> v0, v1, v2;
       v0.init(g02, uz); v0.add(g01, uy); v0.add(g00, ux);
       v1.init(g12, uz); v1.add(g11, uy); v1.add(g01, ux);
@@ -923,26 +962,31 @@ __global__ void k_diag_tensor(const ElemTables tab, const int n_elem, const bool
   out[t] = s;
 }
 
+// Ga: the affine factors (or null: the general kernel). The affine kernel is built for
+// q = k+1 and the FP64 / double-float arithmetic only.
 template <typename T, typename IO, int K, int Q>
 hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
-                      const IO* u, const IO* q, IO* yu, IO* yq) {
+                      const IO* u, const IO* q, IO* yu, IO* yq, const T* Ga = nullptr) {
   constexpr int EB = ElemCfg<T>::EB;
+  constexpr bool HAS_AFF = Q == K + 1 && !std::is_same<T, float>::value;
   using S = Sizes<K, Q>;
   size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
   auto kern = k_elem_op<T, IO, K, Q, EB>;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern_aff = k_elem_op<T, IO, K, Q, EB, HAS_AFF>;
+  const bool aff = HAS_AFF && Ga != nullptr;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[aff]) {
+    cudaError_t e = cudaFuncSetAttribute(aff ? kern_aff : kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_elem_op)");
-    attr_set = true;
+    attr_set[aff] = true;
   }
   TabT<T> tab = make_tab<T>(h->tab);
   const int64_t e_end = h->e_end < 0 ? h->n_elem : h->e_end, e_first = h->e_end < 0 ? 0 : h->e_first;
   int blocks = (int)((e_end - e_first + EB - 1) / EB);
   prof_mark(h, true);
   if (blocks > 0)
-    kern<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(tab, h->L, mode, (int)e_end, (int)e_first, G, winv, cs,
-                                                           cg, u, q, yu, yq);
+    (aff ? kern_aff : kern)<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(
+        tab, h->L, mode, (int)e_end, (int)e_first, G, winv, cs, cg, u, q, yu, yq, Ga);
   prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;
@@ -1031,7 +1075,7 @@ HD_DECLARE_K(5)
     const double* wi = ch ? h->d_wchol : h->d_winv;                                                       \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<double, double, KK, KK + 1>(h, mode, h->d_G, wi, h->d_cscale, cg, u, q, yu, \
-                                                          yq);                                            \
+                                                          yq, h->d_Ga);                                   \
     return hdk::run_elem_op<double, double, KK, KK + 2>(h, mode, h->d_G, wi, h->d_cscale, cg, u, q, yu, yq); \
   }                                                                                                       \
   hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,            \
@@ -1039,7 +1083,7 @@ HD_DECLARE_K(5)
     hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0, 0};                                         \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<dfloat, double, KK, KK + 1>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, \
-                                                          q, yu, yq);                                     \
+                                                          q, yu, yq, h->x_Ga);                            \
     return hdk::run_elem_op<dfloat, double, KK, KK + 2>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, q, \
                                                         yu, yq);                                          \
   }                                                                                                       \
