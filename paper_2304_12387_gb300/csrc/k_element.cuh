@@ -447,16 +447,26 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 // bit 2 its W^-1 block, in L2 as the CTA starts (cp.async.bulk.prefetch). The
 // HBM-bound FP32 kernel gains about 10 % at k = 4; the FP64 and double-float
 // kernels, whose loads already overlap their arithmetic, lose.
-template <typename T>
+#ifndef HD_DFA_EB
+#define HD_DFA_EB 8
+#endif
+#ifndef HD_DFA_THREADS
+#define HD_DFA_THREADS 512
+#endif
+template <typename T, bool AFF = false>
 struct ElemCfg {
   static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH;
 };
 template <>
-struct ElemCfg<dfloat> {
+struct ElemCfg<dfloat, false> {
   static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH;
 };
 template <>
-struct ElemCfg<float> {
+struct ElemCfg<dfloat, true> {  // the affine fast path (no per-element arrays to stream)
+  static constexpr int EB = HD_DFA_EB, THREADS = HD_DFA_THREADS, PREFETCH = 0;
+};
+template <>
+struct ElemCfg<float, false> {
   static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH;
 };
 
@@ -474,7 +484,7 @@ __device__ __forceinline__ void prefetch_l2_block(const void* p, size_t bytes, i
 }
 
 template <typename T, typename IO, int K, int Q, int EB, bool AFF = false>
-__global__ void __launch_bounds__(ElemCfg<T>::THREADS)
+__global__ void __launch_bounds__(ElemCfg<T, AFF>::THREADS)
 k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_elem, const int e_first,
           const T* __restrict__ G, const T* __restrict__ winv, const T* __restrict__ cscale,
           const CgArgs<T> cg, const IO* __restrict__ u, const IO* __restrict__ q, IO* __restrict__ yu,
@@ -493,12 +503,12 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
   const bool use_cg = !AFF && (mode & OP_C) && cg.wdet != nullptr;
   const bool use_chol = !AFF && (mode & OP_C) && !use_cg && cg.chol != 0;
-  if constexpr (ElemCfg<T>::PREFETCH != 0 && !AFF) {
+  if constexpr (ElemCfg<T, AFF>::PREFETCH != 0) {
     if (tid < 32 && e0 < n_elem) {
       const int ne = (n_elem - e0 < EB) ? n_elem - e0 : EB;
-      if ((ElemCfg<T>::PREFETCH & 1) && (mode & OP_M))
+      if ((ElemCfg<T, AFF>::PREFETCH & 1) && (mode & OP_M))
         prefetch_l2_block(G + (size_t)e0 * 6 * NQ, (size_t)ne * 6 * NQ * sizeof(T), tid);
-      if ((ElemCfg<T>::PREFETCH & 2) && (mode & OP_C) && !use_cg)
+      if ((ElemCfg<T, AFF>::PREFETCH & 2) && (mode & OP_C) && !use_cg)
         prefetch_l2_block(winv + (size_t)e0 * NL2 * NL2, (size_t)ne * NL2 * NL2 * sizeof(T), tid);
     }
   }
@@ -962,34 +972,40 @@ __global__ void k_diag_tensor(const ElemTables tab, const int n_elem, const bool
   out[t] = s;
 }
 
-// Ga: the affine factors (or null: the general kernel). The affine kernel is built for
-// q = k+1 and the FP64 / double-float arithmetic only.
-template <typename T, typename IO, int K, int Q>
-hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
-                      const IO* u, const IO* q, IO* yu, IO* yq, const T* Ga = nullptr) {
-  constexpr int EB = ElemCfg<T>::EB;
-  constexpr bool HAS_AFF = Q == K + 1 && !std::is_same<T, float>::value;
+template <typename T, typename IO, int K, int Q, bool AFF>
+hd_status launch_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
+                         const IO* u, const IO* q, IO* yu, IO* yq, const T* Ga) {
+  constexpr int EB = ElemCfg<T, AFF>::EB, THREADS = ElemCfg<T, AFF>::THREADS;
   using S = Sizes<K, Q>;
   size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
-  auto kern = k_elem_op<T, IO, K, Q, EB>;
-  auto kern_aff = k_elem_op<T, IO, K, Q, EB, HAS_AFF>;
-  const bool aff = HAS_AFF && Ga != nullptr;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[aff]) {
-    cudaError_t e = cudaFuncSetAttribute(aff ? kern_aff : kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = k_elem_op<T, IO, K, Q, EB, AFF>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_elem_op)");
-    attr_set[aff] = true;
+    attr_set = true;
   }
   TabT<T> tab = make_tab<T>(h->tab);
   const int64_t e_end = h->e_end < 0 ? h->n_elem : h->e_end, e_first = h->e_end < 0 ? 0 : h->e_first;
   int blocks = (int)((e_end - e_first + EB - 1) / EB);
   prof_mark(h, true);
   if (blocks > 0)
-    (aff ? kern_aff : kern)<<<blocks, ElemCfg<T>::THREADS, smem, h->stream>>>(
-        tab, h->L, mode, (int)e_end, (int)e_first, G, winv, cs, cg, u, q, yu, yq, Ga);
+    kern<<<blocks, THREADS, smem, h->stream>>>(tab, h->L, mode, (int)e_end, (int)e_first, G, winv, cs, cg, u, q,
+                                               yu, yq, Ga);
   prof_mark(h, false);
   HD_LAUNCH_CK(h, "k_elem_op");
   return HD_OK;
+}
+
+// Ga: the affine factors (or null: the general kernel). The affine kernel is built for
+// q = k+1 and the FP64 / double-float arithmetic only.
+template <typename T, typename IO, int K, int Q>
+hd_status run_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T* cs, const CgArgs<T>& cg,
+                      const IO* u, const IO* q, IO* yu, IO* yq, const T* Ga = nullptr) {
+  constexpr bool HAS_AFF = Q == K + 1 && !std::is_same<T, float>::value;
+  if (HAS_AFF && Ga != nullptr)
+    return launch_elem_op<T, IO, K, Q, HAS_AFF>(h, mode, G, winv, cs, cg, u, q, yu, yq, Ga);
+  return launch_elem_op<T, IO, K, Q, false>(h, mode, G, winv, cs, cg, u, q, yu, yq, Ga);
 }
 
 template <int K, int Q>
