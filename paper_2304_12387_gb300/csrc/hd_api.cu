@@ -153,7 +153,8 @@ void build_tables(int k, int q, ElemTables& t) {
 }
 
 // Affine fast path: every element a parallelepiped (its trilinear map has no bilinear or
-// trilinear part, to 1e-14 of the element's edge length). Then J is constant, the
+// trilinear part, to 1e-14 of the element's edge length plus 16 ulps of its largest
+// coordinate: the rounding of the vertex differences themselves). Then J is constant, the
 // geometric factor at point p is w_p times one symmetric 3x3 matrix, and W_e^-1 =
 // det J (H^-1 x H^-1 x H^-1): 8 values per element instead of 6 q^3 + k^6. Fills
 // ga[E][8] and returns true, or returns false at the first element that is not affine.
@@ -167,18 +168,19 @@ static bool affine_factors(const hd_problem_desc* d, const double* bco, std::vec
       const int64_t id = (ex + (c & 1)) + (nx + 1) * ((ey + ((c >> 1) & 1)) + (ny + 1) * (ez + (c >> 2)));
       v[c][0] = d->vx[id]; v[c][1] = d->vy[id]; v[c][2] = d->vz[id];
     }
-    double J[3][3], h = 0.0;  // J[i][a] = d x_i / d xi_a
+    double J[3][3], h = 0.0, vmax = 0.0;  // J[i][a] = d x_i / d xi_a
     for (int i = 0; i < 3; ++i) {
       J[i][0] = v[1][i] - v[0][i];
       J[i][1] = v[2][i] - v[0][i];
       J[i][2] = v[4][i] - v[0][i];
       for (int a = 0; a < 3; ++a) h = std::max(h, std::fabs(J[i][a]));
+      for (int c = 0; c < 8; ++c) vmax = std::max(vmax, std::fabs(v[c][i]));
     }
+    const double tol = 1e-14 * h + 16.0 * 2.220446049250313e-16 * vmax;
     for (int i = 0; i < 3; ++i) {
       const double t01 = v[3][i] - v[1][i] - v[2][i] + v[0][i], t02 = v[5][i] - v[1][i] - v[4][i] + v[0][i],
                    t12 = v[6][i] - v[2][i] - v[4][i] + v[0][i],
                    t012 = v[7][i] - v[3][i] - v[5][i] - v[6][i] + v[1][i] + v[2][i] + v[4][i] - v[0][i];
-      const double tol = 1e-14 * h;
       if (std::fabs(t01) > tol || std::fabs(t02) > tol || std::fabs(t12) > tol || std::fabs(t012) > tol)
         return false;
     }

@@ -45,13 +45,15 @@ def test_fullsize_sampled_rows(name):
     op.close()
 
 
-def test_fullsize_m64_fp64_emulation():
-    """The metric workload with the double-float element kernel, sampled rows at 1e-12."""
+@pytest.mark.parametrize("name", ["m64", "c4"])
+def test_fullsize_m64_fp64_emulation(name):
+    """The metric workload (and the affine bent-tube workload, which takes the affine fast
+    path) with the double-float element kernel, sampled rows at 1e-12."""
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     import paper_2304_12387_gb300 as hd
     from oracle.sampled import SampledOperator
-    d = fullsize("m64")
+    d = fullsize(name)
     op = hd.Operator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
                      kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"], affine=d["affine"], fp64_emulation=1,
                      stream=torch.cuda.current_stream())
