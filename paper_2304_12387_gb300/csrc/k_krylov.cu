@@ -490,6 +490,10 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
     for (outer = 0;; ++outer) {
       if ((st = apply_op_internal(h, x, r)) != HD_OK) return st;
       if ((st = residual_norms(h, b, r, &rn, &bn)) != HD_OK) return st;
+      if (!std::isfinite(rn) || !std::isfinite(bn)) {
+        status = hd_fail(h, HD_ERR_NAN, "non-finite residual: b or the initial guess holds NaN or Inf");
+        break;
+      }
       if (bn == 0.0 || rn <= target * bn) {
         status = HD_OK;
         break;
@@ -1136,6 +1140,10 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
     // true residual r = b - AA x in FP64
     if ((st = apply_op_internal(h, x, r)) != HD_OK) return st;
     if ((st = residual_norms(h, b, r, &rn, &bn)) != HD_OK) return st;
+    if (!std::isfinite(rn) || !std::isfinite(bn)) {
+      status = hd_fail(h, HD_ERR_NAN, "non-finite residual: b or the initial guess holds NaN or Inf");
+      break;
+    }
     if (bn == 0.0 || rn <= o->rtol * bn) {
       status = HD_OK;
       break;
@@ -1162,8 +1170,12 @@ hd_status gmres_run(hd_op* h, const double* b, double* x, const hd_gmres_opts* o
       st = gmres_cycle<dfloat, double>(h, o, r, rn, mc, o->rtol * bn, V, V + (int64_t)m * n, h->gm_w + n,
                                        h->gm_w + 2 * n, r, x, &steps, &est);
     }
-    if (st != HD_OK) return st;
     its += steps;
+    if (st == HD_ERR_NAN) {  // breakdown in the cycle: reported through info as well
+      status = st;
+      break;
+    }
+    if (st != HD_OK) return st;
   }
   HD_CK(h, cudaEventRecord(e1, s));
   HD_CK(h, cudaEventSynchronize(e1));

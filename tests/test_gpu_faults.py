@@ -1,0 +1,64 @@
+"""Failure detection with faults injected on the host.
+
+A NaN in the right-hand side or an Inf in the initial guess must end MINRES
+(plain and with FP64 residual correction) and GMRES with HD_ERR_NAN instead of
+iterating on garbage, and must leave the handle usable: a clean solve on the same
+handle afterwards gives bit for bit the solution of a fresh handle (the solvers
+are deterministic). Nothing here faults, traps or stalls the GPU: the recurrence
+scalars and the residual norms carry the NaN to a status word that the host reads."""
+import numpy as np
+import pytest
+
+from cases import gpu_operator, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _rhs(n, seed):
+    return torch.from_numpy(np.random.Generator(np.random.PCG64(seed)).uniform(-1, 1, n)).cuda()
+
+
+def _clean_solve(op, solver, b):
+    x = torch.zeros_like(b)
+    st, _ = solver(op)(b, x)
+    torch.cuda.synchronize()
+    return st, x.cpu().numpy()
+
+
+SOLVERS = {
+    "minres": lambda op: (lambda b, x, **kw: op.hd_minres_solve(b, x, rtol=1e-8, maxit=2000, check_every=4, **kw)),
+    "minres_refined": lambda op: (lambda b, x, **kw: op.hd_minres_solve(b, x, rtol=1e-4, maxit=4000, precision=1,
+                                                                        outer_rtol=1e-8, max_outer=20, **kw)),
+    "gmres": lambda op: (lambda b, x, **kw: op.hd_gmres_solve(b, x, rtol=1e-8, maxit=400, restart=16, **kw)),
+}
+
+
+@pytest.mark.parametrize("solver", sorted(SOLVERS))
+@pytest.mark.parametrize("fault", ["nan_rhs", "inf_x0"])
+def test_injected_non_finite_values_are_reported(solver, fault):
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    d = inputs("darcy_gamma")
+    op = gpu_operator(d, coarse_max=8)
+    b = _rhs(op.n, 40)
+    bad_b = b.clone()
+    x0 = torch.zeros_like(b)
+    if fault == "nan_rhs":
+        bad_b[op.n // 3] = float("nan")
+        st, info = SOLVERS[solver](op)(bad_b, x0)
+    else:
+        x0[7] = float("inf")
+        st, info = SOLVERS[solver](op)(b, x0, use_x0=True)
+    torch.cuda.synchronize()
+    assert st == hd.HD_ERR_NAN, (solver, fault, st, info)
+    assert info["status"] == hd.HD_ERR_NAN
+    # the handle still works, and gives what a fresh handle gives
+    st1, x1 = _clean_solve(op, SOLVERS[solver], b)
+    fresh = gpu_operator(d, coarse_max=8)
+    st2, x2 = _clean_solve(fresh, SOLVERS[solver], b)
+    assert st1 == hd.HD_OK and st2 == hd.HD_OK
+    assert np.array_equal(x1, x2)
+    op.close()
+    fresh.close()
