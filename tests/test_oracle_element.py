@@ -60,6 +60,56 @@ def _mass_1d(k, which):
     return (B * w) @ B.T
 
 
+def _mixed_1d(k):
+    # C[i, j] = int l_i h_j with the same independent rule
+    t, w = np.polynomial.legendre.leggauss(20)
+    x, w = 0.5 * (t + 1), 0.5 * w
+    return (basis1d.interp_basis(k, x) * w) @ basis1d.histo_basis(k, x).T
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_parallelepiped_closed_form(k):
+    """On the image of the unit cube under x = A xi + t (J = A constant): every block of M
+    is a Kronecker product of 1D matrices, M[(d, n), (d', n')] = G_dd' prod_c X_c with
+    G = beta A^T A / det A and X_c = M_I, M_H or the mixed int l_i h_j along each axis
+    (Piola map, Sec. 2); W = alpha / det A (M_H x M_H x M_H), so W^-1 = det A / alpha
+    (M_H^-1 x M_H^-1 x M_H^-1): the forms the affine fast path of the GPU apply uses."""
+    A = np.array([[0.9, 0.25, -0.1], [0.15, 1.2, 0.2], [-0.05, 0.3, 0.8]])
+    t0 = np.array([0.3, -0.2, 0.5])
+    V = np.zeros((1, 2, 2, 2, 3))
+    for c in range(2):
+        for b in range(2):
+            for a in range(2):
+                V[0, c, b, a] = A @ np.array([a, b, c]) + t0
+    beta, alpha = 1.7, 0.6
+    m = element.element_matrices(V, k, k + 1, np.array([beta]), np.array([alpha]), want=("M", "W"))
+    det = np.linalg.det(A)
+    G = beta * A.T @ A / det
+    MI, MH, C = _mass_1d(k, "I"), _mass_1d(k, "H"), _mixed_1d(k)
+
+    def axis_matrix(c, d, dp):
+        if c == d and c == dp:
+            return MI
+        if c == d:
+            return C
+        if c == dp:
+            return C.T
+        return MH
+
+    n1 = (k + 1) * k * k
+    M = np.zeros((3 * n1, 3 * n1))
+    for d in range(3):
+        for dp in range(3):
+            X = [axis_matrix(c, d, dp) for c in range(3)]
+            M[d * n1:(d + 1) * n1, dp * n1:(dp + 1) * n1] = G[d, dp] * np.kron(X[2], np.kron(X[1], X[0]))
+    assert np.abs(m["M"][0] - M).max() <= 1e-13 * np.abs(M).max()
+    W = alpha / det * np.kron(MH, np.kron(MH, MH))
+    assert np.abs(m["W"][0] - W).max() <= 1e-13 * np.abs(W).max()
+    Hi = np.linalg.inv(MH)
+    Winv = det / alpha * np.kron(Hi, np.kron(Hi, Hi))
+    assert np.abs(np.linalg.inv(m["W"][0]) - Winv).max() <= 1e-12 * np.abs(Winv).max()
+
+
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_cartesian_closed_form(k):
     """On a box hx x hy x hz: M_xx = beta hx/(hy hz) (M_I x M_H x M_H), no coupling
