@@ -215,6 +215,23 @@ def test_manufactured_convergence_rate():
     assert np.all(rates[-1] > 1.8), rates
 
 
+def test_manufactured_convergence_rate_k3():
+    """The same field at k = 3: the errors fall like h^3 (2^3 -> 4^3 elements; a finer
+    mesh is minutes of sparse direct solve)."""
+    errs = []
+    for n in (2, 4):
+        vx, vy, vz = synth.lattice_vertices(n, n, n)
+        p = Problem(n, n, n, 3, vx, vy, vz, 1.0, 1.0, kind=GRAD_DIV, ess_mask=63, affine=True)
+        f = manufactured.rt_load(p, lambda X: manufactured.sinusoid_field(X)[2])
+        f[~p.free] = 0.0
+        b = np.concatenate([f, np.zeros(p.lat.n_l2)])
+        x = sp.linalg.spsolve(p.matrix().tocsc(), b)
+        u, qt = p.split(x)
+        errs.append(manufactured.l2_errors(p, u, p.C @ qt, manufactured.sinusoid_field))
+    rates = np.log2(np.array(errs[0]) / np.array(errs[1]))
+    assert np.all(rates > 2.8), rates
+
+
 def test_sampled_rows_match_assembled():
     n, k = 3, 2
     vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=0.15)
