@@ -62,3 +62,32 @@ def test_injected_non_finite_values_are_reported(solver, fault):
     assert np.array_equal(x1, x2)
     op.close()
     fresh.close()
+
+
+def test_corrupted_learned_network_falls_back_to_the_vcycle():
+    """NaN weights injected into the learned Schur preconditioner: MINRES detects the
+    breakdown, solves again with the V-cycle and reports the fallback; the solution is
+    the plain solver's."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    d = inputs("darcy_k3")
+    op = gpu_operator(d, coarse_max=8)
+    op.hd_learned_init(delta=1e-3)
+    W1, W2 = op.hd_learned_get_weights()
+    W1[3, 5] = np.nan
+    op.hd_learned_set_weights(W1, W2)
+    op.hd_enable_learned(1)
+    b = _rhs(op.n, 41)
+    x = torch.zeros_like(b)
+    st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=3000, check_every=4)
+    torch.cuda.synchronize()
+    assert st == hd.HD_OK and info["fallback"] == 1, info
+    plain = gpu_operator(d, coarse_max=8)
+    st2, x2 = _clean_solve(plain, lambda o: (lambda bb, xx: o.hd_minres_solve(bb, xx, rtol=1e-8, maxit=3000,
+                                                                               check_every=4)), b)
+    assert st2 == hd.HD_OK
+    xn = x.cpu().numpy()
+    assert np.abs(xn - x2).max() <= 1e-12 * np.abs(x2).max()
+    op.close()
+    plain.close()
