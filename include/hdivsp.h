@@ -231,6 +231,14 @@ hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int3
  * faces normal to lattice axis perm[d] and carry the orientation sgn[d] (stored as
  * -1-g when it is -1). hd_lattice_e2l_map writes nx*ny*nz * k^3 cell ids, local order
  * a + k (b + k c). A code outside 0..23 or bad sizes: HD_ERR_INVALID_ARG. */
+/* Whether hd_create takes the affine fast path for this mesh (given affine = 1, q = k+1 and the
+ * dense W^-1): *affine = 1 when every element is a parallelepiped, i.e. for each coordinate the
+ * bilinear and trilinear combinations of its 8 vertices (v110 - v100 - v010 + v000 and the like)
+ * are at most 1e-14 of its largest edge vector component plus 16 ulps of its largest vertex
+ * coordinate, and det J > 0; else 0. Host only (no GPU); vertex layout as in hd_problem_desc.
+ * Bad sizes or NULL pointers: HD_ERR_INVALID_ARG. Not in the paper: the fast path's test. */
+hd_status hd_lattice_is_affine(int32_t nx, int32_t ny, int32_t nz, const double* vx, const double* vy,
+                               const double* vz, int32_t* affine);
 hd_status hd_lattice_e2d_map_rot(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot,
                                  int32_t* out);
 hd_status hd_lattice_e2l_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, const int8_t* rot,

@@ -87,6 +87,7 @@ _SIGS = {
     "hd_lattice_e2d_map_rot": [ctypes.c_int32] * 4 + [_VP, _VP],
     "hd_lattice_e2l_map": [ctypes.c_int32] * 4 + [_VP, _VP],
     "hd_get_e2l_map": [_H, _VP],
+    "hd_lattice_is_affine": [ctypes.c_int32] * 3 + [_VP, _VP, _VP, ctypes.POINTER(ctypes.c_int32)],
     "hd_lattice_ess_dofs": [ctypes.c_int32] * 4 + [ctypes.c_uint32, _VP, ctypes.POINTER(ctypes.c_int64)],
     "hd_apply_A": [_H, _VP, _VP],
     "hd_apply_B": [_H, _VP, _VP],
@@ -193,6 +194,18 @@ def hd_lattice_e2l_map(nx, ny, nz, k, rot=None):
     out = np.zeros((nx * ny * nz, k ** 3), dtype=np.int32)
     _check(lib().hd_lattice_e2l_map(nx, ny, nz, k, _ptr(rot), out.ctypes.data))
     return out
+
+
+def hd_lattice_is_affine(nx, ny, nz, vx, vy, vz):
+    """True when every element of the lattice mesh is a parallelepiped (the affine fast path's test)."""
+    arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (vx, vy, vz)]
+    nv = (nx + 1) * (ny + 1) * (nz + 1)
+    if any(a.shape != (nv,) for a in arrs):
+        raise ValueError("vertex arrays need (nx+1)(ny+1)(nz+1) entries")
+    out = ctypes.c_int32(0)
+    _check(lib().hd_lattice_is_affine(nx, ny, nz, arrs[0].ctypes.data, arrs[1].ctypes.data, arrs[2].ctypes.data,
+                                      ctypes.byref(out)))
+    return bool(out.value)
 
 
 def hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask):

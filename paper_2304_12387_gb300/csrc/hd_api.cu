@@ -607,6 +607,18 @@ hd_status hd_lattice_e2l_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, cons
   return HD_OK;
 }
 
+hd_status hd_lattice_is_affine(int32_t nx, int32_t ny, int32_t nz, const double* vx, const double* vy,
+                               const double* vz, int32_t* affine) {
+  if (!vx || !vy || !vz || !affine || nx < 1 || ny < 1 || nz < 1) return HD_ERR_INVALID_ARG;
+  hd_problem_desc d{};
+  d.nx = nx; d.ny = ny; d.nz = nz;
+  d.vx = vx; d.vy = vy; d.vz = vz;
+  const std::vector<double> ones((size_t)nx * ny * nz, 1.0);
+  std::vector<double> ga;
+  *affine = affine_factors(&d, ones.data(), ga) ? 1 : 0;
+  return HD_OK;
+}
+
 hd_status hd_lattice_e2d_map(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t* out) {
   return hd_lattice_e2d_map_rot(nx, ny, nz, k, nullptr, out);
 }

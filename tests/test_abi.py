@@ -74,3 +74,25 @@ def test_bad_arguments_are_rejected():
         hd.hd_lattice_e2d_map(0, 1, 1, 2)
     with pytest.raises(hd.HdError):
         hd.hd_lattice_ess_dofs(1, 1, 1, 2, 64)
+
+
+def test_affine_mesh_test():
+    """The host-side test that selects the affine fast path: parallelepiped meshes
+    (uniform, graded and sheared, translated to large coordinates) pass; a perturbed
+    mesh, or one vertex moved by 1e-9 of the element size, does not."""
+    import synth
+    A = np.array([[1.0, 0.3, 0.1], [0.05, 0.8, 0.2], [0.1, -0.1, 1.2]])
+    for dims in ((1, 1, 1), (3, 2, 4)):
+        vx, vy, vz = synth.lattice_vertices(*dims)
+        assert hd.hd_lattice_is_affine(*dims, vx, vy, vz)
+        X = A @ (np.stack([vx, vy, vz]) ** 1.3)
+        assert hd.hd_lattice_is_affine(*dims, *X)
+        vx2, vy2, vz2 = synth.lattice_vertices(*dims, extent=(1200.0, 2200.0, 170.0))
+        assert hd.hd_lattice_is_affine(*dims, vx2 + 5e3, vy2 - 7e3, vz2 + 1e4)
+        if min(dims) > 1:  # the perturbation moves interior vertices only
+            assert not hd.hd_lattice_is_affine(*dims, *synth.lattice_vertices(*dims, perturb=0.01))
+        bumped = vx.copy()
+        bumped[-1] += 1e-9 / max(dims)
+        assert not hd.hd_lattice_is_affine(*dims, bumped, vy, vz)
+    with pytest.raises(ValueError):
+        hd.hd_lattice_is_affine(2, 2, 2, np.zeros(3), np.zeros(3), np.zeros(3))
