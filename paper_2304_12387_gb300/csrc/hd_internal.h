@@ -30,6 +30,16 @@ struct ElemTables {
                                        //   (affine elements: W_e^-1 = det J  HI x HI x HI)
 };
 
+// One-time set-up per device (the dynamic shared memory opt-in is a function attribute of
+// each device): the entry of the current device in a caller-owned static flag array, or
+// null when the device cannot be told (then the set-up simply runs again).
+#define HD_MAX_DEVICES 64
+inline bool* device_flag(bool* flags) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= HD_MAX_DEVICES) return nullptr;
+  return flags + dev;
+}
+
 // Mesh/lattice constants passed to kernels.
 struct LatticeDims {
   int nx, ny, nz;      // elements

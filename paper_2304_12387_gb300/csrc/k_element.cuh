@@ -979,11 +979,12 @@ hd_status launch_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T*
   using S = Sizes<K, Q>;
   size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
   auto kern = k_elem_op<T, IO, K, Q, EB, AFF>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static bool attr_set[HD_MAX_DEVICES] = {};
+  bool* done = device_flag(attr_set);
+  if (!done || !*done) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_elem_op)");
-    attr_set = true;
+    if (done) *done = true;
   }
   TabT<T> tab = make_tab<T>(h->tab);
   const int64_t e_end = h->e_end < 0 ? h->n_elem : h->e_end, e_first = h->e_end < 0 ? 0 : h->e_first;

@@ -489,11 +489,12 @@ hd_status net_dot(hd_op* h, const double* a, const double* b, int64_t n, double*
 hd_status conv2(hd_op* h, const __half* W, const __half* in, __half* out) {
   LearnedNet* N = h->net;
   const size_t smem = (size_t)(NT * NC * NC + HCELLS * NC) * sizeof(__half);
-  static bool attr = false;
-  if (!attr) {
+  static bool attr[HD_MAX_DEVICES] = {};
+  bool* done = device_flag(attr);
+  if (!done || !*done) {
     cudaError_t e = cudaFuncSetAttribute(k_conv2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_conv2)");
-    attr = true;
+    if (done) *done = true;
   }
   prof_mark(h, true);
   k_conv2<<<N->conv_blocks, 256, smem, h->stream>>>(N->X, N->Y, N->Z, W, in, out);
