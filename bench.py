@@ -610,7 +610,7 @@ def run_learned(args):
     """Learned Schur preconditioner, evaluated the way it is meant to be used: trained
     on residual/correction pairs from the plain solver on the Darcy recipe (k = 3,
     perturbed mesh, eps = exp(2Z), gamma = 0) at 32^3 and then 64^3 elements,
-    evaluated at 96^3 against the plain hierarchy (same cycle) as judge. Prints one
+    evaluated at 96^3 against the plain hierarchy (same cycle) as referee. Prints one
     JSON line with iteration counts and times of FP64 MINRES to rtol 1e-8."""
     import torch
     import paper_2304_12387_gb300 as hd
@@ -658,7 +658,7 @@ def run_learned(args):
     e = out["eval96"]
     out["learned_vs_plain_96"] = {"iteration_ratio": e["learned"]["iterations"] / e["plain"]["iterations"],
                                   "time_ratio": e["learned"]["ms"] / e["plain"]["ms"],
-                                  "judge": "plain" if e["learned"]["ms"] >= e["plain"]["ms"] else "learned"}
+                                  "referee": "plain" if e["learned"]["ms"] >= e["plain"]["ms"] else "learned"}
     print(json.dumps(out), flush=True)
 
 
