@@ -155,6 +155,15 @@ def reference_tables(k, q):
     return _TABLES[key]
 
 
+def reference_mass_blocks(k, q):
+    """K[a, b] (a, b = 0..2): the reference-cube matrices K_ab[n, m] = int phi_hat_n,a
+    phi_hat_m,b dxi by the q^3 Gauss rule. On a parallelepiped (J = A constant) the
+    Piola-mapped mass is M_e = sum_ab G_ab K_ab with G = beta A^T A / det A (Eq. matrices
+    with the geometric factor taken out of the integral)."""
+    pts, w, Phi, _, _ = reference_tables(k, q)
+    return np.einsum("p,pna,pmb->abnm", w, Phi, Phi)
+
+
 def element_matrices(V, k, q, beta, alpha, want=("M", "W", "B")):
     """Element matrices for elements with corner coordinates V (see module doc).
 

@@ -110,6 +110,29 @@ def test_parallelepiped_closed_form(k):
     assert np.abs(np.linalg.inv(m["W"][0]) - Winv).max() <= 1e-12 * np.abs(Winv).max()
 
 
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_reference_mass_blocks_give_the_parallelepiped_mass(k):
+    """M_e = sum_ab G_ab K_ab on a parallelepiped (the form of a batched, shared-matrix
+    element contraction); the diagonal blocks K_aa are symmetric positive definite and
+    K_ab = K_ba^T."""
+    A = np.array([[1.1, -0.2, 0.15], [0.1, 0.7, 0.3], [0.2, 0.05, 0.9]])
+    V = np.zeros((1, 2, 2, 2, 3))
+    for c in range(2):
+        for b in range(2):
+            for a in range(2):
+                V[0, c, b, a] = A @ np.array([a, b, c]) - 0.4
+    beta = 2.3
+    M = element.element_matrices(V, k, k + 1, np.array([beta]), np.array([1.0]), want=("M",))["M"][0]
+    K = element.reference_mass_blocks(k, k + 1)
+    G = beta * A.T @ A / np.linalg.det(A)
+    Ms = np.einsum("ab,abnm->nm", G, K)
+    assert np.abs(Ms - M).max() <= 1e-13 * np.abs(M).max()
+    for a in range(3):
+        assert np.all(np.linalg.eigvalsh(K[a, a]) > -1e-14)
+        for b in range(3):
+            assert np.allclose(K[a, b], K[b, a].T, atol=1e-15)
+
+
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_cartesian_closed_form(k):
     """On a box hx x hy x hz: M_xx = beta hx/(hy hz) (M_I x M_H x M_H), no coupling
