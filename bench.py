@@ -35,6 +35,8 @@ METRIC = "GDOF/s of block operator apply at p=4; MINRES time-to-1e-8 resid, mixe
 NX, K, Q, PERTURB, SIGMA, ESS, SEED = 64, 4, 6, 0.15, 2.0, 63, 2304
 # measured FP64 FMA rate of this GPU model: 152 SMs x 2 FP64 FMA lanes/clk x 2 flops
 FP64_PEAK_GFLOPS_AT_MAX_CLOCK = 152 * 2 * 2 * 2.070
+# probed double-float FMA rate of this GPU model (FP32 pairs on the FP32 pipe), 2 flops each
+DF_PEAK_FP64_EQUIV_GFLOPS = 2 * 2471.0
 # DRAM bytes (read + write) per element of the element kernel, from one ncu capture of the 24^3
 # case of the same recipe (13,824 elements); to be dropped when the kernel changes
 ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 674.110208e6 / 13824,   # FP64 kernel
@@ -97,33 +99,54 @@ def elem_bytes_affine(n_elem, n_rt, n_l2):
     return 8 * (2 * (n_rt + n_l2) + 8 * n_elem)
 
 
+def alg_bytes(n_rt, n_l2, n_vert, n_elem, q=None):
+    """Algorithmic DRAM bytes of one FP64 block apply (the method's own traffic): read x and
+    write y (8 (2 N_RT + 2 N_L2)), the vertex coordinates (24 per vertex) and two coefficients
+    per element (16). q given: the variant that keeps the geometric factors per quadrature
+    point (7 doubles per point: the 6 entries of J^T J/det J and w/det J), 56 q^3 per element."""
+    b = 8 * (2 * n_rt + 2 * n_l2) + 24 * n_vert + 16 * n_elem
+    return b + (56 * q ** 3 * n_elem if q else 0)
+
+
 def roofline(op, nx, kern_ms, emulated):
-    """Roofline object of the fused element kernel. FP64: bound by the FP64 pipe
-    ("alu", peak derived from the unit count and the maximum clock). Double-float:
-    HBM against the measured copy bandwidth (its FP32-pipe floor, 2471 G double-float
-    FMA/s measured, is about equal: both near 1.9 ms at 64^3)."""
-    flops = elem_flops(K, Q) * op.n_elem
-    abytes = elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2, (nx + 1) ** 3)
+    """Roofline object of the fused element kernel against HBM on the method's algorithmic
+    bytes (the per-point variant: this kernel reads stored geometric factors), with the
+    bytes the kernel streams by its storage choices (per-point factors and the dense
+    per-element W^-1, 8 (2N + E (6 q^3 + k^6 + 1))) beside them. The kernel is bound by
+    arithmetic issue, not by HBM: the "alu" object gives its double-float (or FP64)
+    arithmetic rate against the probed peak of that arithmetic."""
+    nv = (nx + 1) ** 3
+    abytes = alg_bytes(op.n_rt, op.n_l2, nv, op.n_elem, Q)
+    sbytes = elem_bytes(K, Q, op.n_elem, op.n_rt, op.n_l2)
     key = (K, Q, "df" if emulated else "f64")
     traffic = ELEM_TRAFFIC_BYTES_PER_ELEMENT[key] * op.n_elem if key in ELEM_TRAFFIC_BYTES_PER_ELEMENT else None
     gbs = abytes / (kern_ms * 1e-3) / 1e9
+    flops = elem_flops(K, Q) * op.n_elem
     gflops = flops / (kern_ms * 1e-3) / 1e9
     if emulated:
-        return {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS_MEASURED, "unit": "GB/s",
-                "frac": gbs / HBM_GBS_MEASURED, "traffic": traffic, "kernel": "k_elem_op<dfloat,double,4,6,8>",
-                "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)",
-                "fp64_equivalent_gflops": gflops, "fp64_equivalent_frac_of_fp64_peak": gflops / FP64_PEAK_GFLOPS_AT_MAX_CLOCK}
-    return {"bound": "alu", "achieved": gflops, "peak": FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "unit": "GFLOP/s",
-            "frac": gflops / FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "traffic": traffic, "kernel": "k_elem_op<double,double,4,6,8>",
-            "kernel_ms": kern_ms, "flops_per_launch": flops, "algorithmic_bytes_per_launch": abytes,
-            "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (FP64 FMA probe: 1189 GFLOP/s at 2002 MHz)",
-            "hbm_frac_of_measured": gbs / HBM_GBS_MEASURED}
+        alu = {"arithmetic": "double-float (FP32 pairs) on the FP32 pipe", "achieved": gflops,
+               "peak": DF_PEAK_FP64_EQUIV_GFLOPS, "unit": "GFLOP/s (FP64-equivalent)",
+               "frac": gflops / DF_PEAK_FP64_EQUIV_GFLOPS,
+               "peak_source": "probe: 2471 G double-float FMA/s on this GPU model (2 flops each)"}
+    else:
+        alu = {"arithmetic": "FP64", "achieved": gflops, "peak": FP64_PEAK_GFLOPS_AT_MAX_CLOCK, "unit": "GFLOP/s",
+               "frac": gflops / FP64_PEAK_GFLOPS_AT_MAX_CLOCK,
+               "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2070 MHz (probe: 1189 GFLOP/s at 2002 MHz)"}
+    return {"bound": "hbm", "achieved": gbs, "peak": HBM_GBS_MEASURED, "unit": "GB/s",
+            "frac": gbs / HBM_GBS_MEASURED, "traffic": traffic,
+            "traffic_over_algorithmic": traffic / abytes if traffic else None,
+            "kernel": "k_elem_op<%s,double,%d,%d,8>" % ("dfloat" if emulated else "double", K, Q),
+            "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
+            "algorithmic_bytes": "8(2 N_RT + 2 N_L2) + 24 N_vert + 16 E + 56 q^3 E (per-point geometric factors)",
+            "streamed_bytes_per_launch": sbytes,
+            "streamed_bytes": "8 (2 N + E (6 q^3 + k^6 + 1)): per-point factors and the stored dense W_e^-1",
+            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)", "flops_per_launch": flops, "alu": alu}
 
 
-def elem_bytes(k, q, n_elem, n_rt, n_l2, n_vert):
-    """Algorithmic DRAM bytes of one apply: read x (u, q), write y (u, q), the
-    geometric factors (6 q^3 doubles per element) and W_e^-1 (k^6 doubles)."""
+def elem_bytes(k, q, n_elem, n_rt, n_l2):
+    """Bytes the fused element kernel streams by its storage choices: read x (u, q),
+    write y (u, q), the geometric factors (6 q^3 doubles per element), W_e^-1 (k^6
+    doubles) and the coefficient scale."""
     return 8 * (2 * (n_rt + n_l2) + n_elem * (6 * q ** 3 + k ** 6 + 1))
 
 
@@ -179,15 +202,23 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def oracle_sample(seconds=8.0, n=4):
-    """The CPU oracle as it stands on a bounded sample of the same workload (an
-    n^3-element mesh with the same recipe): assembled CSR block apply, repeated
-    for about `seconds`. Returns GDOF/s and a description."""
-    from oracle.assembly import GRAD_DIV, Problem
-    vx, vy, vz, alpha, beta = workload(n)
-    prob = Problem(n, n, n, K, vx, vy, vz, alpha, beta, kind=GRAD_DIV, ess_mask=ESS, q=Q)
-    x = synth.uniform(prob.n, seed=SEED)
-    prob.apply_op(x)
+_ORACLE = {}
+
+
+def _oracle_worker(arg):
+    """One process of the CPU baseline: builds the oracle on an n^3-element mesh of the
+    metric recipe (once per process) and repeats its assembled-CSR block apply for about
+    `seconds` (scipy's SpMV runs on one thread). Returns (DOFs applied, seconds, DOFs
+    per apply)."""
+    seconds, n = arg
+    if n not in _ORACLE:
+        from oracle.assembly import GRAD_DIV, Problem
+        vx, vy, vz, alpha, beta = workload(n)
+        prob = Problem(n, n, n, K, vx, vy, vz, alpha, beta, kind=GRAD_DIV, ess_mask=ESS, q=Q)
+        x = synth.uniform(prob.n, seed=SEED)
+        prob.apply_op(x)
+        _ORACLE[n] = (prob, x)
+    prob, x = _ORACLE[n]
     reps, t0 = 0, time.perf_counter()
     while True:
         prob.apply_op(x)
@@ -195,7 +226,75 @@ def oracle_sample(seconds=8.0, n=4):
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return prob.n * reps / el / 1e9, el, reps, prob.n
+    return prob.n * reps, el, prob.n
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+class OraclePool:
+    """`procs` single-threaded processes (spawned, not forked) that each hold their own copy
+    of the CPU oracle on an n^3-element sample of the metric workload."""
+
+    def __init__(self, procs, n=4):
+        import multiprocessing as mp
+        self.procs, self.n = procs, n
+        saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for v in saved:
+            os.environ[v] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(procs)
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
+        self.pool.map(_oracle_worker, [(0.0, n)] * procs)  # build the samples
+
+    def run(self, seconds):
+        """Every process applies its oracle for about `seconds`. Returns GDOF/s summed over
+        the processes (over the slowest process's time), that time and DOFs per apply."""
+        res = self.pool.map(_oracle_worker, [(seconds, self.n)] * self.procs)
+        el = max(r[1] for r in res)
+        return sum(r[0] for r in res) / el / 1e9, el, res[0][2]
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline(seconds=8.0):
+    """cpu_baseline object: the oracle on every host core (os.cpu_count() processes) and
+    on one core, on a 4^3-element sample of the metric workload."""
+    cores = os.cpu_count() or 1
+    one = OraclePool(1)
+    v1, el1, ndof = one.run(seconds)
+    one.close()
+    every = OraclePool(cores)
+    vall, elall, _ = every.run(seconds)
+    every.close()
+    return {"value": vall, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": ("4^3 elements of the metric recipe (%d DOFs): assembled-CSR block applies (scipy SpMV, one "
+                       "thread per process) for %.1f s in each of %d spawned processes, one per host core"
+                       % (ndof, elall, cores)),
+            "single_core": {"value": v1, "unit": "GDOF/s", "cores": 1, "seconds": el1}}
 
 
 def native_apply(args, nx, vx, vy, vz, alpha, beta, stream):
@@ -249,11 +348,14 @@ def f32_apply(args, op, nx):
     launches, kms = op.hd_profile_read()
     kms = kms / max(1, launches)
     E = nx ** 3
-    alg = 4 * (2 * n + E * (6 * Q ** 3 + K ** 6 + 1))
+    alg = alg_bytes(op.n_rt, op.n_l2, (nx + 1) ** 3, E, Q) // 2   # the same counts in FP32
+    streamed = 4 * (2 * n + E * (6 * Q ** 3 + K ** 6 + 1))
     peak = _measured_hbm_gbs()
     return {"value": n / (e0.elapsed_time(e1) / steps * 1e-3) / 1e9, "unit": "GDOF/s",
             "ms_per_step": e0.elapsed_time(e1) / steps, "steps": steps, "kernel_ms": kms,
-            "algorithmic_bytes_per_launch": alg, "hbm_frac_of_measured": alg / (kms * 1e-3) / 1e9 / peak}
+            "algorithmic_bytes_per_launch": alg, "hbm_frac_of_measured": alg / (kms * 1e-3) / 1e9 / peak,
+            "streamed_bytes_per_launch": streamed,
+            "streamed_hbm_frac_of_measured": streamed / (kms * 1e-3) / 1e9 / peak}
 
 
 def affine_apply(args, stream):
@@ -285,12 +387,13 @@ def affine_apply(args, stream):
     launches, kms = op.hd_profile_read()
     ms = e0.elapsed_time(e1) / steps
     kern_ms = kms / max(1, launches)
-    abytes = elem_bytes_affine(op.n_elem, op.n_rt, op.n_l2)
+    abytes = alg_bytes(op.n_rt, op.n_l2, (nx + 1) ** 3, op.n_elem)
+    sbytes = elem_bytes_affine(op.n_elem, op.n_rt, op.n_l2)
     flops = elem_flops_affine(K, q) * op.n_elem
     r = {"workload": "M%d-affine: the same recipe on the unperturbed mesh, q=%d" % (nx, q),
          "value": op.n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms, "steps": steps,
          "kernel": "k_elem_op<%s,double,%d,%d,8,affine>" % ("dfloat" if args.fp64_emulation else "double", K, q),
-         "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes,
+         "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes, "streamed_bytes_per_launch": sbytes,
          "element_data": "affine fast path: 64 B per element (constant geometric factor, det J)",
          "hbm_frac_of_measured": abytes / (kern_ms * 1e-3) / 1e9 / HBM_GBS_MEASURED,
          "fp64_equivalent_gflops": flops / (kern_ms * 1e-3) / 1e9}
@@ -311,37 +414,33 @@ def max_over_ranks(value, dist):
 
 
 def run_reference(args, rank, world):
-    """The oracle arm: W warm-up and K timed steps on the host cores, each step a
-    bounded sample of the metric workload (R assembled-CSR block applies of an
-    n^3-element mesh of the same recipe, R sized so the whole run takes about a
-    minute at most)."""
+    """The oracle arm: W warm-up and K timed steps on every host core, each step a
+    bounded sample of the metric workload (every core applies the assembled-CSR block
+    operator of its own copy of a 4^3-element mesh of the same recipe for a fixed
+    time, sized so that the whole run takes about a minute at most)."""
     if rank != 0:
         return
-    from oracle.assembly import GRAD_DIV, Problem
-    n = 4
-    vx, vy, vz, alpha, beta = workload(n)
-    prob = Problem(n, n, n, K, vx, vy, vz, alpha, beta, kind=GRAD_DIV, ess_mask=ESS, q=Q)
-    x = synth.uniform(prob.n, seed=SEED)
-    t0 = time.perf_counter()
-    prob.apply_op(x)
-    t_apply = max(time.perf_counter() - t0, 1e-4)
+    cores = os.cpu_count() or 1
     steps, warmup = max(1, args.steps), max(0, args.warmup)
-    step_s = min(0.5, 60.0 / (steps + warmup))
-    reps = max(1, int(round(step_s / t_apply)))
-    for _ in range(warmup * reps):
-        prob.apply_op(x)
-    t0 = time.perf_counter()
-    for _ in range(steps * reps):
-        prob.apply_op(x)
-    el = time.perf_counter() - t0
-    gdofs = prob.n * reps * steps / el / 1e9
-    sample = ("%d^3 elements of the 64^3 recipe (%d DOFs); a step = %d assembled-CSR block applies, "
-              "scipy single-threaded" % (n, prob.n, reps))
+    step_s = min(2.0, 60.0 / (steps + warmup))
+    pool = OraclePool(cores)
+    for _ in range(warmup):
+        pool.run(step_s)
+    vals, els, ndof = [], [], 0
+    for _ in range(steps):
+        v, el, ndof = pool.run(step_s)
+        vals.append(v)
+        els.append(el)
+    pool.close()
+    gdofs = statistics.median(vals)
+    sample = ("4^3 elements of the 64^3 recipe (%d DOFs); a step = %.2f s of assembled-CSR block applies in "
+              "each of %d spawned single-threaded processes (one per host core)" % (ndof, step_s, cores))
     line = {"impl": "reference", "metric": METRIC, "value": gdofs, "unit": "GDOF/s", "n_gpus": args.gpus,
-            "steps": steps, "warmup": warmup, "ms_per_step": el / steps * 1e3, "higher_is_better": True,
+            "steps": steps, "warmup": warmup, "ms_per_step": statistics.median(els) * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "M64-perturbed recipe on a 4^3-element sample (k=4, q=6, %d DOFs)" % prob.n},
-            "cpu_baseline": {"value": gdofs, "unit": "GDOF/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": "M64-perturbed recipe on a 4^3-element sample per core (k=4, q=6, %d DOFs)" % ndof},
+            "cpu_baseline": {"value": gdofs, "unit": "GDOF/s", "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": gdofs, "unit": "GDOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -478,10 +577,7 @@ def run_ours(args, rank, world, dist):
                 "true_relres": info["true_relres"], "ms_per_iteration": info["ms_total"] / max(1, info["iterations"]),
                 **vs_minres(xs, info["ms_total"])}
     if rank == 0 and world == 1 and not args.no_cpu:
-        gd, el, reps, ndof = oracle_sample(seconds=8.0)
-        out["cpu_baseline"] = {"value": gd, "unit": "GDOF/s", "cores": 1, "kind": "oracle",
-                               "sample": "4^3 elements of the same recipe (%d DOFs): %d assembled-CSR block "
-                                         "applies in %.1f s, scipy single-threaded" % (ndof, reps, el)}
+        out["cpu_baseline"] = cpu_baseline(seconds=8.0)
     op.close()
     if rank == 0:
         print(json.dumps(out), flush=True)
