@@ -351,19 +351,30 @@ hd_status hd_profile(hd_handle h, int32_t enable);
 hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms);
 
 /* -- allocation-free solve (no counterpart in the paper) -------------------- */
-/* Same computation and result as hd_minres_solve (FP64 only, precision = 0),
- * for callers that may not allocate device memory once their handle exists:
- * for instance a time-stepping or embedding host that fixes its device memory
- * budget after initialisation, or code running where another component owns
- * the device allocator. hd_minres_solve allocates its nine work vectors with
- * cudaMalloc on its first call; this entry point instead takes its work space
+/* Same computation and result as hd_minres_solve with precision = 0, max_outer <= 1
+ * and the V/W-cycle Schur block, for callers that may not allocate device memory once
+ * their handle exists: for instance a time-stepping or embedding host that fixes its
+ * device memory budget after initialisation, or code running where another component
+ * owns the device allocator. hd_minres_solve allocates, on its first call, eleven work
+ * vectors of n_rt + n_l2 doubles and a device state word with cudaMalloc (and, on first
+ * use for each pair of vectors, a CUDA graph of the V/W-cycle with its own stream and
+ * events); this entry point instead takes ten work vectors and the 256-byte state slot
  * from a fixed device array compiled into the library (HD_NOALLOC_SCRATCH_DOUBLES
- * doubles = 16 MiB, held by every GPU that loads the library until the process
- * exits) and calls no cudaMalloc, cudaFree or other allocating routine.
+ * doubles = 16 MiB, held by every GPU that loads the library until the process exits),
+ * launches the V/W-cycle without a graph, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
  *  - Limit: n_rt + n_l2 <= HD_NOALLOC_MAX_DOFS; larger problems are rejected
  *    with HD_ERR_INVALID_ARG (message in hd_last_error).
- *  - The first call on a device looks up the array's device address (with that
- *    device current); make that first call before any stream capture.
+ *  - precision != 0: HD_ERR_INVALID_ARG. max_outer > 1 (the FP64 residual-correction
+ *    loop), resume, or the learned Schur preconditioner enabled on the handle:
+ *    HD_ERR_NOT_IMPLEMENTED (use hd_minres_solve). The Lanczos-vector capture of
+ *    hd_learned_train does not run inside this call.
+ *  - hd_create, on a problem within the limit, looks up the array's device address
+ *    with the handle's device current and runs this solve once (one iteration on a
+ *    zero right-hand side, in two vectors it frees again), so that every kernel the
+ *    solve launches is loaded before the caller's first call (with lazy module
+ *    loading a kernel's first launch can take device memory). Create the handle
+ *    before any stream capture.
  *  - Every call shares the one array and it keeps the last call's contents
  *    (the call initialises what it reads); calls that overlap on the GPU race.
  *  - Profiling (hd_profile) is suspended during the call; ms_total is host

@@ -475,6 +475,7 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     }
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = hd_cuda_check(h, e, "setup"); break; }
+    if ((st = noalloc_prepare(h)) != HD_OK) break;
     const auto t_end = std::chrono::steady_clock::now();
     h->setup_ms[4] = std::chrono::duration<float, std::milli>(t_end - t_emul).count();
     h->setup_ms[5] = std::chrono::duration<float, std::milli>(t_end - t_create).count();

@@ -299,4 +299,6 @@ hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p);
 
 // Krylov (k_krylov.cu)
 hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info);
+// set-up of hd_minres_solve_noalloc on this handle's device (called by hd_create)
+hd_status noalloc_prepare(hd_op* h);
 hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, double* d_out);

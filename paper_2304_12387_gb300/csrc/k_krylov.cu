@@ -532,12 +532,14 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
 }
 
 // ---- allocation-free MINRES ----------------------------------------------------
-// hd_minres_solve allocates its nine work vectors with cudaMalloc on its first
-// call. hd_minres_solve_noalloc takes its work space from the file-scope device
-// array below instead, so that a caller who may not allocate device memory once
-// its handle exists can still solve. The array is part of the module: every GPU
-// that loads the library holds it until the process exits. Calls share it, so
-// calls that overlap on the GPU (other streams, other threads) race.
+// hd_minres_solve allocates eleven work vectors of n_rt + n_l2 doubles and its
+// device state word with cudaMalloc on its first call (and the V/W-cycle graphs,
+// their stream and events on first use). hd_minres_solve_noalloc takes its work
+// space from the file-scope device array below instead and launches the V/W-cycle
+// directly, so that a caller who may not allocate device memory once its handle
+// exists can still solve. The array is part of the module: every GPU that loads
+// the library holds it until the process exits. Calls share it, so calls that
+// overlap on the GPU (other streams, other threads) race.
 static __device__ __align__(256) double g_noalloc_scratch[HD_NOALLOC_SCRATCH_DOUBLES];
 
 namespace {
@@ -648,6 +650,44 @@ hd_status minres_run_ws(hd_op* h, double* ws, const double* b, double* x, const 
 
 }  // namespace
 
+// Called by hd_create (which may allocate) for problems within the limit: looks up
+// the scratch array's device address on this device and runs the allocation-free
+// solve once, one iteration on a zero right-hand side, so that every kernel it
+// launches has been loaded before the caller's first call (with lazy module
+// loading a kernel's first launch can take device memory) and that call
+// allocates nothing. The two vectors of the warm-up are the only allocations.
+hd_status noalloc_prepare(hd_op* h) {
+  const int64_t n = h->n_rt + h->n_l2;
+  if (n > HD_NOALLOC_MAX_DOFS || n == 0) return HD_OK;
+  double* ws = nullptr;
+  hd_status st = noalloc_scratch(h, &ws);
+  if (st != HD_OK) return st;
+  double *b = nullptr, *x = nullptr;
+  if (cudaMalloc(&b, sizeof(double) * n) != cudaSuccess || cudaMalloc(&x, sizeof(double) * n) != cudaSuccess) {
+    cudaFree(b);
+    return hd_fail(h, HD_ERR_OOM, "allocation-free solve warm-up");
+  }
+  hd_solve_opts o{};
+  o.rtol = 1e-8;
+  o.maxit = 1;
+  o.check_every = 1;
+  hd_solve_info info{};
+  const bool prof = h->prof, graphs_off = h->graphs_off;
+  h->prof = false;
+  h->graphs_off = true;
+  st = HD_OK;
+  if (cudaMemsetAsync(b, 0, sizeof(double) * n, h->stream) != cudaSuccess)
+    st = hd_fail(h, HD_ERR_CUDA, "allocation-free solve warm-up");
+  else
+    st = minres_run_ws(h, ws, b, x, &o, &info);  // zero b: the recurrence stops at once (HD_OK)
+  h->prof = prof;
+  h->graphs_off = graphs_off;
+  cudaStreamSynchronize(h->stream);
+  cudaFree(b);
+  cudaFree(x);
+  return st;
+}
+
 // ---- MINRES checkpoints ----------------------------------------------------------
 // File: header, the device state word, then x, v, r_{j-1}, r_j, w_{j-1}, w_j (FP64,
 // n_rt + n_l2 each, host byte order).
@@ -733,6 +773,12 @@ extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, doubl
   if (!h || !b || !x || !o || b == x || o->maxit < 1 || !(o->rtol > 0)) return HD_ERR_INVALID_ARG;
   if (o->precision != 0) return hd_fail(h, HD_ERR_INVALID_ARG, "hd_minres_solve_noalloc: FP64 only (precision = 0)");
   if (o->resume) return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "hd_minres_solve_noalloc: no resume (use hd_minres_solve)");
+  if (o->max_outer > 1)
+    return hd_fail(h, HD_ERR_NOT_IMPLEMENTED,
+                   "hd_minres_solve_noalloc: one MINRES pass only (max_outer <= 1; use hd_minres_solve)");
+  if (h->schur_mode != 0)
+    return hd_fail(h, HD_ERR_NOT_IMPLEMENTED,
+                   "hd_minres_solve_noalloc: V/W-cycle Schur block only (the learned network is enabled)");
   const int64_t n = h->n_rt + h->n_l2;
   if (n > HD_NOALLOC_MAX_DOFS) {
     char msg[160];
@@ -743,11 +789,15 @@ extern "C" hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, doubl
   double* ws = nullptr;
   hd_status st = noalloc_scratch(h, &ws);
   if (st != HD_OK) return st;
-  // profiling would create its event pairs on first use: keep it off for this call
-  const bool prof = h->prof;
+  // profiling would create its event pairs on first use, and the cached V/W-cycle
+  // graphs are keyed by their vectors (here in the scratch array: a first use would
+  // instantiate new graphs on a stream of their own): both off for this call
+  const bool prof = h->prof, graphs_off = h->graphs_off;
   h->prof = false;
+  h->graphs_off = true;
   st = minres_run_ws(h, ws, b, x, o, info);
   h->prof = prof;
+  h->graphs_off = graphs_off;
   return st;
 }
 
