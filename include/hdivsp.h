@@ -114,7 +114,14 @@ typedef struct {
   int32_t fp64_emulation;/* 0: the element kernel computes in FP64; 1: in double-float (pairs of
                             FP32 numbers, about 48 significant bits) on the FP32 pipe, with FP64
                             vectors in and out and the same FP64 results to ~1e-13 relative;
-                            HD_WINV_DENSE only. Setup, lattice kernels and MINRES stay FP64. */
+                            HD_WINV_DENSE only. Setup, lattice kernels and MINRES stay FP64.
+                            FP32's exponent range applies: hd_create refuses (HD_ERR_INVALID_ARG)
+                            a problem where an element's geometric factors, W_e^-1 or
+                            c_e W_e^-1 have their largest magnitude outside [2^-60, 2^60]
+                            (entries far below their element's largest flush to zero
+                            harmlessly); vector entries with |x| < 2^-126
+                            enter the element kernel as 0 and |x| > 3.4e38 as inf, and entries
+                            below about 2^-102 keep fewer than 48 bits (keep vectors near O(1)). */
   int32_t smooth_levels; /* prolongation of the Schur V-cycle: 0: piecewise constant on the 2x2x2
                             aggregates (unsmoothed aggregation); 1: the first level's prolongator
                             smoothed, P = (I - 4/3 D_l1^-1 S~) P0 (smoothed aggregation; the first

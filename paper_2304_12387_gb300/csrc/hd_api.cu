@@ -261,6 +261,42 @@ __global__ void k_split_df(int64_t n, const double* __restrict__ a, dfloat* __re
   b[i] = dfloat(h, __double2float_rn(v - (double)h));
 }
 
+// Range guard of the double-float element data, one warp per element: the largest
+// magnitude of the element's geometric factors (6 q^3), of its W_e^-1 (k^6) and of
+// c_e W_e^-1 must lie in [2^-60, 2^60] (c_e = 0 allowed), so that the significant
+// entries and their products with O(1) vector entries keep both halves of the FP32
+// pairs normal; entries far below their element's largest (round-off-level zeros)
+// flush harmlessly. flag = 1 otherwise, or on a non-finite value.
+__device__ __forceinline__ bool df_scale_ok(double m) { return m >= 0x1p-60 && m <= 0x1p60; }
+__global__ void k_df_range(int64_t E, int ng, int nw, const double* __restrict__ G, const double* __restrict__ winv,
+                           const double* __restrict__ cs, int* __restrict__ flag) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (e >= E) return;
+  double mg = 0.0, mw = 0.0;
+  bool finite = true;
+  for (int i = lane; i < ng; i += 32) {
+    const double v = fabs(G[e * ng + i]);
+    finite = finite && isfinite(v);
+    mg = fmax(mg, v);
+  }
+  for (int i = lane; i < nw; i += 32) {
+    const double v = fabs(winv[e * nw + i]);
+    finite = finite && isfinite(v);
+    mw = fmax(mw, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mg = fmax(mg, __shfl_xor_sync(0xffffffffu, mg, o));
+    mw = fmax(mw, __shfl_xor_sync(0xffffffffu, mw, o));
+  }
+  finite = __all_sync(0xffffffffu, finite);
+  if (lane != 0) return;
+  const double c = fabs(cs[e]);
+  bool ok = finite && isfinite(c) && df_scale_ok(mg) && (nw == 0 || df_scale_ok(mw));
+  if (c != 0.0 && nw > 0) ok = ok && df_scale_ok(c * mw);
+  if (!ok) atomicOr(flag, 1);
+}
+
 void destroy_all(hd_op* h) {
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
   cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
@@ -446,6 +482,29 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     auto t_emul = std::chrono::steady_clock::now();
     h->setup_ms[3] = std::chrono::duration<float, std::milli>(t_emul - t_pre).count();
     // the affine fast path of the FP64 and double-float applies (dense W^-1 mode, q = k+1)
+    if (h->emul) {
+      // the double-float copies hold the FP64 element data to ~48 bits only inside
+      // FP32's exponent range: refuse elements whose data leave it (k_df_range)
+      const int64_t ng = E * 6 * nq, nw = E * nl2 * nl2;
+      if (cudaMemsetAsync(d_bad, 0, 4, s) != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "range check"); break; }
+      if (E > 0)
+        k_df_range<<<(unsigned)((E * 32 + 255) / 256), 256, 0, s>>>(E, 6 * nq, nw > 0 ? nl2 * nl2 : 0, h->d_G,
+                                                                     h->d_winv, h->d_cscale, d_bad);
+      int out_of_range = 0;
+      if (cudaGetLastError() != cudaSuccess ||
+          cudaMemcpyAsync(&out_of_range, d_bad, 4, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess) {
+        st = hd_fail(h, HD_ERR_CUDA, "range check");
+        break;
+      }
+      if (out_of_range) {
+        st = hd_fail(h, HD_ERR_INVALID_ARG,
+                     "fp64_emulation = 1: an element's geometric factors, W^-1 or C = c_e W^-1 have their "
+                     "largest magnitude outside the double-float range [2^-60, 2^60]; rescale the problem "
+                     "or use fp64_emulation = 0");
+        break;
+      }
+    }
     std::vector<double> ga;
     if (d->affine && h->q == k + 1 && h->winv_mode == HD_WINV_DENSE && E > 0 && affine_factors(d, bco.data(), ga)) {
       if ((st = dalloc(h, &h->d_Ga, E * 8, "affine factors")) != HD_OK) break;
@@ -454,6 +513,15 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
         break;
       }
       if (h->emul) {
+        for (int64_t e = 0; e < E && st == HD_OK; ++e) {
+          double m = 0.0;
+          for (int i = 0; i < 7; ++i) m = std::fmax(m, std::fabs(ga[e * 8 + i]));
+          if (!(m >= 0x1p-60 && m <= 0x1p60))
+            st = hd_fail(h, HD_ERR_INVALID_ARG,
+                         "fp64_emulation = 1: an element's affine factors have their largest magnitude outside "
+                         "the double-float range [2^-60, 2^60]; rescale the problem or use fp64_emulation = 0");
+        }
+        if (st != HD_OK) break;
         if (cudaMalloc(&h->x_Ga, sizeof(dfloat) * E * 8) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "affine factors"); break; }
         k_split_df<<<(unsigned)((E * 8 + 255) / 256), 256, 0, s>>>(E * 8, h->d_Ga, h->x_Ga);
       }

@@ -91,3 +91,35 @@ def test_corrupted_learned_network_falls_back_to_the_vcycle():
     assert np.abs(xn - x2).max() <= 1e-12 * np.abs(x2).max()
     op.close()
     plain.close()
+
+
+@pytest.mark.parametrize("affine", [False, True])
+def test_double_float_refuses_element_data_outside_its_range(affine):
+    """The double-float element kernel holds FP64 data to ~48 bits only inside FP32's
+    exponent range: hd_create must refuse fp64_emulation = 1 when an element's largest
+    geometric factor (beta = 1e-35 makes them ~1e-35 < 2^-60) or its largest entry of
+    C = W^-1/alpha (alpha = 1e40) leaves [2^-60, 2^60], and the FP64 kernel must still
+    take the same problem."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    import synth
+    from oracle.assembly import GRAD_DIV, Problem
+    n, k = 2, 2
+    vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=0.0 if affine else 0.1)
+    for alpha, beta in ((1.0, 1e-35), (1e40, 1.0)):
+        kw = dict(kind=hd.HD_GRAD_DIV, ess_mask=0, q=k + 1 if affine else k + 2, affine=affine, coarse_max=8)
+        with pytest.raises(hd.HdError) as err:
+            hd.Operator(n, n, n, k, vx, vy, vz, alpha, beta, fp64_emulation=1, **kw)
+        assert err.value.status == hd.HD_ERR_INVALID_ARG
+        op = hd.Operator(n, n, n, k, vx, vy, vz, alpha, beta, fp64_emulation=0, **kw)
+        prob = Problem(n, n, n, k, vx, vy, vz, alpha, beta, kind=GRAD_DIV, ess_mask=0, q=kw["q"])
+        x = np.random.Generator(np.random.PCG64(5)).uniform(-1, 1, prob.n)
+        y = torch.empty(prob.n, dtype=torch.float64, device="cuda")
+        op.hd_apply_op(torch.from_numpy(x).cuda(), y)
+        ref = prob.apply_op(x)
+        yu, ru = y.cpu().numpy()[:prob.lat.n_rt], ref[:prob.lat.n_rt]
+        yq, rq = y.cpu().numpy()[prob.lat.n_rt:], ref[prob.lat.n_rt:]
+        assert np.abs(yu - ru).max() <= 1e-12 * np.abs(ru).max()
+        assert np.abs(yq - rq).max() <= 1e-12 * np.abs(rq).max()
+        op.close()
