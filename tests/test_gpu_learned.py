@@ -4,7 +4,7 @@ The GPU network computes in FP16 (activations and weights) with FP32
 accumulation, so it is compared with the reference evaluated on the same
 FP16-rounded weights, at a norm-scaled tolerance of 2e-2 for outputs and 5e-2
 for gradients (FP16 carries 11 significant bits; each output sums 27 x 32
-terms per layer over four layers). The coarse correction is FP64 (1e-11)."""
+terms per layer over four layers). The coarse correction is FP64 (1e-12)."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -64,7 +64,7 @@ def test_coarse_correction_matches_reference(name):
     z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
     op.hd_coarse_correction(torch.from_numpy(r).cuda(), z)
     torch.cuda.synchronize()
-    assert close(z.cpu().numpy(), _Q(bp, r), 1e-11) <= 1e-11
+    assert close(z.cpu().numpy(), _Q(bp, r), 1e-12) <= 1e-12
     op.close()
 
 

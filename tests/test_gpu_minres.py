@@ -84,7 +84,7 @@ def test_wcycle_matches_oracle(name):
     z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
     op.hd_vcycle(torch.from_numpy(r).cuda(), z)
     torch.cuda.synchronize()
-    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-11) <= 1e-11
+    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-12) <= 1e-12
     b = np.random.Generator(np.random.PCG64(14)).uniform(-1, 1, prob.n)
     b[prob.ess] = 0.0
     if bp.singular:
@@ -115,12 +115,12 @@ def test_fp64_emulation_solver_matches_oracle(name, cycle):
     z = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
     op.hd_vcycle(torch.from_numpy(r).cuda(), z)
     torch.cuda.synchronize()
-    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-11) <= 1e-11
+    assert close(z.cpu().numpy(), bp.vc._cycle(0, r), 1e-12) <= 1e-12
     rr = rng.uniform(-1, 1, prob.n)
     zz = torch.empty(prob.n, dtype=torch.float64, device="cuda")
     op.hd_apply_prec(torch.from_numpy(rr).cuda(), zz)
     torch.cuda.synchronize()
-    assert close(zz.cpu().numpy(), bp.apply(rr), 1e-11) <= 1e-11
+    assert close(zz.cpu().numpy(), bp.apply(rr), 1e-12) <= 1e-12
     b = rng.uniform(-1, 1, prob.n)
     b[prob.ess] = 0.0
     if bp.singular:

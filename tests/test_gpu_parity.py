@@ -153,7 +153,7 @@ def test_vcycle_and_levels(pair):
     x = torch.empty(prob.lat.n_l2, dtype=torch.float64, device="cuda")
     op.hd_vcycle(_dev(b), x)
     ref = bp.vc._cycle(0, b)
-    assert close(_host(x), ref, 1e-11) <= 1e-11
+    assert close(_host(x), ref, 1e-12) <= 1e-12
 
 
 def test_apply_prec(pair):
@@ -167,7 +167,7 @@ def test_apply_prec(pair):
     zg = _host(z)
     nrt = prob.lat.n_rt
     assert close(zg[:nrt], zr[:nrt], RTOL) <= RTOL
-    assert close(zg[nrt:], zr[nrt:], 1e-11) <= 1e-11
+    assert close(zg[nrt:], zr[nrt:], 1e-12) <= 1e-12
 
 
 def test_f32_operator_close(pair):
