@@ -433,6 +433,34 @@ hd_status hd_learned_load(hd_handle h, const char* path);
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);
 hd_status hd_apply_prec_f32(hd_handle h, const float* r, float* z);
 
+/* -- tensor-core operator of affine meshes (inner operator, mixed precision) -- */
+/* On parallelepiped elements the Piola-mapped RT mass is M_e = sum_ab G_ab K_ab
+ * (Eq. matrices with J constant: G = beta J^T J / det J per element, K_ab the
+ * reference-cube blocks between velocity components, the same for every element),
+ * so the element loop becomes dense GEMMs with the elements of a tile of 128 as rows,
+ * which these calls run on the tensor cores (tcgen05.mma, FP16 operands, FP32
+ * accumulators in tensor memory). Each operand is split into an FP16 pair
+ * (hi + lo, with power-of-two scaling per element component and per block), three
+ * products per block: an FP32-class operator (relative error about 1e-6 of the
+ * largest entry, against ~1e-16 for hd_apply_op). D, D^T and C = c_e det J
+ * (H^-1 x H^-1 x H^-1) (the affine W_e^-1) run in FP32 on the CUDA cores in the same
+ * kernel. Requires a handle on the affine fast path (hd_create with affine = 1,
+ * q = k + 1, HD_WINV_DENSE, every element a parallelepiped), k = 2..4 and a GPU of
+ * the sm_100 family; else HD_ERR_NOT_IMPLEMENTED. The first call builds the split
+ * reference blocks and FP32 element factors on the handle (allocates).
+ * x, y: device vectors of n_rt + n_l2 entries (FP64, or FP32 for _f32), not aliased. */
+hd_status hd_apply_op_tc(hd_handle h, const double* x, double* y);
+hd_status hd_apply_op_tc_f32(hd_handle h, const float* x, float* y);
+/* Inner operator of the mixed-precision solves (hd_minres_solve and hd_gmres_solve
+ * with precision = 1, and hd_apply_op_f32): 0 = the FP32 element kernel (default),
+ * 1 = the tensor-core operator above (same requirements; HD_ERR_NOT_IMPLEMENTED
+ * otherwise, the mode is then unchanged). */
+hd_status hd_set_inner_operator(hd_handle h, int32_t mode);
+/* HD_OK, or HD_ERR_CUDA when a bounded wait inside the tensor-core kernel ran out
+ * since the last call (the kernel then skipped the rest of its work); synchronises
+ * the handle's stream and clears the record. */
+hd_status hd_tc_status(hd_handle h);
+
 #ifdef __cplusplus
 }
 #endif

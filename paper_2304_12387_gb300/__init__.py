@@ -120,6 +120,10 @@ _SIGS = {
     "hd_resume_minres": [_H, ctypes.c_char_p],
     "hd_apply_op_f32": [_H, _VP, _VP],
     "hd_apply_prec_f32": [_H, _VP, _VP],
+    "hd_apply_op_tc": [_H, _VP, _VP],
+    "hd_apply_op_tc_f32": [_H, _VP, _VP],
+    "hd_set_inner_operator": [_H, ctypes.c_int32],
+    "hd_tc_status": [_H],
 }
 
 
@@ -287,6 +291,16 @@ class Operator:
     def hd_apply_schur(self, x, y): self._call("hd_apply_schur", x, y)
     def hd_vcycle(self, b, x): self._call("hd_vcycle", b, x)
     def hd_apply_op_f32(self, x, y): self._call("hd_apply_op_f32", x, y)
+    def hd_apply_op_tc(self, x, y): self._call("hd_apply_op_tc", x, y)
+    def hd_apply_op_tc_f32(self, x, y): self._call("hd_apply_op_tc_f32", x, y)
+
+    def hd_set_inner_operator(self, mode):
+        """0: FP32 element kernel (CUDA cores); 1: tensor-core operator (affine meshes, k = 2..4)."""
+        _check(lib().hd_set_inner_operator(self.h, int(mode)), self.h)
+
+    def hd_tc_status(self):
+        """Status of the tensor-core kernel's bounded waits since the last call (HD_OK or HD_ERR_CUDA)."""
+        return lib().hd_tc_status(self.h)
     def hd_apply_prec_f32(self, r, z): self._call("hd_apply_prec_f32", r, z)
     def hd_get_diagonals(self, mt, ct): self._call("hd_get_diagonals", mt, ct)
 

@@ -298,6 +298,7 @@ __global__ void k_df_range(int64_t E, int ng, int nw, const double* __restrict__
 }
 
 void destroy_all(hd_op* h) {
+  tc_free(h);
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
   cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
   cudaFree(h->d_wchol);
@@ -348,11 +349,13 @@ hd_status apply_op_internal(hd_op* h, const double* x, double* y) {
 
 // y = AA x with the FP32 element kernel reading and writing FP64 vectors
 hd_status apply_op_mixed_internal(hd_op* h, const double* x, double* y) {
+  if (h->inner_op == 1) return tc_apply(h, x, y);
   HD_CK(h, cudaMemsetAsync(y, 0, sizeof(double) * h->n_rt, h->stream));
   return elem_op_f32io64(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
 }
 
 hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y) {
+  if (h->inner_op == 1) return tc_apply_f32(h, x, y);
   HD_CK(h, cudaMemsetAsync(y, 0, sizeof(float) * h->n_rt, h->stream));
   return elem_op_f32(h, OP_M | OP_DT | OP_D | OP_C, x, x + h->n_rt, y, y + h->n_rt);
 }

@@ -106,6 +106,7 @@ __device__ __forceinline__ void lat_coords(int64_t c, int X, int Y, int& I, int&
 }
 
 struct MinresState;  // device-side scalars of the MINRES recurrence
+struct TcState;      // data of the tensor-core operator (k_op_tc.cu)
 
 struct hd_op {
   // problem
@@ -223,6 +224,10 @@ struct hd_op {
   // streams and events of the pipelined host-buffer apply (copy in, copy out)
   cudaStream_t xstream[2] = {nullptr, nullptr};
   std::vector<cudaEvent_t> xev;
+  // inner operator of the mixed-precision solves: 0 = FP32 element kernel on the CUDA
+  // cores, 1 = the tensor-core operator of affine meshes (k_op_tc.cu)
+  int inner_op = 0;
+  TcState* tc = nullptr;
   // profiling of the fused element kernel
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
@@ -299,6 +304,12 @@ hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p);
 
 // Krylov (k_krylov.cu)
 hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info);
+// tensor-core operator of affine meshes (k_op_tc.cu): y = AA x with FP16-pair operands
+// and FP32 accumulation; set-up on first use
+hd_status tc_setup(hd_op* h);
+void tc_free(hd_op* h);
+hd_status tc_apply(hd_op* h, const double* x, double* y);
+hd_status tc_apply_f32(hd_op* h, const float* x, float* y);
 // set-up of hd_minres_solve_noalloc on this handle's device (called by hd_create)
 hd_status noalloc_prepare(hd_op* h);
 hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, double* d_out);
