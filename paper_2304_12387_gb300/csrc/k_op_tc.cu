@@ -16,13 +16,19 @@
 // CUDA cores in FP32: D u and the own-cell D^T q of the lattice divergence (Sec. 2.1)
 // and C q = c_e det J (H^-1 x H^-1 x H^-1) q (the affine W_e^-1, Sec. 2.5).
 //
-// Kernel structure (persistent, one CTA per SM, 160 threads): warps 0-3 own the 128
-// elements of a tile (gather and split into the A operand, C q and D u, epilogue from
-// TMEM lane t = element t); warp 4 allocates TMEM, and its lane 0 streams the nine
-// K_ab blocks (hi + lo, pre-laid-out in global memory) through a three-stage shared
-// memory ring with bulk copies (cp.async.bulk, mbarrier transaction counts) and issues
-// the MMAs, signalling with tcgen05.commit. Every wait is bounded; a timeout sets the
-// error word, the CTA drains what it has in flight and frees its TMEM.
+// Kernel structure (persistent, one CTA per SM, 288 threads): eight element warps own
+// the 128 elements of a tile, two threads per element (element t & 127, half t >> 7):
+// they stage the tile's L2 coefficients q~ in shared memory with coalesced loads,
+// gather each half of the element's RT coefficients, split them into the FP16 pairs
+// of the A operand (a per-element, per-component power of two from the maximum the two
+// halves exchange through shared memory), compute y_q = D u - C q for half of the
+// element's cells while the tensor core works, and read half of the accumulator
+// columns from TMEM lane t & 127 in the epilogue. Warp 8 allocates TMEM, and its lane
+// 0 streams the nine K_ab blocks (hi + lo, pre-laid-out in global memory) through a
+// two-stage shared-memory ring with bulk copies (cp.async.bulk, mbarrier transaction
+// counts) and issues the MMAs, signalling with tcgen05.commit. Every wait is bounded;
+// a timeout sets the error word, the CTA drains what it has in flight and frees its
+// TMEM.
 #include <cuda_fp16.h>
 
 #include <cmath>
@@ -34,23 +40,28 @@
 
 namespace {
 
-constexpr int TC_TILE = 128;     // elements per tile = TMEM lanes = element threads
-constexpr int TC_THREADS = 160;  // four element warps and the control warp
-constexpr int TC_STAGES = 3;     // K_ab ring depth
+constexpr int TC_TILE = 128;          // elements per tile = TMEM lanes
+constexpr int TC_EW = 8;              // element warps: two threads per element
+constexpr int TC_ET = 32 * TC_EW;     // element threads
+constexpr int TC_THREADS = TC_ET + 32;  // and the control warp
+constexpr int TC_STAGES = 2;          // K_ab ring depth
 constexpr int TC_TMEM_COLS = 512;
 
 template <int K>
 struct TcShape {
   static constexpr int NC = (K + 1) * K * K;             // RT dofs per component
   static constexpr int NP = (NC + 15) / 16 * 16;         // padded to the MMA's N and K granules
+  static constexpr int NH = (NC + 1) / 2;                // dofs per thread of an element's pair
   static constexpr int NL2 = K * K * K;
+  static constexpr int QP = NL2 + 1;                     // staged q~ row (odd: no bank conflicts)
   static constexpr uint32_t U_BYTES = TC_TILE * NP * 2;  // one component, one half of the pair
+  static constexpr uint32_t Q_BYTES = (TC_TILE * QP * 4 + 15) / 16 * 16;
   static constexpr uint32_t KB_BYTES = NP * NP * 2;      // one K_ab block, one half of the pair
-  static constexpr uint32_t SMEM = 6 * U_BYTES + TC_STAGES * 2 * KB_BYTES;
+  static constexpr uint32_t SMEM = 6 * U_BYTES + Q_BYTES + TC_STAGES * 2 * KB_BYTES;
   // accumulator regions of 3 NP columns: a = 2 reuses a = 0's when nine do not fit
   static constexpr bool REUSE = 9 * NP > TC_TMEM_COLS;
   static_assert(3 * NP * (REUSE ? 2 : 3) <= TC_TMEM_COLS, "accumulators exceed TMEM");
-  static_assert(SMEM <= 227 * 1024 - 1024, "shared memory");
+  static_assert(SMEM <= 227 * 1024 - 4096, "shared memory");
 };
 
 struct TcParams {
@@ -122,44 +133,194 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, volatile 
   return false;
 }
 
+// barrier among the element threads only (the control warp does not take part)
+__device__ __forceinline__ void tc_elem_sync() { asm volatile("bar.sync 1, %0;" ::"n"(TC_ET) : "memory"); }
+
+// Gather of component B of the tile's RT coefficients into the FP16 pairs of the A
+// operand (see the kernel). Essential faces and elements past the end give 0.
+// Gather of component B of element el's RT coefficients, half HF of them (dofs
+// [HF*NH, min(NC, (HF+1)*NH))), into the FP16 pairs of the A operand: the two threads of
+// the element exchange their maxima through shared memory (smax[half][element]) and
+// take the same power-of-two scale. Essential faces and elements past the end give 0.
+template <typename IO, int K, int B, int HF>
+__device__ __forceinline__ float tc_gather_half(const LatticeDims& L, bool valid, int ex, int ey, int ez,
+                                                const IO* __restrict__ x, unsigned char* sU, float (*smax)[TC_TILE],
+                                                int el) {
+  using S = TcShape<K>;
+  constexpr int NC = S::NC, NP = S::NP, NH = S::NH, N0 = HF * NH, N1 = HF ? NC : NH;
+  float v[NH];
+  float m = 0.f;
+#pragma unroll
+  for (int jj = 0; jj < NH; ++jj) {
+    const int n = N0 + jj;
+    v[jj] = 0.f;
+    if (n < N1 && valid) {
+      int i, j, l;
+      tc_dof_ijl<K>(B, n, i, j, l);
+      bool ess;
+      const int g = tc_rt_global<K>(L, B, ex, ey, ez, i, j, l, ess);
+      if (!ess) v[jj] = tc_in<IO>(x[g]);
+    }
+    m = fmaxf(m, fabsf(v[jj]));
+  }
+  smax[HF][el] = m;
+  tc_elem_sync();
+  const float sc = tc_scale_for(fmaxf(smax[0][el], smax[1][el]));
+  const float inv = 1.f / sc;
+  unsigned char* hi = sU + B * S::U_BYTES;
+  unsigned char* lo = sU + (3 + B) * S::U_BYTES;
+#pragma unroll
+  for (int jj = 0; jj < NH; ++jj) {
+    const int n = N0 + jj;
+    if (n >= N1) continue;
+    const float w = v[jj] * inv;
+    const __half h = __float2half_rn(w);
+    const uint32_t off = tc::kmajor_offset(el, n, NP);
+    *reinterpret_cast<__half*>(hi + off) = h;
+    *reinterpret_cast<__half*>(lo + off) = __float2half_rn(w - __half2float(h));
+  }
+  return sc;
+}
+
+// value of local dof n of component b of tile element el from its FP16 pair (times the scale)
+template <int K>
+__device__ __forceinline__ float tc_u_smem(const unsigned char* sU, int b, int el, int n, float sc) {
+  using S = TcShape<K>;
+  const uint32_t off = tc::kmajor_offset(el, n, S::NP);
+  const float h = __half2float(*reinterpret_cast<const __half*>(sU + b * S::U_BYTES + off));
+  const float l = __half2float(*reinterpret_cast<const __half*>(sU + (3 + b) * S::U_BYTES + off));
+  return (h + l) * sc;
+}
+
+// y_q = D u - C q on the cells a3 in [HF ? ceil(K/2) : 0, HF ? K : ceil(K/2)) of one element:
+// C q = sC (H^-1 x H^-1 x H^-1) q with the z contraction first (it alone mixes a3), D u
+// from the element's FP16 pairs in shared memory (essential faces were gathered as 0)
+template <typename IO, int K, int HF>
+__device__ __forceinline__ void tc_yq(const LatticeDims& L, const TcParams& P, int ex, int ey, int ez, float sC,
+                                      const float* q, const unsigned char* sU, int el, const float sc[3],
+                                      IO* __restrict__ yq) {
+  constexpr int A3H = (K + 1) / 2, A3LO = HF ? A3H : 0, A3HI = HF ? K : A3H;
+#pragma unroll
+  for (int a3 = A3LO; a3 < A3HI; ++a3) {
+    float t1[K * K], t2[K * K];
+#pragma unroll
+    for (int c = 0; c < K * K; ++c) {
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < K; ++m) s = fmaf(P.HI[a3 * K + m], q[c + K * K * m], s);
+      t1[c] = s;  // c = a1 + K a2
+    }
+#pragma unroll
+    for (int c = 0; c < K * K; ++c) {
+      const int a1 = c % K, a2 = c / K;
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < K; ++m) s = fmaf(P.HI[a2 * K + m], t1[a1 + K * m], s);
+      t2[c] = s;
+    }
+#pragma unroll
+    for (int c = 0; c < K * K; ++c) {
+      const int a1 = c % K, a2 = c / K;
+      float s = 0.f;
+#pragma unroll
+      for (int m = 0; m < K; ++m) s = fmaf(P.HI[a1 * K + m], t2[m + K * a2], s);
+      // x-faces i = a1, a1 + 1; y-faces j = a2, a2 + 1; z-faces l = a3, a3 + 1
+      const float du = tc_u_smem<K>(sU, 0, el, a1 + 1 + (K + 1) * (a2 + K * a3), sc[0]) -
+                       tc_u_smem<K>(sU, 0, el, a1 + (K + 1) * (a2 + K * a3), sc[0]) +
+                       tc_u_smem<K>(sU, 1, el, a1 + K * (a2 + 1 + (K + 1) * a3), sc[1]) -
+                       tc_u_smem<K>(sU, 1, el, a1 + K * (a2 + (K + 1) * a3), sc[1]) +
+                       tc_u_smem<K>(sU, 2, el, a1 + K * (a2 + K * (a3 + 1)), sc[2]) -
+                       tc_u_smem<K>(sU, 2, el, a1 + K * (a2 + K * a3), sc[2]);
+      yq[(ex * K + a1) + (int64_t)L.X * ((ey * K + a2) + (int64_t)L.Y * (ez * K + a3))] = tc_out<IO>(du - sC * s);
+    }
+  }
+}
+
+// epilogue of component a on this thread's chunks of 16 accumulator columns (chunk c16
+// with c16 % 2 == HF): y_u += g_a0 D_a0 + g_a1 D_a1 + g_a2 D_a2 + own-cell D^T q, one
+// atomic per face (a shared face gets exactly two, from its two elements); essential
+// faces get x (the constrained identity)
+template <typename IO, int K, int HF>
+__device__ __forceinline__ void tc_epilogue(const LatticeDims& L, int a, uint32_t base, float ga0, float ga1, float ga2,
+                                            bool valid, int ex, int ey, int ez, const float* q,
+                                            const IO* __restrict__ x, IO* __restrict__ y) {
+  using S = TcShape<K>;
+  constexpr int NC = S::NC, NP = S::NP;
+#pragma unroll 1
+  for (int c0 = 16 * HF; c0 < NC; c0 += 32) {
+    float d0[16], d1[16], d2[16];
+    tc::tmem_ld16(base + c0, d0);
+    tc::tmem_ld16(base + NP + c0, d1);
+    tc::tmem_ld16(base + 2 * NP + c0, d2);
+    tc::tmem_wait_ld();
+    if (!valid) continue;
+#pragma unroll
+    for (int jj = 0; jj < 16; ++jj) {
+      const int n = c0 + jj;
+      if (n >= NC) continue;
+      int i, j, l;
+      tc_dof_ijl<K>(a, n, i, j, l);
+      bool ess;
+      const int gid = tc_rt_global<K>(L, a, ex, ey, ez, i, j, l, ess);
+      if (ess) {
+        atomicAdd(y + gid, x[gid]);
+        continue;
+      }
+      float v = ga0 * d0[jj] + ga1 * d1[jj] + ga2 * d2[jj];
+      // own-cell D^T q: + q of the cell whose high face this is, - q of the cell whose low face
+      const int node = a == 0 ? i : (a == 1 ? j : l);
+      const int st = a == 0 ? 1 : (a == 1 ? K : K * K);
+      const int c = i + K * (j + K * l);  // the cell on the face's high side (when node < K)
+      if (node > 0) v += q[c - st];
+      if (node < K) v -= q[c];
+      atomicAdd(y + gid, tc_out<IO>(v));
+    }
+  }
+}
+
 template <typename IO, int K>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_op_tc(const LatticeDims L, const int n_elem, const TcParams P, const __half* __restrict__ kblocks,
             const float* __restrict__ ef, const IO* __restrict__ x, IO* __restrict__ y, int* __restrict__ err) {
   using S = TcShape<K>;
-  constexpr int NC = S::NC, NP = S::NP, NL2 = S::NL2;
+  constexpr int NC = S::NC, NP = S::NP, NH = S::NH, NL2 = S::NL2, QP = S::QP;
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t bars[B_COUNT];
   __shared__ uint32_t tmem_slot;
-  __shared__ int abort_flag;
+  __shared__ int abort_flag;                   // any thread: others stop polling early
+  __shared__ int elem_abort;                   // element threads: written before, read after a barrier
+  __shared__ float smax[3][2][TC_TILE];        // per-half maxima of |u| per component and element
   unsigned char* sU = smem;                    // [part][component] A operands, K-major
-  unsigned char* sK = smem + 6 * S::U_BYTES;   // [stage][part] K_ab blocks
+  float* sQ = reinterpret_cast<float*>(smem + 6 * S::U_BYTES);                   // [element][QP]
+  unsigned char* sK = smem + 6 * S::U_BYTES + S::Q_BYTES;                         // [stage][part]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t n_tiles = ((int64_t)n_elem + TC_TILE - 1) / TC_TILE;
+  const int64_t off_q = (int64_t)L.n_xf + L.n_yf + (int64_t)L.X * L.Y * (L.Z + 1);  // = n_rt
   volatile int* abort_v = &abort_flag;
   auto bar = [&](int i) { return tc::smem_u32(&bars[i]); };
 
   if (tid == 0) {
     abort_flag = 0;
+    elem_abort = 0;
     for (int s = 0; s < TC_STAGES; ++s) {
       tc::mbar_init(bar(B_KFULL + s), 1);
       tc::mbar_init(bar(B_KEMPTY + s), 1);
     }
-    tc::mbar_init(bar(B_UFULL), TC_TILE);
+    tc::mbar_init(bar(B_UFULL), TC_ET);
     tc::mbar_init(bar(B_UEMPTY), 1);
     for (int a = 0; a < 3; ++a) {
       tc::mbar_init(bar(B_ACC + a), 1);
-      tc::mbar_init(bar(B_REG + a), TC_TILE);
+      tc::mbar_init(bar(B_REG + a), TC_ET);
     }
     tc::mbar_init(bar(B_FIN), 1);
     tc::fence_mbar_init();
   }
-  if (warp == 4) {
+  if (warp == TC_EW) {
     tc::tmem_alloc(tc::smem_u32(&tmem_slot), TC_TMEM_COLS);
     tc::tmem_relinquish();
   } else {
     // zero the A operands once: the padding columns stay zero (finite) for every tile
-    for (uint32_t o = tid * 16; o < 6 * S::U_BYTES; o += TC_TILE * 16)
+    for (uint32_t o = tid * 16; o < 6 * S::U_BYTES; o += TC_ET * 16)
       *reinterpret_cast<uint4*>(sU + o) = make_uint4(0, 0, 0, 0);
     tc::fence_proxy_async_smem();
   }
@@ -168,7 +329,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc::fence_after_sync();
   const uint32_t tbase = tmem_slot;
 
-  if (warp == 4) {
+  if (warp == TC_EW) {
     // ---- control warp: the K_ab ring and the MMAs (lane 0) ------------------------
     if ((tid & 31) == 0) {
       const uint32_t idesc = tc::idesc_f16_f32(TC_TILE, NP);
@@ -227,109 +388,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
     __syncwarp();
   } else {
-    // ---- element warps -------------------------------------------------------------
-    const int t = tid;
-    const uint32_t tlane = tbase + ((uint32_t)(32 * warp) << 16);
-    bool ok = true;
-    for (int64_t tile = blockIdx.x, it = 0; ok && tile < n_tiles; tile += gridDim.x, ++it) {
-      const int64_t e = tile * TC_TILE + t;
+    // ---- element warps ---------------------------------------------------------------
+    // Every exit decision is uniform over the element threads (they share a named
+    // barrier): a failed wait sets elem_abort, and all threads test it after a barrier.
+    const int el = tid & (TC_TILE - 1), hf = tid >> 7;  // own element (epilogue, y_q) and half
+    for (int64_t tile = blockIdx.x, it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
+      if (it > 0 && !tc_wait(bar(B_UEMPTY), (uint32_t)((it - 1) & 1), abort_v)) elem_abort = 1;
+      tc_elem_sync();
+      if (elem_abort) break;
+      const int64_t e0 = tile * TC_TILE;
+      // q~ of the tile's elements into shared memory, consecutive threads on consecutive cells
+      for (int s = tid; s < TC_TILE * NL2; s += TC_ET) {
+        const int a1 = s % K, r = s / K, e2 = r % TC_TILE, o = r / TC_TILE;  // o = a2 + K a3
+        float v = 0.f;
+        if (e0 + e2 < n_elem) {
+          const int f = (int)(e0 + e2), fx = f % L.nx, fy = (f / L.nx) % L.ny, fz = f / (L.nx * L.ny);
+          const int a2 = o % K, a3 = o / K;
+          v = tc_in<IO>(x[off_q + (fx * K + a1) + (int64_t)L.X * ((fy * K + a2) + (int64_t)L.Y * (fz * K + a3))]);
+        }
+        sQ[e2 * QP + a1 + K * o] = v;
+      }
+      // this thread's half of the element's RT coefficients, per component: FP16 pairs
+      const int64_t e = e0 + el;
       const bool valid = e < n_elem;
       const int ee = valid ? (int)e : 0;
       const int ex = ee % L.nx, ey = (ee / L.nx) % L.ny, ez = ee / (L.nx * L.ny);
-      if (it > 0 && !(ok = tc_wait(bar(B_UEMPTY), (uint32_t)((it - 1) & 1), abort_v))) break;
-      // gather u_e per component, scale into FP16's range, split into hi + lo
       float sc[3];
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        float v[NC];
-        float m = 0.f;
-#pragma unroll
-        for (int n = 0; n < NC; ++n) {
-          int i, j, l;
-          tc_dof_ijl<K>(b, n, i, j, l);
-          bool ess;
-          const int g = tc_rt_global<K>(L, b, ex, ey, ez, i, j, l, ess);
-          v[n] = (valid && !ess) ? tc_in<IO>(x[g]) : 0.f;
-          m = fmaxf(m, fabsf(v[n]));
-        }
-        sc[b] = tc_scale_for(m);
-        const float inv = 1.f / sc[b];
-        unsigned char* hi = sU + b * S::U_BYTES;
-        unsigned char* lo = sU + (3 + b) * S::U_BYTES;
-#pragma unroll
-        for (int n = 0; n < NC; ++n) {
-          const float w = v[n] * inv;
-          const __half h = __float2half_rn(w);
-          const uint32_t o = tc::kmajor_offset(t, n, NP);
-          *reinterpret_cast<__half*>(hi + o) = h;
-          *reinterpret_cast<__half*>(lo + o) = __float2half_rn(w - __half2float(h));
-        }
+      if (hf) {
+        sc[0] = tc_gather_half<IO, K, 0, 1>(L, valid, ex, ey, ez, x, sU, smax[0], el);
+        sc[1] = tc_gather_half<IO, K, 1, 1>(L, valid, ex, ey, ez, x, sU, smax[1], el);
+        sc[2] = tc_gather_half<IO, K, 2, 1>(L, valid, ex, ey, ez, x, sU, smax[2], el);
+      } else {
+        sc[0] = tc_gather_half<IO, K, 0, 0>(L, valid, ex, ey, ez, x, sU, smax[0], el);
+        sc[1] = tc_gather_half<IO, K, 1, 0>(L, valid, ex, ey, ez, x, sU, smax[1], el);
+        sc[2] = tc_gather_half<IO, K, 2, 0>(L, valid, ex, ey, ez, x, sU, smax[2], el);
       }
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(bar(B_UFULL));
-
-      // element-local CUDA-core part while the tensor core works: y_q = D u - C q
+      tc_elem_sync();  // sQ and U complete for every element thread
       const float* f = ef + (size_t)ee * 8;
-      float q[NL2];
-      int cell0 = (ex * K) + L.X * ((ey * K) + L.Y * (ez * K));
-#pragma unroll
-      for (int c = 0; c < NL2; ++c) {
-        const int a1 = c % K, a2 = (c / K) % K, a3 = c / (K * K);
-        q[c] = valid ? tc_in<IO>(x[(int64_t)(L.n_xf + L.n_yf) + (int64_t)L.X * L.Y * (L.Z + 1) +
-                                  cell0 + a1 + L.X * (a2 + L.Y * a3)])
-                     : 0.f;
-      }
+      const float* q = sQ + el * QP;
+      // while the tensor core works: y_q = D u - C q on this thread's half of the cells
       if (valid) {
-        float du[NL2];
-#pragma unroll
-        for (int c = 0; c < NL2; ++c) du[c] = 0.f;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-          for (int n = 0; n < NC; ++n) {
-            int i, j, l;
-            tc_dof_ijl<K>(a, n, i, j, l);
-            bool ess;
-            const int g = tc_rt_global<K>(L, a, ex, ey, ez, i, j, l, ess);
-            const float u = ess ? 0.f : tc_in<IO>(x[g]);
-            const int node = a == 0 ? i : (a == 1 ? j : l);
-            const int st = a == 0 ? 1 : (a == 1 ? K : K * K);
-            const int c = i + K * (j + K * l);  // the cell on the face's high side (when node < K)
-            // the face at node index `node` is the low face of cell c and the high face of cell c - st
-            if (node < K) du[c] -= u;
-            if (node > 0) du[c - st] += u;
-          }
-        // C q = c_e det J (HI x HI x HI) q, three 1D contractions
-        float t1[NL2], t2[NL2];
-#pragma unroll
-        for (int c = 0; c < NL2; ++c) {
-          const int a1 = c % K, r = c / K;
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < K; ++m) s = fmaf(P.HI[a1 * K + m], q[m + K * r], s);
-          t1[c] = s;
-        }
-#pragma unroll
-        for (int c = 0; c < NL2; ++c) {
-          const int a1 = c % K, a2 = (c / K) % K, a3 = c / (K * K);
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < K; ++m) s = fmaf(P.HI[a2 * K + m], t1[a1 + K * (m + K * a3)], s);
-          t2[c] = s;
-        }
-        const float sC = f[6];
-        IO* yq = y + (int64_t)L.n_xf + L.n_yf + (int64_t)L.X * L.Y * (L.Z + 1);
-#pragma unroll
-        for (int c = 0; c < NL2; ++c) {
-          const int a1 = c % K, a2 = (c / K) % K, a3 = c / (K * K);
-          float s = 0.f;
-#pragma unroll
-          for (int m = 0; m < K; ++m) s = fmaf(P.HI[a3 * K + m], t2[a1 + K * (a2 + K * m)], s);
-          yq[cell0 + a1 + L.X * (a2 + L.Y * a3)] = tc_out<IO>(du[c] - sC * s);
-        }
+        if (hf)
+          tc_yq<IO, K, 1>(L, P, ex, ey, ez, f[6], q, sU, el, sc, y + off_q);
+        else
+          tc_yq<IO, K, 0>(L, P, ex, ey, ez, f[6], q, sU, el, sc, y + off_q);
       }
-
-      // epilogue: y_u += s_b sum_b G_ab K_ab u_b + own-cell D^T q, from TMEM lane t
+      // epilogue: y_u += sum_b G_ab s_b K_ab u_b + own-cell D^T q on this thread's chunks of
+      // 16 columns, from TMEM lane el
       float g[3][3];
       {
         const float G00 = valid ? f[0] : 0.f, G01 = valid ? f[1] : 0.f, G02 = valid ? f[2] : 0.f;
@@ -340,46 +447,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int b = 0; b < 3; ++b) g[a][b] = Gm[a][b] * P.kscale[a * 3 + b] * sc[b];
       }
+      const uint32_t tlane = tbase + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         const int r = (S::REUSE && a == 2) ? 0 : a;
-        if (!(ok = tc_wait(bar(B_ACC + a), (uint32_t)(it & 1), abort_v))) break;
+        // warp-uniform: the TMEM loads are warp-collective
+        const bool ready = __all_sync(0xffffffffu, tc_wait(bar(B_ACC + a), (uint32_t)(it & 1), abort_v));
+        if (!ready) {
+          elem_abort = 1;
+          break;
+        }
         tc::fence_after_sync();
         const uint32_t base = tlane + (uint32_t)(r * 3 * NP);
-#pragma unroll
-        for (int c0 = 0; c0 < NC; c0 += 16) {
-          float d0[16], d1[16], d2[16];
-          tc::tmem_ld16(base + c0, d0);
-          tc::tmem_ld16(base + NP + c0, d1);
-          tc::tmem_ld16(base + 2 * NP + c0, d2);
-          tc::tmem_wait_ld();
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            const int n = c0 + jj;
-            if (n >= NC || !valid) continue;
-            int i, j, l;
-            tc_dof_ijl<K>(a, n, i, j, l);
-            bool ess;
-            const int gid = tc_rt_global<K>(L, a, ex, ey, ez, i, j, l, ess);
-            if (ess) {
-              atomicAdd(y + gid, x[gid]);
-              continue;
-            }
-            float v = g[a][0] * d0[jj] + g[a][1] * d1[jj] + g[a][2] * d2[jj];
-            // own-cell D^T q: + q of the cell whose high face this is, - q of the cell whose low face
-            const int node = a == 0 ? i : (a == 1 ? j : l);
-            const int st = a == 0 ? 1 : (a == 1 ? K : K * K);
-            const int c = i + K * (j + K * l);
-            if (node > 0) v += q[c - st];
-            if (node < K) v -= q[c];
-            atomicAdd(y + gid, tc_out<IO>(v));
-          }
-        }
+        if (hf)
+          tc_epilogue<IO, K, 1>(L, a, base, g[a][0], g[a][1], g[a][2], valid, ex, ey, ez, q, x, y);
+        else
+          tc_epilogue<IO, K, 0>(L, a, base, g[a][0], g[a][1], g[a][2], valid, ex, ey, ez, q, x, y);
         tc::fence_before_sync();
         tc::mbar_arrive(bar(B_REG + r));
       }
+      tc_elem_sync();
+      if (elem_abort) break;
     }
-    if (!ok) {
+    if (elem_abort && tid == 0) {
       atomicOr(err, 4);
       abort_flag = 1;
     }
@@ -387,7 +477,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
-  if (warp == 4) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
+  if (warp == TC_EW) tc::tmem_dealloc(tbase, TC_TMEM_COLS);
 }
 
 }  // namespace
