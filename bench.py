@@ -390,15 +390,113 @@ def affine_apply(args, stream):
     abytes = alg_bytes(op.n_rt, op.n_l2, (nx + 1) ** 3, op.n_elem)
     sbytes = elem_bytes_affine(op.n_elem, op.n_rt, op.n_l2)
     flops = elem_flops_affine(K, q) * op.n_elem
+    # the same operator on the tensor cores (FP16-pair operands, FP32 accumulation): the inner
+    # operator of the mixed-precision solves on affine meshes, FP64 and FP32 vectors
+    tc = {}
+    for key, xx, yy, fn in (("f64_vectors", x, y, op.hd_apply_op_tc),
+                            ("f32_vectors", x.float(), y.float(), op.hd_apply_op_tc_f32)):
+        for _ in range(3):
+            fn(xx, yy)
+        torch.cuda.synchronize()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(steps):
+            fn(xx, yy)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        tms = t0.elapsed_time(t1) / steps
+        ab = abytes if key == "f64_vectors" else abytes // 2
+        tc[key] = {"value": op.n / (tms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": tms,
+                   "hbm_frac_of_measured": ab / (tms * 1e-3) / 1e9 / HBM_GBS_MEASURED}
+    ref = torch.empty_like(x)
+    op.hd_apply_op(x, ref)
+    op.hd_apply_op_tc(x, y)
+    torch.cuda.synchronize()
+    tc["max_rel_diff_vs_fp64_apply"] = float((y - ref).abs().max() / ref.abs().max())
+    tc["status"] = int(op.hd_tc_status())
+    tc["kernel"] = "k_op_tc<double|float,%d>: tcgen05.mma kind::f16, FP16 pairs, FP32 accumulators in TMEM" % K
     r = {"workload": "M%d-affine: the same recipe on the unperturbed mesh, q=%d" % (nx, q),
          "value": op.n / (ms * 1e-3) / 1e9, "unit": "GDOF/s", "ms_per_step": ms, "steps": steps,
          "kernel": "k_elem_op<%s,double,%d,%d,8,affine>" % ("dfloat" if args.fp64_emulation else "double", K, q),
          "kernel_ms": kern_ms, "algorithmic_bytes_per_launch": abytes, "streamed_bytes_per_launch": sbytes,
          "element_data": "affine fast path: 64 B per element (constant geometric factor, det J)",
          "hbm_frac_of_measured": abytes / (kern_ms * 1e-3) / 1e9 / HBM_GBS_MEASURED,
-         "fp64_equivalent_gflops": flops / (kern_ms * 1e-3) / 1e9}
+         "fp64_equivalent_gflops": flops / (kern_ms * 1e-3) / 1e9, "tensor_core_apply": tc}
     op.close()
     return r
+
+
+def affine_workload(name):
+    """The affine solve workloads: C4, grad-div on the unit cube, 48^3 elements, k = 4, a
+    seeded bent tube (radius 0.15) with alpha = 1e3, beta = 1 inside and alpha = 1,
+    beta = 1e-3 outside, u.n = 0; C3, Darcy on [0,1200]x[0,2200]x[0,170] with 60x220x85
+    elements, k = 2, gamma = 0, eps = exp(3Z) per layer (AR(1) along x, correlation length
+    10 cells), u.n = 0 everywhere (pure Neumann: the q block is singular, projected)."""
+    import paper_2304_12387_gb300 as hd
+    if name == "C4":
+        n = 48
+        vx, vy, vz = synth.lattice_vertices(n, n, n)
+        inside = synth.bent_tube_mask(n, n, n, seed=SEED)
+        return dict(dims=(n, n, n), k=4, kind=hd.HD_GRAD_DIV, v=(vx, vy, vz), c0=np.where(inside, 1e3, 1.0),
+                    c1=np.where(inside, 1.0, 1e-3))
+    nx, ny, nz = 60, 220, 85
+    vx, vy, vz = synth.lattice_vertices(nx, ny, nz, extent=(1200.0, 2200.0, 170.0))
+    eps = synth.layered_permeability(nx, ny, nz, sigma=3.0, corr_len=10.0, seed=SEED)
+    return dict(dims=(nx, ny, nz), k=2, kind=hd.HD_DARCY, v=(vx, vy, vz), c0=eps, c1=np.zeros(nx * ny * nz))
+
+
+def affine_solves(args, stream):
+    """Time to a true relative residual of 1e-8 on the affine workloads (C4, C3): FP64 MINRES
+    (double-float element kernel, FP64 V/W-cycle), mixed-precision MINRES with the FP32
+    CUDA-core inner operator, the same with the tensor-core inner operator, and mixed GMRES
+    (block-triangular) with the tensor-core inner operator; the error of each solution
+    against the FP64 one. Setup is timed separately."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    out = {}
+    for name in ("C4", "C3"):
+        w = affine_workload(name)
+        nx, ny, nz = w["dims"]
+        t0 = time.perf_counter()
+        op = hd.Operator(nx, ny, nz, w["k"], *w["v"], w["c0"], w["c1"], kind=w["kind"], ess_mask=ESS,
+                         q=w["k"] + 1, affine=True, cycle=2, smooth_levels=2, fp64_emulation=1, stream=stream)
+        torch.cuda.synchronize()
+        r = {"dofs": op.n, "elements": op.n_elem, "k": w["k"], "setup_s": time.perf_counter() - t0}
+        b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
+        b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
+        if name == "C3":
+            b[op.n_rt:] -= b[op.n_rt:].mean()  # compatible right-hand side of the singular problem
+        sols = {}
+
+        def rec(key, st, info, xs):
+            sols[key] = xs
+            r[key] = {"status": int(st), "iterations": info["iterations"], "outer": info.get("outer", info.get("cycles")),
+                      "ms": info["ms_total"], "true_relres": info["true_relres"]}
+            if key != "minres_fp64":
+                ref = sols["minres_fp64"]
+                r[key]["rel_diff_vs_fp64_solution"] = float(torch.linalg.vector_norm(xs - ref) /
+                                                             torch.linalg.vector_norm(ref))
+                r[key]["speedup_vs_minres_fp64"] = r["minres_fp64"]["ms"] / max(info["ms_total"], 1e-9)
+
+        xs = torch.zeros_like(b)
+        st, info = op.hd_minres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, check_every=16, outer_rtol=1e-8,
+                                      max_outer=40)
+        rec("minres_fp64", st, info, xs)
+        for key, mode in (("minres_mixed", 0), ("minres_mixed_tc", 1)):
+            op.hd_set_inner_operator(mode)
+            xs = torch.zeros_like(b)
+            st, info = op.hd_minres_solve(b, xs, rtol=args.inner_rtol, maxit=args.solve_maxit, check_every=16,
+                                          precision=1, outer_rtol=1e-8, max_outer=40)
+            rec(key, st, info, xs)
+        op.hd_set_inner_operator(1)
+        xs = torch.zeros_like(b)
+        st, info = op.hd_gmres_solve(b, xs, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
+                                     prec=hd.HD_GMRES_BLOCK_TRI, precision=1, inner_rtol=args.gmres_inner_rtol)
+        rec("gmres_tri_mixed_tc", st, info, xs)
+        r["tc_status"] = int(op.hd_tc_status())
+        op.close()
+        out[name] = r
+    return out
 
 
 def max_over_ranks(value, dist):
@@ -524,6 +622,8 @@ def run_ours(args, rank, world, dist):
         out["apply_native_fp64"] = native_apply(args, nx, vx, vy, vz, alpha, beta, stream)
     if not args.no_affine:
         out["apply_affine"] = affine_apply(args, stream)
+    if not args.no_solve and not args.no_affine:
+        out["affine_solves"] = affine_solves(args, stream)
     # MINRES time to a true relative residual of 1e-8 on the same problem: FP64, and
     # mixed precision (FP32 operator and V-cycle inside an FP64 residual correction)
     if not args.no_solve:

@@ -341,7 +341,9 @@ __device__ __forceinline__ T st_row(const StLevelT<T>& L, int c, int I, int J, i
   const bool fx[7] = {I >= 3, I >= 2, I >= 1, true, I + 1 < L.X, I + 2 < L.X, I + 3 < L.X};
   const bool fy[7] = {J >= 3, J >= 2, J >= 1, true, J + 1 < L.Y, J + 2 < L.Y, J + 3 < L.Y};
   const bool fz[7] = {Z >= 3, Z >= 2, Z >= 1, true, Z + 1 < L.Z, Z + 2 < L.Z, Z + 3 < L.Z};
-  T s = L.a[c] * x_at(I, J, Z, c);
+  // FP32 levels hold the row sum in the centre slot and act on differences (rowsum_form)
+  const T xc = x_at(I, J, Z, c), o = rowsum_form<T>() ? xc : (T)0;
+  T s = L.a[c] * xc;
 #pragma unroll
   for (int h = 1; h < NH; ++h) {
     int dx, dy, dz;
@@ -357,8 +359,8 @@ __device__ __forceinline__ T st_row(const StLevelT<T>& L, int c, int I, int J, i
     const T ap = ah[c];
     T am = ah[okm ? c - d : c];
     am = okm ? am : (T)0;
-    s = fma(ap, x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c), s);
-    s = fma(am, x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c), s);
+    s = fma(ap, x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c) - o, s);
+    s = fma(am, x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c) - o, s);
   }
   return s;
 }
@@ -436,9 +438,11 @@ __device__ __forceinline__ T st_row_part(const StLevelT<T>& L, int c, int I, int
     xv[2 * j] = x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c);
     xv[2 * j + 1] = x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c);
   }
-  T s = W == 0 ? L.a[c] * x_at(I, J, Z, c) : (T)0;
+  // FP32 levels: the row sum in the centre slot, the offsets on differences (rowsum_form)
+  const T xc = (W == 0 || rowsum_form<T>()) ? x_at(I, J, Z, c) : (T)0, o = rowsum_form<T>() ? xc : (T)0;
+  T s = W == 0 ? L.a[c] * xc : (T)0;
 #pragma unroll
-  for (int j = 0; j < 2 * CNT; ++j) s = fma(av[j], xv[j], s);
+  for (int j = 0; j < 2 * CNT; ++j) s = fma(av[j], xv[j] - o, s);
   return s;
 }
 
@@ -900,6 +904,18 @@ __global__ void k_sa_prolong1(StLevelT<T> L, CDims cd, const T* __restrict__ p1,
   x[c] += v;
 }
 
+// row sums of a FP64 stencil level (its row applied to the constant 1), the centre
+// slot of its FP32 copy (rowsum_form)
+template <int NO>
+__global__ void k_st_rowsum(StLevelT<double> L, float* __restrict__ centre) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= L.n()) return;
+  int I, J, Z;
+  lat_coords(c, L.X, L.Y, I, J, Z);
+  auto one = [](int, int, int, int) { return 1.0; };
+  centre[c] = (float)st_row<double, NO>(L, (int)c, I, J, Z, one);
+}
+
 template <typename T>
 __global__ void k_to_f32_sa(int64_t n, const double* __restrict__ a, T* __restrict__ b) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1154,6 +1170,10 @@ hd_status sa_setup_f32(hd_op* h) {
     h->stf.push_back(f);
     if (st != HD_OK) return st;
     k_to_f32_sa<float><<<nblk(d.n() * n_half(d.no)), TPB, 0, h->stream>>>(d.n() * n_half(d.no), d.a, f.a);
+    with_shape(d.no, [&](auto t) {  // centre slot: the FP64 row sum (rowsum_form)
+      constexpr int NO = decltype(t)::value;
+      k_st_rowsum<NO><<<nblk(d.n()), TPB, 0, h->stream>>>(d, f.a);
+    });
     k_to_f32_sa<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
   }
   HD_LAUNCH_CK(h, "SA f32");

@@ -195,12 +195,13 @@ __device__ __forceinline__ T stencil_res_prolong(const LevelT<T>& lv, const Leve
   int64_t zl = I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z);
   int64_t XY = (int64_t)lv.X * lv.Y;
   T r = fma(-lv.diag[c], xself, bc);
-  if (I > 0) r = fma(lv.wx[xl], xv(I - 1, J, Z), r);
-  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], xv(I + 1, J, Z), r);
-  if (J > 0) r = fma(lv.wy[yl], xv(I, J - 1, Z), r);
-  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], xv(I, J + 1, Z), r);
-  if (Z > 0) r = fma(lv.wz[zl], xv(I, J, Z - 1), r);
-  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], xv(I, J, Z + 1), r);
+  const T o = rowsum_form<T>() ? xself : (T)0;  // FP32 levels: differences (see rowsum_form)
+  if (I > 0) r = fma(lv.wx[xl], xv(I - 1, J, Z) - o, r);
+  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], xv(I + 1, J, Z) - o, r);
+  if (J > 0) r = fma(lv.wy[yl], xv(I, J - 1, Z) - o, r);
+  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], xv(I, J + 1, Z) - o, r);
+  if (Z > 0) r = fma(lv.wz[zl], xv(I, J, Z - 1) - o, r);
+  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], xv(I, J, Z + 1) - o, r);
   return r;
 }
 
@@ -624,7 +625,7 @@ hd_status setup_f32(hd_op* h) {
     k_to_f32<float><<<nblk((int64_t)d.X * (d.Y + 1) * d.Z), TPB, 0, h->stream>>>((int64_t)d.X * (d.Y + 1) * d.Z, d.wy, f.wy);
     k_to_f32<float><<<nblk((int64_t)d.X * d.Y * (d.Z + 1)), TPB, 0, h->stream>>>((int64_t)d.X * d.Y * (d.Z + 1), d.wz, f.wz);
     k_to_f32<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.mass, f.mass);
-    k_to_f32<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.diag, f.diag);
+    k_level_rowsum<<<nblk(d.n()), TPB, 0, h->stream>>>(d, f.diag);  // row sums (rowsum_form)
     k_to_f32<float><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
     HD_LAUNCH_CK(h, "f32 level");
   }

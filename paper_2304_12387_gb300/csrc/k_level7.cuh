@@ -6,7 +6,18 @@
 
 namespace {
 
-// residual b - S x at cell (I,J,Z) given the x value there
+// Rounding the operator of a level to FP32 loses its row sums (the mass of S~, C~ =
+// W~^-1, and the boundary faces) where they are small against the diagonal: with a
+// 10^6 coefficient contrast the FP32 W-cycle then differs from the FP64 one by tens of
+// percent (its second coarse correction amplifies the inconsistency). The FP32 copies
+// therefore keep, in place of the diagonal, the row sum computed in FP64, and apply
+// (S x)_c = rs_c x_c + sum_nbr w (x_c - x_nbr): the zero-row-sum part acts on
+// differences, the small part is exact to FP32 rounding.
+template <typename T>
+constexpr bool rowsum_form() { return sizeof(T) == 4; }
+
+// residual b - S x at cell (I,J,Z) given the x value there (FP32 levels: diag holds the
+// row sum, see rowsum_form)
 template <typename T>
 __device__ __forceinline__ T stencil_res(const LevelT<T>& lv, const T* __restrict__ x, T bc, T xc, int I, int J,
                                          int Z, int64_t c) {
@@ -23,6 +34,15 @@ __device__ __forceinline__ T stencil_res(const LevelT<T>& lv, const T* __restric
   const T x0 = x[ml ? c - 1 : c], x1 = x[mh ? c + 1 : c], x2 = x[nl ? c - lv.X : c], x3 = x[nh ? c + lv.X : c],
           x4 = x[ol ? c - XY : c], x5 = x[oh ? c + XY : c];
   T r = fma(-lv.diag[c], xc, bc);
+  if constexpr (rowsum_form<T>()) {
+    r = fma(ml ? w0 : (T)0, x0 - xc, r);
+    r = fma(mh ? w1 : (T)0, x1 - xc, r);
+    r = fma(nl ? w2 : (T)0, x2 - xc, r);
+    r = fma(nh ? w3 : (T)0, x3 - xc, r);
+    r = fma(ol ? w4 : (T)0, x4 - xc, r);
+    r = fma(oh ? w5 : (T)0, x5 - xc, r);
+    return r;
+  }
   r = fma(ml ? w0 : (T)0, x0, r);
   r = fma(mh ? w1 : (T)0, x1, r);
   r = fma(nl ? w2 : (T)0, x2, r);
@@ -30,6 +50,26 @@ __device__ __forceinline__ T stencil_res(const LevelT<T>& lv, const T* __restric
   r = fma(ol ? w4 : (T)0, x4, r);
   r = fma(oh ? w5 : (T)0, x5, r);
   return r;
+}
+
+// row sums of a FP64 7-point level (diag minus the weights of the faces that have a
+// neighbour), the diagonal slot of its FP32 copy
+__global__ void k_level_rowsum(LevelT<double> lv, float* __restrict__ out) {
+  int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= lv.n()) return;
+  int I, J, Z;
+  lat_coords(c, lv.X, lv.Y, I, J, Z);
+  const int64_t xl = I + (int64_t)(lv.X + 1) * (J + (int64_t)lv.Y * Z);
+  const int64_t yl = I + (int64_t)lv.X * (J + (int64_t)(lv.Y + 1) * Z);
+  const int64_t zl = c, XY = (int64_t)lv.X * lv.Y;
+  double s = lv.diag[c];
+  if (I > 0) s -= lv.wx[xl];
+  if (I < lv.X - 1) s -= lv.wx[xl + 1];
+  if (J > 0) s -= lv.wy[yl];
+  if (J < lv.Y - 1) s -= lv.wy[yl + lv.X];
+  if (Z > 0) s -= lv.wz[zl];
+  if (Z < lv.Z - 1) s -= lv.wz[zl + XY];
+  out[c] = (float)s;
 }
 
 // first pre-smoothing sweep from a zero guess: x = D_l1^-1 b
