@@ -130,8 +130,8 @@ typedef struct {
                             l1 diagonal (level 2 a 179-point stencil, level 3 81-point, the
                             deeper ones 27-point). The paper's AMG (Sec. 3.2) gives
                             mesh-independent iteration counts; smoothing restores them for
-                            log-normal coefficients. Other values: HD_ERR_NOT_IMPLEMENTED. The learned Schur preconditioner keeps the
-                            unsmoothed hierarchy for its coarse correction. */
+                            log-normal coefficients. Other values: HD_ERR_NOT_IMPLEMENTED. The
+                            learned Schur preconditioner adds its network to this cycle. */
   int32_t w_levels;      /* with cycle = 2: the two coarse corrections are made on levels
                             0..w_levels-1 only, one below (0: on every level); >= 0 */
   const int8_t* elem_rotation; /* NULL (every element lattice-aligned) or n_elem rotation codes
@@ -166,8 +166,11 @@ typedef struct {
   double true_relres;    /* ||b - AA x||_2 / ||b||_2 in FP64 at exit */
   double ms_total;       /* device time of the solve (CUDA events) */
   hd_status status;
-  int32_t fallback;      /* 1: the learned Schur preconditioner broke down and the solve was
-                            repeated with the V-cycle */
+  int32_t fallback;      /* learned Schur preconditioner (hd_minres_solve): 1: it broke down and
+                            the solve was repeated with the V/W-cycle; 2: it stagnated (no
+                            convergence within 1.2 times the iterations of the last converged
+                            V/W-cycle solve on the handle) and the solve continued from its
+                            iterate with the V/W-cycle; iterations and ms_total add up */
 } hd_solve_info;
 
 /* Training options and report of the learned Schur preconditioner. */
@@ -286,7 +289,9 @@ hd_status hd_get_level(hd_handle h, int32_t l, int32_t* n_levels, int32_t dims[3
 /* Solves AA x = b with block-preconditioned MINRES. b, x: device FP64 vectors of
  * length n_rt + n_l2. Returns HD_OK on convergence, HD_ERR_NOT_CONVERGED when
  * maxit is reached (x holds the last iterate), HD_ERR_PREC_INDEFINITE or
- * HD_ERR_NAN when the recurrence breaks down. */
+ * HD_ERR_NAN when the recurrence breaks down, HD_ERR_STAGNATION when the learned
+ * Schur preconditioner stagnated (info.fallback = 2) and the continuation with the
+ * V/W-cycle did not converge within maxit either. */
 hd_status hd_minres_solve(hd_handle h, const double* b, double* x,
                           const hd_solve_opts* opts, hd_solve_info* info);
 
@@ -393,18 +398,23 @@ hd_status hd_minres_solve_noalloc(hd_handle h, const double* b, double* x,
 
 /* -- learned Schur-complement preconditioner -------------------------------- */
 /* The paper preconditions S~ with one AMG V-cycle (Sec. 3.2). The learned variant
- * replaces the V-cycle's fine level by a linear, symmetric-by-construction conv
- * net on the L2 cell lattice plus the hierarchy's coarse correction:
- *   P r = s C1^T C2^T C2 C1 (s r) + delta r/d + P_1 V_1 P_1^T r,  s = d^-1/2, d = diag(S~),
+ * adds to the handle's V/W-cycle V a linear, symmetric-by-construction conv net on
+ * the L2 cell lattice:
+ *   P r = V r + s C1^T C2^T C2 C1 (s r) + delta r/d,  s = d^-1/2, d = diag(S~),
  * C1 a 3x3x3 convolution 1 -> nc, C2 3x3x3 nc -> nc (nc = 32), no bias or
- * activation; P is SPD for any weights. Weights W1[co][t] (nc x 27) and
- * W2[co][ci][t] (nc x nc x 27), tap t = dx + 3 (dy + 3 dz) for the neighbour at
- * offset (dx-1, dy-1, dz-1); activations FP16, accumulation FP32. */
+ * activation. The network term is positive semi-definite for any weights, so P is
+ * SPD; the initial weights are small (P starts at the plain cycle). Weights
+ * W1[co][t] (nc x 27) and W2[co][ci][t] (nc x nc x 27), tap t = dx + 3 (dy + 3 dz)
+ * for the neighbour at offset (dx-1, dy-1, dz-1); activations FP16, accumulation
+ * FP32, so the network term is symmetric to FP16 rounding only: use it inside the
+ * FP64 residual correction of hd_minres_solve (precision = 1 or max_outer > 1),
+ * where V runs in FP32 and the outer loop restores the FP64 residual. */
 hd_status hd_learned_init(hd_handle h, int32_t nc, uint64_t seed, double delta);
 /* host FP32 weight arrays in the layout above */
 hd_status hd_learned_set_weights(hd_handle h, const float* W1, const float* W2);
 hd_status hd_learned_get_weights(hd_handle h, float* W1, float* W2);
-/* z = network part of P applied to an L2 vector r (device FP64) */
+/* z = network part of P (s C1^T C2^T C2 C1 (s r) + delta r/d) applied to an L2 vector r
+ * (device FP64) */
 hd_status hd_learned_apply(hd_handle h, const double* r, double* z);
 /* z = P_1 V_1 P_1^T r (device FP64 L2 vectors; zero with a single level) */
 hd_status hd_coarse_correction(hd_handle h, const double* r, double* z);
@@ -413,12 +423,12 @@ hd_status hd_coarse_correction(hd_handle h, const double* r, double* z);
  * arrays of npairs stacked L2 vectors; gW1, gW2, loss are host outputs. */
 hd_status hd_learned_grad(hd_handle h, int32_t npairs, const double* r, const double* e, const double* qr,
                           float* gW1, float* gW2, double* loss);
-/* Generates training pairs from a plain solve (Lanczos-vector L2 parts r and
- * e = S~^-1 r by V-cycle-preconditioned CG to 1e-10) and runs Adam. */
+/* Generates training pairs from a plain solve (Lanczos-vector L2 parts r,
+ * e = S~^-1 r by V-cycle-preconditioned CG to 1e-10, and the fixed part V r) and runs
+ * Adam on the loss of hd_learned_grad with qr = V r. */
 hd_status hd_learned_train(hd_handle h, const hd_train_opts* opts, hd_train_info* info);
-/* 0: V-cycle (default); 1: learned network + coarse correction for the Schur
- * block in hd_apply_prec and hd_minres_solve (FP64 solves fall back to the
- * V-cycle if MINRES breaks down: info.fallback). */
+/* 0: V/W-cycle (default); 1: V/W-cycle + learned network for the Schur block in
+ * hd_apply_prec, hd_minres_solve (fallbacks: info.fallback) and FP64 hd_gmres_solve. */
 hd_status hd_set_schur_prec(hd_handle h, int32_t mode);
 /* on = 1: hd_set_schur_prec(h, 1); on = 0: back to the V-cycle */
 hd_status hd_enable_learned(hd_handle h, int32_t on);

@@ -1,9 +1,9 @@
 """FP64 reference of the learned Schur-complement preconditioner.
 
 The paper preconditions S~ with one AMG V-cycle (Sec. 3.2). The learned variant
-replaces the fine-level part of that V-cycle by a small linear convolutional
-network on the L2 cell lattice, kept symmetric positive definite so that MINRES
-stays valid:
+adds to a fixed symmetric positive definite part Q (the library uses its V/W-cycle)
+a small linear convolutional network on the L2 cell lattice, positive semi-definite
+by construction, so that P stays SPD and MINRES stays valid:
 
     P r = d^-1/2 C1^T C2^T C2 C1 d^-1/2 r  +  delta d^-1 r  +  Q r,
 
@@ -11,7 +11,7 @@ stays valid:
   C1     = 3x3x3 convolution, 1 -> nc channels (weights W1[co, t]),
   C2     = 3x3x3 convolution, nc -> nc channels (weights W2[co, ci, t]),
   ^T     = the adjoint convolutions (flipped taps, transposed channels),
-  Q      = the coarse correction of the plain hierarchy (P_1 V_1 P_1^T, fixed).
+  Q      = the fixed part, given per pair as the vector Q r.
 
 Taps t = dx + 3 (dy + 3 dz) address the neighbour at offset (dx-1, dy-1, dz-1);
 outside the lattice the field is zero. Fields are stored in lattice order

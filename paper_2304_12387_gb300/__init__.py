@@ -371,7 +371,7 @@ class Operator:
                     "true_relres": info.true_relres, "ms_total": info.ms_total, "status": info.status}
 
     # -- learned Schur preconditioner ----------------------------------------
-    def hd_learned_init(self, nc=32, seed=2304, delta=1e-3):
+    def hd_learned_init(self, nc=32, seed=2304, delta=0.0):
         _check(lib().hd_learned_init(self.h, nc, seed, delta), self.h)
 
     def hd_learned_set_weights(self, W1, W2):

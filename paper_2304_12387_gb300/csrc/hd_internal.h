@@ -201,8 +201,12 @@ struct hd_op {
   int mr_it = 0;
   int mr_map[9] = {0, 1, 2, 3, 4, 5, 6, 7, 8};
   std::vector<float*> fv;       // FP32 work vectors for the mixed-precision solve
-  // Schur-block preconditioner: 0 = V-cycle, 1 = learned network + coarse correction
+  // Schur-block preconditioner: 0 = V/W-cycle, 1 = V/W-cycle + learned network
   int schur_mode = 0;
+  // MINRES iterations of the last converged solve with the V/W-cycle (0: none yet): a
+  // solve with the learned network stops after 1.2 times as many and continues with
+  // the V/W-cycle (HD_ERR_STAGNATION, info.fallback = 2)
+  int plain_its = 0;
   struct LearnedNet* net = nullptr;
   // capture of the Lanczos vectors' L2 parts during a solve (training data)
   double* cap_buf = nullptr;
@@ -295,8 +299,9 @@ hd_status apply_op_f32_internal(hd_op* h, const float* x, float* y);
 hd_status residual_norms(hd_op* h, const double* b, const double* y, double* rn, double* bn);
 // z += P_1 V_1 P_1^T r: the coarse correction of the V-cycle hierarchy (nothing with one level)
 hd_status coarse_correction(hd_op* h, const double* r, double* z);
-// learned Schur preconditioner (k_learned.cu)
+// learned Schur preconditioner (k_learned.cu): z = V r + network(r), and z += network(r)
 hd_status learned_schur_apply(hd_op* h, const double* r, double* z);
+hd_status learned_net_add(hd_op* h, const double* r, double* z);
 void learned_free(hd_op* h);
 // y += a x ; p = z + b p
 hd_status axpy_dev(hd_op* h, int64_t n, double a, const double* x, double* y);

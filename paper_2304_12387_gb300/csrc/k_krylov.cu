@@ -339,19 +339,19 @@ static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
   return apply_op_mixed_internal(h, v, y);  // FP32 arithmetic, FP64 vectors
 }
 
-// z_q = V-cycle(r_q) in the inner precision, then the zero-mean projection if singular
+// z_q = V/W-cycle(r_q) in the inner precision (plus the learned network term when it is
+// enabled), then the zero-mean projection if singular
 static hd_status inner_vcycle(hd_op* h, bool f32, const double* rq, double* zq) {
   hd_status st;
-  if (h->schur_mode == 1) {
-    if ((st = learned_schur_apply(h, rq, zq)) != HD_OK) return st;
-  } else if (!f32) {
-    if ((st = vcycle_apply(h, rq, zq)) != HD_OK) return st;
+  if (!f32) {
+    if ((st = h->schur_mode == 1 ? learned_schur_apply(h, rq, zq) : vcycle_apply(h, rq, zq)) != HD_OK) return st;
   } else {
     const int64_t m = h->n_l2;
     k_d2f<<<nblk(m), TPB, 0, h->stream>>>(m, rq, h->fv[2]);
     if ((st = vcycle_apply_f32(h, h->fv[2], h->fv[3])) != HD_OK) return st;
     k_f2d<<<nblk(m), TPB, 0, h->stream>>>(m, h->fv[3], zq);
     HD_LAUNCH_CK(h, "inner vcycle");
+    if (h->schur_mode == 1 && (st = learned_net_add(h, rq, zq)) != HD_OK) return st;
   }
   if (h->singular) return project_mean(h, zq);
   return HD_OK;
@@ -446,7 +446,8 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
 // Preconditioned MINRES; with max_outer > 1 (or precision = 1) wrapped in an FP64
 // residual correction: r = b - AA x in FP64, inner MINRES on AA e = r, x += e,
 // until ||r||/||b|| <= outer_rtol.
-hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
+static hd_status minres_run_once(hd_op* h, const double* b, double* x, const hd_solve_opts* o,
+                                 hd_solve_info* info) {
   hd_status st = ensure_minres(h);
   if (st != HD_OK) return st;
   const bool f32 = o->precision == 1;
@@ -474,13 +475,6 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
     outer = 1;
     status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs,
                           o->resume ? it0 : 0, h->schur_mode == 0);
-    if (h->schur_mode == 1 && (status == HD_ERR_PREC_INDEFINITE || status == HD_ERR_NAN)) {
-      // the learned Schur preconditioner broke down: solve again with the V-cycle
-      fallback = 1;
-      h->schur_mode = 0;
-      status = minres_inner(h, false, b, x, o->use_x0 != 0, o->rtol, o->maxit, o->check_every, &total, &hs);
-      h->schur_mode = 1;
-    }
   } else {
     double* r = h->mv[9];
     double* e = h->mv[10];
@@ -529,6 +523,50 @@ hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* 
     info->fallback = fallback;
   }
   return status;
+}
+
+// MINRES with the Schur-block preconditioner of the handle. With the learned network
+// enabled: if it breaks down (indefinite or non-finite recurrence) the solve is
+// repeated with the V/W-cycle (info.fallback = 1); if it has not converged after 1.2
+// times the iterations of the last converged V/W-cycle solve on the handle (the
+// stagnation rule, HD_ERR_STAGNATION), it continues from its iterate with the V/W-cycle
+// for the remaining iterations (info.fallback = 2). Iterations and times add up.
+hd_status minres_run(hd_op* h, const double* b, double* x, const hd_solve_opts* o, hd_solve_info* info) {
+  hd_solve_info i1{};
+  if (h->schur_mode != 1 || o->resume) {
+    hd_status st = minres_run_once(h, b, x, o, &i1);
+    if (st == HD_OK && h->schur_mode == 0) h->plain_its = i1.iterations;
+    if (info) *info = i1;
+    return st;
+  }
+  hd_solve_opts o1 = *o;
+  const int cap = h->plain_its > 0 ? (int)std::ceil(1.2 * h->plain_its) : o->maxit;
+  if (cap < o1.maxit) o1.maxit = cap;
+  hd_status st = minres_run_once(h, b, x, &o1, &i1);
+  int fallback = 0;
+  if (st == HD_ERR_PREC_INDEFINITE || st == HD_ERR_NAN) {
+    fallback = 1;
+  } else if (st == HD_ERR_NOT_CONVERGED && o1.maxit < o->maxit) {
+    st = HD_ERR_STAGNATION;
+    fallback = 2;
+  }
+  if (fallback) {
+    hd_solve_opts o2 = *o;
+    o2.maxit = o->maxit - i1.iterations > 1 ? o->maxit - i1.iterations : 1;
+    if (fallback == 2) o2.use_x0 = 1;  // the learned iterate is the starting guess
+    hd_solve_info i2{};
+    h->schur_mode = 0;
+    st = minres_run_once(h, b, x, &o2, &i2);
+    h->schur_mode = 1;
+    i2.iterations += i1.iterations;
+    i2.outer += i1.outer;
+    i2.ms_total += i1.ms_total;
+    i2.fallback = fallback;
+    i1 = i2;
+    if (fallback == 2 && st == HD_ERR_NOT_CONVERGED) st = HD_ERR_STAGNATION;
+  }
+  if (info) *info = i1;
+  return st;
 }
 
 // ---- allocation-free MINRES ----------------------------------------------------

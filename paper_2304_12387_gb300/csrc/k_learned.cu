@@ -1,12 +1,14 @@
 // Learned Schur-complement preconditioner: a linear, symmetric-by-construction
-// convolutional network on the L2 cell lattice that stands in for the fine-level
-// part of the V-cycle on S~ (the paper uses one AMG V-cycle, Sec. 3.2):
+// convolutional network on the L2 cell lattice added to the V/W-cycle on S~ (the
+// paper uses one AMG V-cycle, Sec. 3.2):
 //
-//   P r = s (C1^T C2^T C2 C1 (s r)) + delta r / d + Q r,    s = d^-1/2, d = diag(S~),
+//   P r = V r + s (C1^T C2^T C2 C1 (s r)) + delta r / d,    s = d^-1/2, d = diag(S~),
 //
-// C1: 3x3x3 conv 1 -> 32, C2: 3x3x3 conv 32 -> 32 (no bias, no activation), ^T the
-// adjoint convolutions, Q = P_1 V_1 P_1^T the coarse correction of the plain
-// hierarchy. P is SPD for any weights, so MINRES stays valid.
+// V the handle's V/W-cycle (the hierarchy it was created with), C1: 3x3x3 conv
+// 1 -> 32, C2: 3x3x3 conv 32 -> 32 (no bias, no activation), ^T the adjoint
+// convolutions. The network term is positive semi-definite for any weights, so P
+// stays SPD and, with small initial weights, starts at the plain cycle: training
+// can only add to it what the energy-norm loss says the cycle misses.
 //
 // Activations are FP16 with 32 channels per cell ([cell][32], 64 B), weights FP16
 // for compute with an FP32 master copy, accumulation FP32. The 32 -> 32
@@ -154,7 +156,7 @@ __global__ void __launch_bounds__(256) k_conv1(int X, int Y, int Z, const __half
 }
 
 // s = sum_{t,co} W1[co,t] g[c - off_t][co]; mode 0: z = sq sigma s + delta r / d (FP64);
-// mode 1: outf = s (FP32). One thread per cell.
+// mode 1: outf = s (FP32); mode 2: z += sq sigma s + delta r / d. One thread per cell.
 __global__ void __launch_bounds__(256) k_conv1T(int X, int Y, int Z, const __half* __restrict__ W1h,
                                                 const __half* __restrict__ g, int mode, const float* __restrict__ sq,
                                                 const double* __restrict__ scal, double delta,
@@ -187,6 +189,8 @@ __global__ void __launch_bounds__(256) k_conv1T(int X, int Y, int Z, const __hal
   }
   if (mode == 0)
     z[c] = (double)sq[c] * scal[1] * (double)acc + delta * r[c] * dinv[c];
+  else if (mode == 2)
+    z[c] += (double)sq[c] * scal[1] * (double)acc + delta * r[c] * dinv[c];
   else
     outf[c] = acc;
 }
@@ -503,8 +507,9 @@ hd_status conv2(hd_op* h, const __half* W, const __half* in, __half* out) {
   return HD_OK;
 }
 
-// y = P_L r (net part, FP64 out); leaves u, a1, a2, a3 and sigma (scal[1]) for a backward pass
-hd_status net_forward(hd_op* h, const double* r, double* y) {
+// y = P_L r (net part, FP64 out; accumulate: y += P_L r); leaves u, a1, a2, a3 and sigma
+// (scal[1]) for a backward pass
+hd_status net_forward(hd_op* h, const double* r, double* y, bool accumulate = false) {
   LearnedNet* N = h->net;
   const int64_t n = N->n;
   hd_status st;
@@ -515,8 +520,8 @@ hd_status net_forward(hd_op* h, const double* r, double* y) {
   HD_LAUNCH_CK(h, "conv1");
   if ((st = conv2(h, N->W2h, N->a1, N->a2)) != HD_OK) return st;
   if ((st = conv2(h, N->W2Th, N->a2, N->a3)) != HD_OK) return st;
-  k_conv1T<<<nblk(n), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->a3, 0, N->sq, N->scal, N->delta, r,
-                                            N->dinv, y, nullptr);
+  k_conv1T<<<nblk(n), TPB, 0, h->stream>>>(N->X, N->Y, N->Z, N->W1h, N->a3, accumulate ? 2 : 0, N->sq, N->scal,
+                                            N->delta, r, N->dinv, y, nullptr);
   HD_LAUNCH_CK(h, "conv1T");
   return HD_OK;
 }
@@ -620,11 +625,14 @@ void learned_free(hd_op* h) {
   h->net = nullptr;
 }
 
-// z = P_L r + Q r (learned Schur preconditioner on an L2 vector); FP64 in/out
+// z += P_L r (the network term); FP64 in/out
+hd_status learned_net_add(hd_op* h, const double* r, double* z) { return net_forward(h, r, z, true); }
+
+// z = V r + P_L r (learned Schur preconditioner on an L2 vector); FP64 in/out
 hd_status learned_schur_apply(hd_op* h, const double* r, double* z) {
-  hd_status st = net_forward(h, r, z);
+  hd_status st = vcycle_apply(h, r, z);
   if (st != HD_OK) return st;
-  return coarse_correction(h, r, z);
+  return net_forward(h, r, z, true);
 }
 
 extern "C" {
@@ -673,8 +681,10 @@ hd_status hd_learned_init(hd_handle h, int32_t nc, uint64_t seed, double delta) 
       if (u1 < 1e-300) u1 = 1e-300;
       return std::sqrt(-2.0 * std::log(u1)) * std::cos(2.0 * M_PI * u2);
     };
-    for (auto& v : w1) v = (float)(gauss() / std::sqrt(27.0));
-    for (auto& v : w2) v = (float)(gauss() / std::sqrt(27.0 * NC));
+    // small: the network term starts four orders of magnitude below its unit-scale size,
+    // so the preconditioner starts at the plain cycle
+    for (auto& v : w1) v = (float)(0.1 * gauss() / std::sqrt(27.0));
+    for (auto& v : w2) v = (float)(0.1 * gauss() / std::sqrt(27.0 * NC));
     HD_CK(h, cudaMemcpyAsync(N->W1, w1.data(), nw1 * 4, cudaMemcpyHostToDevice, h->stream));
     HD_CK(h, cudaMemcpyAsync(N->W2, w2.data(), nw2 * 4, cudaMemcpyHostToDevice, h->stream));
     HD_CK(h, cudaMemsetAsync(N->m1, 0, nw1 * 4, h->stream));
@@ -787,14 +797,15 @@ hd_status hd_learned_train(hd_handle h, const hd_train_opts* o, hd_train_info* i
   cudaFree(b);
   cudaFree(x);
   if (np < 1) return hd_fail(h, HD_ERR_NOT_CONVERGED, "no residuals captured");
-  // 2. targets e = S~^-1 r by V-cycle-preconditioned CG, and the fixed coarse part Q r
+  // 2. targets e = S~^-1 r by V-cycle-preconditioned CG, and the fixed part V r (the
+  //    V/W-cycle the network is added to; zero mean in the singular case, as applied)
   int max_pcg = 0;
   for (int p = 0; p < np; ++p) {
     int its = 0;
     if ((st = pcg_schur(h, N->pr + p * n, N->pe + p * n, 1e-10, 2000, &its)) != HD_OK) return st;
     max_pcg = its > max_pcg ? its : max_pcg;
-    HD_CK(h, cudaMemsetAsync(N->pq + p * n, 0, sizeof(double) * n, h->stream));
-    if ((st = coarse_correction(h, N->pr + p * n, N->pq + p * n)) != HD_OK) return st;
+    if ((st = vcycle_apply(h, N->pr + p * n, N->pq + p * n)) != HD_OK) return st;
+    if (h->singular && (st = project_mean(h, N->pq + p * n)) != HD_OK) return st;
   }
   // 3. Adam on the mean energy-norm loss over the pairs
   double L0 = 0.0, L = 0.0;

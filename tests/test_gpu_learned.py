@@ -4,7 +4,10 @@ The GPU network computes in FP16 (activations and weights) with FP32
 accumulation, so it is compared with the reference evaluated on the same
 FP16-rounded weights, at a norm-scaled tolerance of 2e-2 for outputs and 5e-2
 for gradients (FP16 carries 11 significant bits; each output sums 27 x 32
-terms per layer over four layers). The coarse correction is FP64 (1e-12)."""
+terms per layer over four layers). The coarse correction is FP64 (1e-12). The
+preconditioner P = V + network (V the V/W-cycle) is exercised by training and
+solving: it may not take more iterations than the plain cycle, and a network that
+stalls the solve hands it back to the cycle."""
 import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
@@ -93,25 +96,84 @@ def test_gradient_matches_reference():
     op.close()
 
 
-def test_training_lowers_loss_and_preconditioner_stays_spd():
-    _, prob, op, bp = _setup("darcy_k3")
-    op.hd_learned_init(delta=DELTA)
-    info = op.hd_learned_train(npairs=6, capture_every=3, steps=40, lr=3e-3)
-    assert info["pairs"] == 6
+def _mixed(op, b, **kw):
+    x = torch.zeros_like(b)
+    st, info = op.hd_minres_solve(b, x, rtol=1e-4, maxit=5000, check_every=4, precision=1, outer_rtol=1e-8,
+                                  max_outer=30, **kw)
+    return st, info, x
+
+
+@pytest.mark.parametrize("name", ["darcy_k3", "darcy_neumann"])
+def test_trained_network_on_the_w_cycle(name):
+    """P = V + network on small Darcy lattices: training on 8 residual/correction pairs
+    lowers the energy-norm loss from the plain cycle's, P stays symmetric on zero-mean
+    vectors (to the network's FP16 rounding, a small part of P) and positive, and the
+    learned mixed-precision solve (FP32 operator and cycle, FP16 network, FP64
+    residual correction) reaches the true relative residual 1e-8. On darcy_k3 (9^3
+    cells, which the network's 9^3 receptive field spans) it takes no more MINRES
+    iterations than the same solve with the plain cycle (measured: 57 against 86); on
+    the singular 8 x 4 x 4 lattice and on larger lattices the trained network does not
+    gain (it adds 3-20% iterations), which the stagnation rule bounds."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    d = inputs(name)
+    prob = oracle_problem(d)
+    op = gpu_operator(d, coarse_max=8, cycle=2, smooth_levels=1)
+    rng = np.random.Generator(np.random.PCG64(10))
+    b = rng.uniform(-1, 1, prob.n)
+    b[prob.ess] = 0.0
+    if name == "darcy_neumann":
+        b[prob.lat.n_rt:] -= b[prob.lat.n_rt:].mean()
+    b = torch.from_numpy(b).cuda()
+    st, plain, xp = _mixed(op, b)
+    assert st == 0 and plain["true_relres"] <= 1e-8
+    op.hd_learned_init()
+    info = op.hd_learned_train(npairs=8, capture_every=3, steps=60, lr=3e-3)
+    assert info["pairs"] == 8
     assert info["loss_final"] < info["loss_initial"], info
     op.hd_set_schur_prec(1)
-    rng = np.random.Generator(np.random.PCG64(10))
-    a, b = (torch.from_numpy(rng.uniform(-1, 1, prob.n)).cuda() for _ in range(2))
-    Pa, Pb = torch.empty_like(a), torch.empty_like(b)
+    a, c = (rng.uniform(-1, 1, prob.n) for _ in range(2))
+    for v in (a, c):  # zero-mean q parts (the singular case projects the cycle's output)
+        v[prob.lat.n_rt:] -= v[prob.lat.n_rt:].mean()
+    a, c = torch.from_numpy(a).cuda(), torch.from_numpy(c).cuda()
+    Pa, Pc = torch.empty_like(a), torch.empty_like(c)
     op.hd_apply_prec(a, Pa)
-    op.hd_apply_prec(b, Pb)
+    op.hd_apply_prec(c, Pc)
     torch.cuda.synchronize()
-    ab, ba = float(Pa @ b), float(a @ Pb)
-    assert abs(ab - ba) <= 1e-2 * max(abs(ab), abs(ba))
+    ac, ca = float(Pa @ c), float(a @ Pc)
+    assert abs(ac - ca) <= 1e-3 * max(abs(ac), abs(ca))
     assert float(a @ Pa) > 0
-    rhs = rng.uniform(-1, 1, prob.n)
-    x = torch.zeros(prob.n, dtype=torch.float64, device="cuda")
-    st, sol = op.hd_minres_solve(torch.from_numpy(rhs).cuda(), x, rtol=1e-8, maxit=3000, check_every=4)
-    assert st == 0 and sol["fallback"] == 0, sol
-    assert sol["true_relres"] < 1e-5
+    st, learned, xl = _mixed(op, b)
+    assert st == 0 and learned["fallback"] == 0 and learned["true_relres"] <= 1e-8, learned
+    if name == "darcy_k3":
+        assert learned["iterations"] <= plain["iterations"], (learned["iterations"], plain["iterations"])
+    assert learned["iterations"] <= 1.25 * plain["iterations"], (learned["iterations"], plain["iterations"])
+    assert float(torch.linalg.vector_norm(xl - xp) / torch.linalg.vector_norm(xp)) <= 1e-7
+    op.close()
+
+
+def test_stagnating_network_falls_back_to_the_cycle():
+    """A network that makes the preconditioner much worse (unit-scale weights times 3:
+    its term dominates the cycle, without FP16 overflow) stalls the learned solve past
+    1.2 times the plain solve's iterations: the solve continues from its iterate with
+    the V/W-cycle (fallback 2) and still reaches the solution."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from oracle import conv
+    d = inputs("darcy_k3")
+    prob = oracle_problem(d)
+    op = gpu_operator(d, coarse_max=8, cycle=2, smooth_levels=1)
+    b = torch.from_numpy(np.random.Generator(np.random.PCG64(11)).uniform(-1, 1, prob.n)).cuda()
+    x0 = torch.zeros_like(b)
+    st, plain = op.hd_minres_solve(b, x0, rtol=1e-8, maxit=3000, check_every=4)
+    assert st == 0 and plain["fallback"] == 0
+    W1, W2 = conv.init_weights(32, seed=12)
+    op.hd_learned_init()
+    op.hd_learned_set_weights(3.0 * W1, 3.0 * W2)
+    op.hd_set_schur_prec(1)
+    x = torch.zeros_like(b)
+    st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=3000, check_every=4)
+    assert st == 0 and info["fallback"] == 2, info
+    assert info["iterations"] > int(1.2 * plain["iterations"])
+    assert float(torch.linalg.vector_norm(x - x0) / torch.linalg.vector_norm(x0)) <= 1e-7
     op.close()
