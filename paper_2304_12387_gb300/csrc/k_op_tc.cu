@@ -57,7 +57,8 @@ struct TcShape {
   static constexpr uint32_t U_BYTES = TC_TILE * NP * 2;  // one component, one half of the pair
   static constexpr uint32_t Q_BYTES = (TC_TILE * QP * 4 + 15) / 16 * 16;
   static constexpr uint32_t KB_BYTES = NP * NP * 2;      // one K_ab block, one half of the pair
-  static constexpr uint32_t SMEM = 6 * U_BYTES + Q_BYTES + TC_STAGES * 2 * KB_BYTES;
+  static constexpr uint32_t EF_BYTES = TC_TILE * 8 * 4;    // a tile's element factors
+  static constexpr uint32_t SMEM = 6 * U_BYTES + Q_BYTES + 2 * EF_BYTES + TC_STAGES * 2 * KB_BYTES;
   // accumulator regions of 3 NP columns: a = 2 reuses a = 0's when nine do not fit
   static constexpr bool REUSE = 9 * NP > TC_TMEM_COLS;
   static_assert(3 * NP * (REUSE ? 2 : 3) <= TC_TMEM_COLS, "accumulators exceed TMEM");
@@ -70,7 +71,7 @@ struct TcParams {
 };
 
 enum { B_KFULL = 0, B_KEMPTY = TC_STAGES, B_UFULL = 2 * TC_STAGES, B_UEMPTY, B_ACC, B_REG = B_ACC + 3, B_FIN = B_REG + 3,
-       B_COUNT };
+       B_EF, B_COUNT = B_EF + 2 };
 
 // local dof n of component a -> (i, j, l) along x, y, z (the component's node index
 // runs along its own axis, interval indices along the others)
@@ -292,7 +293,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   __shared__ float smax[3][2][TC_TILE];        // per-half maxima of |u| per component and element
   unsigned char* sU = smem;                    // [part][component] A operands, K-major
   float* sQ = reinterpret_cast<float*>(smem + 6 * S::U_BYTES);                   // [element][QP]
-  unsigned char* sK = smem + 6 * S::U_BYTES + S::Q_BYTES;                         // [stage][part]
+  float* sEF = reinterpret_cast<float*>(smem + 6 * S::U_BYTES + S::Q_BYTES);      // [2][element][8]
+  unsigned char* sK = smem + 6 * S::U_BYTES + S::Q_BYTES + 2 * S::EF_BYTES;       // [stage][part]
   const int tid = threadIdx.x, warp = tid >> 5;
   const int64_t n_tiles = ((int64_t)n_elem + TC_TILE - 1) / TC_TILE;
   const int64_t off_q = (int64_t)L.n_xf + L.n_yf + (int64_t)L.X * L.Y * (L.Z + 1);  // = n_rt
@@ -313,6 +315,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc::mbar_init(bar(B_REG + a), TC_ET);
     }
     tc::mbar_init(bar(B_FIN), 1);
+    tc::mbar_init(bar(B_EF), 1);
+    tc::mbar_init(bar(B_EF + 1), 1);
     tc::fence_mbar_init();
   }
   if (warp == TC_EW) {
@@ -336,7 +340,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t issued = 0, blk = 0;
       int uses[3] = {0, 0, 0};
       bool ok = true;
+      int64_t ef_last = -1;  // last tile iteration whose element factors were requested
       for (int64_t tile = blockIdx.x, it = 0; ok && tile < n_tiles; tile += gridDim.x, ++it) {
+        // the tile's element factors by the copy engine into buffer it & 1 (its previous
+        // user, tile it - 2, finished before the element threads signalled tile it - 1)
+        {
+          const int64_t e0 = tile * TC_TILE;
+          const uint32_t bytes = (uint32_t)((n_elem - e0 < TC_TILE ? n_elem - e0 : TC_TILE) * 32);
+          tc::mbar_arrive_expect_tx(bar(B_EF + (int)(it & 1)), bytes);
+          tc::bulk_g2s(tc::smem_u32(sEF + (it & 1) * TC_TILE * 8), ef + e0 * 8, bytes, bar(B_EF + (int)(it & 1)));
+          ef_last = it;
+        }
         if (!(ok = tc_wait(bar(B_UFULL), (uint32_t)(it & 1), abort_v))) break;
         tc::fence_after_sync();
         for (int a = 0; ok && a < 3; ++a) {
@@ -385,6 +399,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!tc::mbar_wait(bar(B_FIN), 0)) atomicOr(err, 2);
       for (uint32_t c = blk; c < issued; ++c)
         if (!tc::mbar_wait(bar(B_KFULL + c % TC_STAGES), (c / TC_STAGES) & 1)) atomicOr(err, 2);
+      for (int64_t i = ef_last - 1; i <= ef_last; ++i)  // the element-factor copies of the last two tiles
+        if (i >= 0 && !tc::mbar_wait(bar(B_EF + (int)(i & 1)), (uint32_t)((i >> 1) & 1))) atomicOr(err, 2);
     }
     __syncwarp();
   } else {
@@ -426,7 +442,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc::fence_proxy_async_smem();
       tc::mbar_arrive(bar(B_UFULL));
       tc_elem_sync();  // sQ and U complete for every element thread
-      const float* f = ef + (size_t)ee * 8;
+      // the element factors staged by the control warp's bulk copy (warp-uniform wait)
+      if (!__all_sync(0xffffffffu, tc_wait(bar(B_EF + (int)(it & 1)), (uint32_t)((it >> 1) & 1), abort_v)))
+        elem_abort = 1;
+      const float* f = sEF + (it & 1) * TC_TILE * 8 + el * 8;
       const float* q = sQ + el * QP;
       // while the tensor core works: y_q = D u - C q on this thread's half of the cells
       if (valid) {
