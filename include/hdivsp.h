@@ -362,6 +362,44 @@ hd_status hd_gmres_solve(hd_handle h, const double* b, double* x, const hd_gmres
 hd_status hd_profile(hd_handle h, int32_t enable);
 hd_status hd_profile_read(hd_handle h, int32_t* launches, double* ms);
 
+/* -- z-slab partition (the multi-GPU runs of Sec. 4.2; emulated on one GPU) ------ */
+/* Partition p of P (P <= nz) owns the element layers [ez0, ez1) with
+ * ez0 = floor(p nz / P), and the global ids in the half-open ranges below: the x-faces,
+ * y-faces and cells of lattice layers K in [k ez0, k ez1), the z-faces of layers
+ * [k ez0, k ez1) (the last partition: up to and including the top layer K = Z). Its halo
+ * is the z-face layer K = k ez1 (owned by p + 1; empty for the last partition): its top
+ * element layer reads those faces and adds to them. An apply of the block operator needs
+ * per interface two exchanges of X Y values: x on the halo from p + 1 to p before the
+ * element loop, p's partial sums on the halo from p to p + 1 after it (two addends per
+ * interface face, so the result does not depend on P); a MINRES iteration needs one sum
+ * of two scalars over the partitions. */
+typedef struct {
+  int32_t p, P;
+  int32_t ez0, ez1;      /* element layers */
+  int64_t xf[2];         /* owned x-face ids [xf[0], xf[1]) */
+  int64_t yf[2];         /* owned y-face ids */
+  int64_t zf[2];         /* owned z-face ids */
+  int64_t cell[2];       /* owned L2 dofs, as ids of the block vector (n_rt + cell) */
+  int64_t halo[2];       /* z-face ids of the halo layer */
+} hd_slab;
+/* Host only (no GPU). HD_ERR_INVALID_ARG for bad sizes, P > nz or p outside [0, P). */
+hd_status hd_slab_plan(int32_t nx, int32_t ny, int32_t nz, int32_t k, int32_t P, int32_t p, hd_slab* out);
+/* y = AA x (device vectors as hd_apply_op) through P partitions emulated on this GPU:
+ * every partition applies its element layers to its own full-length buffers, which
+ * hold NaN outside its owned and halo entries (a read outside them shows in y); the
+ * halo values and interface sums move by device copies and an add kernel; y gathers
+ * the owned parts. Equal to hd_apply_op bit for bit. The first call for a P allocates
+ * 2 P vectors of n_rt + n_l2 doubles on the handle. */
+hd_status hd_apply_op_partitioned(hd_handle h, int32_t P, const double* x, double* y);
+/* hd_minres_solve (precision 0, no resume, V/W-cycle Schur block) with the operator
+ * applied as in hd_apply_op_partitioned and every inner product summed per partition
+ * over its owned entries, then over the P partitions in order (the allreduce); the
+ * Schur V/W-cycle runs on the whole L2 vector (on P GPUs a gather to one rank and a
+ * scatter back). Iterates equal the unpartitioned solve's to rounding (the sums
+ * associate differently). Other options: HD_ERR_NOT_IMPLEMENTED. */
+hd_status hd_minres_solve_partitioned(hd_handle h, int32_t P, const double* b, double* x,
+                                      const hd_solve_opts* opts, hd_solve_info* info);
+
 /* -- allocation-free solve (no counterpart in the paper) -------------------- */
 /* Same computation and result as hd_minres_solve with precision = 0, max_outer <= 1
  * and the V/W-cycle Schur block, for callers that may not allocate device memory once

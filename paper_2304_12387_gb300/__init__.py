@@ -61,6 +61,12 @@ class SolveInfo(ctypes.Structure):
                 ("fallback", ctypes.c_int32)]
 
 
+class Slab(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int32), ("P", ctypes.c_int32), ("ez0", ctypes.c_int32), ("ez1", ctypes.c_int32),
+                ("xf", ctypes.c_int64 * 2), ("yf", ctypes.c_int64 * 2), ("zf", ctypes.c_int64 * 2),
+                ("cell", ctypes.c_int64 * 2), ("halo", ctypes.c_int64 * 2)]
+
+
 class TrainOpts(ctypes.Structure):
     _fields_ = [("npairs", ctypes.c_int32), ("capture_every", ctypes.c_int32), ("steps", ctypes.c_int32),
                 ("lr", ctypes.c_double), ("seed", ctypes.c_uint64)]
@@ -124,6 +130,9 @@ _SIGS = {
     "hd_apply_op_tc_f32": [_H, _VP, _VP],
     "hd_set_inner_operator": [_H, ctypes.c_int32],
     "hd_tc_status": [_H],
+    "hd_slab_plan": [ctypes.c_int32] * 6 + [ctypes.POINTER(Slab)],
+    "hd_apply_op_partitioned": [_H, ctypes.c_int32, _VP, _VP],
+    "hd_minres_solve_partitioned": [_H, ctypes.c_int32, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
 }
 
 
@@ -212,6 +221,14 @@ def hd_lattice_is_affine(nx, ny, nz, vx, vy, vz):
     return bool(out.value)
 
 
+def hd_slab_plan(nx, ny, nz, k, P, p):
+    """Owned id ranges of z-slab p of P (host only): a dict of half-open (lo, hi) pairs."""
+    s = Slab()
+    _check(lib().hd_slab_plan(nx, ny, nz, k, P, p, ctypes.byref(s)))
+    return {"p": s.p, "P": s.P, "ez": (s.ez0, s.ez1), "xf": tuple(s.xf), "yf": tuple(s.yf), "zf": tuple(s.zf),
+            "cell": tuple(s.cell), "halo": tuple(s.halo)}
+
+
 def hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask):
     n = ctypes.c_int64(0)
     _check(lib().hd_lattice_ess_dofs(nx, ny, nz, k, ess_mask, None, ctypes.byref(n)))
@@ -293,6 +310,18 @@ class Operator:
     def hd_apply_op_f32(self, x, y): self._call("hd_apply_op_f32", x, y)
     def hd_apply_op_tc(self, x, y): self._call("hd_apply_op_tc", x, y)
     def hd_apply_op_tc_f32(self, x, y): self._call("hd_apply_op_tc_f32", x, y)
+
+    def hd_apply_op_partitioned(self, P, x, y):
+        _check(lib().hd_apply_op_partitioned(self.h, int(P), _ptr(x), _ptr(y)), self.h)
+
+    def hd_minres_solve_partitioned(self, P, b, x, rtol=1e-8, maxit=1000, use_x0=False, check_every=8,
+                                    outer_rtol=0.0, max_outer=1):
+        """MINRES through P emulated z-slab partitions (see the header)."""
+        o = SolveOpts(rtol, maxit, int(use_x0), check_every, 0, outer_rtol, max_outer)
+        info = SolveInfo()
+        st = lib().hd_minres_solve_partitioned(self.h, int(P), _ptr(b), _ptr(x), ctypes.byref(o), ctypes.byref(info))
+        return st, {"iterations": info.iterations, "outer": info.outer, "true_relres": info.true_relres,
+                    "ms_total": info.ms_total, "status": info.status}
 
     def hd_set_inner_operator(self, mode):
         """0: FP32 element kernel (CUDA cores); 1: tensor-core operator (affine meshes, k = 2..4)."""

@@ -299,6 +299,7 @@ __global__ void k_df_range(int64_t E, int ng, int nw, const double* __restrict__
 
 void destroy_all(hd_op* h) {
   tc_free(h);
+  part_free(h);
   cudaFree(h->d_vx); cudaFree(h->d_vy); cudaFree(h->d_vz);
   cudaFree(h->d_G); cudaFree(h->d_wdet); cudaFree(h->d_winv); cudaFree(h->d_wdiag); cudaFree(h->d_wgldiag);
   cudaFree(h->d_wchol);
@@ -328,6 +329,10 @@ void destroy_all(hd_op* h) {
 }
 
 }  // namespace
+
+hd_status elem_op_handle(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) {
+  return elem_op(h, mode, u, q, yu, yq);
+}
 
 constexpr int PROF_MAX = 4096;
 

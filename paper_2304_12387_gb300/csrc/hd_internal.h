@@ -107,6 +107,7 @@ __device__ __forceinline__ void lat_coords(int64_t c, int X, int Y, int& I, int&
 
 struct MinresState;  // device-side scalars of the MINRES recurrence
 struct TcState;      // data of the tensor-core operator (k_op_tc.cu)
+struct PartState;    // in-process z-slab partition (slab.cu)
 
 struct hd_op {
   // problem
@@ -232,6 +233,10 @@ struct hd_op {
   // cores, 1 = the tensor-core operator of affine meshes (k_op_tc.cu)
   int inner_op = 0;
   TcState* tc = nullptr;
+  // in-process z-slab partition (hd_apply_op_partitioned, hd_minres_solve_partitioned);
+  // part_on: MINRES applies the operator and sums its dot products through it
+  PartState* part = nullptr;
+  bool part_on = false;
   // profiling of the fused element kernel
   bool prof = false;
   std::vector<cudaEvent_t> prof_ev;  // pairs (start, stop)
@@ -315,6 +320,14 @@ hd_status tc_setup(hd_op* h);
 void tc_free(hd_op* h);
 hd_status tc_apply(hd_op* h, const double* x, double* y);
 hd_status tc_apply_f32(hd_op* h, const float* x, float* y);
+// in-process z-slab partition (slab.cu): the partitioned apply, per-partition dot sums
+// (partial[0..P) of an nout-entry partial array, zeros after) and clean-up
+hd_status part_apply(hd_op* h, const double* x, double* y);
+// the fused element kernel of the handle (FP64 or double-float) on [u; q] into [yu; yq]
+// (hd_api.cu; mode: OP_* bits; the element window e_first / e_end applies)
+hd_status elem_op_handle(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq);
+hd_status part_dot_partials(hd_op* h, const double* a, const double* b, double* partial, int nout);
+void part_free(hd_op* h);
 // set-up of hd_minres_solve_noalloc on this handle's device (called by hd_create)
 hd_status noalloc_prepare(hd_op* h);
 hd_status dot_device(hd_op* h, const double* a, const double* b, int64_t n, double* d_out);

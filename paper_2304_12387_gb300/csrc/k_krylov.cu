@@ -333,8 +333,10 @@ hd_status xpay_dev(hd_op* h, int64_t n, const double* z, double b, double* p) {
   return HD_OK;
 }
 
-// y = AA v with the operator in the inner precision (vectors stay FP64)
+// y = AA v with the operator in the inner precision (vectors stay FP64); through the
+// in-process partition when one is active
 static hd_status inner_apply(hd_op* h, bool f32, const double* v, double* y) {
+  if (h->part_on) return part_apply(h, v, y);
   if (!f32) return apply_op_internal(h, v, y);
   return apply_op_mixed_internal(h, v, y);  // FP32 arithmetic, FP64 vectors
 }
@@ -377,7 +379,7 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
     // the kept state: x from its copy, everything else where the stopped solve left it
     HD_CK(h, cudaMemcpyAsync(x, h->mv[9], sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
   } else if (use_x0) {
-    if ((st = apply_op_internal(h, x, rp)) != HD_OK) return st;
+    if ((st = inner_apply(h, false, x, rp)) != HD_OK) return st;
     k_axpby<<<nblk(n), TPB, 0, s>>>(n, 1.0, b, -1.0, rp);
   } else {
     HD_CK(h, cudaMemsetAsync(x, 0, sizeof(double) * n, s));
@@ -391,6 +393,7 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
     if ((st = diag_scale(h, rp, z)) != HD_OK) return st;
     if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, rp + h->n_rt, z + h->n_rt)) != HD_OK) return st;
     k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, rp, z, h->d_red);
+    if (h->part_on && (st = part_dot_partials(h, rp, z, h->d_red, DOT_BLOCKS)) != HD_OK) return st;
     k_mr_init<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, rtol);
     k_scale_div<<<nblk(n), TPB, 0, s>>>(n, z, h->d_ms, v);
     HD_LAUNCH_CK(h, "minres init");
@@ -402,6 +405,8 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
   for (it = it0 + 1; it <= it_end; ++it) {
     if ((st = inner_apply(h, f32, v, y)) != HD_OK) return st;
     k_mr_lanczos1<<<DOT_BLOCKS, TPB, 0, s>>>(n, it, h->d_ms, v, y, rpp, h->d_red);
+    // partitioned: the partials become the partitions' sums over their owned entries
+    if (h->part_on && (st = part_dot_partials(h, v, y, h->d_red, DOT_BLOCKS)) != HD_OK) return st;
     k_mr_alpha<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red);
     k_mr_lanczos2<<<nblk(n), TPB, 0, s>>>(n, h->n_rt, h->d_ms, y, rp, h->d_mtinv, z);
     HD_LAUNCH_CK(h, "minres lanczos");
@@ -412,6 +417,7 @@ static hd_status minres_inner(hd_op* h, bool f32, const double* b, double* x, bo
     }
     if (h->n_l2 > 0 && (st = inner_vcycle(h, f32, y + h->n_rt, z + h->n_rt)) != HD_OK) return st;
     k_dot_partial<<<DOT_BLOCKS, TPB, 0, s>>>(n, y, z, h->d_red);
+    if (h->part_on && (st = part_dot_partials(h, y, z, h->d_red, DOT_BLOCKS)) != HD_OK) return st;
     k_mr_beta_givens<<<1, DOT_BLOCKS, 0, s>>>(h->d_ms, h->d_red, it);
     k_mr_update<<<nblk(n), TPB, 0, s>>>(n, it, h->d_ms, v, wpp, wp, wn, x, z, vn);
     HD_LAUNCH_CK(h, "minres update");
@@ -482,7 +488,7 @@ static hd_status minres_run_once(hd_op* h, const double* b, double* x, const hd_
     double bn = 0, rn = 0;
     const double target = o->outer_rtol > 0 ? o->outer_rtol : o->rtol;
     for (outer = 0;; ++outer) {
-      if ((st = apply_op_internal(h, x, r)) != HD_OK) return st;
+      if ((st = h->part_on ? part_apply(h, x, r) : apply_op_internal(h, x, r)) != HD_OK) return st;
       if ((st = residual_norms(h, b, r, &rn, &bn)) != HD_OK) return st;
       if (!std::isfinite(rn) || !std::isfinite(bn)) {
         status = hd_fail(h, HD_ERR_NAN, "non-finite residual: b or the initial guess holds NaN or Inf");

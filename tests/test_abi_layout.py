@@ -21,6 +21,7 @@ STRUCTS = {
     "hd_gmres_opts": hd.GmresOpts,
     "hd_train_opts": hd.TrainOpts,
     "hd_train_info": hd.TrainInfo,
+    "hd_slab": hd.Slab,
 }
 
 
