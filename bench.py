@@ -690,7 +690,8 @@ def run_iterations(args):
     MINRES to a true relative residual of 1e-8 on the metric recipe (perturbed mesh,
     beta = exp(2Z), u.n = 0, q = k + 2) at several element counts and degrees, with
     the plain-aggregation W-cycle and the smoothed-aggregation W-cycles with one and
-    with two smoothed levels; mixed precision beside FP64 for the last."""
+    with two smoothed levels; mixed precision beside FP64 for the last. For odd k also
+    the element-aligned aggregates (plain and one smoothed level, FP64 and mixed)."""
     import torch
     import paper_2304_12387_gb300 as hd
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -700,13 +701,16 @@ def run_iterations(args):
     for nx, k in cases:
         vx, vy, vz, alpha, beta = workload(nx)
         row = {"elements": nx, "k": k}
-        for name, sl in (("plain", 0), ("smoothed1", 1), ("smoothed2", 2)):
+        variants = [("plain", 0, 0), ("smoothed1", 1, 0), ("smoothed2", 2, 0)]
+        if k % 2:  # element-aligned aggregates (the pairs straddle element boundaries for odd k)
+            variants += [("aligned_plain", 0, 1), ("aligned_smoothed1", 1, 1)]
+        for name, sl, agg in variants:
             op = hd.Operator(nx, nx, nx, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
-                             cycle=2, fp64_emulation=1, smooth_levels=sl, stream=stream)
+                             cycle=2, fp64_emulation=1, smooth_levels=sl, aggregation=agg, stream=stream)
             row["dofs"] = op.n
             b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
             b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
-            if sl == 2:
+            if sl == 2 and not agg:
                 x = torch.zeros_like(b)
                 st, info = op.hd_gmres_solve(b, x, rtol=1e-8, maxit=args.solve_maxit, restart=args.gmres_restart,
                                              prec=hd.HD_GMRES_BLOCK_TRI)
@@ -719,7 +723,7 @@ def run_iterations(args):
                 row["gmres_tri_mixed"] = {"status": int(st), "iterations": info["iterations"],
                                           "cycles": info["cycles"], "ms": round(info["ms_total"], 1),
                                           "true_relres": info["true_relres"]}
-            for prec in ((0, 1) if sl == 2 else (0,)):
+            for prec in ((0, 1) if sl == 2 or (agg and sl == 1) else (0,)):
                 x = torch.zeros_like(b)
                 st, info = op.hd_minres_solve(b, x, rtol=1e-4 if prec else 1e-8, maxit=args.solve_maxit,
                                               check_every=16, precision=prec, outer_rtol=1e-8, max_outer=40)
@@ -732,6 +736,21 @@ def run_iterations(args):
     # the (1,1)-block scaling tau (tau = 1: the final proposition of Sec. 2.3; tau = 2: Prop. 2's
     # optimum for exact blocks) on the C1 and C2 shapes, smoothed W-cycle
     taus = []
+    # ... and at every degree of the study on the metric recipe (32^3, two smoothed levels)
+    vx, vy, vz, alpha, beta = workload(32)
+    for k in (2, 3, 4, 5):
+        for tau in (1.0, 2.0):
+            op = hd.Operator(32, 32, 32, k, vx, vy, vz, alpha, beta, kind=hd.HD_GRAD_DIV, ess_mask=ESS, q=k + 2,
+                             tau=tau, cycle=2, fp64_emulation=1, smooth_levels=2, stream=stream)
+            b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 7)).cuda()
+            b[torch.from_numpy(op.hd_get_ess_dofs()).cuda()] = 0.0
+            x = torch.zeros_like(b)
+            st, info = op.hd_minres_solve(b, x, rtol=1e-8, maxit=args.solve_maxit, check_every=16,
+                                          outer_rtol=1e-8, max_outer=40)
+            taus.append({"shape": "tau_degree", "k": k, "tau": tau, "status": int(st),
+                         "iterations": info["iterations"], "true_relres": info["true_relres"]})
+            print(json.dumps(taus[-1]), flush=True)
+            op.close()
     n1 = 4
     c1 = dict(nx=n1, k=2, q=3, kind=hd.HD_GRAD_DIV, ess=63, affine=True, rtol=1e-10,
               v=synth.lattice_vertices(n1, n1, n1), c0=np.ones(n1 ** 3), c1=np.ones(n1 ** 3))

@@ -142,6 +142,19 @@ typedef struct {
                             element in its lattice-aligned frame, and the codes shape only the
                             element-local numbering and signs of hd_get_e2d_map and
                             hd_get_e2l_map. A code outside 0..23: HD_ERR_INVALID_ARG. */
+  int32_t aggregation;   /* aggregates of the Schur V/W-cycle. 0: pairs of cells per direction
+                            (a trailing odd cell alone). 1: element-aligned: along an axis where a
+                            level holds c > 1 cells per element (its length a multiple of the
+                            element count), the cells of each element are grouped in pairs taken
+                            alternately from its two ends, an odd middle cell alone ([2, 1] for
+                            c = 3, [2, 1, 2] for c = 5), so that no aggregate straddles an element
+                            boundary; pairs elsewhere. For even k both are the same. For odd k,
+                            pairs straddle half the element boundaries and the cycle needs about
+                            twice the iterations of the aligned one. With odd k the first coarse
+                            level of the smoothed hierarchy is then an 81-point stencil (box and
+                            (+-2, a, b), |a|, |b| <= 1, with its permutations), and
+                            smooth_levels = 2 is not available (HD_ERR_NOT_IMPLEMENTED). Other
+                            values: HD_ERR_INVALID_ARG. */
 } hd_problem_desc;
 
 /* MINRES options and report (Sec. 3). */

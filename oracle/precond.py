@@ -13,7 +13,10 @@ V-cycle on the approximate Schur complement (Sec. 2.3-2.4).
   Sec. 3.2). The geometric V-cycle used here:
     - levels: piecewise-constant aggregation of 2 cells per direction (a trailing
       odd cell is its own aggregate; a direction of length 1 is not coarsened),
-      until at most `coarse_max` cells remain;
+      until at most `coarse_max` cells remain; `aligned` = True groups the cells
+      inside each element instead (element_groups: for odd k the pairs cannot all
+      follow the element boundaries, and aggregates that straddle them slow the
+      cycle down);
     - prolongation: piecewise constant P0 on the aggregates, or, on the first
       `sa_levels` levels when `smooth` = omega > 0, the smoothed-aggregation
       prolongator P = (I - omega D_l1^-1 A_l) P0 (one damped l1-Jacobi step
@@ -52,17 +55,49 @@ def approx_schur(prob):
     return S, Mt, Ct
 
 
-def aggregation(dims):
-    """P (fine cells x coarse cells) for 2-per-direction aggregation; coarse dims."""
+def element_groups(c):
+    """Aggregate index of each of the c cells that one element holds along an axis, for
+    element-aligned aggregation: pairs taken alternately from the two ends of the element
+    (the first from its low end), an odd count leaving one single cell in the middle;
+    c = 3 gives groups [2, 1], c = 5 gives [2, 1, 2], c = 4 gives [2, 2]."""
+    lo, hi, sizes_lo, sizes_hi = 0, c, [], []
+    take_low = True
+    while hi - lo >= 2:
+        if take_low:
+            sizes_lo.append(2)
+            lo += 2
+        else:
+            sizes_hi.append(2)
+            hi -= 2
+        take_low = not take_low
+    sizes = sizes_lo + ([1] if hi - lo == 1 else []) + sizes_hi[::-1]
+    return np.repeat(np.arange(len(sizes)), sizes), len(sizes)
+
+
+def aggregation(dims, elems=None):
+    """P (fine cells x coarse cells) for 2-per-direction aggregation; coarse dims.
+
+    elems = (nx, ny, nz) element counts selects element-aligned aggregation: along an
+    axis whose length is c > 1 cells per element, the aggregates are element_groups(c)
+    inside each element, so that no aggregate straddles an element boundary; an axis
+    with one cell per element (or not a multiple of its element count) takes the pairs
+    of the default."""
     X, Y, Z = dims
-    cd = tuple((n + 1) // 2 if n > 1 else 1 for n in dims)
-    fx = [2 if n > 1 else 1 for n in dims]
+    maps = []
+    for n, ne in zip(dims, elems if elems is not None else (None,) * 3):
+        if n == 1:
+            maps.append((np.zeros(1, dtype=np.int64), 1))
+        elif ne is not None and n % ne == 0 and n // ne > 1:
+            g, m = element_groups(n // ne)
+            maps.append((np.arange(n) // (n // ne) * m + np.tile(g, ne), ne * m))
+        else:
+            maps.append((np.arange(n) // 2, (n + 1) // 2))
+    (ix, cx), (iy, cy), (iz, cz) = maps
     I, J, K = np.meshgrid(np.arange(X), np.arange(Y), np.arange(Z), indexing="ij")
     fine = (I + X * (J + Y * K)).ravel()
-    coarse = ((I // fx[0]) + cd[0] * ((J // fx[1]) + cd[1] * (K // fx[2]))).ravel()
-    P = sp.coo_matrix((np.ones(fine.size), (fine, coarse)),
-                      shape=(X * Y * Z, cd[0] * cd[1] * cd[2])).tocsr()
-    return P, cd
+    coarse = (ix[I] + cx * (iy[J] + cy * iz[K])).ravel()
+    P = sp.coo_matrix((np.ones(fine.size), (fine, coarse)), shape=(X * Y * Z, cx * cy * cz)).tocsr()
+    return P, (cx, cy, cz)
 
 
 def l1_diag(A):
@@ -72,11 +107,11 @@ def l1_diag(A):
 
 class VCycle:
     def __init__(self, A0, dims, nu=2, coarse_max=512, singular=False, max_levels=20, cycle=1,
-                 smooth=0.0, sa_levels=1, w_levels=0):
+                 smooth=0.0, sa_levels=1, w_levels=0, elems=None):
         self.nu, self.singular, self.cycle, self.w_levels = nu, singular, cycle, w_levels
         self.A, self.P, self.dims, self.dl1 = [A0.tocsr()], [], [tuple(dims)], []
         while np.prod(self.dims[-1]) > coarse_max and len(self.A) < max_levels:
-            P, cd = aggregation(self.dims[-1])
+            P, cd = aggregation(self.dims[-1], elems)
             if cd == self.dims[-1]:
                 break
             if smooth and len(self.P) < sa_levels:
@@ -129,14 +164,15 @@ def is_singular(prob, Ct):
 class BlockPrec:
     """z = B^-1 r with B = diag(tau M~, S^)."""
 
-    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1, smooth=0.0, sa_levels=1, w_levels=0):
+    def __init__(self, prob, tau=1.0, nu=2, coarse_max=512, cycle=1, smooth=0.0, sa_levels=1, w_levels=0,
+                 aligned=False):
         self.prob, self.tau = prob, tau
         self.S, self.Mt, self.Ct = approx_schur(prob)
         self.singular = is_singular(prob, self.Ct)
         lat = prob.lat
         self.vc = VCycle(self.S, (lat.X, lat.Y, lat.Z), nu=nu, coarse_max=coarse_max,
                          singular=self.singular, cycle=cycle, smooth=smooth, sa_levels=sa_levels,
-                         w_levels=w_levels)
+                         w_levels=w_levels, elems=(lat.nx, lat.ny, lat.nz) if aligned else None)
 
     def apply(self, r):
         nrt = self.prob.lat.n_rt

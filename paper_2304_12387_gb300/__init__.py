@@ -40,7 +40,8 @@ class ProblemDesc(ctypes.Structure):
                 ("affine", ctypes.c_int32), ("tau", ctypes.c_double), ("winv_mode", ctypes.c_int32),
                 ("nu", ctypes.c_int32), ("coarse_max", ctypes.c_int32), ("cycle", ctypes.c_int32),
                 ("fp64_emulation", ctypes.c_int32), ("smooth_levels", ctypes.c_int32),
-                ("w_levels", ctypes.c_int32), ("elem_rotation", ctypes.POINTER(ctypes.c_int8))]
+                ("w_levels", ctypes.c_int32), ("elem_rotation", ctypes.POINTER(ctypes.c_int8)),
+                ("aggregation", ctypes.c_int32)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -242,7 +243,7 @@ class Operator:
 
     def __init__(self, nx, ny, nz, k, vx, vy, vz, coef0, coef1, kind=HD_GRAD_DIV, ess_mask=0, q=0,
                  affine=False, tau=0.0, winv_mode=HD_WINV_DENSE, nu=0, coarse_max=0, cycle=1,
-                 fp64_emulation=0, smooth_levels=0, w_levels=0, elem_rotation=None, stream=None):
+                 fp64_emulation=0, smooth_levels=0, w_levels=0, elem_rotation=None, aggregation=0, stream=None):
         E = nx * ny * nz
         self._keep = []
         rot = _rot_codes(elem_rotation, E)
@@ -258,7 +259,8 @@ class Operator:
         d = ProblemDesc(kind, nx, ny, nz, k, q, arrs[0], arrs[1], arrs[2], arrs[3], arrs[4], ess_mask,
                         int(affine), tau, winv_mode, nu, coarse_max, cycle, int(fp64_emulation),
                         int(smooth_levels), int(w_levels),
-                        None if rot is None else rot.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)))
+                        None if rot is None else rot.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                        int(aggregation))
         h = ctypes.c_void_p()
         st = lib().hd_create(ctypes.byref(d), ctypes.byref(h))
         _check(st)

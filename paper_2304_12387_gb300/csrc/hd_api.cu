@@ -307,7 +307,7 @@ void destroy_all(hd_op* h) {
   cudaFree(h->x_G); cudaFree(h->x_winv); cudaFree(h->x_cscale);
   cudaFree(h->d_Ga); cudaFree(h->x_Ga);
   cudaFree(h->d_cscale); cudaFree(h->d_mt); cudaFree(h->d_mtinv); cudaFree(h->d_ct);
-  cudaFree(h->d_coarse_inv); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
+  cudaFree(h->d_coarse_inv); cudaFree(h->d_kerr); cudaFree(h->d_red); cudaFree(h->d_tmp); cudaFree(h->d_stage);
   cudaFree(h->f_G); cudaFree(h->f_winv); cudaFree(h->f_cscale); cudaFree(h->f_mtinv); cudaFree(h->f_coarse_inv);
   for (double* p : h->mv) cudaFree(p);
   for (float* p : h->fv) cudaFree(p);
@@ -411,6 +411,9 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
   h->sa = d->smooth_levels;
   if (d->w_levels < 0) { delete h; return HD_ERR_INVALID_ARG; }
   h->w_levels = d->w_levels;
+  if (d->aggregation != 0 && d->aggregation != 1) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->aggregation == 1 && (h->k % 2) == 1 && h->sa == 2) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  h->agg_aligned = d->aggregation;
   const int k = h->k;
   LatticeDims& L = h->L;
   L.nx = d->nx; L.ny = d->ny; L.nz = d->nz;
@@ -464,6 +467,11 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     if ((st = dalloc(h, &h->d_red, 4096, "reduction")) != HD_OK) break;
     if ((st = dalloc(h, &d_b, E, "b coefficient")) != HD_OK) break;
     if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "flag"); break; }
+    if (cudaMalloc(&h->d_kerr, sizeof(int)) != cudaSuccess ||
+        cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->stream) != cudaSuccess) {
+      st = hd_fail(h, HD_ERR_OOM, "kernel error word");
+      break;
+    }
     if (cudaMallocHost(&h->h_pinned, 64 * sizeof(double)) != cudaSuccess) { st = hd_fail(h, HD_ERR_OOM, "pinned"); break; }
     cudaStream_t s = h->stream;
     if (cudaMemcpyAsync(h->d_vx, d->vx, nv * 8, cudaMemcpyHostToDevice, s) != cudaSuccess ||

@@ -48,13 +48,57 @@ struct LatticeDims {
   uint32_t ess;        // essential side mask
 };
 
+// Aggregation along one lattice axis from a finer level to the next coarser one:
+// fine cell i belongs to coarse cell (i / c) m + g[i % c], and coarse cell C covers
+// the fine cells [agg_lo(C), agg_hi(C)). Pairs: c = 2, m = 1 (a trailing odd cell
+// alone); an axis that is not coarsened: c = 1, m = 1. Element-aligned aggregation
+// with an odd number c of cells per element along the axis: c, and m groups per
+// element (pairs from both ends of the element, an odd middle cell alone), so that
+// no aggregate straddles an element boundary.
+struct Agg1 {
+  int c, m;
+  int8_t g[8];   // group of fine offset r < c within its element
+  int8_t s[9];   // first fine offset of group j < m; s[m] = c
+};
+__host__ __device__ __forceinline__ int agg_of(const Agg1& a, int i) {
+  if (a.m == 1) return a.c == 2 ? (i >> 1) : (a.c == 1 ? i : i / a.c);
+  const int p = i / a.c;
+  return p * a.m + a.g[i - p * a.c];
+}
+__host__ __device__ __forceinline__ int agg_lo(const Agg1& a, int C) {
+  if (a.m == 1) return C * a.c;
+  const int p = C / a.m;
+  return p * a.c + a.s[C - p * a.m];
+}
+__host__ __device__ __forceinline__ int agg_hi(const Agg1& a, int C, int n) {
+  int h;
+  if (a.m == 1) {
+    h = C * a.c + a.c;
+  } else {
+    const int p = C / a.m;
+    h = p * a.c + a.s[C - p * a.m + 1];
+  }
+  return h < n ? h : n;
+}
+
+// true when every axis of the aggregation is pairs (or not coarsened)
+inline bool agg_pairs(const Agg1* a) { return a[0].m == 1 && a[1].m == 1 && a[2].m == 1; }
+template <typename Lv>
+void set_agg(Lv& c, const Agg1& ax, const Agg1& ay, const Agg1& az) {
+  c.ag[0] = ax; c.ag[1] = ay; c.ag[2] = az;
+  c.fx = ax.m == 1 ? ax.c : 0;
+  c.fy = ay.m == 1 ? ay.c : 0;
+  c.fz = az.m == 1 ? az.c : 0;
+}
+
 // One level of the V-cycle hierarchy: a 7-point M-matrix stencil on an
 // X x Y x Z cell lattice, stored as face weights (boundary faces included,
 // essential faces 0), per-cell mass, diagonal and inverse l1 diagonal.
 template <typename T>
 struct LevelT {
   int X, Y, Z;
-  int fx, fy, fz;      // aggregation factor from the previous (finer) level
+  int fx, fy, fz;      // pair factor (2, or 1: not coarsened) from the finer level; 0: ag[] holds groups
+  Agg1 ag[3];          // the aggregation from the previous (finer) level, per axis
   T* wx;               // (X+1) Y Z
   T* wy;               // X (Y+1) Z
   T* wz;               // X Y (Z+1)
@@ -78,7 +122,8 @@ struct LevelT {
 template <typename T>
 struct StLevelT {
   int X, Y, Z;
-  int fx, fy, fz;      // aggregation factor from the previous (finer) level
+  int fx, fy, fz;      // as in LevelT
+  Agg1 ag[3];
   int no;              // 27, 33, 81 or 179
   T* a;                // [NH][n] (setup: [no][n])
   T* dinv;             // 1 / sum_o |a[o][c]|  (l1-Jacobi)
@@ -123,6 +168,7 @@ struct hd_op {
   float setup_ms[6] = {0, 0, 0, 0, 0, 0};
   int cycle = 1;
   int w_levels = 0;    // W repetition on levels < w_levels only (0: all)
+  int agg_aligned = 0; // 1: element-aligned aggregation (Agg1) in the Schur hierarchy
   bool singular;
   cudaStream_t stream = nullptr;
   std::string err;
@@ -148,12 +194,14 @@ struct hd_op {
   double* d_mtinv = nullptr;    // [n_rt] 1/(tau diag M) on free dofs, 1 on essential
   double* d_ct = nullptr;       // [n_l2] C~
   double* d_coarse_inv = nullptr;  // dense inverse of the coarsest level (or of A + s 11^T)
+  int* d_kerr = nullptr;        // error word of the element kernel's bounded waits (bit 2)
   int coarse_n = 0;
   std::vector<LevelT<double>> lv;
   // smoothed-aggregation hierarchy (smooth_levels >= 1): prolongator values of
   // level 0 ([4][n_l2]: own aggregate, then the aggregates across the x, y and
   // z faces), stencil levels 1.., dense inverse of its coarsest level
   int sa = 0;
+  bool sa_gen = false;  // level-0 aggregation with groups of one cell: [7][n_l2] prolongator values
   double* sa_p = nullptr;
   float* sa_pf = nullptr;
   double* sa_p1 = nullptr;  // smooth_levels = 2: prolongator of level 1 ([11][n_1])

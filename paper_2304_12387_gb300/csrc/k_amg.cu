@@ -190,7 +190,8 @@ __global__ void k_sa_pvals(LevelT<double> L, int fx, int fy, int fz, double* __r
 
 // coarse coordinates
 struct CDims {
-  int X, Y, Z, fx, fy, fz;
+  int X, Y, Z, fx, fy, fz;  // fx, fy, fz: pair factors (the smoothed transfers need pairs)
+  Agg1 ag[3];               // the aggregation per axis (any)
 };
 // aggregate coordinate of fine coordinate i for an aggregation factor f in {1, 2}
 __device__ __forceinline__ int agg(int i, int f) { return i >> (f - 1); }
@@ -282,9 +283,9 @@ __global__ void k_ua_galerkin(StLevelT<double> F, CDims c, StLevelT<double> A, i
   lat_coords(C, c.X, c.Y, Cx, Cy, Cz);
   double acc[NOUT];
   for (int o = 0; o < NOUT; ++o) acc[o] = 0.0;
-  for (int Z = c.fz * Cz; Z < min(c.fz * Cz + c.fz, F.Z); ++Z)
-    for (int J = c.fy * Cy; J < min(c.fy * Cy + c.fy, F.Y); ++J)
-      for (int I = c.fx * Cx; I < min(c.fx * Cx + c.fx, F.X); ++I) {
+  for (int Z = agg_lo(c.ag[2], Cz); Z < agg_hi(c.ag[2], Cz, F.Z); ++Z)
+    for (int J = agg_lo(c.ag[1], Cy); J < agg_hi(c.ag[1], Cy, F.Y); ++J)
+      for (int I = agg_lo(c.ag[0], Cx); I < agg_hi(c.ag[0], Cx, F.X); ++I) {
         const int64_t i = I + (int64_t)F.X * (J + (int64_t)F.Y * Z);
         for (int o = 0; o < NI; ++o) {
           const double a = F.a[o * n + i];
@@ -296,7 +297,8 @@ __global__ void k_ua_galerkin(StLevelT<double> F, CDims c, StLevelT<double> A, i
             atomicExch(bad, 1);
             continue;
           }
-          const int oc = st_index<NOUT>(jI / c.fx - Cx, jJ / c.fy - Cy, jZ / c.fz - Cz);
+          const int oc =
+              st_index<NOUT>(agg_of(c.ag[0], jI) - Cx, agg_of(c.ag[1], jJ) - Cy, agg_of(c.ag[2], jZ) - Cz);
           if (oc < 0) {
             atomicExch(bad, 1);
             continue;
@@ -521,7 +523,7 @@ __global__ void __launch_bounds__(32 * SplitG<NO>::G)
                               const T* __restrict__ e, T* __restrict__ xo) {
   HD_SPLIT_CELL
   auto xa = [&](int i, int j, int z, int k) {
-    return x[k] + e[agg(i, cd.fx) + cd.X * (agg(j, cd.fy) + cd.Y * agg(z, cd.fz))];
+    return x[k] + e[agg_of(cd.ag[0], i) + cd.X * (agg_of(cd.ag[1], j) + cd.Y * agg_of(cd.ag[2], z))];
   };
   const T ax = st_row_split<T, NO>(L, live, c, I, J, Z, xa);
   if (fin) xo[c] = fma(L.dinv[c], b[c] - ax, xa(I, J, Z, c));
@@ -547,9 +549,9 @@ __global__ void k_agg_sum(int X, int Y, int Z, CDims cd, const T* __restrict__ r
   int Cx, Cy, Cz;
   lat_coords(C, cd.X, cd.Y, Cx, Cy, Cz);
   T s = (T)0;
-  for (int k = cd.fz * Cz; k < min(cd.fz * Cz + cd.fz, Z); ++k)
-    for (int j = cd.fy * Cy; j < min(cd.fy * Cy + cd.fy, Y); ++j)
-      for (int i = cd.fx * Cx; i < min(cd.fx * Cx + cd.fx, X); ++i) s += r[i + (int64_t)X * (j + (int64_t)Y * k)];
+  for (int k = agg_lo(cd.ag[2], Cz); k < agg_hi(cd.ag[2], Cz, Z); ++k)
+    for (int j = agg_lo(cd.ag[1], Cy); j < agg_hi(cd.ag[1], Cy, Y); ++j)
+      for (int i = agg_lo(cd.ag[0], Cx); i < agg_hi(cd.ag[0], Cx, X); ++i) s += r[i + (int64_t)X * (j + (int64_t)Y * k)];
   bc[C] = s;
 }
 
@@ -559,7 +561,7 @@ __global__ void k_st_prolong_add(StLevelT<T> L, CDims cd, const T* __restrict__ 
   if (c >= L.n()) return;
   int I, J, Z;
   lat_coords(c, L.X, L.Y, I, J, Z);
-  x[c] += e[agg(I, cd.fx) + (int64_t)cd.X * (agg(J, cd.fy) + (int64_t)cd.Y * agg(Z, cd.fz))];
+  x[c] += e[agg_of(cd.ag[0], I) + (int64_t)cd.X * (agg_of(cd.ag[1], J) + (int64_t)cd.Y * agg_of(cd.ag[2], Z))];
 }
 
 // x' = x + P0 e, then one l1-Jacobi sweep from x' (the first post-smoothing sweep)
@@ -571,7 +573,7 @@ __global__ void k_st_jacobi_prolong(StLevelT<T> L, CDims cd, const T* __restrict
   int I, J, Z;
   lat_coords(c, L.X, L.Y, I, J, Z);
   auto xa = [&](int i, int j, int z, int k) {
-    return x[k] + e[agg(i, cd.fx) + cd.X * (agg(j, cd.fy) + cd.Y * agg(z, cd.fz))];
+    return x[k] + e[agg_of(cd.ag[0], i) + cd.X * (agg_of(cd.ag[1], j) + cd.Y * agg_of(cd.ag[2], z))];
   };
   const T xs = xa(I, J, Z, (int)c);
   const T r = b[c] - st_row<T, NO>(L, (int)c, I, J, Z, xa);
@@ -652,6 +654,173 @@ __global__ void k_sa_prolong0(LevelT<T> L, CDims cd, const T* __restrict__ pv, c
   v = fma(p1, e1, v);
   v = fma(p2, e2, v);
   v = fma(p3, e3, v);
+  x[c] += v;
+}
+
+// -- level 0 with element-aligned aggregates (any groups per axis) ---------------------
+// A fine cell's row of P_0 = (I - omega D_l1^-1 S~) P0 has its own aggregate and, for
+// each face that leaves the aggregate, the aggregate across it: with groups of one
+// cell both faces along an axis can leave it. Stored as [7][n]: slot 0 the own
+// aggregate, slot 1 + 2 d + t the aggregate across the face of axis d on the low
+// (t = 0) or high (t = 1) side (0 when that face stays inside or is on the boundary).
+constexpr int PG_SLOTS = 7;
+
+__global__ void k_sa_pvals_g(LevelT<double> L, CDims cd, double* __restrict__ pv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = L.n();
+  if (i >= n) return;
+  int crd[3];
+  lat_coords(i, L.X, L.Y, crd[0], crd[1], crd[2]);
+  const int ext[3] = {L.X, L.Y, L.Z};
+  const Face7<double> f = faces7(L, crd[0], crd[1], crd[2]);
+  const double wd = SA_OMEGA * L.dinv[i];
+  double inner = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const int a = agg_of(cd.ag[d], crd[d]);
+    for (int t = 0; t < 2; ++t) {
+      const int nb = crd[d] + (t ? 1 : -1);
+      double v = 0.0;
+      if (nb >= 0 && nb < ext[d]) {
+        if (agg_of(cd.ag[d], nb) == a) inner += f.w[2 * d + t];
+        else v = wd * f.w[2 * d + t];
+      }
+      pv[(1 + 2 * d + t) * n + i] = v;
+    }
+  }
+  pv[i] = 1.0 - wd * (L.diag[i] - inner);
+}
+
+// A_1 = P_0^T S~ P_0 (81-point shape), one thread per coarse cell C: over the support
+// of column C (the aggregate, and the cells one step outside it along one axis), every
+// stencil neighbour j and every nonzero of row j of P_0.
+__global__ void k_sa_galerkin_g(LevelT<double> L, CDims c, const double* __restrict__ pv, StLevelT<double> A1,
+                                int* __restrict__ bad) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nc = A1.n();
+  if (C >= nc) return;
+  int Cc[3];
+  lat_coords(C, c.X, c.Y, Cc[0], Cc[1], Cc[2]);
+  const int ext[3] = {L.X, L.Y, L.Z};
+  const int64_t n = L.n();
+  int lo[3], hi[3];  // aggregate [lo, hi)
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = agg_lo(c.ag[d], Cc[d]);
+    hi[d] = agg_hi(c.ag[d], Cc[d], ext[d]);
+  }
+  double acc[81];
+  for (int o = 0; o < 81; ++o) acc[o] = 0.0;
+  for (int Z = max(lo[2] - 1, 0); Z <= min(hi[2], ext[2] - 1); ++Z)
+    for (int J = max(lo[1] - 1, 0); J <= min(hi[1], ext[1] - 1); ++J)
+      for (int I = max(lo[0] - 1, 0); I <= min(hi[0], ext[0] - 1); ++I) {
+        const int ic[3] = {I, J, Z};
+        int out = -1, nout = 0;
+        for (int d = 0; d < 3; ++d)
+          if (ic[d] < lo[d] || ic[d] >= hi[d]) {
+            out = d;
+            ++nout;
+          }
+        if (nout > 1) continue;
+        const int64_t i = I + (int64_t)L.X * (J + (int64_t)L.Y * Z);
+        // slot of column C in row i: own, or across the face of axis `out` towards the aggregate
+        const int slot = nout == 0 ? 0 : 1 + 2 * out + (ic[out] < lo[out] ? 1 : 0);
+        const double p = pv[slot * n + i];
+        if (p == 0.0) continue;
+        const Face7<double> f = faces7(L, I, J, Z);
+        for (int k = 0; k < 7; ++k) {
+          int jc[3] = {I, J, Z};
+          double a;
+          if (k == 0) {
+            a = L.diag[i];
+          } else {
+            const int d = (k - 1) >> 1, t = (k - 1) & 1;
+            jc[d] += t ? 1 : -1;
+            if (jc[d] < 0 || jc[d] >= ext[d]) continue;
+            a = -f.w[k - 1];
+          }
+          const int64_t j = jc[0] + (int64_t)L.X * (jc[1] + (int64_t)L.Y * jc[2]);
+          const int Dj[3] = {agg_of(c.ag[0], jc[0]), agg_of(c.ag[1], jc[1]), agg_of(c.ag[2], jc[2])};
+          for (int sl = 0; sl < PG_SLOTS; ++sl) {
+            const double q = pv[sl * n + j];
+            if (q == 0.0) continue;
+            int D[3] = {Dj[0], Dj[1], Dj[2]};
+            if (sl > 0) {
+              const int d = (sl - 1) >> 1, t = (sl - 1) & 1;
+              D[d] = agg_of(c.ag[d], jc[d] + (t ? 1 : -1));  // a nonzero slot has this neighbour
+            }
+            const int o = st_index<81>(D[0] - Cc[0], D[1] - Cc[1], D[2] - Cc[2]);
+            if (o < 0) {
+              atomicExch(bad, 1);
+              continue;
+            }
+            acc[o] = fma(p * a, q, acc[o]);
+          }
+        }
+      }
+  for (int o = 0; o < 81; ++o) A1.a[o * nc + C] = acc[o];
+}
+
+// b_C = (P_0^T r)_C: the aggregate's cells (slot 0), then along each axis the layer
+// just below the aggregate (their high-side slot) and just above it (low-side slot)
+template <typename T>
+__global__ void k_sa_restrict0_g(LevelT<T> L, CDims cd, const T* __restrict__ pv, const T* __restrict__ r,
+                                 T* __restrict__ bc) {
+  const int64_t C = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (C >= (int64_t)cd.X * cd.Y * cd.Z) return;
+  int Cc[3];
+  lat_coords(C, cd.X, cd.Y, Cc[0], Cc[1], Cc[2]);
+  const int ext[3] = {L.X, L.Y, L.Z};
+  const int64_t str[3] = {1, (int64_t)L.X, (int64_t)L.X * L.Y};
+  const int64_t n = L.n();
+  int lo[3], hi[3];
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = agg_lo(cd.ag[d], Cc[d]);
+    hi[d] = agg_hi(cd.ag[d], Cc[d], ext[d]);
+  }
+  T s = (T)0;
+  for (int z = lo[2]; z < hi[2]; ++z)
+    for (int y = lo[1]; y < hi[1]; ++y)
+      for (int x = lo[0]; x < hi[0]; ++x) {
+        const int64_t i = x + str[1] * y + str[2] * z;
+        s = fma(pv[i], r[i], s);
+      }
+  for (int d = 0; d < 3; ++d) {
+    const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+    const int layer[2] = {lo[d] - 1, hi[d]};
+    for (int t = 0; t < 2; ++t) {
+      const int c = layer[t];
+      if (c < 0 || c >= ext[d]) continue;
+      const int64_t slot = 1 + 2 * d + (t == 0 ? 1 : 0);
+      for (int b = lo[e2]; b < hi[e2]; ++b)
+        for (int a = lo[e1]; a < hi[e1]; ++a) {
+          const int64_t i = str[d] * c + str[e1] * a + str[e2] * b;
+          s = fma(pv[slot * n + i], r[i], s);
+        }
+    }
+  }
+  bc[C] = s;
+}
+
+// x += P_0 e
+template <typename T>
+__global__ void k_sa_prolong0_g(LevelT<T> L, CDims cd, const T* __restrict__ pv, const T* __restrict__ e,
+                                T* __restrict__ x) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t n = L.n();
+  if (c >= n) return;
+  int crd[3];
+  lat_coords(c, L.X, L.Y, crd[0], crd[1], crd[2]);
+  const int ext[3] = {L.X, L.Y, L.Z};
+  const int D[3] = {agg_of(cd.ag[0], crd[0]), agg_of(cd.ag[1], crd[1]), agg_of(cd.ag[2], crd[2])};
+  auto ev = [&](int ex, int ey, int ez) { return e[ex + (int64_t)cd.X * (ey + (int64_t)cd.Y * ez)]; };
+  T v = pv[c] * ev(D[0], D[1], D[2]);
+  for (int d = 0; d < 3; ++d)
+    for (int t = 0; t < 2; ++t) {
+      const int nb = crd[d] + (t ? 1 : -1);
+      // a slot without a neighbour outside the aggregate holds an exact zero: point it at the own one
+      int A[3] = {D[0], D[1], D[2]};
+      if (nb >= 0 && nb < ext[d]) A[d] = agg_of(cd.ag[d], nb);
+      v = fma(pv[(1 + 2 * d + t) * n + c], ev(A[0], A[1], A[2]), v);
+    }
   x[c] += v;
 }
 
@@ -922,9 +1091,9 @@ __global__ void k_to_f32_sa(int64_t n, const double* __restrict__ a, T* __restri
   if (i < n) b[i] = (T)a[i];
 }
 
-template <typename T>
-CDims cdims_of(const StLevelT<T>& c) {
-  return CDims{c.X, c.Y, c.Z, c.fx, c.fy, c.fz};
+template <typename Lv>
+CDims cdims_of(const Lv& c) {
+  return CDims{c.X, c.Y, c.Z, c.fx, c.fy, c.fz, {c.ag[0], c.ag[1], c.ag[2]}};
 }
 
 // -- the cycle ----------------------------------------------------------------------
@@ -1027,13 +1196,18 @@ void sa_cycle0(hd_op* h, LevelT<T>& L, const T* pv, std::vector<StLevelT<T>>& st
   const int last = (int)st.size();
   const int repeats = (h->cycle == 2 && 1 < last) ? 2 : 1;  // level 0 (w_levels >= 1 or 0)
   const T* xc = nullptr;
+  auto prolong0 = [&](const T* e, T* x) {
+    if (h->sa_gen) k_sa_prolong0_g<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, e, x);
+    else k_sa_prolong0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, e, x);
+  };
   for (int rep = 0; rep < repeats; ++rep) {
-    if (rep > 0) k_sa_prolong0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, xc, cur);
+    if (rep > 0) prolong0(xc, cur);
     k_sa_res0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, L.b);
-    k_sa_restrict0<T><<<nblk(st[0].n()), TPB, 0, h->stream>>>(L, cd, pv, L.b, st[0].b);
+    if (h->sa_gen) k_sa_restrict0_g<T><<<nblk(st[0].n()), TPB, 0, h->stream>>>(L, cd, pv, L.b, st[0].b);
+    else k_sa_restrict0<T><<<nblk(st[0].n()), TPB, 0, h->stream>>>(L, cd, pv, L.b, st[0].b);
     xc = sa_level<T>(h, st, p1, 1, st[0].b, nullptr);
   }
-  k_sa_prolong0<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, cd, pv, xc, cur);
+  prolong0(xc, cur);
   for (int s = 0; s < nu; ++s) {
     T* o = (s == nu - 1) ? out : ((cur == L.x0) ? L.x1 : L.x0);
     k_vc_jacobi<T><<<nblk(L.n()), TPB, 0, h->stream>>>(L, b, cur, o);
@@ -1068,9 +1242,16 @@ hd_status sa_setup(hd_op* h) {
   if (!h->sa || h->lv.size() < 2) return HD_OK;  // one level: nothing to smooth
   const LevelT<double>& L0 = h->lv[0];
   const int64_t n0 = L0.n();
-  if (cudaMalloc(&h->sa_p, sizeof(double) * 4 * n0) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA prolongator");
   const LevelT<double>& l1 = h->lv[1];
-  k_sa_pvals<<<nblk(n0), TPB, 0, h->stream>>>(L0, l1.fx, l1.fy, l1.fz, h->sa_p);
+  // element-aligned groups of one cell: the general level-0 transfer (7 slots per cell)
+  h->sa_gen = !agg_pairs(l1.ag);
+  if (h->sa_gen && h->sa >= 2)
+    return hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "smooth_levels = 2 with element-aligned groups of one cell");
+  const int slots = h->sa_gen ? PG_SLOTS : 4;
+  if (cudaMalloc(&h->sa_p, sizeof(double) * slots * n0) != cudaSuccess)
+    return hd_fail(h, HD_ERR_OOM, "SA prolongator");
+  if (h->sa_gen) k_sa_pvals_g<<<nblk(n0), TPB, 0, h->stream>>>(L0, cdims_of(l1), h->sa_p);
+  else k_sa_pvals<<<nblk(n0), TPB, 0, h->stream>>>(L0, l1.fx, l1.fy, l1.fz, h->sa_p);
   HD_LAUNCH_CK(h, "k_sa_pvals");
   int* d_bad = nullptr;
   if (cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "flag");
@@ -1080,10 +1261,14 @@ hd_status sa_setup(hd_op* h) {
   for (size_t l = 1; l < h->lv.size() && st == HD_OK; ++l) {
     const LevelT<double>& g = h->lv[l];  // same lattice dimensions as the unsmoothed level
     StLevelT<double> s{};
-    s.X = g.X; s.Y = g.Y; s.Z = g.Z; s.fx = g.fx; s.fy = g.fy; s.fz = g.fz;
+    s.X = g.X; s.Y = g.Y; s.Z = g.Z;
+    set_agg(s, g.ag[0], g.ag[1], g.ag[2]);
     // shapes: 33 on level 1; with the second smoothed level 179 on level 2 and 81
-    // on level 3; 27 elsewhere
-    s.no = (l == 1) ? 33 : (two && l == 2) ? 179 : (two && l == 3) ? 81 : 27;
+    // on level 3; 27 elsewhere. Element-aligned groups of one cell (general
+    // transfers): 81 on level 1 and below every general transfer
+    const bool gen = !agg_pairs(g.ag);
+    if (h->sa_gen) s.no = (l == 1 || gen) ? 81 : 27;
+    else s.no = (l == 1) ? 33 : (two && l == 2) ? 179 : (two && l == 3) ? 81 : 27;
     st = alloc_st<double>(h, s, true);
     h->st.push_back(s);
     if (st != HD_OK) break;
@@ -1091,7 +1276,13 @@ hd_status sa_setup(hd_op* h) {
     const CDims cd = cdims_of(S);
     const unsigned gc = nblk(S.n());
     if (l == 1) {
-      k_sa_galerkin<<<gc, TPB, 0, h->stream>>>(L0, cd, h->sa_p, S, d_bad);
+      if (h->sa_gen) k_sa_galerkin_g<<<gc, TPB, 0, h->stream>>>(L0, cd, h->sa_p, S, d_bad);
+      else k_sa_galerkin<<<gc, TPB, 0, h->stream>>>(L0, cd, h->sa_p, S, d_bad);
+    } else if (gen) {
+      const StLevelT<double>& F = h->st[h->st.size() - 2];
+      if (F.no == 81) k_ua_galerkin<81, 81><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+      else if (F.no == 27) k_ua_galerkin<27, 81><<<gc, TPB, 0, h->stream>>>(F, cd, S, d_bad);
+      else st = hd_fail(h, HD_ERR_NOT_IMPLEMENTED, "element-aligned groups below this stencil shape");
     } else if (two && l == 2) {
       const StLevelT<double>& A1 = h->st[0];
       if (cudaMalloc(&h->sa_p1, sizeof(double) * P1_SLOTS * A1.n()) != cudaSuccess) {
@@ -1156,8 +1347,9 @@ hd_status sa_setup(hd_op* h) {
 hd_status sa_setup_f32(hd_op* h) {
   if (h->st.empty() || !h->stf.empty()) return HD_OK;
   const int64_t n0 = h->lv[0].n();
-  if (cudaMalloc(&h->sa_pf, sizeof(float) * 4 * n0) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA f32");
-  k_to_f32_sa<float><<<nblk(4 * n0), TPB, 0, h->stream>>>(4 * n0, h->sa_p, h->sa_pf);
+  const int64_t np0 = (h->sa_gen ? PG_SLOTS : 4) * n0;
+  if (cudaMalloc(&h->sa_pf, sizeof(float) * np0) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA f32");
+  k_to_f32_sa<float><<<nblk(np0), TPB, 0, h->stream>>>(np0, h->sa_p, h->sa_pf);
   if (h->sa_p1) {
     const int64_t np = P1_SLOTS * h->st[0].n();
     if (cudaMalloc(&h->sa_p1f, sizeof(float) * np) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA f32");
@@ -1165,7 +1357,8 @@ hd_status sa_setup_f32(hd_op* h) {
   }
   for (const StLevelT<double>& d : h->st) {
     StLevelT<float> f{};
-    f.X = d.X; f.Y = d.Y; f.Z = d.Z; f.fx = d.fx; f.fy = d.fy; f.fz = d.fz; f.no = d.no;
+    f.X = d.X; f.Y = d.Y; f.Z = d.Z; f.no = d.no;
+    set_agg(f, d.ag[0], d.ag[1], d.ag[2]);
     hd_status st = alloc_st<float>(h, f, true);
     h->stf.push_back(f);
     if (st != HD_OK) return st;

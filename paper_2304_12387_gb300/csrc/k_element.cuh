@@ -15,6 +15,7 @@
 
 #include "dfloat.cuh"
 #include "hd_internal.h"
+#include "tc_ptx.cuh"
 
 namespace hdk {
 
@@ -55,6 +56,7 @@ struct CgArgs {
   T tol2;            // stop when ||r||^2 <= tol2 ||b||^2 (per element)
   int hist;          // 0: CG in the GL nodal basis (Sec. 2.5); 1: in the histopolation basis
   int chol;          // 1 (and wdet null): W_e^-1 q_e by the stored Cholesky factor passed as winv
+  int* err = nullptr;  // error word: bit 2 = a bounded wait for staged W_e^-1 rows ran out
 };
 
 // Sum of products as one FMA chain (one type per arithmetic: double, float or
@@ -470,6 +472,28 @@ struct ElemCfg<float, false> {
   static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH;
 };
 
+// Staging of the dense W_e^-1 rows by the copy engine (double-float kernel): the
+// sum-factorisation buffers T1/T2 are idle while the L2 rows are computed, so they
+// hold two buffers of NB rows of W_e^-1 for each element of the CTA. One thread asks
+// for a chunk with one bulk copy per element (cp.async.bulk, completion counted on
+// the buffer's mbarrier), the first two before the gather; the rows' threads then
+// read W from shared memory instead of waiting on HBM loads. Needs an even NL2 (the
+// per-element blocks and chunks start on 16-byte boundaries) and one thread per row.
+#ifndef HD_DF_STAGE
+#define HD_DF_STAGE 0
+#endif
+template <typename T, int K, int Q, int EB, bool AFF>
+struct StageW {
+  using S = Sizes<K, Q>;
+  static constexpr int NL2 = S::NL2;
+  static constexpr int FIT = EB * (S::R1 + S::R2) / (2 * EB * NL2);  // rows per buffer that fit
+  static constexpr int NB = FIT >= NL2 ? NL2 : FIT >= 32 ? 32 : FIT >= 16 ? 16 : FIT >= 8 ? 8 : FIT >= 4 ? 4 : 2;
+  static constexpr bool ON = HD_DF_STAGE != 0 && std::is_same<T, dfloat>::value && !AFF && NL2 % 2 == 0 &&
+                             NL2 % NB == 0 && FIT >= 2 && EB * NL2 <= ElemCfg<T, AFF>::THREADS;
+  static constexpr int NCH = NL2 / NB;
+  static constexpr int BAR_BYTES = ON ? 16 : 0;
+};
+
 // L2 prefetch of [p, p + bytes) in 16 KB pieces, one piece per lane; the range
 // is trimmed to whole 16-byte units and skipped when p is not 16-byte aligned.
 __device__ __forceinline__ void prefetch_l2_block(const void* p, size_t bytes, int lane) {
@@ -503,6 +527,28 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
   const bool needq = (mode & (OP_DT | OP_C)) != 0;
   const bool use_cg = !AFF && (mode & OP_C) && cg.wdet != nullptr;
   const bool use_chol = !AFF && (mode & OP_C) && !use_cg && cg.chol != 0;
+  using SW = StageW<T, K, Q, EB, AFF>;
+  [[maybe_unused]] const bool stage_w = SW::ON && (mode & OP_C) && !use_cg && !use_chol;
+  [[maybe_unused]] uint64_t* wbar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)EB * S::PER_ELEM * sizeof(T));
+  [[maybe_unused]] const int ne_cta = (n_elem - e0 < EB) ? n_elem - e0 : EB;
+  // chunk c (rows [c NB, (c + 1) NB) of every element's W_e^-1) into buffer c & 1
+  [[maybe_unused]] auto w_issue = [&](int c) {
+    T* buf = s1 + (c & 1) * (EB * SW::NB * NL2);
+    const uint32_t bar = tc::smem_u32(&wbar[c & 1]);
+    tc::mbar_arrive_expect_tx(bar, (uint32_t)(ne_cta * SW::NB * NL2 * sizeof(T)));
+    for (int el = 0; el < ne_cta; ++el)
+      tc::bulk_g2s(tc::smem_u32(buf + el * SW::NB * NL2),
+                   winv + ((size_t)(e0 + el) * NL2 + (size_t)c * SW::NB) * NL2, SW::NB * NL2 * sizeof(T), bar);
+  };
+  if constexpr (SW::ON) {
+    if (stage_w && tid == 0) {  // the barrier after the gather publishes the initialisation
+      tc::mbar_init(tc::smem_u32(&wbar[0]), 1);
+      tc::mbar_init(tc::smem_u32(&wbar[1]), 1);
+      tc::fence_mbar_init();
+      w_issue(0);
+      if (SW::NCH > 1) w_issue(1);
+    }
+  }
   if constexpr (ElemCfg<T, AFF>::PREFETCH != 0) {
     if (tid < 32 && e0 < n_elem) {
       const int ne = (n_elem - e0 < EB) ? n_elem - e0 : EB;
@@ -597,13 +643,53 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
     int i = a % K, j = (a / K) % K, l = a / (K * K);
     yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = Cvt<T, IO>::out(v);
   };
-  if (mode & (OP_D | OP_C)) {
+  bool rows_done = false;
+  if constexpr (SW::ON) {
+    if (stage_w) {  // the rows from the staged chunks (one thread per row)
+      const int el = tid / NL2, a = tid - el * NL2;
+      const bool mine = tid < EB * NL2 && el < ne_cta;
+      const T* qe = sq + el * NL2;
+      Acc<T> acc;
+      for (int c = 0; c < SW::NCH; ++c) {
+        if (mine) {
+          if (!tc::mbar_wait(tc::smem_u32(&wbar[c & 1]), (uint32_t)((c >> 1) & 1)) && cg.err) atomicOr(cg.err, 2);
+          const T* Wc = s1 + (c & 1) * (EB * SW::NB * NL2) + el * SW::NB * NL2 + a;
+          if (c == 0) {
+            acc.init(Wc[0], qe[0]);
+#pragma unroll
+            for (int bb = 1; bb < SW::NB; ++bb) acc.add(Wc[bb * NL2], qe[bb]);
+          } else {
+#pragma unroll
+            for (int bb = 0; bb < SW::NB; ++bb) acc.add(Wc[bb * NL2], qe[c * SW::NB + bb]);
+          }
+        }
+        if (SW::NCH > 2) {  // buffer c & 1 takes chunk c + 2 once every row has read it
+          __syncthreads();
+          if (tid == 0 && c + 2 < SW::NCH) {
+            tc::fence_proxy_async_smem();
+            w_issue(c + 2);
+          }
+        }
+      }
+      if (mine) {
+        const int e = e0 + el;
+        T v = (mode & OP_D) ? div_local<T, K>(su + el * NRT, a) : (T)0;
+        const T s = acc.get() * cscale[e];
+        v = (mode & OP_CPOS) ? v + s : v - s;
+        const int ex = e % L.nx, ey = (e / L.nx) % L.ny, ez = e / (L.nx * L.ny);
+        const int i = a % K, j = (a / K) % K, l = a / (K * K);
+        yq[(ex * K + i) + L.X * ((ey * K + j) + L.Y * (ez * K + l))] = Cvt<T, IO>::out(v);
+      }
+      rows_done = true;
+    }
+  }
+  if ((mode & (OP_D | OP_C)) && !rows_done) {
     for (int t = tid; t < EB * NL2; t += nth) {
       if (e0 + t / NL2 >= n_elem) continue;
       l2_row(t, (mode & OP_D) ? div_local<T, K>(su + (t / NL2) * NRT, t % NL2) : (T)0);
     }
   }
-  if (use_cg || use_chol || (AFF && (mode & OP_C))) __syncthreads();
+  if (use_cg || use_chol || rows_done || (AFF && (mode & OP_C))) __syncthreads();
 
   if (mode & OP_M) {
     // -- interpolation to the points: stage A (contract along x) ----------------
@@ -977,7 +1063,7 @@ hd_status launch_elem_op(hd_op* h, int mode, const T* G, const T* winv, const T*
                          const IO* u, const IO* q, IO* yu, IO* yq, const T* Ga) {
   constexpr int EB = ElemCfg<T, AFF>::EB, THREADS = ElemCfg<T, AFF>::THREADS;
   using S = Sizes<K, Q>;
-  size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T);
+  size_t smem = (size_t)EB * S::PER_ELEM * sizeof(T) + StageW<T, K, Q, EB, AFF>::BAR_BYTES;
   auto kern = k_elem_op<T, IO, K, Q, EB, AFF>;
   static bool attr_set[HD_MAX_DEVICES] = {};
   bool* done = device_flag(attr_set);
@@ -1097,7 +1183,7 @@ HD_DECLARE_K(5)
   }                                                                                                       \
   hd_status elem_op_df_k##KK(hd_op* h, int mode, const double* u, const double* q, double* yu,            \
                              double* yq) {                                                                \
-    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0, 0};                                         \
+    hdk::CgArgs<dfloat> cg{nullptr, nullptr, 0, dfloat(0), 0, 0, h->d_kerr};                              \
     if (h->q == KK + 1)                                                                                   \
       return hdk::run_elem_op<dfloat, double, KK, KK + 1>(h, mode, h->x_G, h->x_winv, h->x_cscale, cg, u, \
                                                           q, yu, yq, h->x_Ga);                            \

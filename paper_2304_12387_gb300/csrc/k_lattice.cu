@@ -140,10 +140,11 @@ __global__ void k_coarsen_x(LevelT<double> f, LevelT<double> c) {
   int64_t n = (int64_t)(c.X + 1) * c.Y * c.Z;
   if (t >= n) return;
   int Ic = (int)(t % (c.X + 1)), Jc = (int)((t / (c.X + 1)) % c.Y), Zc = (int)(t / ((int64_t)(c.X + 1) * c.Y));
-  int I = min(c.fx * Ic, f.X);
+  int I = min(agg_lo(c.ag[0], Ic), f.X);
   double s = 0.0;
-  for (int Z = c.fz * Zc; Z < min(c.fz * Zc + c.fz, f.Z); ++Z)
-    for (int J = c.fy * Jc; J < min(c.fy * Jc + c.fy, f.Y); ++J) s += f.wx[I + (int64_t)(f.X + 1) * (J + (int64_t)f.Y * Z)];
+  for (int Z = agg_lo(c.ag[2], Zc); Z < agg_hi(c.ag[2], Zc, f.Z); ++Z)
+    for (int J = agg_lo(c.ag[1], Jc); J < agg_hi(c.ag[1], Jc, f.Y); ++J)
+      s += f.wx[I + (int64_t)(f.X + 1) * (J + (int64_t)f.Y * Z)];
   c.wx[t] = s;
 }
 __global__ void k_coarsen_y(LevelT<double> f, LevelT<double> c) {
@@ -151,10 +152,11 @@ __global__ void k_coarsen_y(LevelT<double> f, LevelT<double> c) {
   int64_t n = (int64_t)c.X * (c.Y + 1) * c.Z;
   if (t >= n) return;
   int Ic = (int)(t % c.X), Jc = (int)((t / c.X) % (c.Y + 1)), Zc = (int)(t / ((int64_t)c.X * (c.Y + 1)));
-  int J = min(c.fy * Jc, f.Y);
+  int J = min(agg_lo(c.ag[1], Jc), f.Y);
   double s = 0.0;
-  for (int Z = c.fz * Zc; Z < min(c.fz * Zc + c.fz, f.Z); ++Z)
-    for (int I = c.fx * Ic; I < min(c.fx * Ic + c.fx, f.X); ++I) s += f.wy[I + (int64_t)f.X * (J + (int64_t)(f.Y + 1) * Z)];
+  for (int Z = agg_lo(c.ag[2], Zc); Z < agg_hi(c.ag[2], Zc, f.Z); ++Z)
+    for (int I = agg_lo(c.ag[0], Ic); I < agg_hi(c.ag[0], Ic, f.X); ++I)
+      s += f.wy[I + (int64_t)f.X * (J + (int64_t)(f.Y + 1) * Z)];
   c.wy[t] = s;
 }
 __global__ void k_coarsen_z(LevelT<double> f, LevelT<double> c) {
@@ -163,10 +165,11 @@ __global__ void k_coarsen_z(LevelT<double> f, LevelT<double> c) {
   if (t >= n) return;
   int Ic, Jc, Zc;
   lat_coords(t, c.X, c.Y, Ic, Jc, Zc);
-  int Z = min(c.fz * Zc, f.Z);
+  int Z = min(agg_lo(c.ag[2], Zc), f.Z);
   double s = 0.0;
-  for (int J = c.fy * Jc; J < min(c.fy * Jc + c.fy, f.Y); ++J)
-    for (int I = c.fx * Ic; I < min(c.fx * Ic + c.fx, f.X); ++I) s += f.wz[I + (int64_t)f.X * (J + (int64_t)f.Y * Z)];
+  for (int J = agg_lo(c.ag[1], Jc); J < agg_hi(c.ag[1], Jc, f.Y); ++J)
+    for (int I = agg_lo(c.ag[0], Ic); I < agg_hi(c.ag[0], Ic, f.X); ++I)
+      s += f.wz[I + (int64_t)f.X * (J + (int64_t)f.Y * Z)];
   c.wz[t] = s;
 }
 __global__ void k_coarsen_mass(LevelT<double> f, LevelT<double> c) {
@@ -175,9 +178,10 @@ __global__ void k_coarsen_mass(LevelT<double> f, LevelT<double> c) {
   int Ic, Jc, Zc;
   lat_coords(t, c.X, c.Y, Ic, Jc, Zc);
   double s = 0.0;
-  for (int Z = c.fz * Zc; Z < min(c.fz * Zc + c.fz, f.Z); ++Z)
-    for (int J = c.fy * Jc; J < min(c.fy * Jc + c.fy, f.Y); ++J)
-      for (int I = c.fx * Ic; I < min(c.fx * Ic + c.fx, f.X); ++I) s += f.mass[I + (int64_t)f.X * (J + (int64_t)f.Y * Z)];
+  for (int Z = agg_lo(c.ag[2], Zc); Z < agg_hi(c.ag[2], Zc, f.Z); ++Z)
+    for (int J = agg_lo(c.ag[1], Jc); J < agg_hi(c.ag[1], Jc, f.Y); ++J)
+      for (int I = agg_lo(c.ag[0], Ic); I < agg_hi(c.ag[0], Ic, f.X); ++I)
+        s += f.mass[I + (int64_t)f.X * (J + (int64_t)f.Y * Z)];
   c.mass[t] = s;
 }
 
@@ -188,7 +192,7 @@ __device__ __forceinline__ T stencil_res_prolong(const LevelT<T>& lv, const Leve
                                                  int64_t c) {
   auto xv = [&](int i, int j, int z) -> T {
     int64_t cc = i + (int64_t)lv.X * (j + (int64_t)lv.Y * z);
-    return x[cc] + xcrs[(i / cl.fx) + (int64_t)cl.X * ((j / cl.fy) + (int64_t)cl.Y * (z / cl.fz))];
+    return x[cc] + xcrs[agg_of(cl.ag[0], i) + (int64_t)cl.X * (agg_of(cl.ag[1], j) + (int64_t)cl.Y * agg_of(cl.ag[2], z))];
   };
   int64_t xl = I + (int64_t)(lv.X + 1) * (J + (int64_t)lv.Y * Z);
   int64_t yl = I + (int64_t)lv.X * (J + (int64_t)(lv.Y + 1) * Z);
@@ -221,7 +225,7 @@ __global__ void k_vc_jacobi_prolong(LevelT<T> lv, LevelT<T> cl, const T* __restr
   if (c >= lv.n()) return;
   int I, J, Z;
   lat_coords(c, lv.X, lv.Y, I, J, Z);
-  T xs = x[c] + xcrs[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
+  T xs = x[c] + xcrs[agg_of(cl.ag[0], I) + (int64_t)cl.X * (agg_of(cl.ag[1], J) + (int64_t)cl.Y * agg_of(cl.ag[2], Z))];
   xo[c] = fma(lv.dinv[c], stencil_res_prolong<T>(lv, cl, x, xcrs, b[c], xs, I, J, Z, c), xs);
 }
 
@@ -232,7 +236,7 @@ __global__ void k_vc_prolong_add(LevelT<T> lv, LevelT<T> cl, const T* __restrict
   if (c >= lv.n()) return;
   int I, J, Z;
   lat_coords(c, lv.X, lv.Y, I, J, Z);
-  x[c] += xcrs[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
+  x[c] += xcrs[agg_of(cl.ag[0], I) + (int64_t)cl.X * (agg_of(cl.ag[1], J) + (int64_t)cl.Y * agg_of(cl.ag[2], Z))];
 }
 
 // coarse right-hand side: sum over each aggregate of the fine residual b - S x
@@ -244,9 +248,9 @@ __global__ void k_vc_restrict(LevelT<T> lv, LevelT<T> cl, const T* __restrict__ 
   int Ic, Jc, Zc;
   lat_coords(t, cl.X, cl.Y, Ic, Jc, Zc);
   T s = (T)0;
-  for (int Z = cl.fz * Zc; Z < min(cl.fz * Zc + cl.fz, lv.Z); ++Z)
-    for (int J = cl.fy * Jc; J < min(cl.fy * Jc + cl.fy, lv.Y); ++J)
-      for (int I = cl.fx * Ic; I < min(cl.fx * Ic + cl.fx, lv.X); ++I) {
+  for (int Z = agg_lo(cl.ag[2], Zc); Z < agg_hi(cl.ag[2], Zc, lv.Z); ++Z)
+    for (int J = agg_lo(cl.ag[1], Jc); J < agg_hi(cl.ag[1], Jc, lv.Y); ++J)
+      for (int I = agg_lo(cl.ag[0], Ic); I < agg_hi(cl.ag[0], Ic, lv.X); ++I) {
         int64_t c = I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z);
         s += stencil_res<T>(lv, x, b[c], x[c], I, J, Z, c);
       }
@@ -512,12 +516,50 @@ hd_status dense_spd_inverse(hd_op* h, std::vector<double>& A, int n, bool singul
   return HD_OK;
 }
 
+// Aggregation of an axis of n fine cells (ne elements along it); sets the coarse length.
+// Element-aligned groups (`aligned`) where the axis holds an odd number c > 1 of cells
+// per element (even c: the pairs are already aligned with the element boundaries).
+static Agg1 make_agg(int n, int ne, bool aligned, int& nc) {
+  Agg1 a{};
+  const int c = (ne > 0 && n % ne == 0) ? n / ne : 0;
+  if (n == 1) {
+    a.c = 1; a.m = 1;
+  } else if (aligned && c > 1 && (c & 1) && c <= 7) {
+    // pairs alternately from the low and the high end, the middle cell alone
+    int sizes_lo[4], sizes_hi[4], nlo = 0, nhi = 0, lo = 0, hi = c;
+    bool low = true;
+    while (hi - lo >= 2) {
+      if (low) { sizes_lo[nlo++] = 2; lo += 2; } else { sizes_hi[nhi++] = 2; hi -= 2; }
+      low = !low;
+    }
+    int sizes[8], m = 0;
+    for (int i = 0; i < nlo; ++i) sizes[m++] = sizes_lo[i];
+    if (hi - lo == 1) sizes[m++] = 1;
+    for (int i = nhi - 1; i >= 0; --i) sizes[m++] = sizes_hi[i];
+    a.c = c; a.m = m;
+    int r = 0;
+    for (int j = 0; j < m; ++j) {
+      a.s[j] = (int8_t)r;
+      for (int t = 0; t < sizes[j]; ++t) a.g[r++] = (int8_t)j;
+    }
+    a.s[m] = (int8_t)c;
+  } else {
+    a.c = 2; a.m = 1;
+  }
+  nc = a.m == 1 ? (n + a.c - 1) / a.c : (n / a.c) * a.m;
+  return a;
+}
+
 hd_status precond_setup(hd_op* h) {
   const LatticeDims& L = h->L;
   // level 0 lives on the fine lattice: its face weights are an RT-sized vector
   LevelT<double> l0{};
   l0.X = L.X; l0.Y = L.Y; l0.Z = L.Z;
-  l0.fx = l0.fy = l0.fz = 1;
+  {
+    Agg1 one{};
+    one.c = 1; one.m = 1;
+    set_agg(l0, one, one, one);
+  }
   double* w0 = nullptr;
   if (cudaMalloc(&w0, sizeof(double) * h->n_rt) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "face weights");
   l0.wx = w0;
@@ -538,8 +580,8 @@ hd_status precond_setup(hd_op* h) {
   while (h->lv.back().n() > h->coarse_max && (int)h->lv.size() < 24) {
     const LevelT<double>& f = h->lv.back();
     LevelT<double> c{};
-    c.fx = f.X > 1 ? 2 : 1; c.fy = f.Y > 1 ? 2 : 1; c.fz = f.Z > 1 ? 2 : 1;
-    c.X = (f.X + c.fx - 1) / c.fx; c.Y = (f.Y + c.fy - 1) / c.fy; c.Z = (f.Z + c.fz - 1) / c.fz;
+    const bool al = h->agg_aligned != 0;
+    set_agg(c, make_agg(f.X, L.nx, al, c.X), make_agg(f.Y, L.ny, al, c.Y), make_agg(f.Z, L.nz, al, c.Z));
     if (c.X == f.X && c.Y == f.Y && c.Z == f.Z) break;
     st = alloc_level<double>(h, c, true);
     h->lv.push_back(c);
@@ -618,7 +660,8 @@ hd_status setup_f32(hd_op* h) {
   for (size_t l = 0; l < h->lv.size(); ++l) {
     const LevelT<double>& d = h->lv[l];
     LevelT<float> f{};
-    f.X = d.X; f.Y = d.Y; f.Z = d.Z; f.fx = d.fx; f.fy = d.fy; f.fz = d.fz;
+    f.X = d.X; f.Y = d.Y; f.Z = d.Z;
+    set_agg(f, d.ag[0], d.ag[1], d.ag[2]);
     if ((st = alloc_level<float>(h, f, true)) != HD_OK) return st;
     h->lvf.push_back(f);
     k_to_f32<float><<<nblk((int64_t)(d.X + 1) * d.Y * d.Z), TPB, 0, h->stream>>>((int64_t)(d.X + 1) * d.Y * d.Z, d.wx, f.wx);
@@ -709,9 +752,9 @@ __global__ void k_restrict_plain(LevelT<double> lv, LevelT<double> cl, const dou
   int Ic, Jc, Zc;
   lat_coords(t, cl.X, cl.Y, Ic, Jc, Zc);
   double s = 0.0;
-  for (int Z = cl.fz * Zc; Z < min(cl.fz * Zc + cl.fz, lv.Z); ++Z)
-    for (int J = cl.fy * Jc; J < min(cl.fy * Jc + cl.fy, lv.Y); ++J)
-      for (int I = cl.fx * Ic; I < min(cl.fx * Ic + cl.fx, lv.X); ++I) s += r[I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z)];
+  for (int Z = agg_lo(cl.ag[2], Zc); Z < agg_hi(cl.ag[2], Zc, lv.Z); ++Z)
+    for (int J = agg_lo(cl.ag[1], Jc); J < agg_hi(cl.ag[1], Jc, lv.Y); ++J)
+      for (int I = agg_lo(cl.ag[0], Ic); I < agg_hi(cl.ag[0], Ic, lv.X); ++I) s += r[I + (int64_t)lv.X * (J + (int64_t)lv.Y * Z)];
   bc[t] = s;
 }
 __global__ void k_prolong_add(LevelT<double> lv, LevelT<double> cl, const double* __restrict__ xc,
@@ -720,7 +763,7 @@ __global__ void k_prolong_add(LevelT<double> lv, LevelT<double> cl, const double
   if (c >= lv.n()) return;
   int I, J, Z;
   lat_coords(c, lv.X, lv.Y, I, J, Z);
-  z[c] += xc[(I / cl.fx) + (int64_t)cl.X * ((J / cl.fy) + (int64_t)cl.Y * (Z / cl.fz))];
+  z[c] += xc[agg_of(cl.ag[0], I) + (int64_t)cl.X * (agg_of(cl.ag[1], J) + (int64_t)cl.Y * agg_of(cl.ag[2], Z))];
 }
 
 hd_status coarse_correction(hd_op* h, const double* r, double* z) {
