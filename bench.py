@@ -783,7 +783,8 @@ def run_winv_study(args):
     1.7 M L2 DOFs for k = 2..5, the setup of the W^-1 data and 100 applications of W^-1
     (hd_apply_C, FP64) by the stored explicit inverse (batched gemv), the stored Cholesky
     factors (two triangular solves), the fused local CG in the Gauss-Legendre nodal basis
-    and the same CG in the histopolation basis."""
+    and the same CG in the histopolation basis; then the same four approaches for every
+    degree of the paper's table, k = 2..9, through the degree-generic mass inverse."""
     import torch
     import paper_2304_12387_gb300 as hd
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
@@ -821,6 +822,41 @@ def run_winv_study(args):
         print(json.dumps(row), flush=True)
     print(json.dumps({"study": "W^-1 setup and 100 applications, FP64, perturbed mesh, q = k + 2",
                       "rows": rows}), flush=True)
+    # every degree of the paper's table (p = k - 1 = 1..8) through the degree-generic mass
+    # inverse (hd_massinv_*), about 1.7 M L2 DOFs each
+    rows = []
+    for k, nx in ((2, 60), (3, 40), (4, 30), (5, 24), (6, 20), (7, 17), (8, 15), (9, 13)):
+        vx, vy, vz, alpha, _ = workload(nx)
+        row = {"k": k, "p": k - 1, "elements": nx ** 3, "l2_dofs": (nx * k) ** 3}
+        ref = None
+        for name, mode in (("inverse", hd.HD_WINV_DENSE), ("cholesky", hd.HD_WINV_CHOL), ("cg_gl", hd.HD_WINV_CG),
+                           ("cg_hist", hd.HD_WINV_CG_HIST)):
+            mi = hd.MassInverse(nx, nx, nx, k, vx, vy, vz, alpha=alpha, method=mode, stream=stream)
+            q = torch.from_numpy(synth.uniform(mi.n_l2, seed=SEED + 9)).cuda()
+            y = torch.empty_like(q)
+            for _ in range(3):
+                mi.apply(q, y)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(100):
+                mi.apply(q, y)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            yh = y.cpu().numpy()
+            if ref is None:
+                ref = yh
+            setup = mi.setup_ms()
+            row[name] = {"setup_ms": round(setup, 3), "solve_x100_ms": round(ms, 3), "total_ms": round(setup + ms, 3),
+                         "gdof_s": round(mi.n_l2 * 100 / ms / 1e6, 3), "cg_iterations": mi.iterations(),
+                         "max_rel_diff_vs_inverse": float(np.abs(yh - ref).max() / np.abs(ref).max())}
+            mi.close()
+            del q, y
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"study": "DG mass inverse of any degree (hd_massinv_*): setup and 100 applications, FP64, "
+                               "perturbed mesh, q = k + 2, alpha = 1", "rows": rows}), flush=True)
 
 
 def learned_study(args, stream):
@@ -876,6 +912,15 @@ def learned_study(args, stream):
     op.hd_set_schur_prec(1)
     out["learned_mixed"], _ = solve(op, b, 1, x64)
     op.hd_set_schur_prec(0)
+    op.close()
+    # the element-aligned hierarchy (odd k: no aggregate straddles an element boundary), one
+    # smoothed level: the plain cycle at its best on this degree
+    vx, vy, vz = synth.lattice_vertices(96, 96, 96, perturb=PERTURB, seed=SEED)
+    op = hd.Operator(96, 96, 96, 3, vx, vy, vz, synth.lognormal(96 ** 3, SIGMA, seed=SEED + 1), np.zeros(96 ** 3),
+                     kind=hd.HD_DARCY, ess_mask=0, q=5, cycle=args.cycle, smooth_levels=1, aggregation=1,
+                     fp64_emulation=1, stream=stream)
+    out["aligned_fp64"], _ = solve(op, b, 0, x64)
+    out["aligned_mixed"], _ = solve(op, b, 1, x64)
     op.close()
     lm, pf, pm = out["learned_mixed"], out["plain_fp64"], out["plain_mixed"]
     out["learned_mixed_vs_plain_fp64"] = {"time_ratio": lm["ms"] / pf["ms"], "speedup": pf["ms"] / lm["ms"]}

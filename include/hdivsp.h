@@ -517,10 +517,55 @@ hd_status hd_apply_op_tc_f32(hd_handle h, const float* x, float* y);
  * 1 = the tensor-core operator above (same requirements; HD_ERR_NOT_IMPLEMENTED
  * otherwise, the mode is then unchanged). */
 hd_status hd_set_inner_operator(hd_handle h, int32_t mode);
-/* HD_OK, or HD_ERR_CUDA when a bounded wait inside the tensor-core kernel ran out
- * since the last call (the kernel then skipped the rest of its work); synchronises
- * the handle's stream and clears the record. */
+/* HD_OK, or HD_ERR_CUDA when a bounded wait ran out since the last call: inside the
+ * tensor-core kernel (which then skipped the rest of its work), or inside the element
+ * kernel of a library built with HD_DF_STAGE=1 (its W_e^-1 rows staged by bulk copies;
+ * off by default). Synchronises the handle's stream and clears the record. */
 hd_status hd_tc_status(hd_handle h);
+
+/* -- DG mass inverse of any degree (Sec. 3.1, the setup and solve study) ------------ */
+/* The block-diagonal L2 mass W = diag(W_e), W_e[a][b] = integral over element e of
+ * alpha_e psi_a psi_b / det J (the L2 basis psi_a = h_a1 h_a2 h_a3 of Sec. 2.1, Q_{k-1}:
+ * k^3 DOFs per element, integrals by the q^3 Gauss rule on the trilinear element), and
+ * y = W^-1 x by one of the approaches compared in Sec. 3.1, for k = 2..9 (the paper's
+ * p = k - 1 = 1..8; the block operator's handle covers k <= 5):
+ *   HD_WINV_DENSE   setup: W_e assembled and inverted (its Cholesky factor, the factor's
+ *                   inverse, W_e^-1 = L^-T L^-1); apply: one batched gemv (k^6 doubles/element)
+ *   HD_WINV_CHOL    setup: W_e = L L^T; apply: two triangular solves per element
+ *   HD_WINV_CG      setup: w_p alpha / det J at the points and the Jacobi diagonal of W in
+ *                   the Gauss-Legendre nodal basis; apply: change of basis, the fused
+ *                   per-element Jacobi-preconditioned CG to a relative residual of 1e-14
+ *                   (at most 60 iterations), change of basis back (Sec. 2.5)
+ *   HD_WINV_CG_HIST the same CG in the histopolation basis itself (at most 400 iterations)
+ * All in FP64. Vectors: device, n_l2 = (nx k)(ny k)(nz k) doubles in the lattice order
+ * of the block operator's L2 part (cell I + X (J + Y Z)); x and y not aliased. The
+ * handle owns its device data; calls run on its stream. */
+typedef struct hd_massinv* hd_massinv_handle;
+typedef struct {
+  int32_t nx, ny, nz;    /* elements per direction, >= 1 */
+  int32_t k;             /* k^3 L2 DOFs per element; 2..9 */
+  int32_t q;             /* Gauss-Legendre points per direction; 0 -> k + 2; k..12 */
+  const double* vx;      /* host vertex coordinates, layout as in hd_problem_desc */
+  const double* vy;
+  const double* vz;
+  const double* alpha;   /* host, per element, > 0; NULL: 1 */
+  int32_t method;        /* HD_WINV_DENSE, HD_WINV_CHOL, HD_WINV_CG or HD_WINV_CG_HIST */
+} hd_massinv_desc;
+/* Builds the data of `method` on the current device and synchronises. Errors:
+ * HD_ERR_INVALID_ARG (sizes, null pointers, method, alpha <= 0, det J <= 0 at a point),
+ * HD_ERR_OOM, HD_ERR_CUDA, HD_ERR_NAN (a W_e not positive definite in the factorisation). */
+hd_status hd_massinv_create(const hd_massinv_desc* desc, hd_massinv_handle* out);
+/* stream: a cudaStream_t (NULL = legacy default stream). */
+hd_status hd_massinv_set_stream(hd_massinv_handle h, void* stream);
+/* y = W^-1 x (asynchronous on the handle's stream). */
+hd_status hd_massinv_apply(hd_massinv_handle h, const double* x, double* y);
+/* Device time of the setup in ms (geometric factors, diagonal or assembly and
+ * factorisation), measured with events inside hd_massinv_create. */
+hd_status hd_massinv_setup_ms(hd_massinv_handle h, double* ms);
+/* CG methods: the largest number of iterations any element needed in the last apply
+ * (synchronises); 0 for the direct methods. */
+hd_status hd_massinv_iterations(hd_massinv_handle h, int32_t* its);
+hd_status hd_massinv_destroy(hd_massinv_handle h);
 
 #ifdef __cplusplus
 }

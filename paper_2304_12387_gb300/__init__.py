@@ -62,6 +62,13 @@ class SolveInfo(ctypes.Structure):
                 ("fallback", ctypes.c_int32)]
 
 
+class MassInvDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("k", ctypes.c_int32),
+                ("q", ctypes.c_int32), ("vx", ctypes.POINTER(ctypes.c_double)),
+                ("vy", ctypes.POINTER(ctypes.c_double)), ("vz", ctypes.POINTER(ctypes.c_double)),
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("method", ctypes.c_int32)]
+
+
 class Slab(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("P", ctypes.c_int32), ("ez0", ctypes.c_int32), ("ez1", ctypes.c_int32),
                 ("xf", ctypes.c_int64 * 2), ("yf", ctypes.c_int64 * 2), ("zf", ctypes.c_int64 * 2),
@@ -134,6 +141,12 @@ _SIGS = {
     "hd_slab_plan": [ctypes.c_int32] * 6 + [ctypes.POINTER(Slab)],
     "hd_apply_op_partitioned": [_H, ctypes.c_int32, _VP, _VP],
     "hd_minres_solve_partitioned": [_H, ctypes.c_int32, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_massinv_create": [ctypes.POINTER(MassInvDesc), ctypes.POINTER(ctypes.c_void_p)],
+    "hd_massinv_set_stream": [_H, _VP],
+    "hd_massinv_apply": [_H, _VP, _VP],
+    "hd_massinv_setup_ms": [_H, ctypes.POINTER(ctypes.c_double)],
+    "hd_massinv_iterations": [_H, ctypes.POINTER(ctypes.c_int32)],
+    "hd_massinv_destroy": [_H],
 }
 
 
@@ -457,3 +470,57 @@ class Operator:
     def hd_resume_minres(self, path):
         """Loads a checkpoint; the next hd_minres_solve(..., resume=True) continues it."""
         return lib().hd_resume_minres(self.h, os.fsencode(path))
+
+
+class MassInverse:
+    """The DG mass inverse W^-1 of any degree k = 2..9 (hd_massinv_*): vectors are torch
+    CUDA float64 tensors of n_l2 = (nx k)(ny k)(nz k) entries in lattice order."""
+
+    def __init__(self, nx, ny, nz, k, vx, vy, vz, alpha=None, method=HD_WINV_CG, q=0, stream=None):
+        E = nx * ny * nz
+        self._keep = []
+        ptrs = []
+        for a in (vx, vy, vz):
+            a, pa = _dptr(a)
+            self._keep.append(a)
+            ptrs.append(pa)
+        pal = None
+        if alpha is not None:
+            al, pal = _dptr(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (E,)))
+            self._keep.append(al)
+        d = MassInvDesc(nx, ny, nz, k, q, ptrs[0], ptrs[1], ptrs[2], pal, method)
+        h = ctypes.c_void_p()
+        _check(lib().hd_massinv_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        self.k, self.dims = k, (nx, ny, nz)
+        self.n_l2 = E * k ** 3
+        if stream is not None:
+            self.set_stream(stream)
+
+    def set_stream(self, stream):
+        s = getattr(stream, "cuda_stream", stream)
+        _check(lib().hd_massinv_set_stream(self.h, ctypes.c_void_p(s)))
+
+    def apply(self, x, y):
+        _check(lib().hd_massinv_apply(self.h, _ptr(x), _ptr(y)))
+
+    def setup_ms(self):
+        v = ctypes.c_double()
+        _check(lib().hd_massinv_setup_ms(self.h, ctypes.byref(v)))
+        return v.value
+
+    def iterations(self):
+        v = ctypes.c_int32()
+        _check(lib().hd_massinv_iterations(self.h, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.h:
+            lib().hd_massinv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

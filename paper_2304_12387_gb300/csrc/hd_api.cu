@@ -330,6 +330,34 @@ void destroy_all(hd_op* h) {
 
 }  // namespace
 
+// 1D tables of the L2 space of degree k - 1 for q Gauss-Legendre points (Sec. 2.1), any
+// k >= 1: BH[p k + j] = h_j(g_p) (histopolation basis on the GLL subcells), BG[p k + m] =
+// L_m(g_p) (Lagrange basis on the k Gauss-Legendre nodes), TT[j k + m] = integral of L_m
+// over subcell j, and the Gauss points and weights on [0, 1].
+void hd_l2_tables(int k, int q, double* BH, double* BG, double* TT, double* gx, double* gw) {
+  std::vector<double> xi = gll(k), qx, qw, gk, wk, gs, ws;
+  gauss(q, qx, qw);
+  gauss(k, gk, wk);
+  gauss(k + 2, gs, ws);
+  for (int p = 0; p < q; ++p) {
+    gx[p] = qx[p];
+    gw[p] = qw[p];
+    for (int j = 0; j < k; ++j) {
+      double s = 0.0;
+      for (int i = j + 1; i <= k; ++i) s += dlag(xi, i, qx[p]);
+      BH[p * k + j] = s;
+    }
+    for (int m = 0; m < k; ++m) BG[p * k + m] = lag(gk, m, qx[p]);
+  }
+  for (int j = 0; j < k; ++j)
+    for (int m = 0; m < k; ++m) {
+      const double a = xi[j], b = xi[j + 1];
+      double s = 0.0;
+      for (size_t i = 0; i < gs.size(); ++i) s += ws[i] * lag(gk, m, a + (b - a) * gs[i]);
+      TT[j * k + m] = (b - a) * s;
+    }
+}
+
 hd_status elem_op_handle(hd_op* h, int mode, const double* u, const double* q, double* yu, double* yq) {
   return elem_op(h, mode, u, q, yu, yq);
 }

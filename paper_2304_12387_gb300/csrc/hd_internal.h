@@ -81,6 +81,9 @@ __host__ __device__ __forceinline__ int agg_hi(const Agg1& a, int C, int n) {
   return h < n ? h : n;
 }
 
+// 1D tables of the L2 space for any degree (defined in hd_api.cu)
+void hd_l2_tables(int k, int q, double* BH, double* BG, double* TT, double* gx, double* gw);
+
 // true when every axis of the aggregation is pairs (or not coarsened)
 inline bool agg_pairs(const Agg1* a) { return a[0].m == 1 && a[1].m == 1 && a[2].m == 1; }
 template <typename Lv>

@@ -696,10 +696,15 @@ hd_status tc_apply_f32(hd_op* h, const float* x, float* y) {
 
 // error word of the tensor-core kernel (bounded waits that ran out); cleared on read
 hd_status tc_check(hd_op* h) {
-  if (!h->tc) return HD_OK;
-  int e = 0;
-  HD_CK(h, cudaMemcpyAsync(&e, h->tc->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  // the element kernel's word (its W_e^-1 staging, when built with it) and the tensor-core kernel's
+  int e = 0, ek = 0;
+  if (h->d_kerr) HD_CK(h, cudaMemcpyAsync(&ek, h->d_kerr, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  if (h->tc) HD_CK(h, cudaMemcpyAsync(&e, h->tc->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   HD_CK(h, cudaStreamSynchronize(h->stream));
+  if (ek) {
+    HD_CK(h, cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->stream));
+    return hd_fail(h, HD_ERR_CUDA, "element kernel: a bounded wait for staged W^-1 rows ran out");
+  }
   if (e) {
     HD_CK(h, cudaMemsetAsync(h->tc->err, 0, sizeof(int), h->stream));
     return hd_fail(h, HD_ERR_CUDA, "tensor-core operator: a bounded wait ran out (error word " + std::to_string(e) + ")");

@@ -22,6 +22,7 @@ STRUCTS = {
     "hd_train_opts": hd.TrainOpts,
     "hd_train_info": hd.TrainInfo,
     "hd_slab": hd.Slab,
+    "hd_massinv_desc": hd.MassInvDesc,
 }
 
 
