@@ -907,6 +907,23 @@ def learned_study(args, stream):
     op.hd_learned_init()
     op.hd_learned_set_weights(*W)
     b = torch.from_numpy(synth.uniform(op.n, seed=SEED + 9)).cuda()
+    # the network alone (FP64 L2 vector in and out), per engine of its 32 -> 32 convolutions
+    r = b[op.n_rt:].contiguous()
+    zn = torch.empty_like(r)
+    out["net_apply_ms"] = {}
+    for name, engine in (("mma_sync", 1), ("tcgen05", 0)):
+        op.hd_learned_conv_engine(engine)
+        for _ in range(3):
+            op.hd_learned_apply(r, zn)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(10):
+            op.hd_learned_apply(r, zn)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out["net_apply_ms"][name] = round(e0.elapsed_time(e1) / 10, 3)
+    out["net_apply_ms"]["cells"] = int(op.n_l2)
     out["plain_fp64"], x64 = solve(op, b, 0)
     out["plain_mixed"], _ = solve(op, b, 1, x64)
     op.hd_set_schur_prec(1)
@@ -927,6 +944,43 @@ def learned_study(args, stream):
     out["learned_mixed_vs_plain_mixed"] = {"iteration_ratio": lm["iterations"] / max(1, pm["iterations"]),
                                            "time_ratio": lm["ms"] / pm["ms"]}
     return out
+
+
+def run_net_apply(args):
+    """The learned network alone on the Darcy recipe of the learned study (k = 3,
+    +-15% h, eps = exp(2Z)) at n^3 elements, untrained initial weights: milliseconds per
+    application of P_L (FP64 L2 vector in and out) with the 32 -> 32 convolutions on
+    the tcgen05 tensor cores and with mma.sync, and the rate of those two convolutions
+    (2 x 2 x 32 x 32 x 27 flops per cell per application)."""
+    import torch
+    import paper_2304_12387_gb300 as hd
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    stream = torch.cuda.current_stream()
+    n = args.net_apply
+    vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=PERTURB, seed=SEED)
+    op = hd.Operator(n, n, n, 3, vx, vy, vz, synth.lognormal(n ** 3, SIGMA, seed=SEED + 1), np.zeros(n ** 3),
+                     kind=hd.HD_DARCY, ess_mask=0, q=5, cycle=2, smooth_levels=2, fp64_emulation=1, stream=stream)
+    op.hd_learned_init()
+    r = torch.from_numpy(synth.uniform(op.n_l2, seed=SEED + 3)).cuda()
+    z = torch.empty_like(r)
+    out = {"study": "learned network apply", "elements": n ** 3, "cells": op.n_l2}
+    for name, engine in (("mma_sync", 1), ("tcgen05", 0)):
+        op.hd_learned_conv_engine(engine)
+        for _ in range(3):
+            op.hd_learned_apply(r, z)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            op.hd_learned_apply(r, z)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        out[name] = {"ms_per_apply": round(ms, 4)}
+    out["conv_flops_per_apply"] = 2 * 2 * 32 * 32 * 27 * op.n_l2
+    out["tc_status"] = int(op.hd_tc_status())
+    op.close()
+    print(json.dumps(out), flush=True)
 
 
 def run_learned(args):
@@ -969,6 +1023,8 @@ def main():
     ap.add_argument("--no-affine", action="store_true", help="skip the apply on the unperturbed (affine) mesh")
     ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--net-apply", type=int, default=0,
+                    help="time the learned network alone at this many elements per direction (k = 3)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", 1))
     rank = int(os.environ.get("RANK", 0))
@@ -988,6 +1044,8 @@ def main():
         run_learned(args)
     elif args.iterations:
         run_iterations(args)
+    elif args.net_apply:
+        run_net_apply(args)
     elif args.winv_study:
         run_winv_study(args)
     else:

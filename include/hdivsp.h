@@ -489,6 +489,14 @@ hd_status hd_enable_learned(hd_handle h, int32_t on);
  * Training runs as one call, so no optimiser state is kept. */
 hd_status hd_learned_save(hd_handle h, const char* path);
 hd_status hd_learned_load(hd_handle h, const char* path);
+/* The engine of the network's 32 -> 32 convolutions (forward and adjoint, in every apply
+ * and in training): 0 (default) the 5th-generation tensor cores (tcgen05.mma kind::f16,
+ * FP16 operands in shared memory, FP32 accumulators in tensor memory; 128 cells of an
+ * x-line per tile, persistent, one CTA per SM), 1 the warp-level mma.sync m16n8k16 path.
+ * Both accumulate in FP32 and round to FP16, so they agree to FP16 rounding. A bounded
+ * wait of the tensor-core path that runs out is reported by hd_tc_status. Needs
+ * hd_learned_init first; other values: HD_ERR_INVALID_ARG. */
+hd_status hd_learned_conv_engine(hd_handle h, int32_t engine);
 
 /* -- FP32 variants (inner operators of the mixed-precision solve) ---------- */
 hd_status hd_apply_op_f32(hd_handle h, const float* x, float* y);
@@ -518,9 +526,10 @@ hd_status hd_apply_op_tc_f32(hd_handle h, const float* x, float* y);
  * otherwise, the mode is then unchanged). */
 hd_status hd_set_inner_operator(hd_handle h, int32_t mode);
 /* HD_OK, or HD_ERR_CUDA when a bounded wait ran out since the last call: inside the
- * tensor-core kernel (which then skipped the rest of its work), or inside the element
- * kernel of a library built with HD_DF_STAGE=1 (its W_e^-1 rows staged by bulk copies;
- * off by default). Synchronises the handle's stream and clears the record. */
+ * tensor-core kernel (which then skipped the rest of its work), inside the tensor-core
+ * convolution of the learned network, or inside the element kernel of a library built
+ * with HD_DF_STAGE=1 (its W_e^-1 rows staged by bulk copies; off by default).
+ * Synchronises the handle's stream and clears the record. */
 hd_status hd_tc_status(hd_handle h);
 
 /* -- DG mass inverse of any degree (Sec. 3.1, the setup and solve study) ------------ */

@@ -141,6 +141,7 @@ _SIGS = {
     "hd_slab_plan": [ctypes.c_int32] * 6 + [ctypes.POINTER(Slab)],
     "hd_apply_op_partitioned": [_H, ctypes.c_int32, _VP, _VP],
     "hd_minres_solve_partitioned": [_H, ctypes.c_int32, _VP, _VP, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo)],
+    "hd_learned_conv_engine": [_H, ctypes.c_int32],
     "hd_massinv_create": [ctypes.POINTER(MassInvDesc), ctypes.POINTER(ctypes.c_void_p)],
     "hd_massinv_set_stream": [_H, _VP],
     "hd_massinv_apply": [_H, _VP, _VP],
@@ -453,6 +454,10 @@ class Operator:
 
     def hd_enable_learned(self, on):
         _check(lib().hd_enable_learned(self.h, int(bool(on))), self.h)
+
+    def hd_learned_conv_engine(self, engine):
+        """0: tcgen05 tensor cores (default); 1: mma.sync."""
+        _check(lib().hd_learned_conv_engine(self.h, int(engine)), self.h)
 
     def hd_learned_save(self, path):
         """Returns the status (HD_OK or HD_ERR_INVALID_ARG)."""

@@ -12,8 +12,9 @@
 //
 // Activations are FP16 with 32 channels per cell ([cell][32], 64 B), weights FP16
 // for compute with an FP32 master copy, accumulation FP32. The 32 -> 32
-// convolutions (forward and adjoint) run on the tensor cores with mma.sync
-// m16n8k16; the 1 -> 32 / 32 -> 1 convolutions and the weight gradients on the
+// convolutions (forward and adjoint) run on the tensor cores: tcgen05.mma with
+// accumulators in tensor memory (k_conv2_tc, the default), or mma.sync m16n8k16
+// (k_conv2); the 1 -> 32 / 32 -> 1 convolutions and the weight gradients on the
 // CUDA cores. Input fields are normalised to unit RMS before the network and the
 // output rescaled (exactly linear), which keeps FP16 in range.
 #include <cuda_fp16.h>
@@ -24,6 +25,7 @@
 #include <vector>
 
 #include "hd_internal.h"
+#include "tc_ptx.cuh"
 
 namespace {
 
@@ -293,6 +295,177 @@ __global__ void __launch_bounds__(256) k_conv2(int X, int Y, int Z, const __half
   }
 }
 
+// ---- 32 -> 32 convolution on the 5th-generation tensor cores (tcgen05) ----------------
+// Implicit GEMM: a tile is 128 consecutive cells of one x-line (M = 128), N = 32 output
+// channels, K = 27 taps x 32 input channels, per tap two tcgen05.mma.kind::f16 (K = 16)
+// into an FP32 accumulator of 32 TMEM columns. The A operand of tap (dx, dy, dz) is the
+// halo line (y + dy - 1, z + dz - 1) shifted by dx, read in place: the halo is stored
+// channel-chunk-major (16 bytes = 8 channels of one cell, consecutive cells contiguous),
+// so 8 consecutive cells form a core matrix (128 bytes) at any shift, row groups sit 128
+// bytes apart and the two chunks of a K step one chunk slab apart. Weights W[t][o][i] are
+// staged once per CTA as core matrices (8 o x 8 i).
+// Work unit: one x-tile and one z, for a run of CT_YRUN consecutive y. The CTA walks y
+// through a ring of 5 halo slabs (a slab: the lines z - 1, z, z + 1 at one y), so each
+// tile loads one new slab (3 lines) instead of 9 lines. Slabs are loaded by 16-byte
+// cp.async copies (zero fill outside the lattice) two tiles ahead, one commit group per
+// tile, so a slab has a whole tile's MMAs and epilogue to arrive;
+// accumulators are double-buffered, so a tile's epilogue (8 warps: TMEM lane = cell,
+// 16 channels per warp half) overlaps the next tile's MMAs. Every wait is bounded
+// (error word bit 4).
+constexpr int CT_M = 128;                          // cells per tile
+constexpr int CT_H = CT_M + 2;                     // halo cells per line
+constexpr int CT_RING = 5;                         // slabs in the ring
+constexpr int CT_SLOTS = 3 * CT_RING;              // halo lines
+constexpr int CT_CHUNK = CT_SLOTS * CT_H * 16;     // bytes of one 8-channel slab of the ring
+constexpr int CT_HALO = 4 * CT_CHUNK;              // 124,800 bytes
+constexpr int CT_W = NT * 4 * 4 * 128;             // 55,296 bytes of weights
+constexpr int CT_SMEM = CT_HALO + CT_W + 64;
+constexpr int CT_THREADS = 256;
+constexpr int CT_YRUN = 48;                        // y per work unit
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// all but the most recent committed group complete
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ int ring_slot(int y) { return ((y % CT_RING) + CT_RING) % CT_RING; }
+
+__global__ void __launch_bounds__(CT_THREADS, 1)
+k_conv2_tc(int X, int Y, int Z, const __half* __restrict__ Wg, const __half* __restrict__ in,
+           __half* __restrict__ out, int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  unsigned char* wsm = smem_raw + CT_HALO;                  // [27 taps][4 o-groups][4 i-chunks][8 o][8 i]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(wsm + CT_W);  // [2]
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < NT * NC * 4; i += CT_THREADS) {  // 16-byte pieces: (t, o, i-chunk)
+    const int t = i / (NC * 4), o = (i / 4) % NC, c = i % 4;
+    const uint4 v = *reinterpret_cast<const uint4*>(Wg + ((size_t)t * NC + o) * NC + c * 8);
+    *reinterpret_cast<uint4*>(wsm + ((t * 4 + (o >> 3)) * 4 + c) * 128 + (o & 7) * 16) = v;
+  }
+  if (tid == 0) {
+    tc::mbar_init(tc::smem_u32(&bar[0]), 1);
+    tc::mbar_init(tc::smem_u32(&bar[1]), 1);
+    tc::fence_mbar_init();
+  }
+  if (warp == 0) {
+    tc::tmem_alloc(tc::smem_u32(tslot), 64);  // two accumulators of 32 columns
+    tc::tmem_relinquish();
+  }
+  tc::fence_proxy_async_smem();  // the staged weights, for the tensor core
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tslot, hbase = tc::smem_u32(smem_raw), wbase = tc::smem_u32(wsm);
+  const int ntx = (X + CT_M - 1) / CT_M, nyr = (Y + CT_YRUN - 1) / CT_YRUN;
+  const int64_t nunits = (int64_t)ntx * Z * nyr;
+  constexpr uint32_t IDESC = tc::idesc_f16_f32(CT_M, NC);
+  // slab y' (lines z - 1, z, z + 1) of the x-tile at x0 into its ring slot
+  auto load_slab = [&](int x0, int yp, int z) {
+    const int sl = ring_slot(yp);
+    for (int i = tid; i < 3 * CT_H * 4; i += CT_THREADS) {
+      const int c = i & 3, h = (i >> 2) % CT_H, zl = (i >> 2) / CT_H;
+      const int gx = x0 - 1 + h, gz = z - 1 + zl;
+      const bool ok = gx >= 0 && gx < X && yp >= 0 && yp < Y && gz >= 0 && gz < Z;
+      const __half* src = ok ? in + (gx + (int64_t)X * (yp + (int64_t)Y * gz)) * NC + c * 8 : in;
+      cp_async16(hbase + c * CT_CHUNK + ((sl * 3 + zl) * CT_H + h) * 16, src, ok);
+    }
+  };
+  // one thread: 27 taps x 2 K steps into accumulator b. A descriptor's address field is
+  // the shared-memory address in 16-byte units, so every operand's descriptor is a base
+  // descriptor plus a constant offset (the ring slots of the three y-slabs of the tile
+  // are the only run-time part).
+  const uint64_t adesc0 = tc::smem_desc(hbase, CT_CHUNK, 128), bdesc0 = tc::smem_desc(wbase, 128, 512);
+  auto issue = [&](int y, int b) {
+    const int lofs[3] = {ring_slot(y - 1) * 3 * CT_H, ring_slot(y) * 3 * CT_H, ring_slot(y + 1) * 3 * CT_H};
+    const uint32_t d = tmem + 32 * b;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const int dx = t % 3, dy = (t / 3) % 3, dz = t / 9;  // the order of W[t]
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks) {
+        const uint64_t ad = adesc0 + (uint64_t)(2 * ks * (CT_CHUNK / 16) + lofs[dy] + dz * CT_H + dx);
+        const uint64_t bd = bdesc0 + (uint64_t)((t * 16 + 2 * ks) * 8);
+        tc::mma_f16(d, ad, bd, IDESC, t > 0 || ks > 0);
+      }
+    }
+    tc::mma_commit(tc::smem_u32(&bar[b]));
+  };
+  // epilogue: warp w reads TMEM lanes 32 (w % 4) .. (its cells) and channels 16 (w / 4) ..
+  auto epilogue = [&](int x0, int y, int z, int b) {
+    const int lb = 32 * (warp & 3), hf = warp >> 2, x = x0 + lb + (tid & 31);
+    float v[16];
+    tc::tmem_ld16(tmem + ((uint32_t)lb << 16) + 32 * b + 16 * hf, v);
+    tc::tmem_wait_ld();
+    if (x < X) {
+      __half2 hv[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) hv[j] = __floats2half2_rn(v[2 * j], v[2 * j + 1]);
+      uint4* o = reinterpret_cast<uint4*>(out + (x + (int64_t)X * (y + (int64_t)Y * z)) * NC + 16 * hf);
+      o[0] = reinterpret_cast<const uint4*>(hv)[0];
+      o[1] = reinterpret_cast<const uint4*>(hv)[1];
+    }
+  };
+  int64_t issued = 0;                        // tiles issued by this CTA
+  bool pend = false;                         // a tile whose MMAs may still run
+  int px0 = 0, py = 0, pz = 0, pb = 0;
+  int64_t pi = 0;
+  auto wait_pending = [&]() {
+    if (!tc::mbar_wait(tc::smem_u32(&bar[pb]), (uint32_t)((pi >> 1) & 1))) atomicOr(err, 16);
+    tc::fence_after_sync();
+  };
+  for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int tx = (int)(u % ntx);
+    const int64_t r = u / ntx;
+    const int z = (int)(r % Z), yr = (int)(r / Z);
+    const int x0 = tx * CT_M, y0 = yr * CT_YRUN, y1 = min(Y, y0 + CT_YRUN);
+    if (pend) {  // the ring is rewritten below: the last tile's MMAs must be done
+      wait_pending();
+      epilogue(px0, py, pz, pb);
+      pend = false;
+    }
+    cp_async_wait_all();  // no copy of the previous unit still writes the ring
+    tc::fence_before_sync();
+    __syncthreads();
+    load_slab(x0, y0 - 1, z);
+    load_slab(x0, y0, z);
+    load_slab(x0, y0 + 1, z);
+    cp_async_commit();
+    if (y0 + 1 < y1) load_slab(x0, y0 + 2, z);  // for tile y0 + 1
+    cp_async_commit();
+    cp_async_wait_prev();
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    for (int y = y0; y < y1; ++y) {
+      const int b = (int)(issued & 1);
+      if (tid == 0) issue(y, b);
+      if (pend) wait_pending();                   // tile y - 1 read the slot of slab y + 3
+      if (y + 2 < y1) load_slab(x0, y + 3, z);    // for tile y + 2
+      cp_async_commit();                          // (empty at the end of the run)
+      if (pend) epilogue(px0, py, pz, pb);
+      pend = true;
+      px0 = x0; py = y; pz = z; pb = b; pi = issued;
+      ++issued;
+      cp_async_wait_prev();                       // slab y + 2, for tile y + 1, has arrived
+      tc::fence_proxy_async_smem();
+      tc::fence_before_sync();
+      __syncthreads();
+      tc::fence_after_sync();
+    }
+  }
+  if (pend) {
+    wait_pending();
+    epilogue(px0, py, pz, pb);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
 // ---- weight gradients (CUDA cores, per-block partials, fixed-order reduce) ----
 // G2[co][ci][t] += sum_x P[x][co] Q[x + off_t][ci] for two (P, Q) pairs.
 // Tile 4 x 4 x 4 cells, halo 6 x 6 x 6; thread (co = tid / 8, ci = 4 (tid % 8) .. +3).
@@ -467,6 +640,8 @@ struct LearnedNet {
   double *pr = nullptr, *pe = nullptr, *pq = nullptr;  // training pairs
   int npairs = 0;
   int conv_blocks = 0, dw2_blocks = 0, dw1_blocks = 0;
+  int conv_engine = 0;  // 32 -> 32 convolutions: 0 = tcgen05 (k_conv2_tc), 1 = mma.sync (k_conv2)
+  int sms = 1;
 };
 
 namespace {
@@ -492,6 +667,20 @@ hd_status net_dot(hd_op* h, const double* a, const double* b, int64_t n, double*
 
 hd_status conv2(hd_op* h, const __half* W, const __half* in, __half* out) {
   LearnedNet* N = h->net;
+  if (N->conv_engine == 0) {
+    static bool attr_tc[HD_MAX_DEVICES] = {};
+    bool* done = device_flag(attr_tc);
+    if (!done || !*done) {
+      cudaError_t e = cudaFuncSetAttribute(k_conv2_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, CT_SMEM);
+      if (e != cudaSuccess) return hd_cuda_check(h, e, "cudaFuncSetAttribute(k_conv2_tc)");
+      if (done) *done = true;
+    }
+    prof_mark(h, true);
+    k_conv2_tc<<<N->sms, CT_THREADS, CT_SMEM, h->stream>>>(N->X, N->Y, N->Z, W, in, out, h->d_kerr);
+    prof_mark(h, false);
+    HD_LAUNCH_CK(h, "k_conv2_tc");
+    return HD_OK;
+  }
   const size_t smem = (size_t)(NT * NC * NC + HCELLS * NC) * sizeof(__half);
   static bool attr[HD_MAX_DEVICES] = {};
   bool* done = device_flag(attr);
@@ -651,6 +840,7 @@ hd_status hd_learned_init(hd_handle h, int32_t nc, uint64_t seed, double delta) 
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   N->conv_blocks = 2 * (sms > 0 ? sms : 1);
+  N->sms = sms > 0 ? sms : 1;
   N->dw2_blocks = 2 * (sms > 0 ? sms : 1);
   N->dw1_blocks = sms > 0 ? sms : 1;
   hd_status st = HD_OK;
@@ -909,3 +1099,11 @@ hd_status hd_learned_load(hd_handle h, const char* path) {
 }
 
 }  // extern "C"
+
+extern "C" hd_status hd_learned_conv_engine(hd_handle h, int32_t engine) {
+  if (!h) return HD_ERR_INVALID_ARG;
+  if (!h->net) return hd_fail(h, HD_ERR_INVALID_ARG, "hd_learned_init has not been called");
+  if (engine != 0 && engine != 1) return hd_fail(h, HD_ERR_INVALID_ARG, "convolution engine: 0 or 1");
+  h->net->conv_engine = engine;
+  return HD_OK;
+}

@@ -703,7 +703,8 @@ hd_status tc_check(hd_op* h) {
   HD_CK(h, cudaStreamSynchronize(h->stream));
   if (ek) {
     HD_CK(h, cudaMemsetAsync(h->d_kerr, 0, sizeof(int), h->stream));
-    return hd_fail(h, HD_ERR_CUDA, "element kernel: a bounded wait for staged W^-1 rows ran out");
+    return hd_fail(h, HD_ERR_CUDA, std::string("a bounded wait ran out: ") +
+                                       ((ek & 16) ? "tensor-core convolution" : "staged W^-1 rows"));
   }
   if (e) {
     HD_CK(h, cudaMemsetAsync(h->tc->err, 0, sizeof(int), h->stream));
