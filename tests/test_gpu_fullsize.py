@@ -137,3 +137,46 @@ def test_fullsize_m64_gmres():
         rel = float(torch.linalg.vector_norm(x - xm) / torch.linalg.vector_norm(xm))
         assert rel <= 1e-6, rel
     op.close()
+
+
+@pytest.mark.parametrize("name,emul", [("m64", 0), ("m64", 1), ("c2", 0)])
+def test_fullsize_every_element_layer(name, emul):
+    """A strided sample through every element layer of the full-size workload: in each
+    layer the z-face at its bottom and at its top, an x-face and a y-face inside it, and a
+    cell of its first and of its last cell layer (random positions in x and y), against
+    the oracle's rows at 1e-12 of the sampled maximum (FP64 and the double-float kernel)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2304_12387_gb300 as hd
+    from oracle.sampled import SampledOperator
+    d = fullsize(name)
+    op = hd.Operator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                     kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"], affine=d["affine"], fp64_emulation=emul,
+                     stream=torch.cuda.current_stream())
+    rng = np.random.Generator(np.random.PCG64(79))
+    x = rng.uniform(-1, 1, op.n)
+    xd = torch.from_numpy(x).cuda()
+    y = torch.empty_like(xd)
+    op.hd_apply_op(xd, y)
+    torch.cuda.synchronize()
+    so = SampledOperator(d["nx"], d["ny"], d["nz"], d["k"], d["vx"], d["vy"], d["vz"], d["coef0"], d["coef1"],
+                         kind=d["kind"], ess_mask=d["ess_mask"], q=d["q"])
+    k = d["k"]
+    X, Y, Z = d["nx"] * k, d["ny"] * k, d["nz"] * k
+    nxf, nyf = (X + 1) * Y * Z, X * (Y + 1) * Z
+    rt, l2 = [], []
+    for ez in range(d["nz"]):
+        I, J = int(rng.integers(0, X)), int(rng.integers(0, Y))
+        for K in (ez * k, ez * k + k):                       # z-faces at the layer's bottom and top
+            rt.append(nxf + nyf + I + X * (J + Y * K))
+        K = ez * k + int(rng.integers(0, k))
+        rt.append(int(rng.integers(0, X + 1)) + (X + 1) * (J + Y * K))     # an x-face
+        rt.append(nxf + I + X * (int(rng.integers(0, Y + 1)) + (Y + 1) * K))  # a y-face
+        for K in (ez * k, ez * k + k - 1):                   # cells of the first and last cell layer
+            l2.append(I + X * (J + Y * K))
+    rt, l2 = np.array(rt), np.array(l2)
+    ref = np.concatenate([so.rt_rows(x, rt), so.l2_rows(x, l2)])
+    got = y[torch.from_numpy(np.concatenate([rt, op.n_rt + l2])).cuda()].cpu().numpy()
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= 1e-12 * scale, (name, emul, np.abs(got - ref).max() / scale)
+    op.close()
