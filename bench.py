@@ -829,9 +829,11 @@ def run_winv_study(args):
         vx, vy, vz, alpha, _ = workload(nx)
         row = {"k": k, "p": k - 1, "elements": nx ** 3, "l2_dofs": (nx * k) ** 3}
         ref = None
-        for name, mode in (("inverse", hd.HD_WINV_DENSE), ("cholesky", hd.HD_WINV_CHOL), ("cg_gl", hd.HD_WINV_CG),
-                           ("cg_hist", hd.HD_WINV_CG_HIST)):
-            mi = hd.MassInverse(nx, nx, nx, k, vx, vy, vz, alpha=alpha, method=mode, stream=stream)
+        for name, mode, emul in (("inverse", hd.HD_WINV_DENSE, 0), ("cholesky", hd.HD_WINV_CHOL, 0),
+                                 ("cg_gl", hd.HD_WINV_CG, 0), ("cg_hist", hd.HD_WINV_CG_HIST, 0),
+                                 ("cg_gl_df", hd.HD_WINV_CG, 1)):
+            mi = hd.MassInverse(nx, nx, nx, k, vx, vy, vz, alpha=alpha, method=mode, fp64_emulation=emul,
+                                stream=stream)
             q = torch.from_numpy(synth.uniform(mi.n_l2, seed=SEED + 9)).cuda()
             y = torch.empty_like(q)
             for _ in range(3):
@@ -855,8 +857,9 @@ def run_winv_study(args):
             del q, y
         rows.append(row)
         print(json.dumps(row), flush=True)
-    print(json.dumps({"study": "DG mass inverse of any degree (hd_massinv_*): setup and 100 applications, FP64, "
-                               "perturbed mesh, q = k + 2, alpha = 1", "rows": rows}), flush=True)
+    print(json.dumps({"study": "DG mass inverse of any degree (hd_massinv_*): setup and 100 applications, FP64 "
+                               "(cg_gl_df: the CG stages in double-float), perturbed mesh, q = k + 2, alpha = 1",
+                      "rows": rows}), flush=True)
 
 
 def learned_study(args, stream):

@@ -546,7 +546,7 @@ hd_status hd_tc_status(hd_handle h);
  *                   per-element Jacobi-preconditioned CG to a relative residual of 1e-14
  *                   (at most 60 iterations), change of basis back (Sec. 2.5)
  *   HD_WINV_CG_HIST the same CG in the histopolation basis itself (at most 400 iterations)
- * All in FP64. Vectors: device, n_l2 = (nx k)(ny k)(nz k) doubles in the lattice order
+ * All in FP64, or the CG stages in double-float (fp64_emulation). Vectors: device, n_l2 = (nx k)(ny k)(nz k) doubles in the lattice order
  * of the block operator's L2 part (cell I + X (J + Y Z)); x and y not aliased. The
  * handle owns its device data; calls run on its stream. */
 typedef struct hd_massinv* hd_massinv_handle;
@@ -559,6 +559,12 @@ typedef struct {
   const double* vz;
   const double* alpha;   /* host, per element, > 0; NULL: 1 */
   int32_t method;        /* HD_WINV_DENSE, HD_WINV_CHOL, HD_WINV_CG or HD_WINV_CG_HIST */
+  int32_t fp64_emulation;/* CG methods: 0 stages in FP64; 1 the sum-factorised stages and CG vectors
+                            in double-float (FP32 pairs on the FP32 pipe, about 48 significant
+                            bits), inner products, step lengths and stopping test in FP64; the
+                            point weights w_p alpha / det J must lie in FP32's normal range.
+                            Direct methods: 1 is HD_ERR_NOT_IMPLEMENTED. Other values:
+                            HD_ERR_INVALID_ARG */
 } hd_massinv_desc;
 /* Builds the data of `method` on the current device and synchronises. Errors:
  * HD_ERR_INVALID_ARG (sizes, null pointers, method, alpha <= 0, det J <= 0 at a point),

@@ -66,7 +66,8 @@ class MassInvDesc(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("k", ctypes.c_int32),
                 ("q", ctypes.c_int32), ("vx", ctypes.POINTER(ctypes.c_double)),
                 ("vy", ctypes.POINTER(ctypes.c_double)), ("vz", ctypes.POINTER(ctypes.c_double)),
-                ("alpha", ctypes.POINTER(ctypes.c_double)), ("method", ctypes.c_int32)]
+                ("alpha", ctypes.POINTER(ctypes.c_double)), ("method", ctypes.c_int32),
+                ("fp64_emulation", ctypes.c_int32)]
 
 
 class Slab(ctypes.Structure):
@@ -481,7 +482,8 @@ class MassInverse:
     """The DG mass inverse W^-1 of any degree k = 2..9 (hd_massinv_*): vectors are torch
     CUDA float64 tensors of n_l2 = (nx k)(ny k)(nz k) entries in lattice order."""
 
-    def __init__(self, nx, ny, nz, k, vx, vy, vz, alpha=None, method=HD_WINV_CG, q=0, stream=None):
+    def __init__(self, nx, ny, nz, k, vx, vy, vz, alpha=None, method=HD_WINV_CG, q=0, fp64_emulation=0,
+                 stream=None):
         E = nx * ny * nz
         self._keep = []
         ptrs = []
@@ -493,7 +495,7 @@ class MassInverse:
         if alpha is not None:
             al, pal = _dptr(np.broadcast_to(np.asarray(alpha, dtype=np.float64), (E,)))
             self._keep.append(al)
-        d = MassInvDesc(nx, ny, nz, k, q, ptrs[0], ptrs[1], ptrs[2], pal, method)
+        d = MassInvDesc(nx, ny, nz, k, q, ptrs[0], ptrs[1], ptrs[2], pal, method, int(fp64_emulation))
         h = ctypes.c_void_p()
         _check(lib().hd_massinv_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

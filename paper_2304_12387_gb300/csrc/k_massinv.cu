@@ -12,6 +12,7 @@
 #include <cstring>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "hd_internal.h"
 
 #define MI_MAXK 9
@@ -25,15 +26,28 @@ struct MiTab {
   double gx[MI_MAXQ], gw[MI_MAXQ];
 };
 
+// the CG's tables in its arithmetic (double or double-float)
+template <typename T>
+struct MiCgTab {
+  int k, q;
+  T B[MI_MAXQ * MI_MAXK];
+  T TT[MI_MAXK * MI_MAXK];
+};
+
 struct hd_massinv {
   int nx = 0, ny = 0, nz = 0, k = 0, q = 0, method = 0;
   int64_t E = 0, n = 0;          // elements, DOFs per element
   cudaStream_t stream = nullptr;
   MiTab tab{};
+  MiCgTab<double> cgd{};
+  MiCgTab<dfloat> cgx{};
   double* d_wdet = nullptr;      // [E][q^3] w_p alpha / det J
   double* d_diag = nullptr;      // [E][n] Jacobi diagonal (CG methods)
   double* d_mat = nullptr;       // [E][n][n] W_e^-1 (dense) or its Cholesky factor L (lower)
   double* d_aux = nullptr;       // setup scratch: [E][n][n] L^-1 (dense)
+  int emul = 0;                  // CG stages in double-float (fp64_emulation = 1)
+  dfloat* x_wdet = nullptr;      // [E][q^3] double-float copy of wdet
+  dfloat* x_dinv = nullptr;      // [E][n] 1 / Jacobi diagonal, double-float
   int* d_flag = nullptr;         // [0]: det J <= 0; [1]: most CG iterations; [2]: a pivot <= 0
   double setup_ms = 0.0;
 };
@@ -118,28 +132,41 @@ __device__ __forceinline__ int64_t mi_cell(int64_t e, int a, int k, int nx, int 
 }
 
 // ---- fused per-element CG (Sec. 2.5, 3.1) ----------------------------------------------
+// The stages run in T: FP64, or double-float (pairs of FP32 numbers on the FP32 pipe, about
+// 48 significant bits; the FP64 pipe of this GPU has 1/64 of the FP32 rate). The CG's
+// inner products, step lengths and stopping test are FP64 in both.
+__device__ __forceinline__ double mi_d(double v) { return v; }
+__device__ __forceinline__ double mi_d(dfloat v) { return df_to_double(v); }
+template <typename T>
+__device__ __forceinline__ T mi_t(double v);
+template <>
+__device__ __forceinline__ double mi_t<double>(double v) { return v; }
+template <>
+__device__ __forceinline__ dfloat mi_t<dfloat>(double v) { return df_from_double(v); }
+
 // out = (M x M x M) in with M(j, m) = TT[j k + m] (tr = true: the transpose TT^T acting on
 // histopolation data) or TT[m k + j] (tr = false: TT acting on GL nodal data); u, v scratch
-__device__ void mi_tt3(int k, const double* TT, bool tr, const double* in, double* u, double* v, double* out) {
+template <typename T>
+__device__ void mi_tt3(int k, const T* TT, bool tr, const T* in, T* u, T* v, T* out) {
   const int n = k * k * k;
   auto M = [&](int j, int m) { return tr ? TT[j * k + m] : TT[m * k + j]; };
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int m1 = i % k, r = i / k;
-    double s = 0.0;
+    T s = T(0);
     for (int j = 0; j < k; ++j) s = fma(M(j, m1), in[j + k * r], s);
     u[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int m1 = i % k, m2 = (i / k) % k, j3 = i / (k * k);
-    double s = 0.0;
+    T s = T(0);
     for (int j = 0; j < k; ++j) s = fma(M(j, m2), u[m1 + k * (j + k * j3)], s);
     v[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const int r = i % (k * k), m3 = i / (k * k);
-    double s = 0.0;
+    T s = T(0);
     for (int j = 0; j < k; ++j) s = fma(M(j, m3), v[r + k * k * j], s);
     out[i] = s;
   }
@@ -148,47 +175,48 @@ __device__ void mi_tt3(int k, const double* TT, bool tr, const double* in, doubl
 
 // w = W_e p by sum factorisation: B (q x k) to the points along x, y, z, the point
 // weights, and back (T1: q k k, T2: q q k, T3: q^3 values)
-__device__ void mi_apply_w(int k, int q, const double* B, const double* __restrict__ wd, const double* P, double* W,
-                           double* T1, double* T2, double* T3) {
+template <typename T>
+__device__ void mi_apply_w(int k, int q, const T* B, const T* __restrict__ wd, const T* P, T* W, T* T1, T* T2,
+                           T* T3) {
   const int kk = k * k, qq = q * q;
   for (int i = threadIdx.x; i < q * kk; i += blockDim.x) {  // T1[p1 + q r], r = a2 + k a3
     const int p1 = i % q, r = i / q;
-    double s = 0.0;
+    T s = T(0);
     for (int a = 0; a < k; ++a) s = fma(B[p1 * k + a], P[a + k * r], s);
     T1[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < qq * k; i += blockDim.x) {  // T2[p1 + q (p2 + q a3)]
     const int p1 = i % q, p2 = (i / q) % q, a3 = i / qq;
-    double s = 0.0;
+    T s = T(0);
     for (int a = 0; a < k; ++a) s = fma(B[p2 * k + a], T1[p1 + q * (a + k * a3)], s);
     T2[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < qq * q; i += blockDim.x) {  // T3[p], scaled by the point weight
     const int r = i % qq, p3 = i / qq;
-    double s = 0.0;
+    T s = T(0);
     for (int a = 0; a < k; ++a) s = fma(B[p3 * k + a], T2[r + qq * a], s);
     T3[i] = s * wd[i];
   }
   __syncthreads();
   for (int i = threadIdx.x; i < qq * k; i += blockDim.x) {  // back along z
     const int r = i % qq, a3 = i / qq;
-    double s = 0.0;
+    T s = T(0);
     for (int p = 0; p < q; ++p) s = fma(B[p * k + a3], T3[r + qq * p], s);
     T2[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < q * kk; i += blockDim.x) {  // back along y
     const int p1 = i % q, a2 = (i / q) % k, a3 = i / (q * k);
-    double s = 0.0;
+    T s = T(0);
     for (int p = 0; p < q; ++p) s = fma(B[p * k + a2], T2[p1 + q * (p + q * a3)], s);
     T1[i] = s;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kk * k; i += blockDim.x) {  // back along x
     const int a1 = i % k, r = i / k;
-    double s = 0.0;
+    T s = T(0);
     for (int p = 0; p < q; ++p) s = fma(B[p * k + a1], T1[p + q * r], s);
     W[i] = s;
   }
@@ -197,41 +225,46 @@ __device__ void mi_apply_w(int k, int q, const double* B, const double* __restri
 
 // one CTA per element: y_e = W_e^-1 x_e by Jacobi-preconditioned CG from zero, in the
 // GL nodal basis (glb: right-hand side TT^T x, result TT a) or the histopolation basis
+// (T = double: diag is the Jacobi diagonal; T = dfloat: its inverse)
+template <typename T>
 __global__ void __launch_bounds__(MI_THREADS)
-k_mi_cg(int64_t E, int nx, int ny, MiTab t, int glb, int maxit, double tol2, const double* __restrict__ wdet,
-        const double* __restrict__ diag, const double* __restrict__ x, double* __restrict__ y,
-        int* __restrict__ flag) {
-  extern __shared__ double sm[];
+k_mi_cg(int64_t E, int nx, int ny, MiCgTab<T> t, int glb, int maxit, double tol2, const T* __restrict__ wdet,
+        const T* __restrict__ diag, const double* __restrict__ x, double* __restrict__ y, int* __restrict__ flag) {
+  extern __shared__ __align__(16) unsigned char mi_smem[];
   const int k = t.k, q = t.q, n = k * k * k;
   const int64_t e = blockIdx.x;
   if (e >= E) return;
-  double* B = sm;
-  double* TT = B + q * k;
-  double* A = TT + k * k;
-  double* R = A + n;
-  double* P = R + n;
-  double* W = P + n;
-  double* T1 = W + n;
-  double* T2 = T1 + q * k * k;
-  double* T3 = T2 + q * q * k;
-  double* red = T3 + q * q * q;
+  T* B = reinterpret_cast<T*>(mi_smem);
+  T* TT = B + q * k;
+  T* A = TT + k * k;
+  T* R = A + n;
+  T* P = R + n;
+  T* W = P + n;
+  T* T1 = W + n;
+  T* T2 = T1 + q * k * k;
+  T* T3 = T2 + q * q * k;
+  double* red = reinterpret_cast<double*>(T3 + q * q * q);
   for (int i = threadIdx.x; i < q * k; i += blockDim.x) B[i] = t.B[i];
   for (int i = threadIdx.x; i < k * k; i += blockDim.x) TT[i] = t.TT[i];
-  for (int a = threadIdx.x; a < n; a += blockDim.x) W[a] = x[mi_cell(e, a, k, nx, ny)];
+  for (int a = threadIdx.x; a < n; a += blockDim.x) W[a] = mi_t<T>(x[mi_cell(e, a, k, nx, ny)]);
   __syncthreads();
   if (glb) mi_tt3(k, TT, true, W, T1, T2, R);
   else
     for (int a = threadIdx.x; a < n; a += blockDim.x) R[a] = W[a];
   __syncthreads();
-  const double* D = diag + e * n;
-  const double* wd = wdet + e * (int64_t)q * q * q;
+  const T* D = diag + e * n;
+  const T* wd = wdet + e * (int64_t)q * q * q;
+  auto precond = [&](T r, int a) -> T {  // z = r / diag
+    if constexpr (std::is_same<T, double>::value) return r / D[a];
+    else return r * D[a];
+  };
   double rz = 0.0, bb = 0.0;
   for (int a = threadIdx.x; a < n; a += blockDim.x) {
-    const double r = R[a], z = r / D[a];
-    A[a] = 0.0;
+    const T r = R[a], z = precond(r, a);
+    A[a] = T(0);
     P[a] = z;
-    rz = fma(r, z, rz);
-    bb = fma(r, r, bb);
+    rz = fma(mi_d(r), mi_d(z), rz);
+    bb = fma(mi_d(r), mi_d(r), bb);
   }
   rz = block_sum(rz, red);
   bb = block_sum(bb, red);
@@ -240,40 +273,42 @@ k_mi_cg(int64_t E, int nx, int ny, MiTab t, int glb, int maxit, double tol2, con
     while (it < maxit) {
       mi_apply_w(k, q, B, wd, P, W, T1, T2, T3);
       double pw = 0.0;
-      for (int a = threadIdx.x; a < n; a += blockDim.x) pw = fma(P[a], W[a], pw);
+      for (int a = threadIdx.x; a < n; a += blockDim.x) pw = fma(mi_d(P[a]), mi_d(W[a]), pw);
       pw = block_sum(pw, red);
       if (!(pw > 0.0)) {  // breakdown (W_e not positive definite, or a NaN)
         if (threadIdx.x == 0) atomicExch(flag + 2, 1);
         break;
       }
       const double alpha = rz / pw;
+      const T at = mi_t<T>(alpha), mat = mi_t<T>(-alpha);
       double rr = 0.0, rzn = 0.0;
       for (int a = threadIdx.x; a < n; a += blockDim.x) {
-        A[a] = fma(alpha, P[a], A[a]);
-        const double r = fma(-alpha, W[a], R[a]);
+        A[a] = fma(at, P[a], A[a]);
+        const T r = fma(mat, W[a], R[a]);
         R[a] = r;
-        const double z = r / D[a];
+        const T z = precond(r, a);
         W[a] = z;
-        rr = fma(r, r, rr);
-        rzn = fma(r, z, rzn);
+        const double rd = mi_d(r);
+        rr = fma(rd, rd, rr);
+        rzn = fma(rd, mi_d(z), rzn);
       }
       rr = block_sum(rr, red);
       rzn = block_sum(rzn, red);
       ++it;
       if (rr <= tol2 * bb) break;
-      const double beta = rzn / rz;
+      const T beta = mi_t<T>(rzn / rz);
       rz = rzn;
       for (int a = threadIdx.x; a < n; a += blockDim.x) P[a] = fma(beta, P[a], W[a]);
       __syncthreads();
     }
   }
   __syncthreads();
-  const double* res = A;
+  const T* res = A;
   if (glb) {
     mi_tt3(k, TT, false, A, T1, T2, W);
     res = W;
   }
-  for (int a = threadIdx.x; a < n; a += blockDim.x) y[mi_cell(e, a, k, nx, ny)] = res[a];
+  for (int a = threadIdx.x; a < n; a += blockDim.x) y[mi_cell(e, a, k, nx, ny)] = mi_d(res[a]);
   if (threadIdx.x == 0) atomicMax(flag + 1, it);
 }
 
@@ -590,6 +625,12 @@ k_mi_potrs(int64_t E, int nx, int ny, int k, const double* __restrict__ mat, con
   for (int a = threadIdx.x; a < n; a += blockDim.x) y[mi_cell(e, a, k, nx, ny)] = z[a];
 }
 
+// double-float copies for the CG stages: v -> df(v), and 1 / d -> df(1 / d)
+__global__ void k_mi_to_df(int64_t n, const double* __restrict__ v, dfloat* __restrict__ o, int inv) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) o[i] = df_from_double(inv ? 1.0 / v[i] : v[i]);
+}
+
 size_t cg_smem(int k, int q) {
   const int n = k * k * k;
   return sizeof(double) * ((size_t)q * k + k * k + 4 * n + q * k * k + q * q * k + q * q * q + 32);
@@ -606,6 +647,9 @@ void mi_free(hd_massinv* h) {
   cudaFree(h->d_mat);
   cudaFree(h->d_aux);
   cudaFree(h->d_flag);
+  cudaFree(h->x_wdet);
+  cudaFree(h->x_dinv);
+  h->x_wdet = h->x_dinv = nullptr;
   h->d_wdet = h->d_diag = h->d_mat = h->d_aux = nullptr;
   h->d_flag = nullptr;
 }
@@ -632,6 +676,10 @@ hd_status mi_setup(hd_massinv* h, const hd_massinv_desc* d) {
   if (d->alpha) ck(cudaMalloc(&dal, sizeof(double) * E));
   const bool cg = h->method == HD_WINV_CG || h->method == HD_WINV_CG_HIST;
   if (cg) ck(cudaMalloc(&h->d_diag, sizeof(double) * E * n));
+  if (cg && h->emul) {
+    ck(cudaMalloc(&h->x_wdet, sizeof(dfloat) * E * nq));
+    ck(cudaMalloc(&h->x_dinv, sizeof(dfloat) * E * n));
+  }
   else ck(cudaMalloc(&h->d_mat, sizeof(double) * E * n * n));
   if (h->method == HD_WINV_DENSE) ck(cudaMalloc(&h->d_aux, sizeof(double) * E * n * n));
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -648,6 +696,10 @@ hd_status mi_setup(hd_massinv* h, const hd_massinv_desc* d) {
                                                         h->d_flag);
     if (cg) {
       k_mi_diag<<<mi_blocks(E * n), MI_THREADS, 0, s>>>(E, h->tab, h->d_wdet, h->d_diag);
+      if (h->emul) {
+        k_mi_to_df<<<mi_blocks(E * nq), MI_THREADS, 0, s>>>(E * nq, h->d_wdet, h->x_wdet, 0);
+        k_mi_to_df<<<mi_blocks(E * n), MI_THREADS, 0, s>>>(E * n, h->d_diag, h->x_dinv, 1);
+      }
     } else {
       const size_t sm = sizeof(double) * ((size_t)q * k + (size_t)k * k * q * q);
       const size_t sm_max = sizeof(double) * ((size_t)MI_MAXQ * MI_MAXK + (size_t)MI_MAXK * MI_MAXK * MI_MAXQ * MI_MAXQ);
@@ -690,6 +742,9 @@ extern "C" hd_status hd_massinv_create(const hd_massinv_desc* d, hd_massinv_hand
   if (d->method != HD_WINV_DENSE && d->method != HD_WINV_CHOL && d->method != HD_WINV_CG &&
       d->method != HD_WINV_CG_HIST)
     return HD_ERR_INVALID_ARG;
+  if (d->fp64_emulation != 0 && d->fp64_emulation != 1) return HD_ERR_INVALID_ARG;
+  if (d->fp64_emulation == 1 && d->method != HD_WINV_CG && d->method != HD_WINV_CG_HIST)
+    return HD_ERR_NOT_IMPLEMENTED;
   const int64_t E = (int64_t)d->nx * d->ny * d->nz, n = (int64_t)d->k * d->k * d->k;
   if (E * n >= ((int64_t)1 << 31) || E >= ((int64_t)1 << 31)) return HD_ERR_INVALID_ARG;
   if (d->alpha)
@@ -703,10 +758,22 @@ extern "C" hd_status hd_massinv_create(const hd_massinv_desc* d, hd_massinv_hand
   double BG[MI_MAXQ * MI_MAXK];
   hd_l2_tables(d->k, q, t.BH, BG, t.TT, t.gx, t.gw);
   std::memcpy(t.B, d->method == HD_WINV_CG ? BG : t.BH, sizeof(t.B));
+  h->cgd.k = h->cgx.k = d->k;
+  h->cgd.q = h->cgx.q = q;
+  for (int i = 0; i < MI_MAXQ * MI_MAXK; ++i) {
+    h->cgd.B[i] = t.B[i];
+    h->cgx.B[i] = df_split_host(t.B[i]);
+  }
+  for (int i = 0; i < MI_MAXK * MI_MAXK; ++i) {
+    h->cgd.TT[i] = t.TT[i];
+    h->cgx.TT[i] = df_split_host(t.TT[i]);
+  }
+  h->emul = d->fp64_emulation;
   if (h->method == HD_WINV_CG || h->method == HD_WINV_CG_HIST) {
-    // the largest degree's size: handles of other degrees launch the same kernel
+    // the largest degree's size: handles of other degrees launch the same kernels
     const size_t sm = cg_smem(MI_MAXK, MI_MAXQ);
-    if (cudaFuncSetAttribute(k_mi_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+    if (cudaFuncSetAttribute(k_mi_cg<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_mi_cg<dfloat>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
       delete h;
       return HD_ERR_CUDA;
     }
@@ -734,9 +801,13 @@ extern "C" hd_status hd_massinv_apply(hd_massinv_handle h, const double* x, doub
   if (h->method == HD_WINV_CG || h->method == HD_WINV_CG_HIST) {
     const bool glb = h->method == HD_WINV_CG;
     if (cudaMemsetAsync(h->d_flag + 1, 0, sizeof(int), s) != cudaSuccess) return HD_ERR_CUDA;
-    k_mi_cg<<<(unsigned)h->E, MI_THREADS, cg_smem(k, h->q), s>>>(h->E, h->nx, h->ny, h->tab, glb ? 1 : 0,
-                                                                  glb ? 60 : 400, 1e-28, h->d_wdet, h->d_diag, x,
-                                                                  y, h->d_flag);
+    const int maxit = glb ? 60 : 400;
+    if (h->emul)
+      k_mi_cg<dfloat><<<(unsigned)h->E, MI_THREADS, cg_smem(k, h->q), s>>>(
+          h->E, h->nx, h->ny, h->cgx, glb ? 1 : 0, maxit, 1e-28, h->x_wdet, h->x_dinv, x, y, h->d_flag);
+    else
+      k_mi_cg<double><<<(unsigned)h->E, MI_THREADS, cg_smem(k, h->q), s>>>(
+          h->E, h->nx, h->ny, h->cgd, glb ? 1 : 0, maxit, 1e-28, h->d_wdet, h->d_diag, x, y, h->d_flag);
   } else if (h->method == HD_WINV_DENSE) {
     k_mi_gemv<<<(unsigned)h->E, MI_THREADS, sizeof(double) * n, s>>>(h->E, h->nx, h->ny, k, h->d_mat, x, y);
   } else {

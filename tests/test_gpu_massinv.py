@@ -7,7 +7,11 @@ q = k + 2) within 1e-12 of the largest entry. W_e in the histopolation basis has
 condition numbers up to about 110 at k = 9, and the CG stops at a relative residual
 of 1e-14, so every method lands far inside that bar. The GL-basis CG must need few
 iterations at every degree (the basis is conditioned near 1, Sec. 2.5), fewer than
-the histopolation-basis CG. Invalid input is refused on the host."""
+the histopolation-basis CG. The CG methods also run with their stages in double-float
+(FP32 pairs, about 48 bits, unit roundoff ~3.6e-15): the GL-basis CG to the same 1e-12,
+the histopolation-basis CG to 1e-11 (its Jacobi-scaled W has condition numbers up to
+about 100, which multiply the double-float roundoff). Invalid input is refused on the
+host."""
 import numpy as np
 import pytest
 
@@ -16,7 +20,7 @@ import synth
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-METHODS = ["dense", "chol", "cg", "cg_hist"]
+METHODS = ["dense", "chol", "cg", "cg_hist", "cg_df", "cg_hist_df"]
 
 
 def _mesh(k):
@@ -45,19 +49,20 @@ def test_mass_inverse_matches_oracle(k, method):
         pytest.skip("no CUDA device")
     import paper_2304_12387_gb300 as hd
     m = {"dense": hd.HD_WINV_DENSE, "chol": hd.HD_WINV_CHOL, "cg": hd.HD_WINV_CG, "cg_hist": hd.HD_WINV_CG_HIST}
+    df = method.endswith("_df")
     dims, v, alpha = _mesh(k)
-    mi = hd.MassInverse(*dims, k, *v, alpha=alpha, method=m[method])
+    mi = hd.MassInverse(*dims, k, *v, alpha=alpha, method=m[method.replace("_df", "")], fp64_emulation=int(df))
     x = np.random.Generator(np.random.PCG64(60 + k)).uniform(-1, 1, mi.n_l2)
     y = torch.empty(mi.n_l2, dtype=torch.float64, device="cuda")
     mi.apply(torch.from_numpy(x).cuda(), y)
     torch.cuda.synchronize()
     ref = _reference(k, dims, v, alpha, x)
     err = np.abs(y.cpu().numpy() - ref).max() / np.abs(ref).max()
-    assert err <= 1e-12, err
+    assert err <= (1e-11 if method == "cg_hist_df" else 1e-12), err
     its = mi.iterations()
-    if method == "cg":
+    if method in ("cg", "cg_df"):
         assert 1 <= its <= 20, its
-    elif method == "cg_hist":
+    elif method in ("cg_hist", "cg_hist_df"):
         assert its >= 1, its
     else:
         assert its == 0
@@ -93,3 +98,12 @@ def test_mass_inverse_refuses_invalid_input():
     with pytest.raises(hd.HdError) as e:
         hd.MassInverse(*dims, 3, *v, alpha=-alpha)
     assert e.value.status == hd.HD_ERR_INVALID_ARG
+
+
+def test_double_float_direct_methods_are_refused():
+    import paper_2304_12387_gb300 as hd
+    dims, v, alpha = _mesh(3)
+    for method in (hd.HD_WINV_DENSE, hd.HD_WINV_CHOL):
+        with pytest.raises(hd.HdError) as e:
+            hd.MassInverse(*dims, 3, *v, alpha=alpha, method=method, fp64_emulation=1)
+        assert e.value.status == hd.HD_ERR_NOT_IMPLEMENTED
