@@ -150,6 +150,19 @@ void build_tables(int k, int q, ElemTables& t) {
   }
   for (int a = 0; a < k; ++a)
     for (int b = 0; b < k; ++b) t.HI[a * k + b] = A[a][k + b];
+  // even-odd tables of BI (q x k+1), BH (q x k) and their transposes
+  auto eo = [](int R, int C, auto M, double* P, double* N) {
+    const int ec = (C + 1) / 2, hc = C / 2;
+    for (int r = 0; r < (R + 1) / 2; ++r)
+      for (int c = 0; c < ec; ++c)
+        P[r * ec + c] = (2 * c + 1 == C) ? M(r, c) : 0.5 * (M(r, c) + M(r, C - 1 - c));
+    for (int r = 0; r < R / 2; ++r)
+      for (int c = 0; c < hc; ++c) N[r * hc + c] = 0.5 * (M(r, c) - M(r, C - 1 - c));
+  };
+  eo(q, k + 1, [&](int r, int c) { return t.BI[r * (k + 1) + c]; }, t.BIp, t.BIn);
+  eo(q, k, [&](int r, int c) { return t.BH[r * k + c]; }, t.BHp, t.BHn);
+  eo(k + 1, q, [&](int r, int c) { return t.BI[c * (k + 1) + r]; }, t.BITp, t.BITn);
+  eo(k, q, [&](int r, int c) { return t.BH[c * k + r]; }, t.BHTp, t.BHTn);
 }
 
 // Affine fast path: every element a parallelepiped (its trilinear map has no bilinear or

@@ -28,6 +28,14 @@ struct ElemTables {
                                        //   coefficients -> histopolation coefficients
   double HI[HD_MAXK * HD_MAXK];        // inverse of the 1D histopolation mass H[a][b] = int h_a h_b
                                        //   (affine elements: W_e^-1 = det J  HI x HI x HI)
+  // Even-odd form of the centrosymmetric tables (M[R-1-r][C-1-c] = M[r][c]: the GLL and GL
+  // points are symmetric about 1/2, and h_j(1 - x) = h_{k-1-j}(x)): for an R x C matrix M,
+  // P[r][c] = (M[r][c] + M[r][C-1-c]) / 2 for c < C/2 and P[r][C/2] = M[r][C/2] for odd C
+  // (r < ceil(R/2), row stride ceil(C/2)); N[r][c] = (M[r][c] - M[r][C-1-c]) / 2 (r < R/2,
+  // c < C/2, row stride C/2). Then out[r] = E_r + O_r and out[R-1-r] = E_r - O_r with
+  // E_r = P[r] . (x_c + x_{C-1-c}, middle x), O_r = N[r] . (x_c - x_{C-1-c}). For BI and BH
+  // (points x coefficients) and their transposes (BIT, BHT: coefficients x points).
+  double BIp[16], BIn[16], BHp[16], BHn[16], BITp[16], BITn[16], BHTp[16], BHTn[16];
 };
 
 // One-time set-up per device (the dynamic shared memory opt-in is a function attribute of

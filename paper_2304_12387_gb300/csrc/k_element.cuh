@@ -27,6 +27,7 @@ struct TabT {
   T TT[HD_MAXK * HD_MAXK];
   T GW[HD_MAXQ];             // 1D Gauss-Legendre weights on [0,1]
   T HI[HD_MAXK * HD_MAXK];   // inverse 1D histopolation mass
+  T BIp[16], BIn[16], BHp[16], BHn[16], BITp[16], BITn[16], BHTp[16], BHTn[16];  // even-odd forms
 };
 
 template <typename T>
@@ -43,6 +44,16 @@ inline TabT<T> make_tab(const ElemTables& t) {
   for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.TT[i] = tab_cast<T>(t.TT[i]);
   for (int i = 0; i < HD_MAXQ; ++i) o.GW[i] = tab_cast<T>(t.gw[i]);
   for (int i = 0; i < HD_MAXK * HD_MAXK; ++i) o.HI[i] = tab_cast<T>(t.HI[i]);
+  for (int i = 0; i < 16; ++i) {
+    o.BIp[i] = tab_cast<T>(t.BIp[i]);
+    o.BIn[i] = tab_cast<T>(t.BIn[i]);
+    o.BHp[i] = tab_cast<T>(t.BHp[i]);
+    o.BHn[i] = tab_cast<T>(t.BHn[i]);
+    o.BITp[i] = tab_cast<T>(t.BITp[i]);
+    o.BITn[i] = tab_cast<T>(t.BITn[i]);
+    o.BHTp[i] = tab_cast<T>(t.BHTp[i]);
+    o.BHTn[i] = tab_cast<T>(t.BHTn[i]);
+  }
   return o;
 }
 
@@ -98,6 +109,40 @@ __device__ __forceinline__ void contractT(const T* __restrict__ in, T* __restric
 #pragma unroll
     for (int i = 1; i < NI; ++i) s.add(B[i * NO + o], x[i]);
     out[o * SO] = s.get();
+  }
+}
+
+// out[o*SO] = sum_i M[o][i] in[i*SI], o < NO, for a centrosymmetric NO x NI matrix M in
+// its even-odd form P, N (see ElemTables): sums and differences of mirrored inputs, then
+// each pair of mirrored outputs from one even and one odd partial sum. About half the
+// multiply-adds of contract, and chains of at most ceil(NI / 2) terms.
+template <typename T, int NI, int NO, int SI, int SO>
+__device__ __forceinline__ void contract_eo(const T* __restrict__ in, T* __restrict__ out, const T* P, const T* N) {
+  constexpr int EI = (NI + 1) / 2, HI = NI / 2, EO = (NO + 1) / 2, HO = NO / 2;
+  T ev[EI], od[HI > 0 ? HI : 1];
+#pragma unroll
+  for (int i = 0; i < HI; ++i) {
+    const T a = in[i * SI], b = in[(NI - 1 - i) * SI];
+    ev[i] = a + b;
+    od[i] = a - b;
+  }
+  if constexpr (NI % 2 == 1) ev[HI] = in[HI * SI];
+#pragma unroll
+  for (int o = 0; o < EO; ++o) {
+    Acc<T> e;
+    e.init(P[o * EI], ev[0]);
+#pragma unroll
+    for (int i = 1; i < EI; ++i) e.add(P[o * EI + i], ev[i]);
+    if (o < HO) {
+      Acc<T> d;
+      d.init(N[o * HI], od[0]);
+#pragma unroll
+      for (int i = 1; i < HI; ++i) d.add(N[o * HI + i], od[i]);
+      out[o * SO] = e.get() + d.get();
+      out[(NO - 1 - o) * SO] = e.get() - d.get();
+    } else {
+      out[o * SO] = e.get();  // the middle output of an odd NO
+    }
   }
 }
 
@@ -698,14 +743,14 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
         if (t < EB * LX) {
           int el = t / LX, r = t - el * LX;  // r = j + K l
-          contract<T, K + 1, Q, 1, 1>(su + el * NRT + (K + 1) * r, s1 + el * S::R1 + Q * r, tab.BI);
+          contract_eo<T, K + 1, Q, 1, 1>(su + el * NRT + (K + 1) * r, s1 + el * S::R1 + Q * r, tab.BIp, tab.BIn);
         } else if (t < EB * (LX + LY)) {
           int tt = t - EB * LX, el = tt / LY, r = tt - el * LY;  // r = j + (K+1) l
-          contract<T, K, Q, 1, 1>(su + el * NRT + NX1 + K * r, s1 + el * S::R1 + Q * K * K + Q * r, tab.BH);
+          contract_eo<T, K, Q, 1, 1>(su + el * NRT + NX1 + K * r, s1 + el * S::R1 + Q * K * K + Q * r, tab.BHp, tab.BHn);
         } else {
           int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ;  // r = j + K l
-          contract<T, K, Q, 1, 1>(su + el * NRT + 2 * NX1 + K * r,
-                                  s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r, tab.BH);
+          contract_eo<T, K, Q, 1, 1>(su + el * NRT + 2 * NX1 + K * r,
+                                  s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r, tab.BHp, tab.BHn);
         }
       }
     }
@@ -716,15 +761,15 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
         if (t < EB * LX) {
           int el = t / LX, r = t - el * LX, px = r % Q, l = r / Q;
-          contract<T, K, Q, Q, Q>(s1 + el * S::R1 + px + Q * K * l, s2 + el * S::R2 + px + Q * Q * l, tab.BH);
+          contract_eo<T, K, Q, Q, Q>(s1 + el * S::R1 + px + Q * K * l, s2 + el * S::R2 + px + Q * Q * l, tab.BHp, tab.BHn);
         } else if (t < EB * (LX + LY)) {
           int tt = t - EB * LX, el = tt / LY, r = tt - el * LY, px = r % Q, l = r / Q;
-          contract<T, K + 1, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l,
-                                      s2 + el * S::R2 + Q * Q * K + px + Q * Q * l, tab.BI);
+          contract_eo<T, K + 1, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l,
+                                      s2 + el * S::R2 + Q * Q * K + px + Q * Q * l, tab.BIp, tab.BIn);
         } else {
           int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ, px = r % Q, l = r / Q;
-          contract<T, K, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l,
-                                  s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l, tab.BH);
+          contract_eo<T, K, Q, Q, Q>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l,
+                                  s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l, tab.BHp, tab.BHn);
         }
       }
     }
@@ -737,9 +782,9 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         T* out = s1 + el * S::R1 + c * NQ + r;
         const T* in = s2 + el * S::R2 + c * Q * Q * K + r;
         if (c == 2)
-          contract<T, K + 1, Q, Q * Q, Q * Q>(in, out, tab.BI);
+          contract_eo<T, K + 1, Q, Q * Q, Q * Q>(in, out, tab.BIp, tab.BIn);
         else
-          contract<T, K, Q, Q * Q, Q * Q>(in, out, tab.BH);
+          contract_eo<T, K, Q, Q * Q, Q * Q>(in, out, tab.BHp, tab.BHn);
       }
     }
     __syncthreads();
@@ -777,9 +822,9 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         const T* in = s1 + el * S::R1 + c * NQ + r;
         T* out = s2 + el * S::R2 + c * Q * Q * K + r;
         if (c == 2)
-          contractT<T, Q, K + 1, Q * Q, Q * Q>(in, out, tab.BI);
+          contract_eo<T, Q, K + 1, Q * Q, Q * Q>(in, out, tab.BITp, tab.BITn);
         else
-          contractT<T, Q, K, Q * Q, Q * Q>(in, out, tab.BH);
+          contract_eo<T, Q, K, Q * Q, Q * Q>(in, out, tab.BHTp, tab.BHTn);
       }
     }
     __syncthreads();
@@ -789,15 +834,15 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
         if (t < EB * LX) {
           int el = t / LX, r = t - el * LX, px = r % Q, l = r / Q;
-          contractT<T, Q, K, Q, Q>(s2 + el * S::R2 + px + Q * Q * l, s1 + el * S::R1 + px + Q * K * l, tab.BH);
+          contract_eo<T, Q, K, Q, Q>(s2 + el * S::R2 + px + Q * Q * l, s1 + el * S::R1 + px + Q * K * l, tab.BHTp, tab.BHTn);
         } else if (t < EB * (LX + LY)) {
           int tt = t - EB * LX, el = tt / LY, r = tt - el * LY, px = r % Q, l = r / Q;
-          contractT<T, Q, K + 1, Q, Q>(s2 + el * S::R2 + Q * Q * K + px + Q * Q * l,
-                                       s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l, tab.BI);
+          contract_eo<T, Q, K + 1, Q, Q>(s2 + el * S::R2 + Q * Q * K + px + Q * Q * l,
+                                       s1 + el * S::R1 + Q * K * K + px + Q * (K + 1) * l, tab.BITp, tab.BITn);
         } else {
           int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ, px = r % Q, l = r / Q;
-          contractT<T, Q, K, Q, Q>(s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l,
-                                   s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l, tab.BH);
+          contract_eo<T, Q, K, Q, Q>(s2 + el * S::R2 + 2 * Q * Q * K + px + Q * Q * l,
+                                   s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + px + Q * K * l, tab.BHTp, tab.BHTn);
         }
       }
     }
@@ -808,14 +853,14 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
       for (int t = tid; t < EB * (LX + LY + LZ); t += nth) {
         if (t < EB * LX) {
           int el = t / LX, r = t - el * LX;
-          contractT<T, Q, K + 1, 1, 1>(s1 + el * S::R1 + Q * r, su + el * NRT + (K + 1) * r, tab.BI);
+          contract_eo<T, Q, K + 1, 1, 1>(s1 + el * S::R1 + Q * r, su + el * NRT + (K + 1) * r, tab.BITp, tab.BITn);
         } else if (t < EB * (LX + LY)) {
           int tt = t - EB * LX, el = tt / LY, r = tt - el * LY;
-          contractT<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * r, su + el * NRT + NX1 + K * r, tab.BH);
+          contract_eo<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * r, su + el * NRT + NX1 + K * r, tab.BHTp, tab.BHTn);
         } else {
           int tt = t - EB * (LX + LY), el = tt / LZ, r = tt - el * LZ;
-          contractT<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r,
-                                   su + el * NRT + 2 * NX1 + K * r, tab.BH);
+          contract_eo<T, Q, K, 1, 1>(s1 + el * S::R1 + Q * K * K + Q * (K + 1) * K + Q * r,
+                                   su + el * NRT + 2 * NX1 + K * r, tab.BHTp, tab.BHTn);
         }
       }
     }
