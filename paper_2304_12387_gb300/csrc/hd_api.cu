@@ -824,7 +824,9 @@ hd_status hd_apply_op(hd_handle h, const double* x, double* y) {
 // and the outputs of slab s-1 are copied out (a third stream). In lattice order a
 // slab's inputs and outputs are four contiguous ranges (x-, y-, z-faces, cells);
 // the z-face layer between two slabs receives the two slabs' addends (on zero, so
-// in either order the same sum) and is copied out with the upper slab.
+// in either order the same sum) and is copied out with the upper slab. The slabs
+// taper towards both ends (layer weights 1, 2, 5, 8, 8, 5, 2, 1): only the first
+// slab's copy in and the last slab's copy out are not overlapped with element work.
 hd_status hd_apply_op_host(hd_handle h, const double* xh, double* yh) {
   if (!h || !xh || !yh) return HD_ERR_INVALID_ARG;
   const int64_t n = h->n_rt + h->n_l2;
@@ -857,8 +859,24 @@ hd_status hd_apply_op_host(hd_handle h, const double* xh, double* yh) {
   HD_CK(h, cudaEventRecord(h->xev[2 * S], h->stream));
   HD_CK(h, cudaStreamWaitEvent(h->xstream[0], h->xev[2 * S], 0));
   hd_status st = HD_OK;
+  // slab boundaries: cumulative tapered weights, at least one layer per slab
+  int zb[9];
+  {
+    static const int wt[8] = {1, 2, 5, 8, 8, 5, 2, 1};
+    int wsum = 0, acc = 0;
+    for (int i = 0; i < S; ++i) wsum += wt[S == 8 ? i : 3];
+    zb[0] = 0;
+    for (int i = 0; i < S; ++i) {
+      acc += wt[S == 8 ? i : 3];
+      int z = (int)(((int64_t)nz * acc + wsum / 2) / wsum);
+      z = std::max(z, zb[i] + 1);
+      z = std::min(z, nz - (S - 1 - i));
+      zb[i + 1] = z;
+    }
+    zb[S] = nz;
+  }
   for (int s = 0; s < S && st == HD_OK; ++s) {
-    const int z0 = (int)((int64_t)s * nz / S), z1 = (int)((int64_t)(s + 1) * nz / S);
+    const int z0 = zb[s], z1 = zb[s + 1];
     const int64_t Z0 = (int64_t)z0 * K, Z1 = (int64_t)z1 * K;
     const int64_t zin = Z0 + (s > 0 ? 1 : 0);  // the layer Z0 came with the slab below
     HD_CK(h, copy(dx, xh, sx * Z0, sx * Z1, cudaMemcpyHostToDevice, h->xstream[0]));
