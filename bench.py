@@ -1020,8 +1020,9 @@ def main():
                          "and 100 applies")
     ap.add_argument("--iterations", action="store_true",
                     help="run the iteration-count study (mesh sizes and degrees) instead")
-    ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1],
-                    help="1: element kernel in double-float (FP32 pairs, FP64 parity); 0: native FP64")
+    ap.add_argument("--fp64-emulation", type=int, default=1, choices=[0, 1, 2],
+                    help="1: element kernel in double-float (FP32 pairs, FP64 parity); 2: and the Schur cycle of "
+                         "the FP64 preconditioner; 0: native FP64")
     ap.add_argument("--no-native", action="store_true", help="skip the native-FP64 comparison apply")
     ap.add_argument("--no-affine", action="store_true", help="skip the apply on the unperturbed (affine) mesh")
     ap.add_argument("--n", type=int, default=NX, help="elements per direction (64 = the metric workload)")

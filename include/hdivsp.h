@@ -115,6 +115,13 @@ typedef struct {
                             FP32 numbers, about 48 significant bits) on the FP32 pipe, with FP64
                             vectors in and out and the same FP64 results to ~1e-13 relative;
                             HD_WINV_DENSE only. Setup, lattice kernels and MINRES stay FP64.
+                            2: as 1, and the Schur V/W-cycle of the FP64 preconditioner (hd_vcycle,
+                            hd_apply_prec, the FP64 solves) in double-float as well: its levels'
+                            sweeps, residuals and transfers, between FP64 vectors; the coarsest
+                            dense solve and the Krylov recurrences stay FP64. The cycle then
+                            agrees with the FP64 one to ~1e-14 relative and remains a fixed
+                            symmetric operator for MINRES. The double-float copies of the
+                            hierarchy are made in hd_create (about the hierarchy's size again).
                             FP32's exponent range applies: hd_create refuses (HD_ERR_INVALID_ARG)
                             a problem where an element's geometric factors, W_e^-1 or
                             c_e W_e^-1 have their largest magnitude outside [2^-60, 2^60]

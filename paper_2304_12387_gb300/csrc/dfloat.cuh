@@ -18,6 +18,9 @@ struct __align__(8) dfloat {
   __host__ __device__ constexpr dfloat(float h, float l) : hi(h), lo(l) {}
   __host__ __device__ constexpr dfloat(int v) : hi((float)v), lo(0.f) {}
   __host__ __device__ constexpr dfloat(float v) : hi(v), lo(0.f) {}
+  // explicit FP64 conversions (device: the integer split below; see df_from_double)
+  __device__ explicit dfloat(double v);
+  __device__ explicit operator double() const { return (double)hi + (double)lo; }
 };
 
 // s + e = a + b exactly (Knuth TwoSum)
@@ -89,6 +92,7 @@ __device__ __forceinline__ dfloat df_from_double(double x) {
 
 // double-float -> FP64: hi + lo (one FP64 add)
 __device__ __forceinline__ double df_to_double(dfloat a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfloat::dfloat(double v) : dfloat(df_from_double(v)) {}
 
 // host-side split of a table entry (round-to-nearest hi, remainder in lo)
 inline dfloat df_split_host(double v) {

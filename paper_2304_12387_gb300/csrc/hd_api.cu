@@ -437,9 +437,10 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
     delete h;
     return HD_ERR_INVALID_ARG;
   }
-  if (d->fp64_emulation != 0 && d->fp64_emulation != 1) { delete h; return HD_ERR_INVALID_ARG; }
-  if (d->fp64_emulation == 1 && d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
-  h->emul = d->fp64_emulation == 1;
+  if (d->fp64_emulation < 0 || d->fp64_emulation > 2) { delete h; return HD_ERR_INVALID_ARG; }
+  if (d->fp64_emulation >= 1 && d->winv_mode != HD_WINV_DENSE) { delete h; return HD_ERR_NOT_IMPLEMENTED; }
+  h->emul = d->fp64_emulation >= 1;
+  h->cycle_df = d->fp64_emulation == 2;
   h->winv_mode = d->winv_mode;
   h->tau = d->tau > 0 ? d->tau : 1.0;
   h->nu = d->nu > 0 ? d->nu : 2;
@@ -598,6 +599,9 @@ hd_status hd_create(const hd_problem_desc* d, hd_handle* out) {
       if (E > 0) k_split_df<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(E, h->d_cscale, h->x_cscale);
       if (cudaGetLastError() != cudaSuccess) { st = hd_fail(h, HD_ERR_CUDA, "double-float split"); break; }
     }
+    // the double-float copies of the Schur hierarchy (fp64_emulation = 2), made here so that
+    // the allocation-free solve finds them in place
+    if (h->cycle_df && (st = setup_df_cycle(h)) != HD_OK) break;
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { st = hd_cuda_check(h, e, "setup"); break; }
     if ((st = noalloc_prepare(h)) != HD_OK) break;

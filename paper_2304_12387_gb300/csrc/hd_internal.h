@@ -234,6 +234,15 @@ struct hd_op {
   float* f_mtinv = nullptr;
   float* f_coarse_inv = nullptr;
   std::vector<LevelT<float>> lvf;
+  // double-float copies of the Schur hierarchy for the FP64 cycle (fp64_emulation = 2):
+  // levels, stencil levels, prolongator values, cycle input and output
+  bool cycle_df = false;
+  std::vector<LevelT<dfloat>> lvx;
+  std::vector<StLevelT<dfloat>> stx;
+  dfloat* sa_px = nullptr;
+  dfloat* sa_p1x = nullptr;
+  dfloat* cyc_b = nullptr;
+  dfloat* cyc_x = nullptr;
   bool have_f32 = false;
 
   // scratch
@@ -349,6 +358,9 @@ hd_status sa_setup_f32(hd_op* h);
 void sa_free(hd_op* h);
 hd_status sa_vcycle(hd_op* h, const double* b, double* x);
 hd_status sa_vcycle_f32(hd_op* h, const float* b, float* x);
+hd_status sa_vcycle_df(hd_op* h, const dfloat* b, dfloat* x);
+hd_status sa_setup_df(hd_op* h);
+hd_status setup_df_cycle(hd_op* h);
 // runs launch() as a cached CUDA graph keyed by (b, x, key) (k_lattice.cu)
 hd_status run_graphed(hd_op* h, const void* b, void* x, int key, const std::function<void()>& launch);
 // dense SPD inverse on the host (row-major; adds s 1 1^T first when singular)

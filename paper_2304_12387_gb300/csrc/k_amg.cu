@@ -60,7 +60,7 @@ struct Shape {
 __host__ __device__ constexpr int n_half(int no) { return (no + 1) / 2; }
 
 template <int NO>
-__host__ __device__ __forceinline__ void st_off(int o, int& dx, int& dy, int& dz) {
+__host__ __device__ __forceinline__ constexpr void st_off(int o, int& dx, int& dy, int& dz) {
   using S = Shape<NO>;
   if (o < S::NB) {
     dx = o % S::B - S::R;
@@ -69,7 +69,7 @@ __host__ __device__ __forceinline__ void st_off(int o, int& dx, int& dy, int& dz
     return;
   }
   const int a = o - S::NB;
-  int d, v, u = 0, w = 0;
+  int d = 0, v = 0, u = 0, w = 0;
   if (NO == 33) {
     d = a >> 1;
     v = (a & 1) ? -2 : 2;
@@ -97,7 +97,7 @@ inline void st_off_any(int no, int o, int& dx, int& dy, int& dz) {
 // stored (half) offset h -> full offset index: h = 0 the centre, then the box
 // offsets after it in lattice order, then the positive axial offsets
 template <int NO>
-__host__ __device__ __forceinline__ int half_full_index(int h) {
+__host__ __device__ __forceinline__ constexpr int half_full_index(int h) {
   using S = Shape<NO>;
   constexpr int cb = (S::NB - 1) / 2;
   if (h <= cb) return cb + h;
@@ -361,8 +361,8 @@ __device__ __forceinline__ T st_row(const StLevelT<T>& L, int c, int I, int J, i
     const T ap = ah[c];
     T am = ah[okm ? c - d : c];
     am = okm ? am : (T)0;
-    s = fma(ap, x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c) - o, s);
-    s = fma(am, x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c) - o, s);
+    s = fma(ap, rs_diff(x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c), o), s);
+    s = fma(am, rs_diff(x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c), o), s);
   }
   return s;
 }
@@ -444,27 +444,98 @@ __device__ __forceinline__ T st_row_part(const StLevelT<T>& L, int c, int I, int
   const T xc = (W == 0 || rowsum_form<T>()) ? x_at(I, J, Z, c) : (T)0, o = rowsum_form<T>() ? xc : (T)0;
   T s = W == 0 ? L.a[c] * xc : (T)0;
 #pragma unroll
-  for (int j = 0; j < 2 * CNT; ++j) s = fma(av[j], xv[j] - o, s);
+  for (int j = 0; j < 2 * CNT; ++j) s = fma(av[j], rs_diff(xv[j], o), s);
+  return s;
+}
+
+// The stored offsets of the wide shapes as a table in constant memory, packed
+// (dx + 3) | (dy + 3) << 4 | (dz + 3) << 8.
+template <int NO>
+struct HalfOffs {
+  int v[Shape<NO>::NH];
+};
+template <int NO>
+constexpr HalfOffs<NO> half_offs() {
+  HalfOffs<NO> t{};
+  for (int h = 0; h < Shape<NO>::NH; ++h) {
+    int dx = 0, dy = 0, dz = 0;
+    st_off<NO>(half_full_index<NO>(h), dx, dy, dz);
+    t.v[h] = (dx + 3) | (dy + 3) << 4 | (dz + 3) << 8;
+  }
+  return t;
+}
+__constant__ HalfOffs<81> c_hoffs81 = half_offs<81>();
+__constant__ HalfOffs<179> c_hoffs179 = half_offs<179>();
+template <int NO>
+__device__ __forceinline__ int half_off_packed(int h) {
+  if constexpr (NO == 179) return c_hoffs179.v[h];
+  else return c_hoffs81.v[h];
+}
+
+// st_row_part for the double-float levels of the wide shapes: one loop body for
+// every warp (the warp index only picks the first offset), the offsets from the
+// table above, U offsets' loads issued before their products are added. The sum
+// runs over the same terms in the same order as st_row_part. The unrolled form
+// has G distinct bodies, which in double-float outgrow the instruction cache
+// (179 points: 2.3x the FP64 kernel's time).
+template <typename T, int NO, typename XA>
+__device__ __forceinline__ T st_row_part_loop(const StLevelT<T>& L, int c, int I, int J, int Z, int w, XA x_at) {
+  static_assert(!rowsum_form<T>(), "row-sum levels act on differences");
+  static_assert(NO == 81 || NO == 179, "wide shapes only");
+  constexpr int NH = Shape<NO>::NH, G = SplitG<NO>::G, U = 4;
+  const int64_t n = L.n();
+  const int X = L.X, XY = L.X * L.Y;
+  T s = w == 0 ? L.a[c] * x_at(I, J, Z, c) : (T)0;
+  for (int h0 = w == 0 ? G : w; h0 < NH; h0 += G * U) {
+    T av[2 * U], xv[2 * U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int h = h0 + G * u;
+      const bool in = h < NH;
+      const int p = half_off_packed<NO>(in ? h : 0);  // h = 0: the zero offset
+      const int dx = (p & 15) - 3, dy = (p >> 4 & 15) - 3, dz = (p >> 8) - 3;
+      const int d = dx + X * dy + XY * dz;
+      const bool okp = in && (unsigned)(I + dx) < (unsigned)L.X && (unsigned)(J + dy) < (unsigned)L.Y &&
+                       (unsigned)(Z + dz) < (unsigned)L.Z;
+      const bool okm = in && (unsigned)(I - dx) < (unsigned)L.X && (unsigned)(J - dy) < (unsigned)L.Y &&
+                       (unsigned)(Z - dz) < (unsigned)L.Z;
+      // as in st_row_part: loads at the own cell where a neighbour is missing, the
+      // stored +d coefficient there is an exact zero, the mirrored one selected away
+      const T* ah = L.a + (int64_t)(in ? h : 0) * n;
+      const T ap = ah[c];
+      const T am = ah[okm ? c - d : c];
+      av[2 * u] = in ? ap : (T)0;
+      av[2 * u + 1] = okm ? am : (T)0;
+      xv[2 * u] = x_at(okp ? I + dx : I, okp ? J + dy : J, okp ? Z + dz : Z, okp ? c + d : c);
+      xv[2 * u + 1] = x_at(okm ? I - dx : I, okm ? J - dy : J, okm ? Z - dz : Z, okm ? c - d : c);
+    }
+#pragma unroll
+    for (int j = 0; j < 2 * U; ++j) s = fma(av[j], xv[j], s);
+  }
   return s;
 }
 
 template <typename T, int NO, typename XA>
 __device__ __forceinline__ T st_row_part_any(const StLevelT<T>& L, int c, int I, int J, int Z, int w, XA x_at) {
-  switch (w) {  // uniform per warp
-    case 0: return st_row_part<T, NO, 0>(L, c, I, J, Z, x_at);
-    case 1: return st_row_part<T, NO, 1>(L, c, I, J, Z, x_at);
-    case 2: return st_row_part<T, NO, 2>(L, c, I, J, Z, x_at);
-    case 3: return st_row_part<T, NO, 3>(L, c, I, J, Z, x_at);
-  }
-  if constexpr (SplitG<NO>::G > 4) {
-    switch (w) {
-      case 4: return st_row_part<T, NO, 4>(L, c, I, J, Z, x_at);
-      case 5: return st_row_part<T, NO, 5>(L, c, I, J, Z, x_at);
-      case 6: return st_row_part<T, NO, 6>(L, c, I, J, Z, x_at);
-      case 7: return st_row_part<T, NO, 7>(L, c, I, J, Z, x_at);
+  if constexpr (std::is_same<T, dfloat>::value) {
+    return st_row_part_loop<T, NO>(L, c, I, J, Z, w, x_at);
+  } else {
+    switch (w) {  // uniform per warp
+      case 0: return st_row_part<T, NO, 0>(L, c, I, J, Z, x_at);
+      case 1: return st_row_part<T, NO, 1>(L, c, I, J, Z, x_at);
+      case 2: return st_row_part<T, NO, 2>(L, c, I, J, Z, x_at);
+      case 3: return st_row_part<T, NO, 3>(L, c, I, J, Z, x_at);
     }
+    if constexpr (SplitG<NO>::G > 4) {
+      switch (w) {
+        case 4: return st_row_part<T, NO, 4>(L, c, I, J, Z, x_at);
+        case 5: return st_row_part<T, NO, 5>(L, c, I, J, Z, x_at);
+        case 6: return st_row_part<T, NO, 6>(L, c, I, J, Z, x_at);
+        case 7: return st_row_part<T, NO, 7>(L, c, I, J, Z, x_at);
+      }
+    }
+    return (T)0;
   }
-  return (T)0;
 }
 
 // (A x)_c for the cell of this lane, complete in warp 0 (other warps: undefined).
@@ -1220,7 +1291,7 @@ template <typename T>
 hd_status alloc_st(hd_op* h, StLevelT<T>& L, bool coefs) {
   const int64_t n = L.n();
   // FP64 setup needs all offsets; the FP32 copy is made from the half storage
-  const int64_t na = sizeof(T) == 8 ? L.no : n_half(L.no);
+  const int64_t na = std::is_same<T, double>::value ? L.no : n_half(L.no);
   if (coefs && cudaMalloc(&L.a, sizeof(T) * n * na) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "stencil level");
   if (cudaMalloc(&L.dinv, sizeof(T) * n) != cudaSuccess || cudaMalloc(&L.x0, sizeof(T) * n) != cudaSuccess ||
       cudaMalloc(&L.x1, sizeof(T) * n) != cudaSuccess || cudaMalloc(&L.b, sizeof(T) * n) != cudaSuccess)
@@ -1376,8 +1447,13 @@ hd_status sa_setup_f32(hd_op* h) {
 void sa_free(hd_op* h) {
   for (auto& s : h->st) free_st<double>(s);
   for (auto& s : h->stf) free_st<float>(s);
+  for (auto& s : h->stx) free_st<dfloat>(s);
   h->st.clear();
   h->stf.clear();
+  h->stx.clear();
+  cudaFree(h->sa_px);
+  cudaFree(h->sa_p1x);
+  h->sa_px = h->sa_p1x = nullptr;
   cudaFree(h->sa_p);
   cudaFree(h->sa_pf);
   cudaFree(h->sa_p1);
@@ -1392,6 +1468,36 @@ void sa_free(hd_op* h) {
 
 hd_status sa_vcycle(hd_op* h, const double* b, double* x) {
   return run_graphed(h, b, x, 2, [&]() { sa_cycle0<double>(h, h->lv[0], h->sa_p, h->st, h->sa_p1, b, x); });
+}
+
+hd_status sa_vcycle_df(hd_op* h, const dfloat* b, dfloat* x) {
+  return run_graphed(h, b, x, 4, [&]() { sa_cycle0<dfloat>(h, h->lvx[0], h->sa_px, h->stx, h->sa_p1x, b, x); });
+}
+
+// double-float copies of the smoothed hierarchy (the stencil levels in half storage, the
+// prolongator values), for the FP64 cycle of fp64_emulation = 2
+hd_status sa_setup_df(hd_op* h) {
+  if (h->st.empty() || !h->stx.empty()) return HD_OK;
+  const int64_t np0 = (h->sa_gen ? PG_SLOTS : 4) * h->lv[0].n();
+  if (cudaMalloc(&h->sa_px, sizeof(dfloat) * np0) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA df");
+  k_to_f32_sa<dfloat><<<nblk(np0), TPB, 0, h->stream>>>(np0, h->sa_p, h->sa_px);
+  if (h->sa_p1) {
+    const int64_t np = P1_SLOTS * h->st[0].n();
+    if (cudaMalloc(&h->sa_p1x, sizeof(dfloat) * np) != cudaSuccess) return hd_fail(h, HD_ERR_OOM, "SA df");
+    k_to_f32_sa<dfloat><<<nblk(np), TPB, 0, h->stream>>>(np, h->sa_p1, h->sa_p1x);
+  }
+  for (const StLevelT<double>& d : h->st) {
+    StLevelT<dfloat> f{};
+    f.X = d.X; f.Y = d.Y; f.Z = d.Z; f.no = d.no;
+    set_agg(f, d.ag[0], d.ag[1], d.ag[2]);
+    hd_status st = alloc_st<dfloat>(h, f, true);
+    h->stx.push_back(f);
+    if (st != HD_OK) return st;
+    k_to_f32_sa<dfloat><<<nblk(d.n() * n_half(d.no)), TPB, 0, h->stream>>>(d.n() * n_half(d.no), d.a, f.a);
+    k_to_f32_sa<dfloat><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
+  }
+  HD_LAUNCH_CK(h, "SA df");
+  return HD_OK;
 }
 
 hd_status sa_vcycle_f32(hd_op* h, const float* b, float* x) {

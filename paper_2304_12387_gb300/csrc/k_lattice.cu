@@ -200,12 +200,12 @@ __device__ __forceinline__ T stencil_res_prolong(const LevelT<T>& lv, const Leve
   int64_t XY = (int64_t)lv.X * lv.Y;
   T r = fma(-lv.diag[c], xself, bc);
   const T o = rowsum_form<T>() ? xself : (T)0;  // FP32 levels: differences (see rowsum_form)
-  if (I > 0) r = fma(lv.wx[xl], xv(I - 1, J, Z) - o, r);
-  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], xv(I + 1, J, Z) - o, r);
-  if (J > 0) r = fma(lv.wy[yl], xv(I, J - 1, Z) - o, r);
-  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], xv(I, J + 1, Z) - o, r);
-  if (Z > 0) r = fma(lv.wz[zl], xv(I, J, Z - 1) - o, r);
-  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], xv(I, J, Z + 1) - o, r);
+  if (I > 0) r = fma(lv.wx[xl], rs_diff(xv(I - 1, J, Z), o), r);
+  if (I < lv.X - 1) r = fma(lv.wx[xl + 1], rs_diff(xv(I + 1, J, Z), o), r);
+  if (J > 0) r = fma(lv.wy[yl], rs_diff(xv(I, J - 1, Z), o), r);
+  if (J < lv.Y - 1) r = fma(lv.wy[yl + lv.X], rs_diff(xv(I, J + 1, Z), o), r);
+  if (Z > 0) r = fma(lv.wz[zl], rs_diff(xv(I, J, Z - 1), o), r);
+  if (Z < lv.Z - 1) r = fma(lv.wz[zl + XY], rs_diff(xv(I, J, Z + 1), o), r);
   return r;
 }
 
@@ -691,6 +691,45 @@ void precond_free(hd_op* h) {
   h->lv.clear();
   for (auto& f : h->lvf) free_level<float>(f, true);
   h->lvf.clear();
+  for (auto& f : h->lvx) free_level<dfloat>(f, true);
+  h->lvx.clear();
+  cudaFree(h->cyc_b);
+  cudaFree(h->cyc_x);
+  h->cyc_b = h->cyc_x = nullptr;
+}
+
+// double-float copies of the unsmoothed levels (the smoothed ones: sa_setup_df), made on
+// first use by the FP64 cycle of fp64_emulation = 2
+hd_status setup_df_cycle(hd_op* h) {
+  if (!h->lvx.empty()) return HD_OK;
+  hd_status st;
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    const LevelT<double>& d = h->lv[l];
+    LevelT<dfloat> f{};
+    f.X = d.X; f.Y = d.Y; f.Z = d.Z;
+    set_agg(f, d.ag[0], d.ag[1], d.ag[2]);
+    if ((st = alloc_level<dfloat>(h, f, true)) != HD_OK) return st;
+    h->lvx.push_back(f);
+    const int64_t nxw = (int64_t)(d.X + 1) * d.Y * d.Z, nyw = (int64_t)d.X * (d.Y + 1) * d.Z,
+                  nzw = (int64_t)d.X * d.Y * (d.Z + 1);
+    k_to_f32<dfloat><<<nblk(nxw), TPB, 0, h->stream>>>(nxw, d.wx, f.wx);
+    k_to_f32<dfloat><<<nblk(nyw), TPB, 0, h->stream>>>(nyw, d.wy, f.wy);
+    k_to_f32<dfloat><<<nblk(nzw), TPB, 0, h->stream>>>(nzw, d.wz, f.wz);
+    k_to_f32<dfloat><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.mass, f.mass);
+    k_to_f32<dfloat><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.diag, f.diag);
+    k_to_f32<dfloat><<<nblk(d.n()), TPB, 0, h->stream>>>(d.n(), d.dinv, f.dinv);
+    HD_LAUNCH_CK(h, "double-float level");
+  }
+  if (cudaMalloc(&h->cyc_b, sizeof(dfloat) * (h->n_l2 > 0 ? h->n_l2 : 1)) != cudaSuccess ||
+      cudaMalloc(&h->cyc_x, sizeof(dfloat) * (h->n_l2 > 0 ? h->n_l2 : 1)) != cudaSuccess)
+    return hd_fail(h, HD_ERR_OOM, "double-float cycle vectors");
+  if (!h->st.empty() && (st = sa_setup_df(h)) != HD_OK) return st;
+  return HD_OK;
+}
+
+__global__ void k_from_df(int64_t n, const dfloat* __restrict__ a, double* __restrict__ b) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
 }
 
 hd_status schur_apply(hd_op* h, const double* x, double* y) {
@@ -702,6 +741,17 @@ hd_status schur_apply(hd_op* h, const double* x, double* y) {
 
 hd_status vcycle_apply(hd_op* h, const double* b, double* x) {
   if (h->n_l2 == 0) return HD_OK;
+  if (h->cycle_df) {  // the cycle in double-float between FP64 vectors
+    hd_status st = setup_df_cycle(h);
+    if (st != HD_OK) return st;
+    const int64_t n = h->n_l2;
+    k_to_f32<dfloat><<<nblk(n), TPB, 0, h->stream>>>(n, b, h->cyc_b);
+    st = !h->st.empty() ? sa_vcycle_df(h, h->cyc_b, h->cyc_x) : vcycle_graphed<dfloat>(h, h->lvx, h->cyc_b, h->cyc_x, 5);
+    if (st != HD_OK) return st;
+    k_from_df<<<nblk(n), TPB, 0, h->stream>>>(n, h->cyc_x, x);
+    HD_LAUNCH_CK(h, "double-float cycle");
+    return HD_OK;
+  }
   if (!h->st.empty()) return sa_vcycle(h, b, x);
   return vcycle_graphed<double>(h, h->lv, b, x, 0);
 }

@@ -15,6 +15,13 @@ namespace {
 // differences, the small part is exact to FP32 rounding.
 template <typename T>
 constexpr bool rowsum_form() { return sizeof(T) == 4; }
+// x - o on the row-sum levels; x on the others, where o is zero (a double-float
+// subtraction of zero would still cost a full TwoSum)
+template <typename T>
+__device__ __forceinline__ T rs_diff(T x, T o) {
+  if constexpr (rowsum_form<T>()) return x - o;
+  else return x;
+}
 
 // residual b - S x at cell (I,J,Z) given the x value there (FP32 levels: diag holds the
 // row sum, see rowsum_form)
