@@ -589,6 +589,108 @@ hd_status hd_massinv_setup_ms(hd_massinv_handle h, double* ms);
 hd_status hd_massinv_iterations(hd_massinv_handle h, int32_t* its);
 hd_status hd_massinv_destroy(hd_massinv_handle h);
 
+/* -- grey nonlinear radiation diffusion (Sec. 4.3) ----------------------------------- */
+/* The time integrator and nonlinear iteration that drive repeated Darcy solves. Model
+ * (Eq. rad-diff-e, rad-diff-E, rad-diff-F), with T = e / Cv:
+ *   rho de/dt = -c sigma (a T^4 - E) + Q,   dE/dt + div F = c sigma (a T^4 - E) + S,
+ *   F = -(c / (3 sigma)) grad E,            F.n = 0 on every side (reflecting walls).
+ * e and E lie in the L2 space (k^3 histopolation DOFs per element), and F lies in RT_k.
+ * The opacity sigma is constant on each element; rho, Cv, a and c are constants.
+ * E is carried as Eh = W E (W the L2 mass), the transformed L2 unknown of Eq.
+ * transformed-system-darcy up to its sign.
+ * Time stepping: Alexander's three-stage, L-stable, stiffly accurate SDIRK method. A
+ * stage with beta = 1 / (dt a_ii), stage-start values (e*, Eh*) and source loads
+ * Q_j = (Q, psi_j), S_j = (S, psi_j) solves
+ *   R1 = rho beta W (e - e*) + c sigma (a N(e) - Eh) - Q      = 0
+ *   R2 = beta (Eh - Eh*) + W D F - c sigma (a N(e) - Eh) - S  = 0
+ *   R3 = M_{3 sigma/c} F - D^T Eh                              = 0   (essential rows: F)
+ * with N(e)_j = (T(e)^4, psi_j) by the q^3 Gauss rule and D the lattice divergence.
+ * The stage iteration follows Sec. 4.3, with two steps per pass:
+ *   (1) F lagged: element-wise Newton on (R1, R2) for (e, Eh). Each Newton system is
+ *       solved exactly by eliminating Eh (its block is (beta + c sigma) I). That leaves
+ *       the SPD weighted mass (rho beta W + c sigma a theta N'(e)), theta = beta /
+ *       (beta + c sigma), solved by Jacobi-preconditioned CG in the Gauss-Legendre
+ *       nodal basis (Sec. 2.5). The step stops per element once ||(R1_e, R2_e)|| falls to
+ *       newton_rtol times its first value, or to 1e-14 times ||(rho beta W e_e,
+ *       beta Eh_e)||.
+ *   (2) e fixed: the Darcy system of Eq. transformed-system-darcy, with eps = c /
+ *       (3 sigma), gamma = beta + c sigma, x = [F; -Eh] and right-hand side
+ *       [0; W^-1 (S + c sigma a N(e) + beta Eh*)]. It is solved by the handle's MINRES and
+ *       block preconditioner, warm-started, to linear_rtol.
+ * Passes repeat until ||(R1, R2, R3)||_2 <= outer_rtol times its value at the stage's
+ * initial guess, or until it no longer halves (its rounding floor). Every stage of every
+ * step shares one Darcy operator, because a_ii is the same for all three stages.
+ * The handle owns the Darcy operator (hd_rad_get_op) and its own device data.
+ * Vectors are device FP64, in the lattice order of the block operator: n_l2 for e, Eh
+ * and loads, n_rt for F, [E][q^3] for point values. Calls run on the handle's stream;
+ * the stage and step calls synchronise it. */
+typedef struct hd_rad* hd_rad_handle;
+typedef struct {
+  hd_problem_desc mesh;  /* nx, ny, nz, k, q, vx, vy, vz and the solver options of the Darcy
+                            operator (tau, winv_mode, nu, coarse_max, cycle, fp64_emulation,
+                            smooth_levels, w_levels, aggregation). kind, coef0, coef1, ess_mask,
+                            affine and elem_rotation are ignored: hd_rad_create sets them */
+  const double* sigma;   /* host, per element opacity > 0 */
+  double rho, cv, a, c;  /* density, specific heat, radiation constant, speed of light; > 0 */
+  double dt;             /* time step > 0 */
+  double outer_rtol;     /* stage tolerance; 0 -> 1e-12 */
+  int32_t outer_maxit;   /* passes per stage; 0 -> 10 */
+  double newton_rtol;    /* 0 -> 1e-8 */
+  int32_t newton_maxit;  /* Newton steps per pass; 0 -> 30 */
+  double linear_rtol;    /* MINRES tolerance (on eta_j / eta_0); 0 -> 1e-8 */
+  int32_t linear_maxit;  /* 0 -> 20000 */
+} hd_rad_desc;
+typedef struct {
+  int32_t stages;            /* stages solved by the call */
+  int32_t outer;             /* passes, summed over the stages */
+  int32_t outer_max;         /* most passes of one stage */
+  int32_t newton_max;        /* most Newton steps of one element in one pass */
+  int32_t linear_solves;
+  int32_t linear_iterations; /* MINRES iterations, summed */
+  double relres;             /* largest final ||R|| / ||R_0|| over the stages */
+  double ms_newton;          /* device time of step (1), with the Darcy right-hand side */
+  double ms_linear;          /* device time of step (2) */
+  double ms_residual;        /* device time of the residual norms */
+  hd_status status;
+} hd_rad_info;
+/* Builds the Darcy operator (hd_create), the point weights and the work vectors, and
+ * synchronises. Errors: HD_ERR_INVALID_ARG (mesh as in hd_create, sigma or a constant
+ * <= 0, dt <= 0, det J <= 0 at a point), HD_ERR_OOM, HD_ERR_CUDA. */
+hd_status hd_rad_create(const hd_rad_desc* desc, hd_rad_handle* out);
+hd_status hd_rad_destroy(hd_rad_handle h);
+/* stream: a cudaStream_t (NULL = legacy default stream); also set on the Darcy operator. */
+hd_status hd_rad_set_stream(hd_rad_handle h, void* stream);
+/* The message of the last error on this handle ("" if none). */
+const char* hd_rad_last_error(hd_rad_handle h);
+/* Sizes: RT and L2 DOFs, elements, Gauss points per direction. */
+hd_status hd_rad_get_sizes(hd_rad_handle h, int64_t* n_rt, int64_t* n_l2, int64_t* n_elem, int32_t* q);
+/* The Darcy operator of the handle (owned by it; valid until hd_rad_destroy). */
+hd_status hd_rad_get_op(hd_rad_handle h, hd_handle* op);
+/* Host: physical coordinates of the Gauss points, [E][q^3][3] doubles, point p = p1 +
+ * q (p2 + q p3) of element e = ex + nx (ey + ny ez); for sampling sources and fields. */
+hd_status hd_rad_points(hd_rad_handle h, double* xyz);
+/* load_j = (v, psi_j) = sum_p w_p v_p psi_j(xi_p) from point values v ([E][q^3]). */
+hd_status hd_rad_load(hd_rad_handle h, const double* values, double* load);
+/* y = W^-1 x (per element CG in the Gauss-Legendre basis to a relative residual of 1e-14);
+ * E = W^-1 Eh, or the L2 projection of a field as hd_rad_winv(hd_rad_load(values)). */
+hd_status hd_rad_winv(hd_rad_handle h, const double* x, double* y);
+/* The stage residual at (e, Eh, F): r = [R1; R2; R3] (2 n_l2 + n_rt, device; may be NULL)
+ * and ||r||_2 (host; may be NULL). Loads may be NULL (zero). Synchronises. */
+hd_status hd_rad_residual(hd_rad_handle h, const double* e_star, const double* Eh_star, const double* q_load,
+                          const double* s_load, const double* e, const double* Eh, const double* F, double* r,
+                          double* norm);
+/* One stage: (e, Eh, F) hold the initial guess and receive the solution. Loads may be
+ * NULL. Errors: HD_ERR_NOT_CONVERGED (outer_maxit passes without reaching outer_rtol or
+ * the rounding floor; the last iterate is kept), HD_ERR_NAN (a Newton system not
+ * positive definite, or a non-finite residual), and those of hd_minres_solve. */
+hd_status hd_rad_stage(hd_rad_handle h, const double* e_star, const double* Eh_star, const double* q_load,
+                       const double* s_load, double* e, double* Eh, double* F, hd_rad_info* info);
+/* One SDIRK step of size dt from (e, Eh, F), in place. q_loads and s_loads: NULL (no
+ * sources), or the loads at the three stage times t + c_i dt, [3][n_l2] each, with
+ * c = (gamma, (1 + gamma) / 2, 1). The flux F of each stage starts from the previous one. */
+hd_status hd_rad_step(hd_rad_handle h, double* e, double* Eh, double* F, const double* q_loads,
+                      const double* s_loads, hd_rad_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,21 @@ class MassInvDesc(ctypes.Structure):
                 ("fp64_emulation", ctypes.c_int32)]
 
 
+class RadDesc(ctypes.Structure):
+    _fields_ = [("mesh", ProblemDesc), ("sigma", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.c_double),
+                ("cv", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double), ("dt", ctypes.c_double),
+                ("outer_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
+                ("newton_maxit", ctypes.c_int32), ("linear_rtol", ctypes.c_double),
+                ("linear_maxit", ctypes.c_int32)]
+
+
+class RadInfo(ctypes.Structure):
+    _fields_ = [("stages", ctypes.c_int32), ("outer", ctypes.c_int32), ("outer_max", ctypes.c_int32),
+                ("newton_max", ctypes.c_int32), ("linear_solves", ctypes.c_int32),
+                ("linear_iterations", ctypes.c_int32), ("relres", ctypes.c_double), ("ms_newton", ctypes.c_double),
+                ("ms_linear", ctypes.c_double), ("ms_residual", ctypes.c_double), ("status", ctypes.c_int32)]
+
+
 class Slab(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int32), ("P", ctypes.c_int32), ("ez0", ctypes.c_int32), ("ez1", ctypes.c_int32),
                 ("xf", ctypes.c_int64 * 2), ("yf", ctypes.c_int64 * 2), ("zf", ctypes.c_int64 * 2),
@@ -149,6 +164,18 @@ _SIGS = {
     "hd_massinv_setup_ms": [_H, ctypes.POINTER(ctypes.c_double)],
     "hd_massinv_iterations": [_H, ctypes.POINTER(ctypes.c_int32)],
     "hd_massinv_destroy": [_H],
+    "hd_rad_create": [ctypes.POINTER(RadDesc), ctypes.POINTER(ctypes.c_void_p)],
+    "hd_rad_destroy": [_H],
+    "hd_rad_set_stream": [_H, _VP],
+    "hd_rad_get_sizes": [_H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                         ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
+    "hd_rad_get_op": [_H, ctypes.POINTER(ctypes.c_void_p)],
+    "hd_rad_points": [_H, _VP],
+    "hd_rad_load": [_H, _VP, _VP],
+    "hd_rad_winv": [_H, _VP, _VP],
+    "hd_rad_residual": [_H, _VP, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double)],
+    "hd_rad_stage": [_H, _VP, _VP, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(RadInfo)],
+    "hd_rad_step": [_H, _VP, _VP, _VP, _VP, _VP, ctypes.POINTER(RadInfo)],
 }
 
 
@@ -165,6 +192,8 @@ def lib():
             f.restype = ctypes.c_int32
         L.hd_last_error.argtypes = [_H]
         L.hd_last_error.restype = ctypes.c_char_p
+        L.hd_rad_last_error.argtypes = [_H]
+        L.hd_rad_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -524,6 +553,93 @@ class MassInverse:
     def close(self):
         if self.h:
             lib().hd_massinv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _rad_info(i):
+    return {f: getattr(i, f) for f, _ in RadInfo._fields_}
+
+
+class RadDiff:
+    """Grey nonlinear radiation diffusion (hd_rad_*, Sec. 4.3) on a structured hex mesh with
+    reflecting walls: the SDIRK3 stages, the outer iteration of element-wise Newton and
+    Darcy solves. Vectors are torch CUDA float64 tensors: e, Eh and loads n_l2, F n_rt,
+    point values [E][q^3]."""
+
+    def __init__(self, nx, ny, nz, k, vx, vy, vz, sigma, dt, rho=1.0, cv=1.0, a=1.0, c=1.0, q=0, cycle=2,
+                 smooth_levels=2, fp64_emulation=1, aggregation=0, outer_rtol=0.0, outer_maxit=0,
+                 newton_rtol=0.0, newton_maxit=0, linear_rtol=0.0, linear_maxit=0, stream=None):
+        E = nx * ny * nz
+        self._keep = []
+        ptrs = []
+        for arr in (vx, vy, vz):
+            arr, pa = _dptr(arr)
+            self._keep.append(arr)
+            ptrs.append(pa)
+        sg, psg = _dptr(np.broadcast_to(np.asarray(sigma, dtype=np.float64), (E,)))
+        self._keep.append(sg)
+        mesh = ProblemDesc(HD_DARCY, nx, ny, nz, k, q, ptrs[0], ptrs[1], ptrs[2], None, None, 0, 0, 0.0,
+                           HD_WINV_DENSE, 0, 0, cycle, int(fp64_emulation), int(smooth_levels), 0, None,
+                           int(aggregation))
+        d = RadDesc(mesh, psg, rho, cv, a, c, dt, outer_rtol, outer_maxit, newton_rtol, newton_maxit, linear_rtol,
+                    linear_maxit)
+        h = ctypes.c_void_p()
+        _check(lib().hd_rad_create(ctypes.byref(d), ctypes.byref(h)))
+        self.h = h
+        nrt, nl2, ne, qq = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        self._call("hd_rad_get_sizes", ctypes.byref(nrt), ctypes.byref(nl2), ctypes.byref(ne), ctypes.byref(qq))
+        self.n_rt, self.n_l2, self.n_elem, self.q = nrt.value, nl2.value, ne.value, qq.value
+        self.k, self.dims = k, (nx, ny, nz)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _call(self, name, *args):
+        st = getattr(lib(), name)(self.h, *args)
+        if st != HD_OK:
+            raise HdError(st, lib().hd_rad_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        s = getattr(stream, "cuda_stream", stream)
+        self._call("hd_rad_set_stream", ctypes.c_void_p(s))
+
+    def points(self):
+        """Physical coordinates of the Gauss points (E, q^3, 3), host numpy."""
+        out = np.zeros((self.n_elem, self.q ** 3, 3))
+        self._call("hd_rad_points", out.ctypes.data)
+        return out
+
+    def load(self, values, out):
+        self._call("hd_rad_load", _ptr(values), _ptr(out))
+
+    def winv(self, x, y):
+        self._call("hd_rad_winv", _ptr(x), _ptr(y))
+
+    def residual(self, e_star, Eh_star, q_load, s_load, e, Eh, F, r=None):
+        v = ctypes.c_double()
+        self._call("hd_rad_residual", *[_ptr(t) for t in (e_star, Eh_star, q_load, s_load, e, Eh, F, r)],
+                   ctypes.byref(v))
+        return v.value
+
+    def stage(self, e_star, Eh_star, q_load, s_load, e, Eh, F):
+        info = RadInfo()
+        self._call("hd_rad_stage", *[_ptr(t) for t in (e_star, Eh_star, q_load, s_load, e, Eh, F)],
+                   ctypes.byref(info))
+        return _rad_info(info)
+
+    def step(self, e, Eh, F, q_loads=None, s_loads=None):
+        info = RadInfo()
+        self._call("hd_rad_step", *[_ptr(t) for t in (e, Eh, F, q_loads, s_loads)], ctypes.byref(info))
+        return _rad_info(info)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().hd_rad_destroy(self.h)
             self.h = None
 
     def __del__(self):

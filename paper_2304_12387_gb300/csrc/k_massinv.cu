@@ -14,6 +14,7 @@
 
 #include "dfloat.cuh"
 #include "hd_internal.h"
+#include "k_l2elem.cuh"
 
 #define MI_MAXK 9
 #define MI_MAXQ 12
@@ -56,17 +57,6 @@ namespace {
 
 constexpr int MI_THREADS = 256;
 constexpr int TILE = 32;
-
-__device__ __forceinline__ double block_sum(double v, double* red) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  for (int i = 0; i < nw; ++i) s += red[i];
-  return s;
-}
 
 // w_p alpha_e / det J(xi_p) on the trilinear element, one thread per (element, point)
 __global__ void k_mi_geom(int64_t E, int nx, int ny, MiTab t, const double* __restrict__ vx,
@@ -123,13 +113,6 @@ __global__ void k_mi_diag(int64_t E, MiTab t, const double* __restrict__ wdet, d
   diag[g] = s;
 }
 
-// global lattice index of element-local cell a of element e
-__device__ __forceinline__ int64_t mi_cell(int64_t e, int a, int k, int nx, int ny) {
-  const int64_t ex = e % nx, ey = (e / nx) % ny, ez = e / ((int64_t)nx * ny);
-  const int a1 = a % k, a2 = (a / k) % k, a3 = a / (k * k);
-  const int64_t X = (int64_t)nx * k, Y = (int64_t)ny * k;
-  return (ex * k + a1) + X * ((ey * k + a2) + Y * (ez * k + a3));
-}
 
 // ---- fused per-element CG (Sec. 2.5, 3.1) ----------------------------------------------
 // The stages run in T: FP64, or double-float (pairs of FP32 numbers on the FP32 pipe, about
@@ -144,84 +127,7 @@ __device__ __forceinline__ double mi_t<double>(double v) { return v; }
 template <>
 __device__ __forceinline__ dfloat mi_t<dfloat>(double v) { return df_from_double(v); }
 
-// out = (M x M x M) in with M(j, m) = TT[j k + m] (tr = true: the transpose TT^T acting on
-// histopolation data) or TT[m k + j] (tr = false: TT acting on GL nodal data); u, v scratch
-template <typename T>
-__device__ void mi_tt3(int k, const T* TT, bool tr, const T* in, T* u, T* v, T* out) {
-  const int n = k * k * k;
-  auto M = [&](int j, int m) { return tr ? TT[j * k + m] : TT[m * k + j]; };
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int m1 = i % k, r = i / k;
-    T s = T(0);
-    for (int j = 0; j < k; ++j) s = fma(M(j, m1), in[j + k * r], s);
-    u[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int m1 = i % k, m2 = (i / k) % k, j3 = i / (k * k);
-    T s = T(0);
-    for (int j = 0; j < k; ++j) s = fma(M(j, m2), u[m1 + k * (j + k * j3)], s);
-    v[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int r = i % (k * k), m3 = i / (k * k);
-    T s = T(0);
-    for (int j = 0; j < k; ++j) s = fma(M(j, m3), v[r + k * k * j], s);
-    out[i] = s;
-  }
-  __syncthreads();
-}
 
-// w = W_e p by sum factorisation: B (q x k) to the points along x, y, z, the point
-// weights, and back (T1: q k k, T2: q q k, T3: q^3 values)
-template <typename T>
-__device__ void mi_apply_w(int k, int q, const T* B, const T* __restrict__ wd, const T* P, T* W, T* T1, T* T2,
-                           T* T3) {
-  const int kk = k * k, qq = q * q;
-  for (int i = threadIdx.x; i < q * kk; i += blockDim.x) {  // T1[p1 + q r], r = a2 + k a3
-    const int p1 = i % q, r = i / q;
-    T s = T(0);
-    for (int a = 0; a < k; ++a) s = fma(B[p1 * k + a], P[a + k * r], s);
-    T1[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < qq * k; i += blockDim.x) {  // T2[p1 + q (p2 + q a3)]
-    const int p1 = i % q, p2 = (i / q) % q, a3 = i / qq;
-    T s = T(0);
-    for (int a = 0; a < k; ++a) s = fma(B[p2 * k + a], T1[p1 + q * (a + k * a3)], s);
-    T2[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < qq * q; i += blockDim.x) {  // T3[p], scaled by the point weight
-    const int r = i % qq, p3 = i / qq;
-    T s = T(0);
-    for (int a = 0; a < k; ++a) s = fma(B[p3 * k + a], T2[r + qq * a], s);
-    T3[i] = s * wd[i];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < qq * k; i += blockDim.x) {  // back along z
-    const int r = i % qq, a3 = i / qq;
-    T s = T(0);
-    for (int p = 0; p < q; ++p) s = fma(B[p * k + a3], T3[r + qq * p], s);
-    T2[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < q * kk; i += blockDim.x) {  // back along y
-    const int p1 = i % q, a2 = (i / q) % k, a3 = i / (q * k);
-    T s = T(0);
-    for (int p = 0; p < q; ++p) s = fma(B[p * k + a2], T2[p1 + q * (p + q * a3)], s);
-    T1[i] = s;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < kk * k; i += blockDim.x) {  // back along x
-    const int a1 = i % k, r = i / k;
-    T s = T(0);
-    for (int p = 0; p < q; ++p) s = fma(B[p * k + a1], T1[p + q * r], s);
-    W[i] = s;
-  }
-  __syncthreads();
-}
 
 // one CTA per element: y_e = W_e^-1 x_e by Jacobi-preconditioned CG from zero, in the
 // GL nodal basis (glb: right-hand side TT^T x, result TT a) or the histopolation basis

@@ -23,6 +23,8 @@ STRUCTS = {
     "hd_train_info": hd.TrainInfo,
     "hd_slab": hd.Slab,
     "hd_massinv_desc": hd.MassInvDesc,
+    "hd_rad_desc": hd.RadDesc,
+    "hd_rad_info": hd.RadInfo,
 }
 
 
