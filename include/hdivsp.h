@@ -618,7 +618,8 @@ hd_status hd_massinv_destroy(hd_massinv_handle h);
  *       [0; W^-1 (S + c sigma a N(e) + beta Eh*)]. It is solved by the handle's MINRES and
  *       block preconditioner, warm-started, to linear_rtol.
  * Passes repeat until ||(R1, R2, R3)||_2 <= outer_rtol times its value at the stage's
- * initial guess, or until it no longer halves (its rounding floor). Every stage of every
+ * initial guess, or until, already below 1e3 outer_rtol times that value, it no longer
+ * halves (its rounding floor). Every stage of every
  * step shares one Darcy operator, because a_ii is the same for all three stages.
  * The handle owns the Darcy operator (hd_rad_get_op) and its own device data.
  * Vectors are device FP64, in the lattice order of the block operator: n_l2 for e, Eh

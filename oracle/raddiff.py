@@ -34,8 +34,8 @@ Then e is fixed and (R2, R3) are solved for (Eh, F). That is the Darcy system of
 transformed-system-darcy with eps = c / (3 sigma), gamma = beta + c sigma, x = [F; -Eh]
 and right-hand side [0; W^-1 G], where G = S + c sigma a N(e) + beta Eh*. The two steps
 repeat until ||(R1, R2, R3)|| <= outer_rtol times its value at the stage's initial guess,
-or until the residual no longer halves from one pass to the next (its rounding floor,
-which lies above 1e-12 on finer meshes). The Newton solve stops per element once
+or until the residual, already below 1e3 outer_rtol times that value, no longer halves
+from one pass to the next (its rounding floor, which lies above 1e-12 on finer meshes). The Newton solve stops per element once
 ||(R1_e, R2_e)|| <= newton_rtol times its first value, or <= 1e-14 times the size of the
 element's leading terms ||(rho beta W e_e, beta Eh_e)|| (the rounding floor: later passes
 start close to it). Here the Newton systems are solved densely and the Darcy system
@@ -194,7 +194,7 @@ class RadDiff:
             info["outer"] = m + 1
             info["newton_max"] = max(info["newton_max"], s)
             info["relres"] = r / r0
-            if r <= outer_rtol * r0 or r > 0.5 * r_prev:
+            if r <= outer_rtol * r0 or (r > 0.5 * r_prev and r <= 1e3 * outer_rtol * r0):
                 break
             r_prev = r
         return e, Eh, F, info
