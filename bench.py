@@ -39,8 +39,8 @@ FP64_PEAK_GFLOPS_AT_MAX_CLOCK = 152 * 2 * 2 * 2.070
 DF_PEAK_FP64_EQUIV_GFLOPS = 2 * 2471.0
 # DRAM bytes (read + write) per element of the element kernel, from one ncu capture of the 24^3
 # case of the same recipe (13,824 elements); to be dropped when the kernel changes
-ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 674.110208e6 / 13824,   # FP64 kernel
-                                  (4, 6, "df"): 673.752320e6 / 13824}    # double-float kernel
+ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 673.985024e6 / 13824,   # FP64 kernel
+                                  (4, 6, "df"): 674.652672e6 / 13824}    # double-float kernel
 
 
 def _measured_hbm_gbs(default=6792.4):

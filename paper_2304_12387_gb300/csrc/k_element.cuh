@@ -524,6 +524,15 @@ struct ElemCfg<float, false> {
 // the buffer's mbarrier), the first two before the gather; the rows' threads then
 // read W from shared memory instead of waiting on HBM loads. Needs an even NL2 (the
 // per-element blocks and chunks start on 16-byte boundaries) and one thread per row.
+// The W_e^-1 rows read from global memory (one thread per row): the unrolled batch sets the
+// loads in flight per thread. Measured at 64^3, k = 4 (double-float kernel): 8 -> 3.69 ms,
+// 16 -> 3.60, 32 -> 3.58, 64 -> 3.67; two or four partial sums per row instead of one
+// chain: 3.93 and 4.30 ms (the chain is not the limit, the load latency is).
+#ifndef HD_WINV_UNROLL
+#define HD_WINV_UNROLL 32
+#endif
+constexpr int kWinvUnroll = HD_WINV_UNROLL;
+
 #ifndef HD_DF_STAGE
 #define HD_DF_STAGE 0
 #endif
@@ -677,7 +686,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         const T* qe = sq + el * NL2;
         Acc<T> acc;
         acc.init(W[a], qe[0]);
-#pragma unroll 8
+#pragma unroll kWinvUnroll
         for (int b = 1; b < NL2; ++b) acc.add(W[b * NL2 + a], qe[b]);
         s = acc.get();
       }
