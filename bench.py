@@ -40,7 +40,7 @@ DF_PEAK_FP64_EQUIV_GFLOPS = 2 * 2471.0
 # DRAM bytes (read + write) per element of the element kernel, from one ncu capture of the 24^3
 # case of the same recipe (13,824 elements); to be dropped when the kernel changes
 ELEM_TRAFFIC_BYTES_PER_ELEMENT = {(4, 6, "f64"): 673.985024e6 / 13824,   # FP64 kernel
-                                  (4, 6, "df"): 674.652672e6 / 13824}    # double-float kernel
+                                  (4, 6, "df"): 674.329088e6 / 13824}    # double-float kernel
 
 
 def _measured_hbm_gbs(default=6792.4):

@@ -500,30 +500,30 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 #ifndef HD_DFA_THREADS
 #define HD_DFA_THREADS 512
 #endif
+// POINTS: quadrature points per thread and pass of the pointwise stage, whose geometric
+// factors are all loaded before any is used (more loads in flight). Double-float kernel at
+// 64^3, k = 4: 1 -> 3.58 ms, 3 -> 3.44, 4 -> 3.48 (two, written as a pair of named points:
+// 3.44; as the loop below: 3.79, where the compiler kept fewer loads in flight).
+#ifndef HD_DF_POINTS
+#define HD_DF_POINTS 3
+#endif
 template <typename T, bool AFF = false>
 struct ElemCfg {
-  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH;
+  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH, POINTS = 1;
 };
 template <>
 struct ElemCfg<dfloat, false> {
-  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH;
+  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH, POINTS = HD_DF_POINTS;
 };
 template <>
 struct ElemCfg<dfloat, true> {  // the affine fast path (no per-element arrays to stream)
-  static constexpr int EB = HD_DFA_EB, THREADS = HD_DFA_THREADS, PREFETCH = 0;
+  static constexpr int EB = HD_DFA_EB, THREADS = HD_DFA_THREADS, PREFETCH = 0, POINTS = 1;
 };
 template <>
 struct ElemCfg<float, false> {
-  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH;
+  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH, POINTS = 1;
 };
 
-// Staging of the dense W_e^-1 rows by the copy engine (double-float kernel): the
-// sum-factorisation buffers T1/T2 are idle while the L2 rows are computed, so they
-// hold two buffers of NB rows of W_e^-1 for each element of the CTA. One thread asks
-// for a chunk with one bulk copy per element (cp.async.bulk, completion counted on
-// the buffer's mbarrier), the first two before the gather; the rows' threads then
-// read W from shared memory instead of waiting on HBM loads. Needs an even NL2 (the
-// per-element blocks and chunks start on 16-byte boundaries) and one thread per row.
 // The W_e^-1 rows read from global memory (one thread per row): the unrolled batch sets the
 // loads in flight per thread. Measured at 64^3, k = 4 (double-float kernel): 8 -> 3.69 ms,
 // 16 -> 3.60, 32 -> 3.58, 64 -> 3.67; two or four partial sums per row instead of one
@@ -533,6 +533,13 @@ struct ElemCfg<float, false> {
 #endif
 constexpr int kWinvUnroll = HD_WINV_UNROLL;
 
+// Staging of the dense W_e^-1 rows by the copy engine (double-float kernel): the
+// sum-factorisation buffers T1/T2 are idle while the L2 rows are computed, so they
+// hold two buffers of NB rows of W_e^-1 for each element of the CTA. One thread asks
+// for a chunk with one bulk copy per element (cp.async.bulk, completion counted on
+// the buffer's mbarrier), the first two before the gather; the rows' threads then
+// read W from shared memory instead of waiting on HBM loads. Needs an even NL2 (the
+// per-element blocks and chunks start on 16-byte boundaries) and one thread per row.
 #ifndef HD_DF_STAGE
 #define HD_DF_STAGE 0
 #endif
@@ -798,29 +805,62 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
     }
     __syncthreads();
     // -- pointwise: v = G u --------------------------------------------------------
-    for (int t = tid; t < EB * NQ; t += nth) {
-      int el = t / NQ, p = t - el * NQ, e = e0 + el;
-      if (e >= n_elem) continue;
-      T g00, g01, g02, g11, g12, g22;
-      T* U = s1 + el * S::R1 + p;
-      T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
-      if constexpr (AFF) {
-        const T* g = Ga + (size_t)e * 8;
-        g00 = g[0]; g01 = g[1]; g02 = g[2]; g11 = g[3]; g12 = g[4]; g22 = g[5];
-        const int px = p % Q, py = (p / Q) % Q, pz = p / (Q * Q);
-        const T w = tab.GW[px] * tab.GW[py] * tab.GW[pz];
-        ux = ux * w; uy = uy * w; uz = uz * w;
-      } else {
-        const T* g = G + (size_t)e * 6 * NQ + p;
-        g00 = g[0]; g01 = g[NQ]; g02 = g[2 * NQ]; g11 = g[3 * NQ]; g12 = g[4 * NQ]; g22 = g[5 * NQ];
+    // NPT points per pass (see ElemCfg); from k = 4 on, where shared memory already keeps
+    // two CTAs per SM and the extra registers cost no occupancy
+    if constexpr (!AFF && ElemCfg<T, AFF>::POINTS > 1 && K >= 4) {
+      constexpr int NPT = ElemCfg<T, AFF>::POINTS;
+      auto point = [&](T* U, const T* gg) {
+        const T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
+        Acc<T> v0, v1, v2;
+        v0.init(gg[2], uz); v0.add(gg[1], uy); v0.add(gg[0], ux);
+        v1.init(gg[4], uz); v1.add(gg[3], uy); v1.add(gg[1], ux);
+        v2.init(gg[5], uz); v2.add(gg[4], uy); v2.add(gg[2], ux);
+        U[0] = v0.get();
+        U[NQ] = v1.get();
+        U[2 * NQ] = v2.get();
+      };
+      for (int t = tid; t < EB * NQ; t += NPT * nth) {
+        T gv[NPT][6];
+        int off[NPT];
+        bool okv[NPT];
+#pragma unroll
+        for (int j = 0; j < NPT; ++j) {
+          const int tj = t + j * nth, el = tj / NQ, p = tj - el * NQ, e = e0 + el;
+          okv[j] = tj < EB * NQ && e < n_elem;
+          off[j] = el * S::R1 + p;
+          const T* g = G + (size_t)(okv[j] ? e : 0) * 6 * NQ + (okv[j] ? p : 0);
+#pragma unroll
+          for (int c = 0; c < 6; ++c) gv[j][c] = g[c * NQ];
+        }
+#pragma unroll
+        for (int j = 0; j < NPT; ++j)
+          if (okv[j]) point(s1 + off[j], gv[j]);
       }
-      Acc<T> v0, v1, v2;
-      v0.init(g02, uz); v0.add(g01, uy); v0.add(g00, ux);
-      v1.init(g12, uz); v1.add(g11, uy); v1.add(g01, ux);
-      v2.init(g22, uz); v2.add(g12, uy); v2.add(g02, ux);
-      U[0] = v0.get();
-      U[NQ] = v1.get();
-      U[2 * NQ] = v2.get();
+    } else {
+      for (int t = tid; t < EB * NQ; t += nth) {
+        int el = t / NQ, p = t - el * NQ, e = e0 + el;
+        if (e >= n_elem) continue;
+        T g00, g01, g02, g11, g12, g22;
+        T* U = s1 + el * S::R1 + p;
+        T ux = U[0], uy = U[NQ], uz = U[2 * NQ];
+        if constexpr (AFF) {
+          const T* g = Ga + (size_t)e * 8;
+          g00 = g[0]; g01 = g[1]; g02 = g[2]; g11 = g[3]; g12 = g[4]; g22 = g[5];
+          const int px = p % Q, py = (p / Q) % Q, pz = p / (Q * Q);
+          const T w = tab.GW[px] * tab.GW[py] * tab.GW[pz];
+          ux = ux * w; uy = uy * w; uz = uz * w;
+        } else {
+          const T* g = G + (size_t)e * 6 * NQ + p;
+          g00 = g[0]; g01 = g[NQ]; g02 = g[2 * NQ]; g11 = g[3 * NQ]; g12 = g[4 * NQ]; g22 = g[5 * NQ];
+        }
+        Acc<T> v0, v1, v2;
+        v0.init(g02, uz); v0.add(g01, uy); v0.add(g00, ux);
+        v1.init(g12, uz); v1.add(g11, uy); v1.add(g01, ux);
+        v2.init(g22, uz); v2.add(g12, uy); v2.add(g02, ux);
+        U[0] = v0.get();
+        U[NQ] = v1.get();
+        U[2 * NQ] = v2.get();
+      }
     }
     __syncthreads();
     // -- transposed interpolation: stage C^T (z) -------------------------------
