@@ -503,10 +503,13 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 // POINTS: quadrature points per thread and pass of the pointwise stage, whose geometric
 // factors are all loaded before any is used (more loads in flight). Double-float kernel at
 // 64^3, k = 4: 1 -> 3.58 ms, 3 -> 3.44, 4 -> 3.48 (two, written as a pair of named points:
-// 3.44; as the loop below: 3.79, where the compiler kept fewer loads in flight).
+// 3.44; as the loop below: 3.79, where the compiler kept fewer loads in flight). The same
+// batching of the gather of u (3 or 5 loads per pass) measured 3.46 ms, and 1.55 against
+// 1.46 ms for the FP32 kernel: not kept.
 #ifndef HD_DF_POINTS
 #define HD_DF_POINTS 3
 #endif
+
 template <typename T, bool AFF = false>
 struct ElemCfg {
   static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH, POINTS = 1;
