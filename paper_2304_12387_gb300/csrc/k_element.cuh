@@ -500,6 +500,14 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 #ifndef HD_DFA_THREADS
 #define HD_DFA_THREADS 512
 #endif
+// The W_e^-1 rows read from global memory (one thread per row): the unrolled batch sets the
+// loads in flight per thread (ElemCfg::WINV_UNROLL). Measured at 64^3, k = 4: double-float
+// kernel 8 -> 3.69 ms, 16 -> 3.60, 32 -> 3.58, 64 -> 3.67; two or four partial sums per row
+// instead of one chain: 3.93 and 4.30 ms (the chain is not the limit, the load latency is).
+// The FP32 kernel, bound by HBM, keeps 8 (1.44 ms, 1.46 with 32); FP64 is the same either way.
+#ifndef HD_WINV_UNROLL
+#define HD_WINV_UNROLL 32
+#endif
 // POINTS: quadrature points per thread and pass of the pointwise stage, whose geometric
 // factors are all loaded before any is used (more loads in flight). Double-float kernel at
 // 64^3, k = 4: 1 -> 3.58 ms, 3 -> 3.44, 4 -> 3.48 (two, written as a pair of named points:
@@ -512,29 +520,23 @@ __device__ T* local_chol(const T* __restrict__ Lg, const T* sq, T* s1, int s1str
 
 template <typename T, bool AFF = false>
 struct ElemCfg {
-  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH, POINTS = 1;
+  static constexpr int EB = HD_F64_EB, THREADS = HD_F64_THREADS, PREFETCH = HD_F64_PREFETCH, POINTS = 1,
+                       WINV_UNROLL = HD_WINV_UNROLL;
 };
 template <>
 struct ElemCfg<dfloat, false> {
-  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH, POINTS = HD_DF_POINTS;
+  static constexpr int EB = HD_DF_EB, THREADS = HD_DF_THREADS, PREFETCH = HD_DF_PREFETCH, POINTS = HD_DF_POINTS,
+                       WINV_UNROLL = HD_WINV_UNROLL;
 };
 template <>
 struct ElemCfg<dfloat, true> {  // the affine fast path (no per-element arrays to stream)
-  static constexpr int EB = HD_DFA_EB, THREADS = HD_DFA_THREADS, PREFETCH = 0, POINTS = 1;
+  static constexpr int EB = HD_DFA_EB, THREADS = HD_DFA_THREADS, PREFETCH = 0, POINTS = 1, WINV_UNROLL = 8;
 };
 template <>
 struct ElemCfg<float, false> {
-  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH, POINTS = 1;
+  static constexpr int EB = HD_F32_EB, THREADS = HD_F32_THREADS, PREFETCH = HD_F32_PREFETCH, POINTS = 1,
+                       WINV_UNROLL = 8;
 };
-
-// The W_e^-1 rows read from global memory (one thread per row): the unrolled batch sets the
-// loads in flight per thread. Measured at 64^3, k = 4 (double-float kernel): 8 -> 3.69 ms,
-// 16 -> 3.60, 32 -> 3.58, 64 -> 3.67; two or four partial sums per row instead of one
-// chain: 3.93 and 4.30 ms (the chain is not the limit, the load latency is).
-#ifndef HD_WINV_UNROLL
-#define HD_WINV_UNROLL 32
-#endif
-constexpr int kWinvUnroll = HD_WINV_UNROLL;
 
 // Staging of the dense W_e^-1 rows by the copy engine (double-float kernel): the
 // sum-factorisation buffers T1/T2 are idle while the L2 rows are computed, so they
@@ -696,7 +698,7 @@ k_elem_op(const TabT<T> tab, const LatticeDims L, const int mode, const int n_el
         const T* qe = sq + el * NL2;
         Acc<T> acc;
         acc.init(W[a], qe[0]);
-#pragma unroll kWinvUnroll
+#pragma unroll ElemCfg<T, AFF>::WINV_UNROLL
         for (int b = 1; b < NL2; ++b) acc.add(W[b * NL2 + a], qe[b]);
         s = acc.get();
       }
