@@ -1004,7 +1004,7 @@ def run_raddiff(args):
     t0 = time.time()
     rd = hd.RadDiff(n, n, n, K, vx, vy, vz, sigma, 1.0 / n, rho=1.0, cv=1.0, a=1.0, c=1.0, cycle=args.cycle,
                     smooth_levels=args.smooth_levels, fp64_emulation=args.fp64_emulation,
-                    linear_rtol=args.rad_linear_rtol, stream=stream)
+                    linear_rtol=args.rad_linear_rtol, linear_precision=args.rad_linear_precision, stream=stream)
     setup_s = time.time() - t0
     nl = rd.n_l2
     X = rd.points()
@@ -1038,7 +1038,7 @@ def run_raddiff(args):
     ms = e0.elapsed_time(e1)
     phases = tot["ms_newton"] + tot["ms_linear"] + tot["ms_residual"]
     out = {"study": "radiation diffusion (Sec. 4.3)", "elements": E, "k": K, "n_rt": rd.n_rt, "n_l2": nl,
-           "linear_rtol": args.rad_linear_rtol,
+           "linear_rtol": args.rad_linear_rtol, "linear_precision": args.rad_linear_precision,
            "dofs": rd.n_rt + nl, "dt": 1.0 / n, "steps": args.rad_steps, "setup_s": round(setup_s, 3),
            "ms_total": round(ms, 1), "ms_per_stage": round(ms / max(tot["stages"], 1), 1),
            "share": {"nonlinear_residual": round(tot["ms_residual"] / phases, 4),
@@ -1098,6 +1098,8 @@ def main():
     ap.add_argument("--raddiff", type=int, default=0,
                     help="run the radiation-diffusion study alone at this many elements per direction (k = 4)")
     ap.add_argument("--rad-steps", type=int, default=1, help="SDIRK3 steps of the radiation-diffusion study")
+    ap.add_argument("--rad-linear-precision", type=int, default=0, choices=[0, 1],
+                    help="Darcy solves of the radiation-diffusion study: 0 FP64 MINRES, 1 mixed precision")
     ap.add_argument("--rad-linear-rtol", type=float, default=1e-8,
                     help="MINRES tolerance of each Darcy solve in the radiation-diffusion study (paper: 1e-8)")
     ap.add_argument("--net-apply", type=int, default=0,

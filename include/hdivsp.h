@@ -640,6 +640,14 @@ typedef struct {
   int32_t newton_maxit;  /* Newton steps per pass; 0 -> 30 */
   double linear_rtol;    /* MINRES tolerance (on eta_j / eta_0); 0 -> 1e-8 */
   int32_t linear_maxit;  /* 0 -> 20000 */
+  int32_t linear_precision; /* 0: FP64 MINRES; 1: the mixed-precision solve of hd_minres_solve
+                            (FP32 operator and cycle inside an FP64 residual correction, inner
+                            tolerance 1e-4), run until the true residual ||b - AA x||_2 has
+                            fallen to linear_rtol times its value at the warm start, but not
+                            below 1e-12 ||b||_2 (the FP64 operator's rounding level; a warm
+                            start already there is kept), with at most 6 FP64 corrections per
+                            Darcy step: where the true residual's rounding lies above the target,
+                            the iterate is kept and the stage residual decides */
 } hd_rad_desc;
 typedef struct {
   int32_t stages;            /* stages solved by the call */

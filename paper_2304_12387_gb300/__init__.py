@@ -75,7 +75,7 @@ class RadDesc(ctypes.Structure):
                 ("cv", ctypes.c_double), ("a", ctypes.c_double), ("c", ctypes.c_double), ("dt", ctypes.c_double),
                 ("outer_rtol", ctypes.c_double), ("outer_maxit", ctypes.c_int32), ("newton_rtol", ctypes.c_double),
                 ("newton_maxit", ctypes.c_int32), ("linear_rtol", ctypes.c_double),
-                ("linear_maxit", ctypes.c_int32)]
+                ("linear_maxit", ctypes.c_int32), ("linear_precision", ctypes.c_int32)]
 
 
 class RadInfo(ctypes.Structure):
@@ -574,7 +574,8 @@ class RadDiff:
 
     def __init__(self, nx, ny, nz, k, vx, vy, vz, sigma, dt, rho=1.0, cv=1.0, a=1.0, c=1.0, q=0, cycle=2,
                  smooth_levels=2, fp64_emulation=1, aggregation=0, outer_rtol=0.0, outer_maxit=0,
-                 newton_rtol=0.0, newton_maxit=0, linear_rtol=0.0, linear_maxit=0, stream=None):
+                 newton_rtol=0.0, newton_maxit=0, linear_rtol=0.0, linear_maxit=0, linear_precision=0,
+                 stream=None):
         E = nx * ny * nz
         self._keep = []
         ptrs = []
@@ -588,7 +589,7 @@ class RadDiff:
                            HD_WINV_DENSE, 0, 0, cycle, int(fp64_emulation), int(smooth_levels), 0, None,
                            int(aggregation))
         d = RadDesc(mesh, psg, rho, cv, a, c, dt, outer_rtol, outer_maxit, newton_rtol, newton_maxit, linear_rtol,
-                    linear_maxit)
+                    linear_maxit, int(linear_precision))
         h = ctypes.c_void_p()
         _check(lib().hd_rad_create(ctypes.byref(d), ctypes.byref(h)))
         self.h = h

@@ -97,11 +97,13 @@ def test_stage_residual_matches_the_oracle(k):
     assert abs(nrm0 - np.linalg.norm(ref0)) <= 1e-12 * np.linalg.norm(ref0)
 
 
-@pytest.mark.parametrize("k,emul", [(2, 0), (3, 1), (4, 1), (3, 2)])
-def test_stage_matches_the_oracle(k, emul):
+@pytest.mark.parametrize("k,emul,lp", [(2, 0, 0), (3, 1, 0), (4, 1, 0), (3, 2, 0), (3, 1, 1), (4, 1, 1)])
+def test_stage_matches_the_oracle(k, emul, lp):
+    """lp = 1: the Darcy step by the mixed-precision solve (FP32 operator and cycle inside the
+    FP64 residual correction); the stage converges to the same solution."""
     _need_gpu()
     sigma = synth.lognormal(12, 0.5, seed=13)
-    ora, gpu = _pair(3, 2, 2, k, sigma, 0.05, emul=emul)
+    ora, gpu = _pair(3, 2, 2, k, sigma, 0.05, emul=emul, linear_precision=lp)
     e_s, Eh_s = _state(ora, 30)
     rng = np.random.Generator(np.random.PCG64(31))
     Ql, Sl = ora.load(rng.uniform(0, 1, ora.detJ.shape)), ora.load(rng.uniform(0, 1, ora.detJ.shape))
@@ -195,7 +197,8 @@ def test_energy_is_conserved_at_larger_sizes(dims, k):
 def test_invalid_input_is_refused():
     import paper_2304_12387_gb300 as hd
     v = _mesh(2, 2, 2)
-    for kw in (dict(sigma=-1.0), dict(dt=0.0), dict(rho=0.0), dict(cv=-1.0), dict(a=0.0), dict(c=0.0)):
+    for kw in (dict(sigma=-1.0), dict(dt=0.0), dict(rho=0.0), dict(cv=-1.0), dict(a=0.0), dict(c=0.0),
+               dict(linear_precision=2)):
         args = dict(sigma=1.0, dt=0.1)
         args.update(kw)
         sigma, dt = args.pop("sigma"), args.pop("dt")
