@@ -1051,7 +1051,50 @@ def run_raddiff(args):
                "nonlinear_residual": 0.0445, "inner_newton": 0.0387, "linear_solver": 0.9168},
                "minres_iterations_per_solve": 84, "outer_per_stage": 2}}
     rd.close()
+    out["value"] = out["dofs"] * args.rad_steps / (ms * 1e-3)
+    out["unit"] = "DOF-steps/s"
+    if not args.no_cpu:
+        out["cpu_baseline"] = rad_cpu_baseline(1.0 / n)
     print(json.dumps(out), flush=True)
+
+
+def _rad_oracle_worker(arg):
+    """The oracle's SDIRK3 step on an n^3-element sample of the radiation-diffusion recipe
+    with the time step dt of the measured workload (one process, one thread): (DOFs,
+    seconds for the step, passes per stage)."""
+    from oracle.raddiff import RadDiff
+    n, dt = arg
+    vx, vy, vz = synth.lattice_vertices(n, n, n, perturb=PERTURB, seed=SEED)
+    sigma = synth.lognormal(n ** 3, 0.5, seed=SEED + 7)
+    rd = RadDiff(n, n, n, K, vx, vy, vz, sigma, dt, q=Q)
+    X = rd.points()
+    e = rd.project(1.0 + np.exp(-30.0 * np.sum((X - 0.5) ** 2, axis=-1)))
+    Eh = rd.load(np.ones(X.shape[:2]))
+    F = np.zeros(rd.n_rt)
+    t0 = time.perf_counter()
+    _, _, _, infos = rd.step(e, Eh, F)
+    return rd.n_rt + rd.n_l2, time.perf_counter() - t0, sum(i["outer"] for i in infos) / 3.0
+
+
+def rad_cpu_baseline(dt, n=4):
+    """The oracle's radiation-diffusion step timed on one host core (a spawned process with
+    one BLAS thread), on an n^3-element sample of the same recipe and time step."""
+    import multiprocessing as mp
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    try:
+        with mp.get_context("spawn").Pool(1) as pool:
+            dofs, sec, passes = pool.apply(_rad_oracle_worker, ((n, dt),))
+    finally:
+        for v, old in saved.items():
+            if old is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = old
+    return {"value": dofs / sec, "unit": "DOF-steps/s", "cores": 1, "kind": "oracle", "cpu_model": cpu_model(),
+            "sample": "%d^3 elements of the same recipe and dt (%d DOFs): one SDIRK3 step, dense Newton systems "
+                      "and a sparse LU of the Darcy system, %.2f s, %.1f passes per stage" % (n, dofs, sec, passes)}
 
 
 def run_learned(args):
