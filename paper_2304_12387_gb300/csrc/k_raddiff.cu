@@ -72,8 +72,14 @@ __host__ __device__ inline int rd_smem_doubles(int k, int q) {
 
 // One CTA per element: (R1, R2) at (e, Eh), and with NEWTON the Newton loop of step (1)
 // and the Darcy right-hand side.
+// The Newton kernel holds 126 registers unbounded (two CTAs per SM); asked for three CTAs per
+// SM it fits 80 with a small spill and its FP64 pipe stays busier: 2.80 -> 1.86 s of Newton
+// per SDIRK3 step at 48^3, k = 4 (four or five CTAs: 1.87, 1.88 s).
+#ifndef HD_RAD_MINB
+#define HD_RAD_MINB 3
+#endif
 template <bool NEWTON>
-__global__ void __launch_bounds__(RD_THREADS) k_rad_elem(RdArgs A) {
+__global__ void __launch_bounds__(RD_THREADS, NEWTON ? HD_RAD_MINB : 1) k_rad_elem(RdArgs A) {
   extern __shared__ __align__(16) double rd_smem[];
   const int k = A.t.k, q = A.t.q, n = k * k * k, nq = q * q * q;
   const int64_t el = blockIdx.x;
