@@ -96,3 +96,21 @@ def test_affine_mesh_test():
         assert not hd.hd_lattice_is_affine(*dims, bumped, vy, vz)
     with pytest.raises(ValueError):
         hd.hd_lattice_is_affine(2, 2, 2, np.zeros(3), np.zeros(3), np.zeros(3))
+
+
+def test_radiation_diffusion_create_refuses_invalid_input_on_the_host():
+    """hd_rad_create checks its descriptor before any device work: a non-positive opacity,
+    constant or time step, or an unknown linear_precision, is HD_ERR_INVALID_ARG."""
+    import synth
+    v = synth.lattice_vertices(2, 2, 2, perturb=0.1, seed=3)
+    sigma = np.ones(8)
+    sigma[5] = 0.0
+    cases = [dict(sigma=sigma), dict(dt=-0.1), dict(rho=0.0), dict(cv=-2.0), dict(a=0.0), dict(c=0.0),
+             dict(linear_precision=3), dict(outer_rtol=-1.0), dict(newton_maxit=-1)]
+    for kw in cases:
+        args = dict(sigma=1.0, dt=0.1)
+        args.update(kw)
+        sg, dt = args.pop("sigma"), args.pop("dt")
+        with pytest.raises(hd.HdError) as e:
+            hd.RadDiff(2, 2, 2, 3, *v, sg, dt, **args)
+        assert e.value.status == hd.HD_ERR_INVALID_ARG, kw

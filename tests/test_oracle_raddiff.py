@@ -170,3 +170,46 @@ def test_newton_converges_quadratically():
     ratio = [norms[i + 1] / norms[i] for i in range(5)]
     assert norms[4] < 1e-9 * norms[0], norms
     assert ratio[2] < 1e-2 and ratio[3] < 0.1 * ratio[2], norms
+
+
+def _random_stage(seed=51):
+    nx, ny, nz, k = 3, 2, 2, 3
+    vx, vy, vz = synth.lattice_vertices(nx, ny, nz, perturb=0.2, seed=seed)
+    sigma = synth.lognormal(nx * ny * nz, 0.5, seed=seed + 1)
+    rd = RadDiff(nx, ny, nz, k, vx, vy, vz, sigma, 0.05, rho=1.1, cv=0.8, a=0.5, c=1.0)
+    rng = np.random.Generator(np.random.PCG64(seed + 2))
+    shape = rd.detJ.shape
+    e_s = rd.project(0.8 * (1.0 + 0.5 * rng.uniform(0, 1, shape)))
+    Eh_s = rd.load(0.5 * (1.0 + 0.8 * rng.uniform(0, 1, shape)))
+    Ql, Sl = rd.load(rng.uniform(0, 1, shape)), rd.load(rng.uniform(0, 1, shape))
+    return rd, rng, e_s, Eh_s, Ql, Sl
+
+
+def test_each_step_of_a_pass_solves_its_own_equations():
+    """Newton with F fixed zeroes (R1, R2); the Darcy step with e fixed zeroes (R2, R3). The
+    residuals are evaluated from their definitions, independently of how each step maps its
+    unknowns (the sign of Eh in the Darcy unknown, the right-hand side W^-1 G)."""
+    rd, rng, e_s, Eh_s, Ql, Sl = _random_stage()
+    F = rng.uniform(-1, 1, rd.n_rt)
+    F[rd.prob.ess] = 0.0
+    e, Eh, _ = rd.newton(e_s.copy(), Eh_s.copy(), F, e_s, Eh_s, Ql, Sl, rtol=1e-14, maxit=30)
+    R1, R2 = rd.residual_12(e, Eh, F, e_s, Eh_s, Ql, Sl)
+    scale = np.abs(rd.beta * Eh).max()
+    assert np.abs(R1).max() <= 1e-12 * scale and np.abs(R2).max() <= 1e-12 * scale
+    Eh2, F2 = rd.darcy(e, Eh_s, Sl)
+    R = rd.residual(e, Eh2, F2, e_s, Eh_s, Ql, Sl)
+    n = rd.n_l2
+    assert np.abs(R[n:2 * n]).max() <= 1e-11 * scale          # R2
+    assert np.abs(R[2 * n:]).max() <= 1e-11 * np.abs(F2).max() * rd.beta  # R3
+    assert np.abs(R[:n]).max() > 1e-6 * scale                  # R1 moved: the flux changed
+
+
+def test_stage_solution_does_not_depend_on_the_initial_guess():
+    rd, rng, e_s, Eh_s, Ql, Sl = _random_stage(61)
+    F0 = np.zeros(rd.n_rt)
+    a = rd.stage(e_s, Eh_s, Ql, Sl, e_s.copy(), Eh_s.copy(), F0.copy())
+    g = rng.uniform(0.9, 1.1, rd.n_l2)
+    b = rd.stage(e_s, Eh_s, Ql, Sl, e_s * g, Eh_s * g[::-1], F0 + 1e-3 * rng.uniform(-1, 1, rd.n_rt) * (
+        np.isin(np.arange(rd.n_rt), rd.prob.ess, invert=True)))
+    for x, y in zip(a[:3], b[:3]):
+        assert np.abs(x - y).max() <= 1e-9 * np.abs(x).max()
