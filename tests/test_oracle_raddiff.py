@@ -213,3 +213,33 @@ def test_stage_solution_does_not_depend_on_the_initial_guess():
         np.isin(np.arange(rd.n_rt), rd.prob.ess, invert=True)))
     for x, y in zip(a[:3], b[:3]):
         assert np.abs(x - y).max() <= 1e-9 * np.abs(x).max()
+
+
+def test_sdirk3_steps_converge_at_third_order_in_time():
+    """A spatially uniform state with no sources keeps F = 0 and reduces the system to the ODEs
+    rho de/dt = -c sigma (a (e/Cv)^4 - E), dE/dt = c sigma (a (e/Cv)^4 - E). The oracle's steps
+    (stage starts, stage rates, the stiffly accurate update) against scipy's Radau solution to
+    1e-13: the error falls by about 2^3 per halving of dt (above 6.5 here: a second-order
+    method gives about 4)."""
+    from scipy.integrate import solve_ivp
+    rho, cv, a, c, sigma = 1.0, 1.0, 1.0, 1.0, 0.5
+    e0, E0, t_end = 2.0, 0.5, 0.4
+
+    def f(t, y):
+        cpl = c * sigma * (a * (y[0] / cv) ** 4 - y[1])
+        return [-cpl / rho, cpl]
+
+    ref = solve_ivp(f, (0.0, t_end), [e0, E0], method="Radau", rtol=1e-13, atol=1e-14).y[:, -1]
+    vx, vy, vz = synth.lattice_vertices(1, 1, 1)
+    errs = []
+    for dt in (0.05, 0.025, 0.0125):
+        rd = RadDiff(1, 1, 1, 2, vx, vy, vz, sigma, dt, rho=rho, cv=cv, a=a, c=c)
+        e = rd.project(np.full(rd.detJ.shape, e0))
+        Eh = rd.load(np.full(rd.detJ.shape, E0))
+        F = np.zeros(rd.n_rt)
+        for _ in range(int(round(t_end / dt))):
+            e, Eh, F, _ = rd.step(e, Eh, F, outer_rtol=1e-13)
+        # on the unit cube the coefficients of a constant field sum to its value
+        errs.append(max(abs(e.sum() - ref[0]), abs(rd.winv(Eh).sum() - ref[1])))
+    assert errs[2] < 1e-5, errs
+    assert errs[1] / errs[2] > 6.5 and errs[0] / errs[1] > 6.0, errs
