@@ -73,8 +73,8 @@ __host__ __device__ inline int rd_smem_doubles(int k, int q) {
 // One CTA per element: (R1, R2) at (e, Eh), and with NEWTON the Newton loop of step (1)
 // and the Darcy right-hand side.
 // The Newton kernel holds 126 registers unbounded (two CTAs per SM); asked for three CTAs per
-// SM it fits 80 with a small spill and its FP64 pipe stays busier: 2.80 -> 1.86 s of Newton
-// per SDIRK3 step at 48^3, k = 4 (four or five CTAs: 1.87, 1.88 s).
+// SM it fits 80 with a small spill: 0.73 us per element and pass at 48^3 and 64^3, k = 4,
+// against 1.10 and 0.76 us (four or five CTAs per SM: no better).
 #ifndef HD_RAD_MINB
 #define HD_RAD_MINB 3
 #endif
